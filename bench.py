@@ -1,0 +1,323 @@
+"""Throughput of one full WCSPH-RANS advection step with the bidirectional
+buffer on GB300, in particle-steps/s.
+
+A "step" is one sph_step advection step: cell-list rebuild, labelling, time
+step, B / viscous / k-epsilon sweep, all acoustic sub-steps (momentum and
+continuity sweeps, boundary values) and the buffer update.  The workload is
+the turbulent straight channel (6 x 2, dp = 0.005, ~480k particles, k-eps
+RANS, velocity inlet with 5% Philox fluctuation, zero-pressure outlet) with
+FP32 pair sweeps and FP64 integration.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs its own replica of the workload (the
+path is replicas-only, no exchange) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s vs plain FP64 at stated error; HBM GB/s; adjoint/forward time"
+UNIT = "particle-steps/s"
+
+
+def workload(name: str, seed: int = 2):
+    from paper_2510_25702_gb300 import cases
+
+    if name == "turbulent_channel":
+        return cases.turbulent_channel(length=6.0, height=2.0, dp=0.005, seed=seed)
+    if name == "turbulent_channel_small":
+        return cases.turbulent_channel(length=0.6, height=0.2, dp=0.005, seed=seed)
+    if name == "poiseuille":
+        return cases.poiseuille_channel(seed=seed)
+    raise ValueError(name)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# algorithmic bytes per live particle and launch, 2D, FP32 packs (16 B),
+# FP64 masters (8 B); every array element a kernel needs, once
+def algorithmic_bytes(stage: str, dim: int, R: int, rans: bool) -> int:
+    pk = 4 * R  # one pack vector
+    vec = 8 * dim  # FP64 vector master
+    nsym = 3 if dim == 2 else 6
+    idx = 2 + 4 + 4  # instance, cell key, label
+    if stage == "momentum_sweep":
+        rd = idx + 2 * pk + pk * (1 if dim == 2 else 2) + 8 + 8 * nsym + vec + vec + vec + (16 if rans else 0)
+        wr = vec + vec + pk
+        return rd + wr
+    if stage == "continuity_sweep":
+        rd = idx + 2 * pk + 8 + 8 + vec + vec
+        wr = 8 + 8 + 8 + vec + 2 * pk
+        return rd + wr
+    if stage == "advection_sweep":
+        rd = idx + 2 * pk + (pk + 24 if rans else 0) + 8 + 8 + 8 + vec + vec
+        wr = 8 * nsym + vec + (24 if rans else 0) + pk * (1 if dim == 2 else 2) + 8 + 8 + vec + 2 * pk
+        return rd + wr
+    raise ValueError(stage)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def sample_case(work: str):
+    """The bounded CPU sample of a workload: the same channel physics and
+    spacing on a 0.75 x 2 section (60k particles) for the full 6 x 2 channel."""
+    from paper_2510_25702_gb300 import cases
+
+    if work == "turbulent_channel":
+        return cases.turbulent_channel(length=0.75, height=2.0, dp=0.005, seed=2)
+    return workload(work)
+
+
+def time_oracle(case, steps: int, warmup: int = 0):
+    import oracle
+
+    o = oracle.OracleSim(case)
+    for _ in range(warmup):
+        o.step(1)
+    ps = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ps += o.n - int(o.a["dead"][: o.n].sum())
+        o.step(1)
+    dt = time.perf_counter() - t0
+    return ps / dt, dt, o
+
+
+def cpu_baseline(work: str, steps: int = 20):
+    """The FP64 oracle, as it stands, on one host core, over a bounded sample
+    of the workload (10-30 s of CPU work)."""
+    case = sample_case(work)
+    value, dt, o = time_oracle(case, steps)
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} advection steps ({o.stats['n_ac']} sub-steps each) of {case.name} "
+                      f"({case.n} particles, a section of the workload), {dt:.1f} s single-threaded FP64"}
+
+
+def run_reference(args, rank: int):
+    """--impl reference: the oracle on the host cores, each step one oracle
+    advection step of the bounded sample; rank 0 only."""
+    if rank != 0:
+        return
+    case = sample_case(args.workload)
+    value, dt, o = time_oracle(case, max(1, args.steps), warmup=args.warmup)
+    sample = (f"each step one advection step of {case.name} ({case.n} particles, a section of the "
+              f"workload), single-threaded FP64 oracle")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload(args.workload).name, "sample": case.name, "particles": case.n,
+                       "rans": True},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="turbulent_channel")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison run")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2510_25702_gb300 import build as _b
+    from paper_2510_25702_gb300 import sph
+
+    if not os.path.exists(_b.LIB):
+        _b.build()
+    case = workload(args.workload, seed=2 + rank)
+    sim = sph.Simulation(case, precision=args.precision)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sim.step(args.warmup)
+    s0 = sim.stats()
+    n0 = s0["n"]
+    sim.set_profiling(2)
+    barrier()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        sim.step(args.steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = start.elapsed_time(end)
+    sim.set_profiling(0)
+    stages = sim.stage_times()
+    s1 = sim.stats()
+    n1 = s1["n"]
+    launches = s1["kernel_launches"] - s0["kernel_launches"]
+    particle_steps = 0.5 * (n0 + n1) * args.steps
+    if dist is not None:
+        t = torch.tensor([ms, particle_steps], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms, particle_steps = float(mx[0]), float(t[1])
+    value = particle_steps / (ms * 1e-3)
+
+    # dominant kernel and its roofline
+    dom = max(("advection_sweep", "momentum_sweep", "continuity_sweep"), key=lambda s: stages[s][0])
+    dom_ms, dom_n = stages[dom]
+    R = 4 if args.precision == "fp32" else 8
+    per_particle = algorithmic_bytes(dom, case.dim, R, case.rans)
+    nbar = 0.5 * (n0 + n1)
+    achieved = per_particle * nbar / (dom_ms / dom_n * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+
+    # end to end through the C ABI: per step the inlet profile goes host ->
+    # device (sph_set_profile), the step runs, the statistics come back
+    e2e_steps = max(10, args.steps // 4)
+    theta = np.array([1.0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ps = 0.0
+    for s in range(e2e_steps):
+        sim.set_profile(0, 0, theta)
+        sim.step(1)
+        ps += sim.stats()["n"]
+    t1 = time.perf_counter()
+    e2e = {"value": ps / (t1 - t0) * (world if dist is not None else 1), "unit": UNIT,
+           "h2d_bytes_per_step": 4 + 8 * theta.size, "d2h_bytes_per_step": 4 + 40 + 40}
+
+    fp64 = None
+    if not args.no_fp64 and args.precision == "fp32" and rank == 0:
+        sim64 = sph.Simulation(case, precision="fp64")
+        sim64.step(args.warmup)
+        k64 = max(5, args.steps // 4)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim64.step(k64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fp64 = sim64.stats()["n"] * k64 / (a.elapsed_time(b) * 1e-3)
+        sim64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload)
+
+    st = sim.stats()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": case.name, "particles": int(nbar), "walls": case.nw, "rans": bool(case.rans),
+                       "sweeps": args.precision, "integration": "f64", "sub_steps": st["n_ac"],
+                       "l2": f"working set {st['device_bytes'] / 2**20:.0f} MiB > 129 MB L2, no flush",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "bytes_per_particle": per_particle, "avg_launch_ms": dom_ms / dom_n},
+            "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+            "fp64_value": fp64, "fp32_over_fp64": (value / fp64) if fp64 else None,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

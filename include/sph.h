@@ -1,0 +1,252 @@
+/*
+ * sph.h -- C ABI of the GB300 (sm_103a) WCSPH(-RANS) time step with the
+ * improved bidirectional buffer (Wang & Hu, arXiv 2510.25702).
+ *
+ * One call of sph_step advances every instance by whole advection steps:
+ * cell-linked-list rebuild (Sec. 2.4.1, 2.4.3), region-constrained buffer
+ * labelling (Sec. 3.2), dual-criteria time step (Sec. 2.3), kernel
+ * correction matrix with the mirror condition (Sec. 2.2, 3.3), ARD viscosity
+ * and k-epsilon sweeps (Sec. 2.1, 2.2), acoustic sub-steps with the RKGC
+ * momentum sweep, the compensated open-boundary pressure term (Sec. 3.3,
+ * final Eq.) and the Riemann continuity sweep (Sec. 2.2), buffer boundary
+ * values (Sec. 2.4.2, buffer table of Sec. 4.3), and the buffer update:
+ * injection across the generation line (Sec. 2.4.2, 3.1), ID-checked
+ * deletion (Sec. 2.4.3, 3.2) and stable compaction with appended copies
+ * (Sec. 2.4.2).
+ *
+ * Conventions
+ *  - Every function returns int: 0 (SPH_OK) or a negative SPH_ERR_* code;
+ *    nothing throws across this boundary.  sph_error_string() names codes.
+ *  - Vectors are [n][3] row-major doubles (z = 0 in 2D); matrices [n][9].
+ *  - The library owns all device state.  The caller owns every array it
+ *    passes; arrays are copied in (sph_create, sph_write_fields) or out
+ *    (sph_read_fields) before the call returns.
+ *  - Work is ordered on the context's CUDA stream (sph_alloc.stream, or the
+ *    legacy default stream when NULL).  sph_step does not synchronise with
+ *    the host except for reading its 4-byte status word at the end;
+ *    sph_read_fields, sph_write_fields and sph_get_stats synchronise.
+ *  - Rows read or written by sph_read_fields / sph_write_fields are ordered
+ *    by (instance, uid).
+ *  - A context is used from one host thread at a time.
+ */
+#ifndef SPH_GB300_H
+#define SPH_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPH_ABI_VERSION 1
+
+/* return codes */
+#define SPH_OK 0
+#define SPH_ERR_ARG -1       /* invalid argument (message via sph_last_error) */
+#define SPH_ERR_CUDA -2      /* a CUDA call failed */
+#define SPH_ERR_CAPACITY -3  /* particle capacity exceeded; buffer update not committed */
+#define SPH_ERR_NONFINITE -4 /* a density or velocity became NaN/Inf */
+#define SPH_ERR_TIMEOUT -5   /* a bounded device wait ran out */
+#define SPH_ERR_OVERLAP -6   /* buffer boxes of one instance intersect */
+#define SPH_ERR_STATE -7     /* call not valid in the context's state */
+#define SPH_ERR_ALLOC -8     /* device allocation failed */
+
+/* sph_config.precision: arithmetic of the pair sweeps.  Positions,
+   velocities, densities, the time integration, the B inversion and the
+   time-step reductions are FP64 in both modes. */
+#define SPH_PREC_FP64 0
+#define SPH_PREC_FP32 1 /* FP32 pair sweeps with FP32 accumulation */
+
+/* sph_config.dt_mode (Sec. 2.3 dual-criteria time stepping) */
+#define SPH_DT_DUAL 0   /* advection step + n = ceil(dt_ad/dt_ac) equal sub-steps */
+#define SPH_DT_SINGLE 1 /* one sub-step of min(dt_ad, dt_ac) per step */
+#define SPH_DT_FIXED 2  /* dt_ad_fixed split into n_ac_fixed sub-steps */
+
+/* buffer types (Sec. 2.4.2; buffer table of Sec. 4.3) */
+#define SPH_BUF_VELOCITY 0 /* prescribed velocity, pressure extrapolated */
+#define SPH_BUF_PRESSURE 1 /* prescribed pressure p_ob, velocity extrapolated */
+#define SPH_TURB_ZERO_GRADIENT 0
+#define SPH_TURB_FREESTREAM 1
+
+#define SPH_MAX_THETA 64
+#define SPH_MAX_BUFFERS 16 /* per instance */
+
+/* One instance (an independent problem).  h is the smoothing length
+   (1.3 dp in the paper, Sec. 2.2); the cell grid covers [domain_lo,
+   domain_hi) with cells of 2h (points outside are clamped to the edge
+   cells); periodic axes wrap with length domain_hi - domain_lo and need at
+   least 3 cells. */
+typedef struct sph_config {
+  int32_t dim;        /* 2 or 3 */
+  int32_t rans;       /* 0 laminar, 1 k-epsilon RANS */
+  int32_t precision;  /* SPH_PREC_* */
+  int32_t dt_mode;    /* SPH_DT_* */
+  int32_t n_ac_fixed; /* sub-steps in SPH_DT_FIXED */
+  int32_t kinematic;  /* 1: no physics, only the topology and buffer stages
+                         (positions are set by the caller) */
+  int32_t periodic[3];
+  uint32_t seed;      /* Philox4x32-10 key word 0 of the inlet fluctuation */
+  double dp, h, rho0, c0, nu_l;
+  double eta;         /* ARD limiter (3 in the paper) */
+  double U_ref;       /* reference speed of the advection criterion */
+  double dt_ad_fixed;
+  double gravity[3];
+  double domain_lo[3], domain_hi[3];
+} sph_config;
+
+/* Initial particles of one instance.  Pointers are host memory when
+   on_device == 0, device memory of the context's GPU when 1.  k, eps, uid
+   and wall_vel may be NULL (zeros; uid = 0..n-1). */
+typedef struct sph_particles {
+  int64_t n;        /* real (fluid + buffer) particles */
+  int64_t nw;       /* wall dummies (fixed positions, volume dp^dim) */
+  int64_t capacity; /* real-particle capacity of this instance, >= n */
+  int32_t on_device;
+  int32_t reserved;
+  const double *pos;      /* [n][3] */
+  const double *vel;      /* [n][3] */
+  const double *rho;      /* [n] */
+  const double *mass;     /* [n] */
+  const double *k;        /* [n] turbulent kinetic energy (RANS) */
+  const double *eps;      /* [n] dissipation rate (RANS) */
+  const uint32_t *uid;    /* [n] */
+  const double *wall_pos; /* [nw][3] */
+  const double *wall_vel; /* [nw][3] prescribed wall velocity */
+} sph_particles;
+
+/* One bidirectional buffer (Sec. 2.4.1): the aligned box
+   0 <= x'_0 < length, |x'_1| <= half[0], |x'_2| <= half[1] in the frame
+   x' = F (x - origin), whose rows are n_b (pointing from the open face into
+   the domain), t1, t2.  Velocity buffers impose U(s) n_b with U linearly
+   interpolated in theta[0..n_theta) across s = x'_1 in [-half[0], half[0]]
+   and a Philox relative fluctuation of amplitude noise; pressure buffers
+   impose p_ob.  Freestream turbulence sets (k_in, eps_in). */
+typedef struct sph_buffer_desc {
+  int32_t type;    /* SPH_BUF_* */
+  int32_t turb_bc; /* SPH_TURB_* */
+  int32_t n_theta; /* 1..SPH_MAX_THETA */
+  int32_t reserved;
+  double origin[3];
+  double frame[9];
+  double length;
+  double half[2];
+  double p_ob;
+  double noise;
+  double k_in, eps_in;
+  double theta[SPH_MAX_THETA];
+} sph_buffer_desc;
+
+/* Optional device allocator (e.g. a caching allocator); NULL functions mean
+   cudaMalloc / cudaFree.  stream is a cudaStream_t (NULL = legacy stream). */
+typedef struct sph_alloc {
+  void *(*alloc)(void *user, size_t bytes, void *stream);
+  void (*free)(void *user, void *ptr, void *stream);
+  void *user;
+  void *stream;
+} sph_alloc;
+
+typedef struct sph_stats {
+  int64_t n;         /* live real particles, all instances */
+  int64_t step;      /* advection steps taken */
+  double t;          /* simulated time of instance 0 */
+  double dt_ad;      /* last advection step of instance 0 */
+  double dt_ac;      /* last acoustic criterion of instance 0 */
+  int32_t n_ac;      /* last sub-step count of instance 0 */
+  int32_t n_instances;
+  int64_t spawned;   /* cumulative injected particles */
+  int64_t deleted;   /* cumulative deleted particles */
+  int64_t capacity;
+  int64_t device_bytes; /* device memory owned by the context */
+  int64_t kernel_launches; /* cumulative kernels this context launched */
+} sph_stats;
+
+typedef struct sph_ctx sph_ctx;
+
+/* Create a context of n_instances independent problems; cfg and init are
+   arrays of n_instances.  All instances of one context share precision
+   and dimension.  Returns SPH_ERR_ARG on an invalid configuration,
+   SPH_ERR_ALLOC / SPH_ERR_CUDA on device failure; *out is NULL on error. */
+int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *init,
+               const sph_alloc *alloc, sph_ctx **out);
+
+/* Add a buffer to an instance before its first step (Sec. 2.4.1, 3.2).
+   *out_id receives the buffer ID (0-based in call order per instance);
+   particles inside it carry label ID+1.  SPH_ERR_OVERLAP if its box
+   intersects another buffer box of the same instance, SPH_ERR_STATE after
+   the first step, SPH_ERR_ARG on a bad frame or profile. */
+int sph_add_buffer(sph_ctx *ctx, int32_t instance, const sph_buffer_desc *b, int32_t *out_id);
+
+/* Replace the velocity profile theta of a velocity buffer (any time). */
+int sph_set_profile(sph_ctx *ctx, int32_t instance, int32_t buffer_id, const double *theta,
+                    int32_t n_theta);
+
+/* Advance every instance by nsteps advection steps.  Returns the first
+   device error (SPH_ERR_CAPACITY, SPH_ERR_NONFINITE, SPH_ERR_TIMEOUT) seen
+   in the status word; *t_out (may be NULL) receives instance 0's time. */
+int sph_step(sph_ctx *ctx, int32_t nsteps, double *t_out);
+
+/* Field selectors for sph_read_fields / sph_write_fields.  dst[k] (src[k])
+   is the array of the k-th set bit in increasing bit order. */
+#define SPH_F_POS (1u << 0)    /* double [n][3] */
+#define SPH_F_VEL (1u << 1)    /* double [n][3] */
+#define SPH_F_RHO (1u << 2)    /* double [n] */
+#define SPH_F_MASS (1u << 3)   /* double [n] */
+#define SPH_F_DRHO (1u << 4)   /* double [n] density rate of the last sub-step */
+#define SPH_F_P (1u << 5)      /* double [n] pressure */
+#define SPH_F_K (1u << 6)      /* double [n] */
+#define SPH_F_EPS (1u << 7)    /* double [n] */
+#define SPH_F_NUT (1u << 8)    /* double [n] eddy viscosity */
+#define SPH_F_LABEL (1u << 9)  /* int32 [n] 0 fluid, b+1 in buffer b */
+#define SPH_F_UID (1u << 10)   /* uint32 [n] */
+#define SPH_F_B (1u << 11)     /* double [n][9] correction matrix of the last step */
+#define SPH_F_ACC_NU (1u << 12) /* double [n][3] viscous acceleration of the last step */
+#define SPH_F_INST (1u << 13)  /* int32 [n] instance */
+#define SPH_F_KEY (1u << 14)   /* int64 [n] cell index of the current position */
+#define SPH_F_ALL_READ 0x7FFFu
+#define SPH_F_ALL_WRITE (SPH_F_POS | SPH_F_VEL | SPH_F_RHO | SPH_F_MASS | SPH_F_DRHO | SPH_F_K | SPH_F_EPS)
+
+/* Copy the live particles' selected fields into caller arrays (host when
+   dst_on_device == 0, device otherwise) sized for *n_out rows; call with
+   dst == NULL to query *n_out only.  Synchronises the stream. */
+int sph_read_fields(sph_ctx *ctx, uint32_t mask, void *const *dst, int32_t dst_on_device,
+                    int64_t *n_out);
+
+/* Overwrite selected fields of the live particles (rows in the order of
+   sph_read_fields; n must equal the live count).  Only SPH_F_ALL_WRITE
+   fields may be written.  Synchronises the stream. */
+int sph_write_fields(sph_ctx *ctx, uint32_t mask, const void *const *src, int32_t src_on_device,
+                     int64_t n);
+
+int sph_get_stats(sph_ctx *ctx, sph_stats *out);
+
+/* Stage timing (tracing aid, no counterpart in the paper).  While enabled,
+   sph_step brackets every kernel stage with CUDA events on the context's
+   stream and accumulates, per stage, the summed event time (ms) and the
+   number of launches.  Stages, in step order: 0 sort, 1 cells, 2 permute,
+   3 time step, 4 advection sweep, 5 momentum sweep, 6 continuity sweep,
+   7 buffer update.  enable = 0 stops timing; enable = 2 also clears the
+   totals.  sph_get_stage_times writes up to max_stages entries. */
+#define SPH_N_STAGES 8
+int sph_set_profiling(sph_ctx *ctx, int32_t enable);
+int sph_get_stage_times(sph_ctx *ctx, double *ms_total, int64_t *launches, int32_t max_stages,
+                        int32_t *n_stages);
+const char *sph_stage_name(int32_t stage);
+
+/* Neighbour pairs of the configuration at the current positions
+   (0 < |r_ij|^2 < (2h)^2 in FP64, Sec. 2.4.1 cell-linked list): rows
+   (uid_i, uid_j or wall index, is_wall, instance).  Writes up to max rows
+   into out (host memory, [max][4] int64) and the total into *count.
+   Test and debug aid; re-sorts the particles by cell. */
+int sph_debug_pairs(sph_ctx *ctx, int64_t *out, int64_t max, int64_t *count);
+
+void sph_destroy(sph_ctx *ctx);
+const char *sph_error_string(int code);
+/* Message of the last SPH_ERR_ARG / SPH_ERR_CUDA on this thread. */
+const char *sph_last_error(void);
+int sph_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1108 @@
+// sph_api.cu -- host side of the C ABI declared in include/sph.h: context
+// creation and validation, device memory layout, the per-step launch
+// sequence, field transfer and statistics.
+//
+// Per advection step, all on the context's stream and without a host round
+// trip (counts stay in device memory and kernels read them):
+//   radix sort of pending (key, index) pairs -> cell offsets -> permute
+//   (+ labels, + time-step maxima) -> time step -> advection sweep ->
+//   n_ac_max x (momentum sweep, continuity sweep) -> buffer update (flags,
+//   scan, spawn + recycle + keys of the next step).
+// Instances whose own sub-step count is smaller skip the surplus sub-steps
+// inside the kernels, so the launch sequence is the same every step.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "sph_internal.cuh"
+
+using namespace sphk;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CUDA_TRY(x)                                                                   \
+  do {                                                                                \
+    cudaError_t e_ = (x);                                                             \
+    if (e_ != cudaSuccess) return fail(SPH_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+const double kPi = 3.14159265358979323846;
+
+}  // namespace
+
+struct sph_ctx {
+  int dim = 2, prec = SPH_PREC_FP64, ninst = 0;
+  bool kinematic = false;
+  std::vector<sph_config> cfg;
+  std::vector<InstDev> inst;
+  std::vector<std::vector<BufDev>> bufs;  // per instance
+  sph_alloc alloc{};
+  cudaStream_t stream = nullptr;
+  int64_t cap = 0, nw = 0;
+  uint32_t ncell = 0;  // all instances; also the sentinel key of deleted entries
+  int key_bits = 8;
+  int n_ac_max = 1;
+  bool started = false;
+  int64_t step = 0;
+  int64_t launches = 0;  // kernels enqueued by this context
+  std::vector<void *> blocks;
+  size_t bytes = 0;
+  // device
+  InstDev *d_inst = nullptr;
+  BufDev *d_buf = nullptr;
+  Masters M[2];
+  int cur = 0;
+  Derived der;
+  Packs<float> pkf{};
+  Packs<double> pkd{};
+  uint32_t *K[2] = {nullptr, nullptr}, *Vv[2] = {nullptr, nullptr};
+  uint32_t *off = nullptr, *woff = nullptr, *wall_index = nullptr;
+  double *wx[3] = {nullptr, nullptr, nullptr};
+  Counters *cnt = nullptr;
+  unsigned long long *v2max = nullptr, *nutmax = nullptr, *pair_counter = nullptr;
+  uint32_t *next_uid = nullptr;
+  int32_t *inst_spawn = nullptr;
+  uint8_t *flag = nullptr;
+  int32_t *block_cnt = nullptr;
+  SortTemp sort_tmp{};
+  uint32_t *sorted_keys = nullptr;
+  // stage timing (CUDA event pairs on the context's stream)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_stage;
+  size_t ev_used = 0;
+  double stage_ms[SPH_N_STAGES] = {0};
+  int64_t stage_n[SPH_N_STAGES] = {0};
+
+  int prof_begin(int stage) {
+    if (!prof) return -1;
+    if (ev_used + 2 > ev_pool.size()) {
+      for (int t = 0; t < 64; ++t) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        ev_pool.push_back(e);
+      }
+      ev_stage.resize(ev_pool.size());
+    }
+    int idx = (int)ev_used;
+    ev_used += 2;
+    ev_stage[idx] = stage;
+    cudaEventRecord(ev_pool[idx], stream);
+    return idx;
+  }
+  void prof_end(int idx) {
+    if (idx >= 0) cudaEventRecord(ev_pool[idx + 1], stream);
+  }
+  // after a synchronisation: fold the recorded pairs into the totals
+  void prof_collect() {
+    for (size_t t = 0; t + 1 < ev_used; t += 2) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev_pool[t], ev_pool[t + 1]) == cudaSuccess) {
+        stage_ms[ev_stage[t]] += ms;
+        stage_n[ev_stage[t]] += 1;
+      }
+    }
+    ev_used = 0;
+  }
+
+  void *packs() { return prec == SPH_PREC_FP32 ? (void *)&pkf : (void *)&pkd; }
+
+  void *dalloc(size_t n) {
+    if (n == 0) n = 16;
+    n = (n + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (alloc.alloc) {
+      p = alloc.alloc(alloc.user, n, alloc.stream);
+    } else if (cudaMalloc(&p, n) != cudaSuccess) {
+      p = nullptr;
+    }
+    if (p) {
+      blocks.push_back(p);
+      bytes += n;
+    }
+    return p;
+  }
+
+  void release() {
+    for (void *p : blocks) {
+      if (alloc.free)
+        alloc.free(alloc.user, p, alloc.stream);
+      else
+        cudaFree(p);
+    }
+    blocks.clear();
+  }
+
+  TopoArgs topo() {
+    TopoArgs a{};
+    a.inst = d_inst;
+    a.buf = d_buf;
+    a.src = M[cur];
+    a.dst = M[1 - cur];
+    a.der = der;
+    a.keys = K[0];
+    a.idx = Vv[0];
+    a.sorted_vals = nullptr;
+    a.cnt = cnt;
+    a.v2max = v2max;
+    a.nutmax = nutmax;
+    a.next_uid = next_uid;
+    a.inst_spawn = inst_spawn;
+    a.flag = flag;
+    a.block_cnt = block_cnt;
+    a.sentinel = ncell;
+    a.ninst = ninst;
+    a.n_ac_max = n_ac_max;
+    a.step = step;
+    a.capacity = cap;
+    return a;
+  }
+
+  SweepArgs sweep(int sub) {
+    SweepArgs a{};
+    a.inst = d_inst;
+    a.buf = d_buf;
+    a.m = M[cur];
+    a.der = der;
+    a.keys = sorted_keys;
+    a.off = off;
+    a.woff = woff;
+    a.cnt = cnt;
+    a.status = &cnt->status;
+    a.step = step;
+    a.sub = sub;
+    a.last_sub = n_ac_max - 1;
+    return a;
+  }
+};
+
+// ------------------------------------------------------------------------
+// host-side derived constants (compiled without FP contraction so that the
+// cell size, cut-off, lengths and boundary values match the plain
+// definitions bit for bit)
+// ------------------------------------------------------------------------
+static int build_inst(const sph_config &c, InstDev &I, std::string &why) {
+  memset(&I, 0, sizeof(I));
+  if (c.dim != 2 && c.dim != 3) return why = "dim must be 2 or 3", -1;
+  if (!(c.dp > 0) || !(c.h > 0) || !(c.rho0 > 0) || !(c.c0 > 0) || !(c.nu_l >= 0))
+    return why = "dp, h, rho0, c0 must be > 0 and nu_l >= 0", -1;
+  if (c.rans && !(c.nu_l > 0)) return why = "RANS needs nu_l > 0", -1;
+  if (c.dt_mode < 0 || c.dt_mode > 2) return why = "bad dt_mode", -1;
+  if (c.dt_mode == SPH_DT_FIXED && (c.n_ac_fixed < 1 || !(c.dt_ad_fixed > 0)))
+    return why = "fixed dt needs dt_ad_fixed > 0 and n_ac_fixed >= 1", -1;
+  if (c.dt_mode != SPH_DT_FIXED && !(c.U_ref > 0)) return why = "U_ref must be > 0", -1;
+  if (c.dt_mode != SPH_DT_FIXED && !c.rans && !(c.nu_l > 0)) return why = "nu_l must be > 0", -1;
+  I.dim = c.dim;
+  I.rans = c.rans ? 1 : 0;
+  I.dt_mode = c.dt_mode;
+  I.n_ac_fixed = c.n_ac_fixed;
+  I.kinematic = c.kinematic ? 1 : 0;
+  I.seed = c.seed;
+  I.dp = c.dp;
+  I.h = c.h;
+  I.rho0 = c.rho0;
+  I.c0 = c.c0;
+  I.nu_l = c.nu_l;
+  I.eta = c.eta;
+  I.U_ref = c.U_ref;
+  I.dt_ad_fixed = c.dt_ad_fixed;
+  I.cs = 2.0 * c.h;
+  I.cut2 = I.cs * I.cs;
+  uint64_t ncell = 1;
+  for (int a = 0; a < 3; ++a) {
+    I.g[a] = c.gravity[a];
+    I.lo[a] = c.domain_lo[a];
+    I.hi[a] = c.domain_hi[a];
+    I.L[a] = c.domain_hi[a] - c.domain_lo[a];
+    I.periodic[a] = (a < c.dim) ? (c.periodic[a] ? 1 : 0) : 0;
+    I.nc[a] = 1;
+    if (a < c.dim) {
+      if (!(I.L[a] > 0)) return why = "domain_hi must exceed domain_lo", -1;
+      double f = std::floor(I.L[a] / I.cs);
+      if (f > 1.0e6) return why = "cell grid too large", -1;
+      I.nc[a] = (f >= 1.0) ? (int32_t)f : 1;
+      if (I.periodic[a] && I.nc[a] < 3) return why = "periodic axes need at least 3 cells of 2h", -1;
+    }
+    ncell *= (uint64_t)I.nc[a];
+  }
+  if (ncell > (1ull << 31)) return why = "cell grid too large", -1;
+  I.ncell = (uint32_t)ncell;
+  double alpha = (c.dim == 2) ? 7.0 / (4.0 * kPi * c.h * c.h) : 21.0 / (16.0 * kPi * c.h * c.h * c.h);
+  I.alpha_h = alpha / c.h;
+  I.Vw = (c.dim == 2) ? c.dp * c.dp : c.dp * c.dp * c.dp;
+  I.rc0 = c.rho0 * c.c0;
+  I.eos_k = c.rho0 * c.c0 * c.c0;
+  I.muR_k = 0.5 * c.rho0 * c.h;
+  I.reg = 0.01 * c.h;
+  I.n_ac = 1;
+  return 0;
+}
+
+static int n_ac_bound(const sph_config &c) {
+  if (c.dt_mode == SPH_DT_FIXED) return c.n_ac_fixed;
+  if (c.dt_mode == SPH_DT_SINGLE) return 1;
+  // n = ceil(dt_ad / dt_ac) <= ceil((c0 + U_ref) / (2.4 U_ref)) for every
+  // |v|max (the ratio is largest at |v|max <= U_ref); one more for rounding
+  double b = (c.c0 + c.U_ref) / (2.4 * c.U_ref);
+  return (int)std::ceil(b) + 1;
+}
+
+static uint32_t host_cell_key(const InstDev &I, const double *x) {
+  uint32_t c[3] = {0, 0, 0};
+  for (int a = 0; a < I.dim; ++a) {
+    double f = std::floor((x[a] - I.lo[a]) / I.cs);
+    if (!(f >= 0.0))
+      c[a] = 0;
+    else if (f >= (double)I.nc[a])
+      c[a] = (uint32_t)I.nc[a] - 1;
+    else
+      c[a] = (uint32_t)f;
+  }
+  return I.cell_base + (c[2] * (uint32_t)I.nc[1] + c[1]) * (uint32_t)I.nc[0] + c[0];
+}
+
+// copy n doubles (or other bytes) from host or device into a host vector
+template <typename T>
+static int fetch(std::vector<T> &out, const T *src, int64_t n, int on_device) {
+  out.resize((size_t)n);
+  if (n == 0) return 0;
+  if (!src) return fail(SPH_ERR_ARG, "required input array is NULL");
+  if (on_device) {
+    CUDA_TRY(cudaMemcpy(out.data(), src, sizeof(T) * (size_t)n, cudaMemcpyDeviceToHost));
+  } else {
+    memcpy(out.data(), src, sizeof(T) * (size_t)n);
+  }
+  return 0;
+}
+
+template <typename T>
+static T *alloc_arr(sph_ctx *c, int64_t n) {
+  return (T *)c->dalloc(sizeof(T) * (size_t)(n > 0 ? n : 1));
+}
+
+template <typename R>
+static int alloc_packs(sph_ctx *c, Packs<R> &pk, int64_t cap, int64_t nw) {
+  for (int s = 0; s < 2; ++s) {
+    pk.P[s] = alloc_arr<V4<R>>(c, cap);
+    pk.Q[s] = alloc_arr<V4<R>>(c, cap);
+    if (!pk.P[s] || !pk.Q[s]) return -1;
+  }
+  pk.Bm0 = alloc_arr<V4<R>>(c, cap);
+  pk.Bm1 = alloc_arr<V4<R>>(c, c->dim == 3 ? cap : 1);
+  pk.T = alloc_arr<V4<R>>(c, cap);
+  pk.WP = alloc_arr<V4<R>>(c, nw);
+  pk.WV = alloc_arr<V4<R>>(c, nw);
+  if (!pk.Bm0 || !pk.Bm1 || !pk.T || !pk.WP || !pk.WV) return -1;
+  return 0;
+}
+
+template <typename R>
+static int upload_walls(sph_ctx *c, Packs<R> &pk, const std::vector<double> &wpos, const std::vector<double> &wvel,
+                        const std::vector<double> &wV) {
+  int64_t nw = (int64_t)wV.size();
+  std::vector<V4<R>> P((size_t)std::max<int64_t>(nw, 1)), V((size_t)std::max<int64_t>(nw, 1));
+  for (int64_t w = 0; w < nw; ++w) {
+    P[w] = V4<R>{(R)wpos[3 * w], (R)wpos[3 * w + 1], (R)wpos[3 * w + 2], (R)wV[w]};
+    V[w] = V4<R>{(R)wvel[3 * w], (R)wvel[3 * w + 1], (R)wvel[3 * w + 2], (R)0};
+  }
+  if (nw) {
+    CUDA_TRY(cudaMemcpy(pk.WP, P.data(), sizeof(V4<R>) * nw, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(pk.WV, V.data(), sizeof(V4<R>) * nw, cudaMemcpyHostToDevice));
+  }
+  return 0;
+}
+
+extern "C" {
+
+int sph_abi_version(void) { return SPH_ABI_VERSION; }
+
+const char *sph_last_error(void) { return g_err.c_str(); }
+
+const char *sph_error_string(int code) {
+  switch (code) {
+    case SPH_OK: return "ok";
+    case SPH_ERR_ARG: return "invalid argument";
+    case SPH_ERR_CUDA: return "CUDA error";
+    case SPH_ERR_CAPACITY: return "particle capacity exceeded";
+    case SPH_ERR_NONFINITE: return "non-finite density or velocity";
+    case SPH_ERR_TIMEOUT: return "device wait timed out";
+    case SPH_ERR_OVERLAP: return "buffer boxes overlap";
+    case SPH_ERR_STATE: return "call not valid in this state";
+    case SPH_ERR_ALLOC: return "device allocation failed";
+    default: return "unknown error";
+  }
+}
+
+int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *init, const sph_alloc *alloc,
+               sph_ctx **out) {
+  if (!out) return fail(SPH_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfg || !init || n_instances < 1 || n_instances > 65535)
+    return fail(SPH_ERR_ARG, "need 1..65535 instances with cfg and init arrays");
+  sph_ctx *c = new sph_ctx();
+  if (alloc) c->alloc = *alloc;
+  c->stream = (cudaStream_t)c->alloc.stream;
+  c->ninst = n_instances;
+  c->dim = cfg[0].dim;
+  c->prec = cfg[0].precision;
+  c->kinematic = cfg[0].kinematic != 0;
+  if (c->prec != SPH_PREC_FP64 && c->prec != SPH_PREC_FP32) {
+    delete c;
+    return fail(SPH_ERR_ARG, "precision must be SPH_PREC_FP64 or SPH_PREC_FP32");
+  }
+  c->cfg.assign(cfg, cfg + n_instances);
+  c->inst.resize(n_instances);
+  c->bufs.resize(n_instances);
+  uint64_t cell_base = 0;
+  int64_t n_total = 0, cap_total = 0, nw_total = 0;
+  for (int i = 0; i < n_instances; ++i) {
+    std::string why;
+    if (cfg[i].dim != c->dim || cfg[i].precision != c->prec || (cfg[i].kinematic != 0) != c->kinematic) {
+      delete c;
+      return fail(SPH_ERR_ARG, "all instances must share dim, precision and kinematic mode");
+    }
+    if (build_inst(cfg[i], c->inst[i], why)) {
+      delete c;
+      return fail(SPH_ERR_ARG, "instance " + std::to_string(i) + ": " + why);
+    }
+    if (init[i].n < 0 || init[i].nw < 0 || init[i].capacity < init[i].n) {
+      delete c;
+      return fail(SPH_ERR_ARG, "instance " + std::to_string(i) + ": need 0 <= n <= capacity, nw >= 0");
+    }
+    c->inst[i].cell_base = (uint32_t)cell_base;
+    cell_base += c->inst[i].ncell;
+    n_total += init[i].n;
+    cap_total += init[i].capacity;
+    nw_total += init[i].nw;
+    c->n_ac_max = std::max(c->n_ac_max, n_ac_bound(cfg[i]));
+  }
+  if (cell_base + 1 >= (1ull << 31) || cap_total >= (1ll << 31) - 1 || nw_total >= (1ll << 31) - 1) {
+    delete c;
+    return fail(SPH_ERR_ARG, "too many cells or particles for 32-bit indices");
+  }
+  if (c->n_ac_max > 4096) {
+    delete c;
+    return fail(SPH_ERR_ARG, "sub-step bound above 4096 (c0 / U_ref too large)");
+  }
+  c->ncell = (uint32_t)cell_base;
+  c->key_bits = 1;
+  while ((1ull << c->key_bits) <= (uint64_t)c->ncell) ++c->key_bits;
+  c->key_bits = ((c->key_bits + 7) / 8) * 8;
+  c->cap = cap_total;
+  c->nw = nw_total;
+
+  // ---- gather initial state on the host (SoA), walls sorted by cell ----
+  std::vector<double> X[3], Vv[3], rho, mass, k, eps, nut;
+  std::vector<uint32_t> uid;
+  std::vector<uint16_t> instid;
+  std::vector<uint32_t> next_uid(n_instances, 0);
+  std::vector<double> wpos, wvel, wV;
+  std::vector<uint32_t> wkey, windex;
+  for (int a = 0; a < 3; ++a) {
+    X[a].reserve(n_total);
+    Vv[a].reserve(n_total);
+  }
+  for (int i = 0; i < n_instances; ++i) {
+    const sph_particles &p = init[i];
+    const InstDev &I = c->inst[i];
+    std::vector<double> pos, vel, r, m, kk, ee, wp, wv;
+    std::vector<uint32_t> u;
+    int rc = 0;
+    if ((rc = fetch(pos, p.pos, 3 * p.n, p.on_device)) || (rc = fetch(vel, p.vel, 3 * p.n, p.on_device)) ||
+        (rc = fetch(r, p.rho, p.n, p.on_device)) || (rc = fetch(m, p.mass, p.n, p.on_device)) ||
+        (rc = fetch(wp, p.wall_pos, 3 * p.nw, p.on_device))) {
+      delete c;
+      return rc;
+    }
+    if (p.k && (rc = fetch(kk, p.k, p.n, p.on_device))) return delete c, rc;
+    if (p.eps && (rc = fetch(ee, p.eps, p.n, p.on_device))) return delete c, rc;
+    if (p.uid && (rc = fetch(u, p.uid, p.n, p.on_device))) return delete c, rc;
+    if (p.wall_vel && (rc = fetch(wv, p.wall_vel, 3 * p.nw, p.on_device))) return delete c, rc;
+    uint32_t umax = 0;
+    for (int64_t j = 0; j < p.n; ++j) {
+      for (int a = 0; a < 3; ++a) {
+        X[a].push_back(a < I.dim ? pos[3 * j + a] : 0.0);
+        Vv[a].push_back(a < I.dim ? vel[3 * j + a] : 0.0);
+      }
+      if (!(r[j] > 0) || !(m[j] > 0)) {
+        delete c;
+        return fail(SPH_ERR_ARG, "densities and masses must be positive");
+      }
+      rho.push_back(r[j]);
+      mass.push_back(m[j]);
+      double kj = kk.empty() ? 0.0 : kk[j], ej = ee.empty() ? 0.0 : ee[j];
+      if (I.rans && !(kj > 0 && ej > 0)) {
+        delete c;
+        return fail(SPH_ERR_ARG, "RANS needs k > 0 and eps > 0 for every particle");
+      }
+      k.push_back(kj);
+      eps.push_back(ej);
+      nut.push_back(I.rans ? kCmu * kj * kj / ej : 0.0);
+      uint32_t uj = u.empty() ? (uint32_t)j : u[j];
+      uid.push_back(uj);
+      umax = std::max(umax, uj);
+      instid.push_back((uint16_t)i);
+    }
+    next_uid[i] = p.n ? umax + 1 : 0;
+    for (int64_t w = 0; w < p.nw; ++w) {
+      double x[3] = {wp[3 * w], wp[3 * w + 1], I.dim == 3 ? wp[3 * w + 2] : 0.0};
+      for (int a = 0; a < 3; ++a) {
+        wpos.push_back(x[a]);
+        wvel.push_back(wv.empty() || a >= I.dim ? 0.0 : wv[3 * w + a]);
+      }
+      wV.push_back(I.Vw);
+      wkey.push_back(host_cell_key(I, x));
+      windex.push_back((uint32_t)w);
+    }
+  }
+  // sort walls by cell (stable)
+  std::vector<int64_t> word((size_t)nw_total);
+  std::iota(word.begin(), word.end(), 0);
+  std::stable_sort(word.begin(), word.end(), [&](int64_t a, int64_t b) { return wkey[a] < wkey[b]; });
+  std::vector<double> swpos(3 * nw_total), swvel(3 * nw_total), swV(nw_total);
+  std::vector<uint32_t> swkey(nw_total), swindex(nw_total);
+  for (int64_t t = 0; t < nw_total; ++t) {
+    int64_t s = word[t];
+    for (int a = 0; a < 3; ++a) {
+      swpos[3 * t + a] = wpos[3 * s + a];
+      swvel[3 * t + a] = wvel[3 * s + a];
+    }
+    swV[t] = wV[s];
+    swkey[t] = wkey[s];
+    swindex[t] = windex[s];
+  }
+  std::vector<uint32_t> hwoff(c->ncell + 1);
+  {
+    int64_t t = 0;
+    for (uint32_t cc = 0; cc <= c->ncell; ++cc) {
+      while (t < nw_total && swkey[t] < cc) ++t;
+      hwoff[cc] = (uint32_t)t;
+    }
+  }
+
+  // ---- device memory ----
+  const int64_t cap = c->cap;
+  bool ok = true;
+  for (int s = 0; s < 2; ++s) {
+    Masters &M = c->M[s];
+    for (int a = 0; a < 3; ++a) {
+      ok &= (M.x[a] = alloc_arr<double>(c, cap)) != nullptr;
+      ok &= (M.v[a] = alloc_arr<double>(c, cap)) != nullptr;
+    }
+    ok &= (M.rho = alloc_arr<double>(c, cap)) != nullptr;
+    ok &= (M.mass = alloc_arr<double>(c, cap)) != nullptr;
+    ok &= (M.drho = alloc_arr<double>(c, cap)) != nullptr;
+    ok &= (M.p = alloc_arr<double>(c, cap)) != nullptr;
+    ok &= (M.k = alloc_arr<double>(c, cap)) != nullptr;
+    ok &= (M.eps = alloc_arr<double>(c, cap)) != nullptr;
+    ok &= (M.nut = alloc_arr<double>(c, cap)) != nullptr;
+    ok &= (M.label = alloc_arr<int32_t>(c, cap)) != nullptr;
+    ok &= (M.uid = alloc_arr<uint32_t>(c, cap)) != nullptr;
+    ok &= (M.inst = alloc_arr<uint16_t>(c, cap)) != nullptr;
+    ok &= (c->K[s] = alloc_arr<uint32_t>(c, cap)) != nullptr;
+    ok &= (c->Vv[s] = alloc_arr<uint32_t>(c, cap)) != nullptr;
+  }
+  for (int q = 0; q < 6; ++q) ok &= (c->der.B[q] = alloc_arr<double>(c, cap)) != nullptr;
+  for (int a = 0; a < 3; ++a) {
+    ok &= (c->der.an[a] = alloc_arr<double>(c, cap)) != nullptr;
+    ok &= (c->wx[a] = alloc_arr<double>(c, nw_total)) != nullptr;
+  }
+  ok &= (c->off = alloc_arr<uint32_t>(c, (int64_t)c->ncell + 1)) != nullptr;
+  ok &= (c->woff = alloc_arr<uint32_t>(c, (int64_t)c->ncell + 1)) != nullptr;
+  ok &= (c->wall_index = alloc_arr<uint32_t>(c, nw_total)) != nullptr;
+  ok &= (c->cnt = alloc_arr<Counters>(c, 1)) != nullptr;
+  ok &= (c->v2max = alloc_arr<unsigned long long>(c, 2 * (int64_t)n_instances)) != nullptr;
+  c->nutmax = c->v2max ? c->v2max + n_instances : nullptr;
+  ok &= (c->pair_counter = alloc_arr<unsigned long long>(c, 1)) != nullptr;
+  ok &= (c->next_uid = alloc_arr<uint32_t>(c, n_instances)) != nullptr;
+  ok &= (c->inst_spawn = alloc_arr<int32_t>(c, 2 * (int64_t)n_instances)) != nullptr;
+  ok &= (c->flag = alloc_arr<uint8_t>(c, cap)) != nullptr;
+  ok &= (c->block_cnt = alloc_arr<int32_t>(c, (cap + kBlock - 1) / kBlock + 1)) != nullptr;
+  c->sort_tmp.max_blocks = (int)((cap + 2047) / 2048) + 1;
+  ok &= (c->sort_tmp.hist = alloc_arr<uint32_t>(c, 256 * (int64_t)c->sort_tmp.max_blocks)) != nullptr;
+  ok &= (c->d_inst = alloc_arr<InstDev>(c, n_instances)) != nullptr;
+  ok &= (c->d_buf = alloc_arr<BufDev>(c, (int64_t)n_instances * SPH_MAX_BUFFERS)) != nullptr;
+  if (ok) ok = (c->prec == SPH_PREC_FP32) ? alloc_packs(c, c->pkf, cap, nw_total) == 0
+                                          : alloc_packs(c, c->pkd, cap, nw_total) == 0;
+  if (!ok) {
+    c->release();
+    delete c;
+    return fail(SPH_ERR_ALLOC, "device allocation failed");
+  }
+
+  // ---- uploads ----
+  auto up = [&](void *dst, const void *src, size_t n) -> int {
+    if (n == 0) return 0;
+    CUDA_TRY(cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice));
+    return 0;
+  };
+  int rc = 0;
+  Masters &M = c->M[0];
+  for (int a = 0; a < 3 && !rc; ++a) {
+    rc |= up(M.x[a], X[a].data(), sizeof(double) * n_total);
+    rc |= up(M.v[a], Vv[a].data(), sizeof(double) * n_total);
+  }
+  std::vector<double> zeros((size_t)std::max<int64_t>(n_total, 1), 0.0);
+  std::vector<double> p0((size_t)std::max<int64_t>(n_total, 1), 0.0);
+  for (int64_t j = 0; j < n_total; ++j) {
+    const InstDev &I = c->inst[instid[j]];
+    p0[j] = I.eos_k * (rho[j] / I.rho0 - 1.0);
+  }
+  std::vector<int32_t> lab((size_t)std::max<int64_t>(n_total, 1), 0);
+  rc |= up(M.rho, rho.data(), sizeof(double) * n_total);
+  rc |= up(M.mass, mass.data(), sizeof(double) * n_total);
+  rc |= up(M.drho, zeros.data(), sizeof(double) * n_total);
+  rc |= up(M.p, p0.data(), sizeof(double) * n_total);
+  rc |= up(M.k, k.data(), sizeof(double) * n_total);
+  rc |= up(M.eps, eps.data(), sizeof(double) * n_total);
+  rc |= up(M.nut, nut.data(), sizeof(double) * n_total);
+  rc |= up(M.label, lab.data(), sizeof(int32_t) * n_total);
+  rc |= up(M.uid, uid.data(), sizeof(uint32_t) * n_total);
+  rc |= up(M.inst, instid.data(), sizeof(uint16_t) * n_total);
+  {
+    std::vector<double> wa(std::max<int64_t>(nw_total, 1));
+    for (int a = 0; a < 3; ++a) {
+      for (int64_t t = 0; t < nw_total; ++t) wa[t] = swpos[3 * t + a];
+      rc |= up(c->wx[a], wa.data(), sizeof(double) * nw_total);
+    }
+  }
+  rc |= up(c->woff, hwoff.data(), sizeof(uint32_t) * (c->ncell + 1));
+  rc |= up(c->wall_index, swindex.data(), sizeof(uint32_t) * nw_total);
+  rc |= up(c->next_uid, next_uid.data(), sizeof(uint32_t) * n_instances);
+  rc |= (c->prec == SPH_PREC_FP32) ? upload_walls(c, c->pkf, swpos, swvel, swV)
+                                   : upload_walls(c, c->pkd, swpos, swvel, swV);
+  Counters h{};
+  h.m_pending = (int32_t)n_total;
+  rc |= up(c->cnt, &h, sizeof(h));
+  std::vector<int32_t> zi(2 * n_instances, 0);
+  rc |= up(c->inst_spawn, zi.data(), sizeof(int32_t) * 2 * n_instances);
+  rc |= up(c->d_inst, c->inst.data(), sizeof(InstDev) * n_instances);
+  if (rc) {
+    c->release();
+    delete c;
+    return SPH_ERR_CUDA;
+  }
+  // keys of the initial (pending) entries
+  launch_keys(c->topo(), (int)std::max<int64_t>(cap, 1), 1, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    c->release();
+    delete c;
+    return fail(SPH_ERR_CUDA, std::string("initial keys: ") + cudaGetErrorString(e));
+  }
+  *out = c;
+  return SPH_OK;
+}
+
+void sph_destroy(sph_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  c->release();
+  delete c;
+}
+
+const char *sph_stage_name(int32_t stage) {
+  static const char *names[SPH_N_STAGES] = {"sort", "cells", "permute", "time_step",
+                                            "advection_sweep", "momentum_sweep", "continuity_sweep",
+                                            "buffer_update"};
+  return (stage >= 0 && stage < SPH_N_STAGES) ? names[stage] : "unknown";
+}
+
+int sph_set_profiling(sph_ctx *c, int32_t enable) {
+  if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->prof_collect();
+  if (enable == 2) {
+    for (int s = 0; s < SPH_N_STAGES; ++s) {
+      c->stage_ms[s] = 0.0;
+      c->stage_n[s] = 0;
+    }
+  }
+  c->prof = enable != 0;
+  return SPH_OK;
+}
+
+int sph_get_stage_times(sph_ctx *c, double *ms_total, int64_t *launches, int32_t max_stages, int32_t *n_stages) {
+  if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->prof_collect();
+  int n = std::min<int>(max_stages, SPH_N_STAGES);
+  for (int s = 0; s < n; ++s) {
+    if (ms_total) ms_total[s] = c->stage_ms[s];
+    if (launches) launches[s] = c->stage_n[s];
+  }
+  if (n_stages) *n_stages = SPH_N_STAGES;
+  return SPH_OK;
+}
+
+// separating-axis test of two oriented boxes (2D rectangles / 3D cuboids);
+// touching faces do not count as overlap
+static bool boxes_overlap(int dim, const sph_buffer_desc &a, const sph_buffer_desc &b) {
+  auto corners = [&](const sph_buffer_desc &q, std::vector<std::array<double, 3>> &out) {
+    out.clear();
+    int nz = dim == 3 ? 2 : 1;
+    for (int i0 = 0; i0 < 2; ++i0)
+      for (int i1 = 0; i1 < 2; ++i1)
+        for (int i2 = 0; i2 < nz; ++i2) {
+          double u0 = i0 ? q.length : 0.0, u1 = i1 ? q.half[0] : -q.half[0];
+          double u2 = dim == 3 ? (i2 ? q.half[1] : -q.half[1]) : 0.0;
+          std::array<double, 3> p;
+          for (int d = 0; d < 3; ++d) p[d] = q.origin[d] + u0 * q.frame[d] + u1 * q.frame[3 + d] + u2 * q.frame[6 + d];
+          out.push_back(p);
+        }
+  };
+  std::vector<std::array<double, 3>> ca, cb;
+  corners(a, ca);
+  corners(b, cb);
+  std::vector<std::array<double, 3>> axes;
+  for (const sph_buffer_desc *q : {&a, &b})
+    for (int r = 0; r < dim; ++r) axes.push_back({q->frame[3 * r], q->frame[3 * r + 1], q->frame[3 * r + 2]});
+  if (dim == 3) {
+    for (int r = 0; r < 3; ++r)
+      for (int s = 0; s < 3; ++s) {
+        const double *u = &a.frame[3 * r], *v = &b.frame[3 * s];
+        std::array<double, 3> w = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+        double nn = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        if (nn > 1e-9) axes.push_back({w[0] / nn, w[1] / nn, w[2] / nn});
+      }
+  }
+  double scale = std::max({a.length, b.length, a.half[0], b.half[0], 1e-12});
+  for (auto &ax : axes) {
+    double amin = 1e300, amax = -1e300, bmin = 1e300, bmax = -1e300;
+    for (auto &p : ca) {
+      double s = p[0] * ax[0] + p[1] * ax[1] + p[2] * ax[2];
+      amin = std::min(amin, s);
+      amax = std::max(amax, s);
+    }
+    for (auto &p : cb) {
+      double s = p[0] * ax[0] + p[1] * ax[1] + p[2] * ax[2];
+      bmin = std::min(bmin, s);
+      bmax = std::max(bmax, s);
+    }
+    if (amax <= bmin + 1e-12 * scale || bmax <= amin + 1e-12 * scale) return false;
+  }
+  return true;
+}
+
+int sph_add_buffer(sph_ctx *c, int32_t instance, const sph_buffer_desc *b, int32_t *out_id) {
+  if (!c || !b) return fail(SPH_ERR_ARG, "ctx or buffer is NULL");
+  if (instance < 0 || instance >= c->ninst) return fail(SPH_ERR_ARG, "instance out of range");
+  if (c->started) return fail(SPH_ERR_STATE, "buffers must be added before the first step");
+  const InstDev &I = c->inst[instance];
+  const sph_config &cfg = c->cfg[instance];
+  if (b->type != SPH_BUF_VELOCITY && b->type != SPH_BUF_PRESSURE) return fail(SPH_ERR_ARG, "bad buffer type");
+  if (b->turb_bc != SPH_TURB_ZERO_GRADIENT && b->turb_bc != SPH_TURB_FREESTREAM)
+    return fail(SPH_ERR_ARG, "bad turbulence BC");
+  if (b->n_theta < 1 || b->n_theta > SPH_MAX_THETA) return fail(SPH_ERR_ARG, "n_theta must be 1..64");
+  if (!(b->length > 0) || !(b->half[0] > 0) || (I.dim == 3 && !(b->half[1] > 0)))
+    return fail(SPH_ERR_ARG, "buffer length and half widths must be > 0");
+  if (I.rans && b->turb_bc == SPH_TURB_FREESTREAM && !(b->k_in > 0 && b->eps_in > 0))
+    return fail(SPH_ERR_ARG, "freestream turbulence needs k_in, eps_in > 0");
+  for (int r = 0; r < I.dim; ++r)
+    for (int s = 0; s < I.dim; ++s) {
+      double d = 0;
+      for (int a = 0; a < I.dim; ++a) d += b->frame[3 * r + a] * b->frame[3 * s + a];
+      if (std::fabs(d - (r == s ? 1.0 : 0.0)) > 1e-9) return fail(SPH_ERR_ARG, "buffer frame not orthonormal");
+    }
+  if (c->bufs[instance].size() >= SPH_MAX_BUFFERS) return fail(SPH_ERR_ARG, "too many buffers in this instance");
+  // overlap check against the boxes already added to this instance
+  for (const BufDev &o : c->bufs[instance]) {
+    sph_buffer_desc od{};
+    memcpy(od.origin, o.origin, sizeof(od.origin));
+    memcpy(od.frame, o.frame, sizeof(od.frame));
+    od.length = o.length;
+    od.half[0] = o.half[0];
+    od.half[1] = o.half[1];
+    if (boxes_overlap(I.dim, *b, od)) return fail(SPH_ERR_OVERLAP, "buffer boxes intersect");
+  }
+  BufDev d;
+  memset(&d, 0, sizeof(d));
+  d.type = b->type;
+  d.turb = b->turb_bc;
+  d.n_theta = b->n_theta;
+  d.inst = instance;
+  d.local_id = (int32_t)c->bufs[instance].size();
+  for (int a = 0; a < 3; ++a) d.origin[a] = b->origin[a];
+  for (int a = 0; a < 9; ++a) d.frame[a] = b->frame[a];
+  d.length = b->length;
+  d.half[0] = b->half[0];
+  d.half[1] = b->half[1];
+  d.p_ob = b->p_ob;
+  d.rho_ob = cfg.rho0 * (1.0 + b->p_ob / (cfg.rho0 * cfg.c0 * cfg.c0));
+  d.noise = b->noise;
+  d.k_in = b->k_in;
+  d.eps_in = b->eps_in;
+  d.nut_in = (b->eps_in > 0) ? kCmu * b->k_in * b->k_in / b->eps_in : 0.0;
+  d.gen_line = b->length + 0.5 * cfg.dp;
+  for (int q = 0; q < b->n_theta; ++q) d.theta[q] = b->theta[q];
+  c->bufs[instance].push_back(d);
+  if (out_id) *out_id = d.local_id;
+  return SPH_OK;
+}
+
+static int upload_buffers(sph_ctx *c) {
+  std::vector<BufDev> all;
+  for (int i = 0; i < c->ninst; ++i) {
+    c->inst[i].buf0 = (int32_t)all.size();
+    c->inst[i].nbuf = (int32_t)c->bufs[i].size();
+    for (auto &b : c->bufs[i]) all.push_back(b);
+  }
+  if (!all.empty()) CUDA_TRY(cudaMemcpyAsync(c->d_buf, all.data(), sizeof(BufDev) * all.size(), cudaMemcpyHostToDevice, c->stream));
+  // only the buffer fields of the instance table change here; the rest of
+  // the device copy (time, dt) is authoritative
+  for (int i = 0; i < c->ninst; ++i) {
+    CUDA_TRY(cudaMemcpyAsync(&c->d_inst[i].nbuf, &c->inst[i].nbuf, 2 * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             c->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return 0;
+}
+
+int sph_set_profile(sph_ctx *c, int32_t instance, int32_t buffer_id, const double *theta, int32_t n_theta) {
+  if (!c || !theta) return fail(SPH_ERR_ARG, "NULL argument");
+  if (instance < 0 || instance >= c->ninst) return fail(SPH_ERR_ARG, "instance out of range");
+  if (buffer_id < 0 || buffer_id >= (int32_t)c->bufs[instance].size()) return fail(SPH_ERR_ARG, "no such buffer");
+  if (n_theta < 1 || n_theta > SPH_MAX_THETA) return fail(SPH_ERR_ARG, "n_theta must be 1..64");
+  BufDev &b = c->bufs[instance][buffer_id];
+  b.n_theta = n_theta;
+  for (int q = 0; q < n_theta; ++q) b.theta[q] = theta[q];
+  if (c->started) {
+    // only the profile moves: n_theta and theta[0..n_theta)
+    int g = c->inst[instance].buf0 + buffer_id;
+    CUDA_TRY(cudaMemcpyAsync(&c->d_buf[g].n_theta, &b.n_theta, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->d_buf[g].theta, b.theta, sizeof(double) * n_theta, cudaMemcpyHostToDevice,
+                             c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+  }
+  return SPH_OK;
+}
+
+// sort + cell offsets + permute (+labels, +time-step maxima)
+static void enqueue_topology(sph_ctx *c) {
+  uint32_t *ks = nullptr, *vs = nullptr;
+  int ev = c->prof_begin(0);
+  radix_sort(c->K[0], c->Vv[0], c->K[1], c->Vv[1], &c->cnt->m_pending, (int)c->cap, c->key_bits, c->sort_tmp,
+             c->stream, &ks, &vs);
+  c->prof_end(ev);
+  ev = c->prof_begin(1);
+  cell_offsets(ks, &c->cnt->m_pending, c->ncell, c->off, &c->cnt->n_live, c->stream);
+  cudaMemsetAsync(c->v2max, 0, sizeof(unsigned long long) * 2 * c->ninst, c->stream);
+  c->prof_end(ev);
+  TopoArgs t = c->topo();
+  t.sorted_vals = vs;
+  ev = c->prof_begin(2);
+  launch_permute(t, (int)c->cap, c->prec, c->stream, c->packs());
+  c->prof_end(ev);
+  c->cur = 1 - c->cur;
+  c->sorted_keys = ks;
+  c->launches += 3 * (c->key_bits / 8) + 2;
+}
+
+static void enqueue_step(sph_ctx *c) {
+  enqueue_topology(c);
+  const int maxn = (int)c->cap;
+  if (!c->kinematic) {
+    int ev = c->prof_begin(3);
+    launch_time_step(c->topo(), c->stream);
+    c->prof_end(ev);
+    ev = c->prof_begin(4);
+    launch_advection_sweep(c->sweep(0), c->packs(), c->prec, c->dim, maxn, c->stream);
+    c->prof_end(ev);
+    for (int s = 0; s < c->n_ac_max; ++s) {
+      ev = c->prof_begin(5);
+      launch_momentum_sweep(c->sweep(s), c->packs(), c->prec, c->dim, maxn, s, c->stream);
+      c->prof_end(ev);
+      ev = c->prof_begin(6);
+      launch_continuity_sweep(c->sweep(s), c->packs(), c->prec, c->dim, maxn, s, c->stream);
+      c->prof_end(ev);
+    }
+  }
+  int ev = c->prof_begin(7);
+  launch_buffer_update(c->topo(), maxn, c->stream);
+  c->prof_end(ev);
+  c->launches += 3 + (c->kinematic ? 0 : 2 + 2 * c->n_ac_max);
+  c->step += 1;
+}
+
+static int read_status(sph_ctx *c, int32_t *status) {
+  CUDA_TRY(cudaMemcpyAsync(status, &c->cnt->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->prof_collect();
+  return 0;
+}
+
+int sph_step(sph_ctx *c, int32_t nsteps, double *t_out) {
+  if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
+  if (nsteps < 0) return fail(SPH_ERR_ARG, "nsteps < 0");
+  if (!c->started) {
+    int rc = upload_buffers(c);
+    if (rc) return rc;
+    c->started = true;
+  }
+  for (int s = 0; s < nsteps; ++s) enqueue_step(c);
+  CUDA_TRY(cudaGetLastError());
+  int32_t status = 0;
+  int rc = read_status(c, &status);
+  if (rc) return rc;
+  if (t_out) CUDA_TRY(cudaMemcpy(t_out, &c->d_inst[0].t, sizeof(double), cudaMemcpyDeviceToHost));
+  return status;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------
+// field transfer
+// ------------------------------------------------------------------------
+struct LiveView {
+  std::vector<int64_t> rows;  // device index of each output row
+};
+
+static int live_rows(sph_ctx *c, LiveView &lv) {
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  Counters h;
+  CUDA_TRY(cudaMemcpy(&h, c->cnt, sizeof(h), cudaMemcpyDeviceToHost));
+  int64_t m = h.m_pending;
+  std::vector<uint32_t> keys(m), uid(m);
+  std::vector<uint16_t> inst(m);
+  if (m) {
+    CUDA_TRY(cudaMemcpy(keys.data(), c->K[0], 4 * m, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(uid.data(), c->M[c->cur].uid, 4 * m, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(inst.data(), c->M[c->cur].inst, 2 * m, cudaMemcpyDeviceToHost));
+  }
+  lv.rows.clear();
+  for (int64_t i = 0; i < m; ++i)
+    if (keys[i] != c->ncell) lv.rows.push_back(i);
+  std::sort(lv.rows.begin(), lv.rows.end(), [&](int64_t a, int64_t b) {
+    if (inst[a] != inst[b]) return inst[a] < inst[b];
+    return uid[a] < uid[b];
+  });
+  return 0;
+}
+
+template <typename T>
+static int pull(const T *dev, int64_t m, std::vector<T> &out) {
+  out.resize((size_t)m);
+  if (m) CUDA_TRY(cudaMemcpy(out.data(), dev, sizeof(T) * m, cudaMemcpyDeviceToHost));
+  return 0;
+}
+
+static int store_out(void *dst, const void *src, size_t bytes, int on_device) {
+  if (!dst) return fail(SPH_ERR_ARG, "destination array is NULL");
+  if (bytes == 0) return 0;
+  if (on_device) {
+    CUDA_TRY(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+  } else {
+    memcpy(dst, src, bytes);
+  }
+  return 0;
+}
+
+extern "C" {
+
+int sph_read_fields(sph_ctx *c, uint32_t mask, void *const *dst, int32_t dst_on_device, int64_t *n_out) {
+  if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
+  if (mask & ~SPH_F_ALL_READ) return fail(SPH_ERR_ARG, "unknown field bits");
+  LiveView lv;
+  int rc = live_rows(c, lv);
+  if (rc) return rc;
+  const int64_t n = (int64_t)lv.rows.size();
+  if (n_out) *n_out = n;
+  if (!dst) return SPH_OK;
+  Counters h;
+  CUDA_TRY(cudaMemcpy(&h, c->cnt, sizeof(h), cudaMemcpyDeviceToHost));
+  const int64_t m = h.m_pending;
+  const Masters &M = c->M[c->cur];
+  int slot = 0;
+  for (int bit = 0; bit < 15; ++bit) {
+    uint32_t f = 1u << bit;
+    if (!(mask & f)) continue;
+    void *out = dst[slot++];
+    if (f == SPH_F_POS || f == SPH_F_VEL || f == SPH_F_ACC_NU) {
+      double *const *src = f == SPH_F_POS ? M.x : (f == SPH_F_VEL ? M.v : c->der.an);
+      std::vector<double> comp[3], buf(3 * n);
+      for (int a = 0; a < 3; ++a)
+        if ((rc = pull(src[a], m, comp[a]))) return rc;
+      for (int64_t r = 0; r < n; ++r)
+        for (int a = 0; a < 3; ++a) buf[3 * r + a] = comp[a][lv.rows[r]];
+      if ((rc = store_out(out, buf.data(), sizeof(double) * 3 * n, dst_on_device))) return rc;
+    } else if (f == SPH_F_B) {
+      std::vector<double> comp[6], buf(9 * n);
+      for (int q = 0; q < 6; ++q)
+        if ((rc = pull(c->der.B[q], m, comp[q]))) return rc;
+      for (int64_t r = 0; r < n; ++r) {
+        int64_t i = lv.rows[r];
+        double xx = comp[0][i], yy = comp[1][i], zz = comp[2][i], xy = comp[3][i], xz = comp[4][i], yz = comp[5][i];
+        double B9[9] = {xx, xy, xz, xy, yy, yz, xz, yz, zz};
+        memcpy(&buf[9 * r], B9, sizeof(B9));
+      }
+      if ((rc = store_out(out, buf.data(), sizeof(double) * 9 * n, dst_on_device))) return rc;
+    } else if (f == SPH_F_LABEL || f == SPH_F_UID) {
+      std::vector<uint32_t> v, buf(n);
+      if ((rc = pull(f == SPH_F_LABEL ? (const uint32_t *)M.label : M.uid, m, v))) return rc;
+      for (int64_t r = 0; r < n; ++r) buf[r] = v[lv.rows[r]];
+      if ((rc = store_out(out, buf.data(), 4 * n, dst_on_device))) return rc;
+    } else if (f == SPH_F_INST) {
+      std::vector<uint16_t> v;
+      std::vector<int32_t> buf(n);
+      if ((rc = pull(M.inst, m, v))) return rc;
+      for (int64_t r = 0; r < n; ++r) buf[r] = v[lv.rows[r]];
+      if ((rc = store_out(out, buf.data(), 4 * n, dst_on_device))) return rc;
+    } else if (f == SPH_F_KEY) {
+      std::vector<uint32_t> v;
+      std::vector<uint16_t> ins;
+      std::vector<int64_t> buf(n);
+      if ((rc = pull(c->K[0], m, v)) || (rc = pull(M.inst, m, ins))) return rc;
+      for (int64_t r = 0; r < n; ++r) buf[r] = (int64_t)v[lv.rows[r]] - (int64_t)c->inst[ins[lv.rows[r]]].cell_base;
+      if ((rc = store_out(out, buf.data(), 8 * n, dst_on_device))) return rc;
+    } else {
+      const double *src = nullptr;
+      switch (f) {
+        case SPH_F_RHO: src = M.rho; break;
+        case SPH_F_MASS: src = M.mass; break;
+        case SPH_F_DRHO: src = M.drho; break;
+        case SPH_F_P: src = M.p; break;
+        case SPH_F_K: src = M.k; break;
+        case SPH_F_EPS: src = M.eps; break;
+        case SPH_F_NUT: src = M.nut; break;
+      }
+      std::vector<double> v, buf(n);
+      if ((rc = pull(src, m, v))) return rc;
+      for (int64_t r = 0; r < n; ++r) buf[r] = v[lv.rows[r]];
+      if ((rc = store_out(out, buf.data(), 8 * n, dst_on_device))) return rc;
+    }
+  }
+  return SPH_OK;
+}
+
+int sph_write_fields(sph_ctx *c, uint32_t mask, const void *const *src, int32_t src_on_device, int64_t n) {
+  if (!c || !src) return fail(SPH_ERR_ARG, "NULL argument");
+  if (mask & ~SPH_F_ALL_WRITE) return fail(SPH_ERR_ARG, "only pos, vel, rho, mass, drho, k, eps are writable");
+  LiveView lv;
+  int rc = live_rows(c, lv);
+  if (rc) return rc;
+  if (n != (int64_t)lv.rows.size()) return fail(SPH_ERR_ARG, "row count differs from the live particle count");
+  Counters h;
+  CUDA_TRY(cudaMemcpy(&h, c->cnt, sizeof(h), cudaMemcpyDeviceToHost));
+  const int64_t m = h.m_pending;
+  const Masters &M = c->M[c->cur];
+  int slot = 0;
+  for (int bit = 0; bit < 15; ++bit) {
+    uint32_t f = 1u << bit;
+    if (!(mask & f)) continue;
+    const void *in = src[slot++];
+    if (!in) return fail(SPH_ERR_ARG, "source array is NULL");
+    int width = (f == SPH_F_POS || f == SPH_F_VEL) ? 3 : 1;
+    std::vector<double> hin((size_t)(width * n));
+    if (n) {
+      if (src_on_device)
+        CUDA_TRY(cudaMemcpy(hin.data(), in, sizeof(double) * width * n, cudaMemcpyDeviceToHost));
+      else
+        memcpy(hin.data(), in, sizeof(double) * width * n);
+    }
+    if (width == 3) {
+      double *const *dstv = f == SPH_F_POS ? M.x : M.v;
+      for (int a = 0; a < 3; ++a) {
+        std::vector<double> cur;
+        if ((rc = pull(dstv[a], m, cur))) return rc;
+        for (int64_t r = 0; r < n; ++r) cur[lv.rows[r]] = (a < c->dim) ? hin[3 * r + a] : 0.0;
+        if (m) CUDA_TRY(cudaMemcpy(dstv[a], cur.data(), 8 * m, cudaMemcpyHostToDevice));
+      }
+    } else {
+      double *dstp = nullptr;
+      switch (f) {
+        case SPH_F_RHO: dstp = M.rho; break;
+        case SPH_F_MASS: dstp = M.mass; break;
+        case SPH_F_DRHO: dstp = M.drho; break;
+        case SPH_F_K: dstp = M.k; break;
+        case SPH_F_EPS: dstp = M.eps; break;
+      }
+      std::vector<double> cur;
+      if ((rc = pull(dstp, m, cur))) return rc;
+      for (int64_t r = 0; r < n; ++r) cur[lv.rows[r]] = hin[r];
+      if (m) CUDA_TRY(cudaMemcpy(dstp, cur.data(), 8 * m, cudaMemcpyHostToDevice));
+    }
+  }
+  if (mask & SPH_F_POS) {
+    launch_keys(c->topo(), (int)c->cap, 0, c->stream);
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    CUDA_TRY(cudaGetLastError());
+  }
+  return SPH_OK;
+}
+
+int sph_get_stats(sph_ctx *c, sph_stats *out) {
+  if (!c || !out) return fail(SPH_ERR_ARG, "NULL argument");
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  Counters h;
+  CUDA_TRY(cudaMemcpy(&h, c->cnt, sizeof(h), cudaMemcpyDeviceToHost));
+  // dt_ad, dt_ac, dt, t, n_ac are the trailing fields of the instance record
+  InstDev i0;
+  const size_t tail = offsetof(InstDev, dt_ad);
+  CUDA_TRY(cudaMemcpy((char *)&i0 + tail, (const char *)c->d_inst + tail, sizeof(InstDev) - tail,
+                      cudaMemcpyDeviceToHost));
+  memset(out, 0, sizeof(*out));
+  out->n = (int64_t)h.m_pending - (int64_t)h.n_del_step;
+  out->step = c->step;
+  out->t = i0.t;
+  out->dt_ad = i0.dt_ad;
+  out->dt_ac = i0.dt_ac;
+  out->n_ac = i0.n_ac;
+  out->n_instances = c->ninst;
+  out->spawned = (int64_t)h.spawned;
+  out->deleted = (int64_t)h.deleted;
+  out->capacity = c->cap;
+  out->device_bytes = (int64_t)c->bytes;
+  out->kernel_launches = c->launches;
+  return SPH_OK;
+}
+
+int sph_debug_pairs(sph_ctx *c, int64_t *out, int64_t max, int64_t *count) {
+  if (!c || !count) return fail(SPH_ERR_ARG, "NULL argument");
+  if (!c->started) {
+    int rc = upload_buffers(c);
+    if (rc) return rc;
+    c->started = true;
+  }
+  // bring the live particles into cell order, then restore a pending state
+  // equal to that order (keys sorted, identity indices)
+  enqueue_topology(c);
+  if (c->sorted_keys != c->K[0])
+    CUDA_TRY(cudaMemcpyAsync(c->K[0], c->sorted_keys, 4 * (size_t)c->cap, cudaMemcpyDeviceToDevice, c->stream));
+  c->sorted_keys = c->K[0];
+  CUDA_TRY(cudaMemcpyAsync(&c->cnt->m_pending, &c->cnt->n_live, 4, cudaMemcpyDeviceToDevice, c->stream));
+  launch_iota(c->Vv[0], (int)c->cap, c->stream);
+  CUDA_TRY(cudaMemsetAsync(c->pair_counter, 0, 8, c->stream));
+  // test aid, not on the stepping path: a temporary device buffer
+  int64_t *dout = nullptr;
+  if (max > 0 && cudaMalloc(&dout, sizeof(int64_t) * 4 * (size_t)max) != cudaSuccess)
+    return fail(SPH_ERR_ALLOC, "pair buffer");
+  launch_debug_pairs(c->sweep(0), c->wx[0], c->wx[1], c->wx[2], c->wall_index, dout, max, c->pair_counter, (int)c->cap,
+                     c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  unsigned long long n = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&n, c->pair_counter, 8, cudaMemcpyDeviceToHost);
+  int64_t k = std::min<int64_t>((int64_t)n, max);
+  if (e == cudaSuccess && dout && out && k > 0)
+    e = cudaMemcpy(out, dout, sizeof(int64_t) * 4 * k, cudaMemcpyDeviceToHost);
+  if (dout) cudaFree(dout);
+  if (e != cudaSuccess) return fail(SPH_ERR_CUDA, std::string("debug pairs: ") + cudaGetErrorString(e));
+  *count = (int64_t)n;
+  return SPH_OK;
+}
+
+}  // extern "C"

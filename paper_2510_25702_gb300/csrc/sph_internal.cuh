@@ -1,0 +1,291 @@
+// sph_internal.cuh -- device-side data layout and helpers of the GB300 SPH
+// step library (the C ABI is include/sph.h).
+//
+// Layout in HBM (one context):
+//  * master particle state, FP64 structure-of-arrays, two copies (the cell
+//    sort gathers one into the other every advection step);
+//  * per-step "packs": 4-wide vectors in the sweep precision R (float or
+//    double) that the pair sweeps read for neighbours -- P = (x, y, z, V),
+//    Q = (vx, vy, vz, p), Bm0/Bm1 = symmetric B and kappa = 2/3 k m,
+//    T = (k, eps, nu_t, -).  P and Q are double-buffered across the
+//    acoustic sub-steps so a sweep never reads what it writes;
+//  * sorted cell keys, cell offsets (exclusive prefix over all cells of
+//    all instances) and the same for the fixed wall dummies;
+//  * a device status word (first error wins) and counters.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sph.h"
+
+namespace sphk {
+
+constexpr uint32_t kSubRecycle = 0xFFFFFFFFu;
+constexpr int kBlock = 128;
+
+// k-epsilon constants (App. A table)
+constexpr double kC1 = 1.44, kC2 = 1.92, kCmu = 0.09, kSigK = 1.0, kSigE = 1.3;
+constexpr double kFloor = 1e-12;
+
+struct InstDev {
+  int32_t dim, rans, dt_mode, n_ac_fixed;
+  int32_t kinematic;
+  int32_t periodic[3];
+  int32_t nc[3];
+  int32_t nbuf, buf0;
+  uint32_t seed;
+  uint32_t cell_base;  // first global cell key of this instance
+  uint32_t ncell;
+  double dp, h, rho0, c0, nu_l, eta, U_ref, dt_ad_fixed;
+  double g[3], lo[3], hi[3], L[3];
+  double cs;       // cell size 2h
+  double cut2;     // (2h)^2
+  double alpha_h;  // Wendland normalisation / h
+  double Vw;       // wall dummy volume dp^dim
+  double rc0;      // rho0 * c0
+  double eos_k;    // rho0 * c0^2
+  double muR_k;    // 0.5 * rho0 * h
+  double reg;      // 0.01 h
+  // written every advection step by the time-step kernel
+  double dt_ad, dt_ac, dt, t;
+  int32_t n_ac;
+  int32_t pad1;
+};
+
+struct BufDev {
+  int32_t type, turb, n_theta, inst;
+  int32_t local_id, pad0;
+  double origin[3];
+  double frame[9];
+  double length, half[2];
+  double p_ob, rho_ob, noise, k_in, eps_in, nut_in;
+  double gen_line;  // length + 0.5 dp (Sec. 3.1)
+  double theta[SPH_MAX_THETA];
+};
+
+// master state (FP64 SoA)
+struct Masters {
+  double *x[3], *v[3];
+  double *rho, *mass, *drho, *p, *k, *eps, *nut;
+  int32_t *label;
+  uint32_t *uid;
+  uint16_t *inst;
+};
+
+// per-step derived masters (not permuted)
+struct Derived {
+  double *B[6];  // xx, yy, zz, xy, xz, yz
+  double *an[3]; // viscous acceleration
+};
+
+template <typename R>
+struct alignas(4 * sizeof(R)) V4 {
+  R x, y, z, w;
+};
+
+template <typename R>
+struct Packs {
+  V4<R> *P[2], *Q[2];
+  V4<R> *Bm0, *Bm1, *T;
+  V4<R> *WP, *WV;  // walls: (x, y, z, V) and (vx, vy, vz, 0)
+};
+
+struct Counters {
+  int32_t status;
+  int32_t n_live;     // live real particles after the sort
+  int32_t m_pending;  // entries to sort (live + spawned copies, deleted keyed out)
+  int32_t n_spawn;    // copies appended by the last buffer update
+  int32_t overflow;
+  int32_t n_del_step;  // entries deleted by the last buffer update
+  unsigned long long spawned, deleted;
+};
+
+// ------------------------------------------------------------------------
+// exact FP64 operations for every floating-point decision that sets an
+// integer (cell index, cut-off, box containment, generation line): no
+// contraction, same operation order as the plain definition
+// ------------------------------------------------------------------------
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+
+__device__ __forceinline__ int32_t cell_coord(const InstDev &I, double x, int a) {
+  double f = floor(ddiv(dsub(x, I.lo[a]), I.cs));
+  if (!(f >= 0.0)) return 0;
+  if (f >= (double)I.nc[a]) return I.nc[a] - 1;
+  return (int32_t)f;
+}
+
+__device__ __forceinline__ uint32_t cell_key(const InstDev &I, double x, double y, double z) {
+  uint32_t cx = (uint32_t)cell_coord(I, x, 0);
+  uint32_t cy = (uint32_t)cell_coord(I, y, 1);
+  uint32_t cz = I.dim == 3 ? (uint32_t)cell_coord(I, z, 2) : 0u;
+  return I.cell_base + (cz * (uint32_t)I.nc[1] + cy) * (uint32_t)I.nc[0] + cx;
+}
+
+// buffer-local coordinate k: (x - o) . frame row k, left-to-right sum
+__device__ __forceinline__ double local_coord(const BufDev &b, int dim, double x, double y, double z, int k) {
+  const double *f = &b.frame[3 * k];
+  double s = dmul(dsub(x, b.origin[0]), f[0]);
+  s = dadd(s, dmul(dsub(y, b.origin[1]), f[1]));
+  if (dim == 3) s = dadd(s, dmul(dsub(z, b.origin[2]), f[2]));
+  return s;
+}
+
+// region-constrained containment (Sec. 3.2)
+__device__ __forceinline__ bool box_contains(const BufDev &b, int dim, double x, double y, double z) {
+  double s0 = local_coord(b, dim, x, y, z, 0);
+  if (!(s0 >= 0.0 && s0 < b.length)) return false;
+  double s1 = local_coord(b, dim, x, y, z, 1);
+  if (!(fabs(s1) <= b.half[0])) return false;
+  if (dim == 3) {
+    double s2 = local_coord(b, dim, x, y, z, 2);
+    if (!(fabs(s2) <= b.half[1])) return false;
+  }
+  return true;
+}
+
+// Philox4x32-10 (Salmon et al., SC'11)
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+    uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+    uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// 53-bit uniform in [-1, 1) from two words (top 27 + 26 bits)
+__device__ __forceinline__ double uniform_pm1(uint32_t a, uint32_t b) {
+  double m = dadd(dmul((double)(a >> 5), 67108864.0), (double)(b >> 6));
+  return dsub(dmul(2.0, dmul(m, 1.0 / 9007199254740992.0)), 1.0);
+}
+
+__device__ __forceinline__ void set_status(int32_t *status, int32_t code) {
+  atomicCAS(status, 0, code);
+}
+
+// velocity-profile value at transverse coordinate s1 (linear in theta)
+__device__ __forceinline__ double profile_U(const BufDev &b, double s1) {
+  if (b.n_theta <= 1) return b.theta[0];
+  double w = b.half[0];
+  double u = dmul(ddiv(dadd(s1, w), dmul(2.0, w)), (double)(b.n_theta - 1));
+  if (!(u > 0.0)) return b.theta[0];
+  if (u >= (double)(b.n_theta - 1)) return b.theta[b.n_theta - 1];
+  int k = (int)floor(u);
+  double f = dsub(u, (double)k);
+  return dadd(b.theta[k], dmul(f, dsub(b.theta[k + 1], b.theta[k])));
+}
+
+// Buffer boundary values on particle i (Sec. 2.4.2, buffer table of
+// Sec. 4.3), in the plain operation order (no contraction).
+__device__ __forceinline__ void apply_bc(const InstDev &I, const BufDev &b, const Masters &m, int i,
+                                         int64_t step, uint32_t sub) {
+  if (b.type == SPH_BUF_VELOCITY) {
+    double s1 = local_coord(b, I.dim, m.x[0][i], m.x[1][i], I.dim == 3 ? m.x[2][i] : 0.0, 1);
+    double U = profile_U(b, s1);
+    double xi[3] = {0.0, 0.0, 0.0};
+    if (b.noise != 0.0) {
+      uint32_t c[4] = {(uint32_t)step, sub, 0u, 0u};
+      philox4x32_10(c, I.seed, m.uid[i]);
+      xi[0] = uniform_pm1(c[0], c[1]);
+      xi[1] = uniform_pm1(c[2], c[3]);
+      if (I.dim == 3) {
+        uint32_t c2[4] = {(uint32_t)step, sub, 1u, 0u};
+        philox4x32_10(c2, I.seed, m.uid[i]);
+        xi[2] = uniform_pm1(c2[0], c2[1]);
+      }
+    }
+    for (int a = 0; a < I.dim; ++a) m.v[a][i] = dadd(dmul(U, b.frame[a]), dmul(dmul(b.noise, U), xi[a]));
+  } else {
+    m.p[i] = b.p_ob;
+    m.rho[i] = b.rho_ob;
+  }
+  if (I.rans && b.turb == SPH_TURB_FREESTREAM) {
+    m.k[i] = b.k_in;
+    m.eps[i] = b.eps_in;
+    m.nut[i] = b.nut_in;
+  }
+}
+
+// ------------------------------------------------------------------------
+// host-side launch wrappers implemented in the .cu files
+// ------------------------------------------------------------------------
+struct SortTemp {
+  uint32_t *hist;  // [256 * max_blocks]
+  int max_blocks;
+};
+
+// radix sort of (keys, vals) over *d_count entries (device count); bits of
+// key to sort; results in keys_out / vals_out.  Uses keys_tmp/vals_tmp.
+void radix_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                const int32_t *d_count, int max_count, int bits, const SortTemp &tmp,
+                cudaStream_t st, uint32_t **keys_result, uint32_t **vals_result);
+// cell offsets (lower bounds) for cells [0, ncell] over sorted keys
+void cell_offsets(const uint32_t *keys, const int32_t *d_count, uint32_t ncell, uint32_t *off,
+                  int32_t *d_nlive, cudaStream_t st);
+
+struct TopoArgs {
+  const InstDev *inst;
+  const BufDev *buf;
+  Masters src, dst;
+  Derived der;
+  uint32_t *keys, *idx;
+  const uint32_t *sorted_vals;
+  Counters *cnt;
+  unsigned long long *v2max, *nutmax;  // per instance
+  uint32_t *next_uid;                  // per instance
+  int32_t *inst_spawn;                 // per instance spawn counts / bases
+  uint8_t *flag;
+  int32_t *block_cnt;
+  uint32_t sentinel;
+  int32_t ninst, n_ac_max;
+  int64_t step;
+  int64_t capacity;
+};
+
+void launch_permute(const TopoArgs &a, int max_n, int prec, cudaStream_t st, void *packs);
+void launch_time_step(const TopoArgs &a, cudaStream_t st);
+void launch_buffer_update(const TopoArgs &a, int max_n, cudaStream_t st);
+void launch_keys(const TopoArgs &a, int max_n, int all_live, cudaStream_t st);
+void launch_iota(uint32_t *idx, int max_n, cudaStream_t st);
+
+struct SweepArgs {
+  const InstDev *inst;
+  const BufDev *buf;
+  Masters m;
+  Derived der;
+  const uint32_t *keys;  // sorted cell keys of the live particles
+  const uint32_t *off;   // cell offsets
+  const uint32_t *woff;  // wall cell offsets
+  const Counters *cnt;
+  int32_t *status;
+  int64_t step;
+  int32_t sub;
+  int32_t last_sub;  // n_ac_max - 1
+};
+
+// sweeps: prec 0 -> double packs, 1 -> float packs; dim 2 / 3
+void launch_advection_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n,
+                            cudaStream_t st);
+void launch_momentum_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n, int sub,
+                           cudaStream_t st);
+void launch_continuity_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n, int sub,
+                             cudaStream_t st);
+void launch_debug_pairs(const SweepArgs &a, const double *wx, const double *wy, const double *wz,
+                        const uint32_t *wall_index, int64_t *out, int64_t max, unsigned long long *counter,
+                        int max_n, cudaStream_t st);
+
+}  // namespace sphk

@@ -1,0 +1,324 @@
+// sph_topology.cu -- particle bookkeeping of one advection step:
+//   * permute  : gather every master field into cell order (a2), label each
+//                particle by the buffer boxes of its instance (a3,
+//                Sec. 3.2) and fold the time-step maxima (a4);
+//   * time step: dual-criteria advection / acoustic steps (a4, Sec. 2.3);
+//   * buffer update: injection across the generation line and ID-checked
+//                deletion (a12, a13; Sec. 2.4.2, 2.4.3, 3.1, 3.2) with stable
+//                compaction (a14): survivors keep index order, copies are
+//                appended in index order, deleted entries get the sentinel
+//                key so the next sort drops them.
+#include "sph_internal.cuh"
+
+namespace sphk {
+
+// ------------------------------------------------------------------------
+// permute + label + time-step maxima
+// ------------------------------------------------------------------------
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *slot, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(slot, (unsigned long long)__double_as_longlong(v));
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_permute(TopoArgs a, Packs<R> pk) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = a.cnt->n_live;
+  if (t >= n) return;
+  const int s = (int)a.sorted_vals[t];
+  const Masters S = a.src, D = a.dst;
+  const int ii = S.inst[s];
+  const InstDev &I = a.inst[ii];
+  double x = S.x[0][s], y = S.x[1][s], z = S.x[2][s];
+  double vx = S.v[0][s], vy = S.v[1][s], vz = S.v[2][s];
+  double rho = S.rho[s], mass = S.mass[s];
+  D.x[0][t] = x;
+  D.x[1][t] = y;
+  D.x[2][t] = z;
+  D.v[0][t] = vx;
+  D.v[1][t] = vy;
+  D.v[2][t] = vz;
+  D.rho[t] = rho;
+  D.mass[t] = mass;
+  D.drho[t] = S.drho[s];
+  D.p[t] = S.p[s];
+  double k = S.k[s], eps = S.eps[s], nut = S.nut[s];
+  D.k[t] = k;
+  D.eps[t] = eps;
+  D.nut[t] = nut;
+  D.uid[t] = S.uid[s];
+  D.inst[t] = (uint16_t)ii;
+  int32_t lab = S.label[s];
+  for (int b = 0; b < I.nbuf; ++b) {
+    const BufDev &B = a.buf[I.buf0 + b];
+    if (box_contains(B, I.dim, x, y, z)) lab = B.local_id + 1;
+  }
+  D.label[t] = lab;
+  V4<R> P = {(R)x, (R)y, (R)z, (R)(mass / rho)};
+  V4<R> Q = {(R)vx, (R)vy, (R)vz, (R)S.p[s]};
+  pk.P[0][t] = P;
+  pk.Q[0][t] = Q;
+  if (I.rans) {
+    V4<R> T = {(R)k, (R)eps, (R)nut, (R)0};
+    pk.T[t] = T;
+  }
+  // |v|^2 with the plain left-to-right sum, nu_t
+  double v2 = dmul(vx, vx);
+  v2 = dadd(v2, dmul(vy, vy));
+  if (I.dim == 3) v2 = dadd(v2, dmul(vz, vz));
+  atomic_max_nonneg(&a.v2max[ii], v2);
+  if (I.rans) atomic_max_nonneg(&a.nutmax[ii], nut);
+}
+
+void launch_permute(const TopoArgs &a, int max_n, int prec, cudaStream_t st, void *packs) {
+  int g = (max_n + kBlock - 1) / kBlock;
+  if (g < 1) g = 1;
+  if (prec == SPH_PREC_FP32)
+    k_permute<float><<<g, kBlock, 0, st>>>(a, *(Packs<float> *)packs);
+  else
+    k_permute<double><<<g, kBlock, 0, st>>>(a, *(Packs<double> *)packs);
+}
+
+// ------------------------------------------------------------------------
+// a4 dual-criteria time step, one thread per instance
+// ------------------------------------------------------------------------
+__global__ void k_time_step(TopoArgs a) {
+  const int ii = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ii >= a.ninst) return;
+  InstDev &I = const_cast<InstDev &>(a.inst[ii]);
+  double v2max = __longlong_as_double((long long)a.v2max[ii]);
+  double nutmax = __longlong_as_double((long long)a.nutmax[ii]);
+  double vmax = __dsqrt_rn(v2max);
+  double u = (vmax > I.U_ref) ? vmax : I.U_ref;
+  double dt_adv = ddiv(dmul(0.25, I.h), u);
+  double nu_eff = dadd(I.nu_l, nutmax);
+  double dt_visc = ddiv(dmul(dmul(0.125, I.h), I.h), nu_eff);
+  double dt_ad = (dt_adv < dt_visc) ? dt_adv : dt_visc;
+  double dt_ac = ddiv(dmul(0.6, I.h), dadd(I.c0, vmax));
+  int n;
+  if (I.dt_mode == SPH_DT_FIXED) {
+    dt_ad = I.dt_ad_fixed;
+    n = I.n_ac_fixed;
+  } else if (I.dt_mode == SPH_DT_SINGLE) {
+    if (dt_ac < dt_ad) dt_ad = dt_ac;
+    n = 1;
+  } else {
+    double f = ceil(ddiv(dt_ad, dt_ac));
+    n = (f >= 1.0) ? (int)fmin(f, 1.0e9) : 1;
+  }
+  if (n > a.n_ac_max) {
+    set_status(&a.cnt->status, SPH_ERR_STATE);
+    n = a.n_ac_max;
+  }
+  I.dt_ad = dt_ad;
+  I.dt_ac = dt_ac;
+  I.n_ac = n;
+  I.dt = ddiv(dt_ad, (double)n);
+  I.t = dadd(I.t, dt_ad);
+}
+
+void launch_time_step(const TopoArgs &a, cudaStream_t st) {
+  k_time_step<<<(a.ninst + 63) / 64, 64, 0, st>>>(a);
+}
+
+// ------------------------------------------------------------------------
+// buffer update
+// ------------------------------------------------------------------------
+enum : uint8_t { kKeep = 0, kInject = 1, kDelete = 2 };
+
+__global__ void __launch_bounds__(kBlock) k_flags(TopoArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = a.cnt->n_live;
+  uint8_t f = kKeep;
+  if (i < n) {
+    int32_t lab = a.src.label[i];
+    const int ii = a.src.inst[i];
+    const InstDev &I = a.inst[ii];
+    if (lab > 0 && lab <= I.nbuf) {
+      const BufDev &B = a.buf[I.buf0 + lab - 1];
+      double s0 = local_coord(B, I.dim, a.src.x[0][i], a.src.x[1][i], a.src.x[2][i], 0);
+      if (s0 >= B.gen_line) {
+        f = kInject;
+        atomicAdd(&a.inst_spawn[ii], 1);
+      } else if (s0 < 0.0) {
+        f = kDelete;
+      }
+    }
+    a.flag[i] = f;
+  }
+  unsigned bal = __ballot_sync(0xffffffffu, f == kInject);
+  __shared__ int32_t wc[kBlock / 32];
+  if ((threadIdx.x & 31) == 0) wc[threadIdx.x >> 5] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t s = 0;
+    for (int w = 0; w < kBlock / 32; ++w) s += wc[w];
+    a.block_cnt[blockIdx.x] = s;
+  }
+}
+
+// single block: exclusive scan of the per-block inject counts, per-instance
+// uid bases, capacity check (nothing is committed on overflow)
+__global__ void __launch_bounds__(1024) k_spawn_scan(TopoArgs a, int nblocks, uint32_t *uid_base) {
+  __shared__ int32_t carry;
+  __shared__ int32_t ws[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = 0; base < nblocks; base += 1024) {
+    int i = base + threadIdx.x;
+    int32_t v = i < nblocks ? a.block_cnt[i] : 0;
+    int32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int32_t s = ws[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      ws[lane] = s;
+    }
+    __syncthreads();
+    int32_t excl = carry + (warp > 0 ? ws[warp - 1] : 0) + x - v;
+    if (i < nblocks) a.block_cnt[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int32_t total = carry;
+    int32_t n = a.cnt->n_live;
+    int over = (int64_t)n + total > a.capacity;
+    a.cnt->overflow = over;
+    if (over) set_status(&a.cnt->status, SPH_ERR_CAPACITY);
+    int32_t S = over ? 0 : total;
+    a.cnt->n_spawn = S;
+    a.cnt->m_pending = n + S;
+    a.cnt->n_del_step = 0;
+    a.cnt->spawned += (unsigned long long)S;
+    // per-instance uid bases: copy number r (global rank) of instance ii gets
+    // uid next_uid[ii] + (r - first global rank of ii)
+    int32_t run = 0;
+    for (int ii = 0; ii < a.ninst; ++ii) {
+      int32_t c = a.inst_spawn[ii];
+      uid_base[ii] = a.next_uid[ii] - (uint32_t)run;
+      if (!over) a.next_uid[ii] += (uint32_t)c;
+      run += c;
+      a.inst_spawn[ii] = 0;
+    }
+  }
+}
+
+// periodic wrap of the position (same test and order as the plain
+// definition), then the cell key of the wrapped position
+__device__ __forceinline__ void wrap_and_key(const InstDev &I, const Masters &m, int i, uint32_t *keys) {
+  double p[3] = {m.x[0][i], m.x[1][i], m.x[2][i]};
+  for (int d = 0; d < I.dim; ++d) {
+    if (!I.periodic[d]) continue;
+    if (p[d] >= I.hi[d])
+      p[d] = dsub(p[d], I.L[d]);
+    else if (p[d] < I.lo[d])
+      p[d] = dadd(p[d], I.L[d]);
+    m.x[d][i] = p[d];
+  }
+  keys[i] = cell_key(I, p[0], p[1], p[2]);
+}
+
+__global__ void __launch_bounds__(kBlock) k_spawn(TopoArgs a, const uint32_t *uid_base) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = a.cnt->n_live;
+  const Masters m = a.src;
+  uint8_t f = (i < n) ? a.flag[i] : kKeep;
+  const int over = a.cnt->overflow;
+  const unsigned bal = __ballot_sync(0xffffffffu, f == kInject);
+  __shared__ int32_t wc[kBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) wc[warp] = __popc(bal);
+  __syncthreads();
+  int32_t off = a.block_cnt[blockIdx.x];
+  for (int w = 0; w < warp; ++w) off += wc[w];
+  const int32_t rank = off + __popc(bal & ((1u << lane) - 1u));
+  if (i >= n) return;
+  a.idx[i] = (uint32_t)i;
+  const int ii = m.inst[i];
+  const InstDev &I = a.inst[ii];
+  if (over || f == kKeep) {
+    wrap_and_key(I, m, i, a.keys);
+    return;
+  }
+  if (f == kDelete) {
+    a.keys[i] = a.sentinel;
+    atomicAdd(&a.cnt->deleted, 1ull);
+    atomicAdd(&a.cnt->n_del_step, 1);
+    return;
+  }
+  // injection: copy at the parent's position, parent recycled by -L_b n_b
+  const int dst = n + rank;
+  for (int d = 0; d < 3; ++d) {
+    m.x[d][dst] = m.x[d][i];
+    m.v[d][dst] = m.v[d][i];
+    a.der.an[d][dst] = a.der.an[d][i];
+  }
+  for (int c = 0; c < 6; ++c) a.der.B[c][dst] = a.der.B[c][i];
+  m.rho[dst] = m.rho[i];
+  m.mass[dst] = m.mass[i];
+  m.drho[dst] = m.drho[i];
+  m.p[dst] = m.p[i];
+  m.k[dst] = m.k[i];
+  m.eps[dst] = m.eps[i];
+  m.nut[dst] = m.nut[i];
+  m.inst[dst] = (uint16_t)ii;
+  m.label[dst] = 0;
+  m.uid[dst] = uid_base[ii] + (uint32_t)rank;
+  a.idx[dst] = (uint32_t)dst;
+  wrap_and_key(I, m, dst, a.keys);
+  const BufDev &B = a.buf[I.buf0 + m.label[i] - 1];
+  for (int d = 0; d < I.dim; ++d) m.x[d][i] = dsub(m.x[d][i], dmul(B.length, B.frame[d]));
+  apply_bc(I, B, m, i, a.step, kSubRecycle);
+  wrap_and_key(I, m, i, a.keys);
+}
+
+void launch_buffer_update(const TopoArgs &a, int max_n, cudaStream_t st) {
+  int g = (max_n + kBlock - 1) / kBlock;
+  if (g < 1) g = 1;
+  k_flags<<<g, kBlock, 0, st>>>(a);
+  // uid bases live after the per-instance spawn counters
+  uint32_t *uid_base = reinterpret_cast<uint32_t *>(a.inst_spawn + a.ninst);
+  k_spawn_scan<<<1, 1024, 0, st>>>(a, g, uid_base);
+  k_spawn<<<g, kBlock, 0, st>>>(a, uid_base);
+}
+
+// keys of every live entry from its current position (after creation or a
+// write of positions); entries keyed out as deleted stay deleted
+__global__ void k_keys(TopoArgs a, int all_live) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.cnt->m_pending) return;
+  a.idx[i] = (uint32_t)i;
+  if (!all_live && a.keys[i] == a.sentinel) return;
+  const InstDev &I = a.inst[a.src.inst[i]];
+  wrap_and_key(I, a.src, i, a.keys);
+}
+
+void launch_keys(const TopoArgs &a, int max_n, int all_live, cudaStream_t st) {
+  int g = (max_n + kBlock - 1) / kBlock;
+  if (g < 1) g = 1;
+  k_keys<<<g, kBlock, 0, st>>>(a, all_live);
+}
+
+__global__ void k_iota(uint32_t *idx, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) idx[i] = (uint32_t)i;
+}
+
+void launch_iota(uint32_t *idx, int max_n, cudaStream_t st) {
+  int g = (max_n + 255) / 256;
+  if (g < 1) g = 1;
+  k_iota<<<g, 256, 0, st>>>(idx, max_n);
+}
+
+}  // namespace sphk
