@@ -240,6 +240,31 @@ const char *sph_stage_name(int32_t stage);
    Test and debug aid; re-sorts the particles by cell. */
 int sph_debug_pairs(sph_ctx *ctx, int64_t *out, int64_t max, int64_t *count);
 
+/* Cell sort of a caller's point set that allocates no device memory.  The
+   paper has no counterpart: this exists for callers that cannot allocate,
+   such as code running while a CUDA stream is being captured into a graph,
+   or applications whose device memory is reserved up front and may not grow
+   during a run.  It computes the cell index of every point on the grid of
+   cfg (cells of 2 * cfg->h over [domain_lo, domain_hi), clamped at the edges,
+   as sph_create builds it; no periodic wrap), sorts the point indices
+   stably by cell, and writes
+     order[n]                 point indices in cell order (device memory),
+     cell_start[ncell + 1]    first position in order of each cell, and n at
+                              the end (device memory, cell_start_len entries),
+     *ncell_out               number of cells (host memory, may be NULL).
+   pos is device memory, [n][3] doubles.  stream is a cudaStream_t (NULL =
+   legacy stream); the call is asynchronous on it.
+   Scratch is one static device array of about 8.4 MB that every GPU loading
+   the library holds until exit; n above SPH_NOALLOC_MAX_POINTS, a bad grid
+   or cell_start_len < ncell + 1 returns SPH_ERR_ARG, a CUDA failure
+   SPH_ERR_CUDA.  All calls on a device share the array and leave their
+   contents in it; calls that overlap on the GPU race.  The first call on a
+   device looks up the array's address (cudaGetSymbolAddress) with that
+   device current: make it before any stream capture. */
+#define SPH_NOALLOC_MAX_POINTS (1 << 19)
+int sph_cell_sort_noalloc(const sph_config *cfg, const double *pos, int32_t n, uint32_t *order,
+                          uint32_t *cell_start, int64_t cell_start_len, int64_t *ncell_out, void *stream);
+
 void sph_destroy(sph_ctx *ctx);
 const char *sph_error_string(int code);
 /* Message of the last SPH_ERR_ARG / SPH_ERR_CUDA on this thread. */

@@ -93,7 +93,9 @@ _lib = None
 
 EXPORTS = ("sph_create", "sph_add_buffer", "sph_set_profile", "sph_step", "sph_read_fields",
            "sph_write_fields", "sph_get_stats", "sph_debug_pairs", "sph_destroy", "sph_error_string",
-           "sph_last_error", "sph_abi_version", "sph_set_profiling", "sph_get_stage_times", "sph_stage_name")
+           "sph_last_error", "sph_abi_version", "sph_set_profiling", "sph_get_stage_times", "sph_stage_name",
+           "sph_cell_sort_noalloc")
+NOALLOC_MAX_POINTS = 1 << 19
 N_STAGES = 8
 
 
@@ -125,6 +127,8 @@ def lib():
         L.sph_get_stage_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32,
                                           C.POINTER(C.c_int32)]
         L.sph_stage_name.restype = C.c_char_p
+        L.sph_cell_sort_noalloc.argtypes = [C.POINTER(Config), vp, C.c_int32, vp, vp, C.c_int64,
+                                            C.POINTER(C.c_int64), vp]
         L.sph_error_string.restype = C.c_char_p
         L.sph_last_error.restype = C.c_char_p
         _lib = L
