@@ -45,7 +45,9 @@ extern "C" {
 #define SPH_OK 0
 #define SPH_ERR_ARG -1       /* invalid argument (message via sph_last_error) */
 #define SPH_ERR_CUDA -2      /* a CUDA call failed */
-#define SPH_ERR_CAPACITY -3  /* particle capacity exceeded; buffer update not committed */
+#define SPH_ERR_CAPACITY -3  /* particle capacity exceeded (buffer update not committed), or a
+                                particle has more neighbours than its list holds (2.5 x the
+                                full-support count; the surplus is dropped from that step) */
 #define SPH_ERR_NONFINITE -4 /* a density or velocity became NaN/Inf */
 #define SPH_ERR_TIMEOUT -5   /* a bounded device wait ran out */
 #define SPH_ERR_OVERLAP -6   /* buffer boxes of one instance intersect */
@@ -223,11 +225,12 @@ int sph_get_stats(sph_ctx *ctx, sph_stats *out);
 /* Stage timing (tracing aid, no counterpart in the paper).  While enabled,
    sph_step brackets every kernel stage with CUDA events on the context's
    stream and accumulates, per stage, the summed event time (ms) and the
-   number of launches.  Stages, in step order: 0 sort, 1 cells, 2 permute,
-   3 time step, 4 advection sweep, 5 momentum sweep, 6 continuity sweep,
-   7 buffer update.  enable = 0 stops timing; enable = 2 also clears the
-   totals.  sph_get_stage_times writes up to max_stages entries. */
-#define SPH_N_STAGES 8
+   number of launches.  Stages: 0 sort, 1 cells, 2 permute, 3 time step,
+   4 advection sweep, 5 momentum sweep, 6 continuity sweep, 7 buffer update,
+   8 neighbour list (built once per advection step, before the advection
+   sweep).  enable = 0 stops timing; enable = 2 also clears the totals.
+   sph_get_stage_times writes up to max_stages entries. */
+#define SPH_N_STAGES 9
 int sph_set_profiling(sph_ctx *ctx, int32_t enable);
 int sph_get_stage_times(sph_ctx *ctx, double *ms_total, int64_t *launches, int32_t max_stages,
                         int32_t *n_stages);
@@ -254,7 +257,7 @@ int sph_debug_pairs(sph_ctx *ctx, int64_t *out, int64_t max, int64_t *count);
      *ncell_out               number of cells (host memory, may be NULL).
    pos is device memory, [n][3] doubles.  stream is a cudaStream_t (NULL =
    legacy stream); the call is asynchronous on it.
-   Scratch is one static device array of about 8.4 MB that every GPU loading
+   Scratch is one static device array of about 9.4 MB that every GPU loading
    the library holds until exit; n above SPH_NOALLOC_MAX_POINTS, a bad grid
    or cell_start_len < ncell + 1 returns SPH_ERR_ARG, a CUDA failure
    SPH_ERR_CUDA.  All calls on a device share the array and leave their

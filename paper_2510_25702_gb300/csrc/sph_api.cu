@@ -78,6 +78,7 @@ struct sph_ctx {
   int32_t *block_cnt = nullptr;
   SortTemp sort_tmp{};
   uint32_t *sorted_keys = nullptr;
+  NbrList nl{};
   // stage timing (CUDA event pairs on the context's stream)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -176,6 +177,7 @@ struct sph_ctx {
     a.buf = d_buf;
     a.m = M[cur];
     a.der = der;
+    a.nl = nl;
     a.keys = sorted_keys;
     a.off = off;
     a.woff = woff;
@@ -183,7 +185,8 @@ struct sph_ctx {
     a.status = &cnt->status;
     a.step = step;
     a.sub = sub;
-    a.last_sub = n_ac_max - 1;
+    a.any_periodic = 0;
+    for (const InstDev &I : inst) a.any_periodic |= I.periodic[0] | I.periodic[1] | I.periodic[2];
     return a;
   }
 };
@@ -246,6 +249,10 @@ static int build_inst(const sph_config &c, InstDev &I, std::string &why) {
   I.eos_k = c.rho0 * c.c0 * c.c0;
   I.muR_k = 0.5 * c.rho0 * c.h;
   I.reg = 0.01 * c.h;
+  I.inv_h = 1.0 / c.h;
+  I.inv_cs = 1.0 / I.cs;
+  I.inv_rc0 = 1.0 / (c.rho0 * c.c0);
+  I.c0sq = c.c0 * c.c0;
   I.n_ac = 1;
   return 0;
 }
@@ -302,6 +309,8 @@ static int alloc_packs(sph_ctx *c, Packs<R> &pk, int64_t cap, int64_t nw) {
   pk.Bm0 = alloc_arr<V4<R>>(c, cap);
   pk.Bm1 = alloc_arr<V4<R>>(c, c->dim == 3 ? cap : 1);
   pk.T = alloc_arr<V4<R>>(c, cap);
+  pk.Ap = alloc_arr<V4<R>>(c, cap);
+  if (!pk.Ap) return -1;
   pk.WP = alloc_arr<V4<R>>(c, nw);
   pk.WV = alloc_arr<V4<R>>(c, nw);
   if (!pk.Bm0 || !pk.Bm1 || !pk.T || !pk.WP || !pk.WV) return -1;
@@ -399,7 +408,6 @@ int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *
   c->ncell = (uint32_t)cell_base;
   c->key_bits = 1;
   while ((1ull << c->key_bits) <= (uint64_t)c->ncell) ++c->key_bits;
-  c->key_bits = ((c->key_bits + 7) / 8) * 8;
   c->cap = cap_total;
   c->nw = nw_total;
 
@@ -530,8 +538,25 @@ int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *
   ok &= (c->inst_spawn = alloc_arr<int32_t>(c, 2 * (int64_t)n_instances)) != nullptr;
   ok &= (c->flag = alloc_arr<uint8_t>(c, cap)) != nullptr;
   ok &= (c->block_cnt = alloc_arr<int32_t>(c, (cap + kBlock - 1) / kBlock + 1)) != nullptr;
+  {
+    // neighbour-list entries per particle: 2.5 x the full-support count
+    // pi (2h/dp)^2 (2D) or 4/3 pi (2h/dp)^3 (3D), a multiple of 8
+    double expect = 0.0;
+    for (int i = 0; i < n_instances; ++i) {
+      double s = 2.0 * cfg[i].h / cfg[i].dp;
+      double e = (c->dim == 2) ? kPi * s * s : 4.0 / 3.0 * kPi * s * s * s;
+      expect = std::max(expect, e);
+    }
+    int kmax = (int)std::ceil(2.5 * expect / 8.0) * 8;
+    kmax = std::max(16, std::min(kmax, 4096));
+    c->nl.kmax = kmax;
+    c->nl.stride = (int32_t)cap;
+    ok &= (c->nl.nbr = alloc_arr<uint32_t>(c, cap * (int64_t)kmax)) != nullptr;
+    ok &= (c->nl.n_real = alloc_arr<uint16_t>(c, cap)) != nullptr;
+    ok &= (c->nl.n_wall = alloc_arr<uint16_t>(c, cap)) != nullptr;
+  }
   c->sort_tmp.max_blocks = (int)((cap + 2047) / 2048) + 1;
-  ok &= (c->sort_tmp.hist = alloc_arr<uint32_t>(c, 256 * (int64_t)c->sort_tmp.max_blocks)) != nullptr;
+  ok &= (c->sort_tmp.hist = alloc_arr<uint32_t>(c, (int64_t)radix_hist_words((int)cap, c->key_bits))) != nullptr;
   ok &= (c->d_inst = alloc_arr<InstDev>(c, n_instances)) != nullptr;
   ok &= (c->d_buf = alloc_arr<BufDev>(c, (int64_t)n_instances * SPH_MAX_BUFFERS)) != nullptr;
   if (ok) ok = (c->prec == SPH_PREC_FP32) ? alloc_packs(c, c->pkf, cap, nw_total) == 0
@@ -618,7 +643,7 @@ void sph_destroy(sph_ctx *c) {
 const char *sph_stage_name(int32_t stage) {
   static const char *names[SPH_N_STAGES] = {"sort", "cells", "permute", "time_step",
                                             "advection_sweep", "momentum_sweep", "continuity_sweep",
-                                            "buffer_update"};
+                                            "buffer_update", "neighbour_list"};
   return (stage >= 0 && stage < SPH_N_STAGES) ? names[stage] : "unknown";
 }
 
@@ -708,6 +733,10 @@ int sph_add_buffer(sph_ctx *c, int32_t instance, const sph_buffer_desc *b, int32
   if (b->turb_bc != SPH_TURB_ZERO_GRADIENT && b->turb_bc != SPH_TURB_FREESTREAM)
     return fail(SPH_ERR_ARG, "bad turbulence BC");
   if (b->n_theta < 1 || b->n_theta > SPH_MAX_THETA) return fail(SPH_ERR_ARG, "n_theta must be 1..64");
+  // the mirror search of a pressure buffer spans two cells each way
+  for (int a = 0; a < I.dim; ++a)
+    if (b->type == SPH_BUF_PRESSURE && I.periodic[a] && I.nc[a] < 5)
+      return fail(SPH_ERR_ARG, "pressure buffers need at least 5 cells on periodic axes");
   if (!(b->length > 0) || !(b->half[0] > 0) || (I.dim == 3 && !(b->half[1] > 0)))
     return fail(SPH_ERR_ARG, "buffer length and half widths must be > 0");
   if (I.rans && b->turb_bc == SPH_TURB_FREESTREAM && !(b->k_in > 0 && b->eps_in > 0))
@@ -801,6 +830,7 @@ static void enqueue_topology(sph_ctx *c) {
   ev = c->prof_begin(1);
   cell_offsets(ks, &c->cnt->m_pending, c->ncell, c->off, &c->cnt->n_live, c->stream);
   cudaMemsetAsync(c->v2max, 0, sizeof(unsigned long long) * 2 * c->ninst, c->stream);
+  cudaMemsetAsync(&c->cnt->n_ac_all, 0, sizeof(int32_t), c->stream);
   c->prof_end(ev);
   TopoArgs t = c->topo();
   t.sorted_vals = vs;
@@ -809,7 +839,7 @@ static void enqueue_topology(sph_ctx *c) {
   c->prof_end(ev);
   c->cur = 1 - c->cur;
   c->sorted_keys = ks;
-  c->launches += 3 * (c->key_bits / 8) + 2;
+  c->launches += kSortKernelsPerPass * radix_passes(c->key_bits) + 2;
 }
 
 static void enqueue_step(sph_ctx *c) {
@@ -818,6 +848,9 @@ static void enqueue_step(sph_ctx *c) {
   if (!c->kinematic) {
     int ev = c->prof_begin(3);
     launch_time_step(c->topo(), c->stream);
+    c->prof_end(ev);
+    ev = c->prof_begin(8);
+    launch_neighbour_list(c->sweep(0), c->packs(), c->prec, c->dim, maxn, c->stream);
     c->prof_end(ev);
     ev = c->prof_begin(4);
     launch_advection_sweep(c->sweep(0), c->packs(), c->prec, c->dim, maxn, c->stream);
@@ -834,7 +867,7 @@ static void enqueue_step(sph_ctx *c) {
   int ev = c->prof_begin(7);
   launch_buffer_update(c->topo(), maxn, c->stream);
   c->prof_end(ev);
-  c->launches += 3 + (c->kinematic ? 0 : 2 + 2 * c->n_ac_max);
+  c->launches += 3 + (c->kinematic ? 0 : 3 + 2 * c->n_ac_max);
   c->step += 1;
 }
 
@@ -937,7 +970,7 @@ int sph_read_fields(sph_ctx *c, uint32_t mask, void *const *dst, int32_t dst_on_
       for (int a = 0; a < 3; ++a)
         if ((rc = pull(src[a], m, comp[a]))) return rc;
       for (int64_t r = 0; r < n; ++r)
-        for (int a = 0; a < 3; ++a) buf[3 * r + a] = comp[a][lv.rows[r]];
+        for (int a = 0; a < 3; ++a) buf[3 * r + a] = (a < c->dim) ? comp[a][lv.rows[r]] : 0.0;
       if ((rc = store_out(out, buf.data(), sizeof(double) * 3 * n, dst_on_device))) return rc;
     } else if (f == SPH_F_B) {
       std::vector<double> comp[6], buf(9 * n);
@@ -945,7 +978,9 @@ int sph_read_fields(sph_ctx *c, uint32_t mask, void *const *dst, int32_t dst_on_
         if ((rc = pull(c->der.B[q], m, comp[q]))) return rc;
       for (int64_t r = 0; r < n; ++r) {
         int64_t i = lv.rows[r];
-        double xx = comp[0][i], yy = comp[1][i], zz = comp[2][i], xy = comp[3][i], xz = comp[4][i], yz = comp[5][i];
+        const bool d3 = c->dim == 3;  // a 2D step writes xx, yy, xy only
+        double xx = comp[0][i], yy = comp[1][i], xy = comp[3][i];
+        double zz = d3 ? comp[2][i] : 0.0, xz = d3 ? comp[4][i] : 0.0, yz = d3 ? comp[5][i] : 0.0;
         double B9[9] = {xx, xy, xz, xy, yy, yz, xz, yz, zz};
         memcpy(&buf[9 * r], B9, sizeof(B9));
       }

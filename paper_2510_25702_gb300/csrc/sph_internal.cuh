@@ -47,6 +47,10 @@ struct InstDev {
   double eos_k;    // rho0 * c0^2
   double muR_k;    // 0.5 * rho0 * h
   double reg;      // 0.01 h
+  double inv_h;    // 1 / h
+  double inv_cs;   // 1 / (2h)
+  double inv_rc0;  // 1 / (rho0 c0)
+  double c0sq;     // c0^2: p = c0^2 (rho - rho0), the stiff EOS of Sec. 2.1
   // written every advection step by the time-step kernel
   double dt_ad, dt_ac, dt, t;
   int32_t n_ac;
@@ -88,6 +92,7 @@ template <typename R>
 struct Packs {
   V4<R> *P[2], *Q[2];
   V4<R> *Bm0, *Bm1, *T;
+  V4<R> *Ap;       // a_nu + g of the advection step (sweep precision)
   V4<R> *WP, *WV;  // walls: (x, y, z, V) and (vx, vy, vz, 0)
 };
 
@@ -98,6 +103,8 @@ struct Counters {
   int32_t n_spawn;    // copies appended by the last buffer update
   int32_t overflow;
   int32_t n_del_step;  // entries deleted by the last buffer update
+  int32_t n_ac_all;    // largest sub-step count of any instance this step
+  int32_t pad2;
   unsigned long long spawned, deleted;
 };
 
@@ -111,8 +118,16 @@ __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a,
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
 
+// floor((x - lo) / (2h)) with the correctly rounded quotient, clamped.  The
+// product with 1/(2h) is within 3.4e-10 cells of that quotient for grids of
+// up to 1e6 cells per axis, so when it lies more than 1e-9 away from an
+// integer both have the same floor; only then is the division skipped.
 __device__ __forceinline__ int32_t cell_coord(const InstDev &I, double x, int a) {
-  double f = floor(ddiv(dsub(x, I.lo[a]), I.cs));
+  const double t = dsub(x, I.lo[a]);
+  const double qa = dmul(t, I.inv_cs);
+  double f = floor(qa);
+  const double frac = qa - f;
+  if (!(frac > 1e-9 && frac < 1.0 - 1e-9)) f = floor(ddiv(t, I.cs));
   if (!(f >= 0.0)) return 0;
   if (f >= (double)I.nc[a]) return I.nc[a] - 1;
   return (int32_t)f;
@@ -208,7 +223,9 @@ __device__ __forceinline__ void apply_bc(const InstDev &I, const BufDev &b, cons
         xi[2] = uniform_pm1(c2[0], c2[1]);
       }
     }
-    for (int a = 0; a < I.dim; ++a) m.v[a][i] = dadd(dmul(U, b.frame[a]), dmul(dmul(b.noise, U), xi[a]));
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a < I.dim) m.v[a][i] = dadd(dmul(U, b.frame[a]), dmul(dmul(b.noise, U), xi[a]));
   } else {
     m.p[i] = b.p_ob;
     m.rho[i] = b.rho_ob;
@@ -224,9 +241,15 @@ __device__ __forceinline__ void apply_bc(const InstDev &I, const BufDev &b, cons
 // host-side launch wrappers implemented in the .cu files
 // ------------------------------------------------------------------------
 struct SortTemp {
-  uint32_t *hist;  // [256 * max_blocks]
+  uint32_t *hist;  // radix_hist_words(max_count, bits) words
   int max_blocks;
 };
+
+// passes and histogram words (digit histogram + scan chunk totals) of a sort
+// of up to max_count keys of the given bit length
+int radix_passes(int bits);
+size_t radix_hist_words(int max_count, int bits);
+constexpr int kSortKernelsPerPass = 4;
 
 // radix sort of (keys, vals) over *d_count entries (device count); bits of
 // key to sort; results in keys_out / vals_out.  Uses keys_tmp/vals_tmp.
@@ -262,11 +285,22 @@ void launch_buffer_update(const TopoArgs &a, int max_n, cudaStream_t st);
 void launch_keys(const TopoArgs &a, int max_n, int all_live, cudaStream_t st);
 void launch_iota(uint32_t *idx, int max_n, cudaStream_t st);
 
+// Neighbour list of the frozen configuration (rebuilt every advection
+// step): entry k of particle i at nbr[k * stride + i], the n_real[i] real
+// neighbours first, then n_wall[i] wall dummies.
+struct NbrList {
+  uint32_t *nbr;
+  uint16_t *n_real, *n_wall;
+  int32_t stride;  // particle capacity
+  int32_t kmax;    // entries per particle
+};
+
 struct SweepArgs {
   const InstDev *inst;
   const BufDev *buf;
   Masters m;
   Derived der;
+  NbrList nl;
   const uint32_t *keys;  // sorted cell keys of the live particles
   const uint32_t *off;   // cell offsets
   const uint32_t *woff;  // wall cell offsets
@@ -274,10 +308,11 @@ struct SweepArgs {
   int32_t *status;
   int64_t step;
   int32_t sub;
-  int32_t last_sub;  // n_ac_max - 1
+  int32_t any_periodic;  // some instance has a periodic axis
 };
 
 // sweeps: prec 0 -> double packs, 1 -> float packs; dim 2 / 3
+void launch_neighbour_list(const SweepArgs &a, void *packs, int prec, int dim, int max_n, cudaStream_t st);
 void launch_advection_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n,
                             cudaStream_t st);
 void launch_momentum_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n, int sub,

@@ -12,7 +12,7 @@
 // Limits and sharing:
 //  * at most SPH_NOALLOC_MAX_POINTS points per call (larger n is rejected
 //    with SPH_ERR_ARG);
-//  * the array (about 8.4 MB) exists on every GPU that loads the library,
+//  * the array (about 9.4 MB) exists on every GPU that loads the library,
 //    for the life of the process;
 //  * every call on a device uses the same array and leaves its contents
 //    behind; everything a call reads is written earlier in the same call,
@@ -33,11 +33,14 @@ constexpr int kMaxPoints = SPH_NOALLOC_MAX_POINTS;
 constexpr int kTile = 2048;  // radix tile of sph_sort.cu
 constexpr int kMaxBlocks = (kMaxPoints + kTile - 1) / kTile;
 
-// keys[2][max], vals[2][max], histogram[256][blocks], counters
+// digit histograms of up to 10-bit digits plus their scan chunk totals
+constexpr int kHistWords = (1 << 10) * kMaxBlocks + ((1 << 10) * kMaxBlocks + 2047) / 2048 + 1;
+
+// keys[2][max], vals[2][max], histogram, counters
 struct Scratch {
   uint32_t keys[2][kMaxPoints];
   uint32_t vals[2][kMaxPoints];
-  uint32_t hist[256 * kMaxBlocks];
+  uint32_t hist[kHistWords];
   int32_t count;
   int32_t nlive;
 };
@@ -127,7 +130,6 @@ extern "C" int sph_cell_sort_noalloc(const sph_config *cfg, const double *pos, i
   k_noalloc_keys<<<blocks, 256, 0, st>>>(pos, n, g, s);
   int bits = 1;
   while ((1ll << bits) <= ncell) ++bits;
-  bits = ((bits + 7) / 8) * 8;
   sphk::SortTemp tmp{s->hist, kMaxBlocks};
   uint32_t *kr = nullptr, *vr = nullptr;
   sphk::radix_sort(s->keys[0], s->vals[0], s->keys[1], s->vals[1], &s->count, n > 0 ? n : 1, bits, tmp, st, &kr,

@@ -2,15 +2,21 @@
 // cell offsets of the cell-linked list (Sec. 2.4.1: the list is rebuilt
 // after deletion every advection step, Sec. 2.4.3).
 //
-// One pass per 8-bit digit, three kernels per pass:
-//   upsweep   : per-tile digit histogram (shared-memory atomics)
-//   scan      : exclusive scan of the [digit][tile] histogram (one block)
-//   downsweep : stable rank of every element inside its tile -- warps walk
-//               their 256 consecutive elements in 8 rounds of 32, peers of
-//               a digit are found with __match_any_sync, per-warp digit
-//               counters make the rank stable -- then scatter.
-// The element count lives in device memory, so the whole step can be
-// enqueued without a host round trip; tiles past the count exit.
+// Digit width RB (8..10 bits) is chosen from the key length so that keys of
+// up to 20 bits sort in two passes.  Per pass:
+//   upsweep   : per-tile digit histogram (shared-memory atomics), laid out
+//               [digit][tile] so that one exclusive scan yields every
+//               (digit, tile) output offset;
+//   scan      : the [digit][tile] array is scanned in chunks of 2048 by many
+//               blocks (local exclusive scans + chunk totals), the chunk
+//               totals by one block; the chunk offset is added in the
+//               downsweep;
+//   downsweep : stable rank of every element inside its tile -- each warp
+//               walks 256 consecutive elements in 8 rounds of 32, peers of a
+//               digit are found with __match_any_sync, per-warp digit
+//               counters keep the rank stable -- then scatter.
+// Element counts live in device memory so the whole step is enqueued without
+// a host round trip; tiles past the count exit.
 #include "sph_internal.cuh"
 
 namespace sphk {
@@ -19,15 +25,18 @@ constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ROUNDS = 8;
 constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;  // 2048
-constexpr int RADIX = 256;
+constexpr int SC_THREADS = 1024;
+constexpr int SC_CHUNK = 2 * SC_THREADS;  // scan chunk
 
+template <int RB>
 __global__ void __launch_bounds__(RS_THREADS) rs_upsweep(const uint32_t *__restrict__ keys,
                                                          const int32_t *__restrict__ d_count, int shift,
                                                          uint32_t *__restrict__ hist, int nblocks) {
+  constexpr int RADIX = 1 << RB;
   __shared__ uint32_t cnt[RADIX];
   const int n = *d_count;
   const int base = blockIdx.x * RS_TILE;
-  cnt[threadIdx.x] = 0;
+  for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) cnt[d] = 0;
   __syncthreads();
   if (base < n) {
 #pragma unroll
@@ -37,49 +46,75 @@ __global__ void __launch_bounds__(RS_THREADS) rs_upsweep(const uint32_t *__restr
     }
   }
   __syncthreads();
-  hist[threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+  for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) hist[d * nblocks + blockIdx.x] = cnt[d];
 }
 
-// exclusive scan of hist[0 .. total) in place, one block of 1024 threads
-__global__ void __launch_bounds__(1024) rs_scan(uint32_t *__restrict__ hist, int total) {
-  __shared__ uint32_t warp_sums[32];
+// block-wide exclusive scan of one value per thread (1024 threads)
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_sums, uint32_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t s = warp_sums[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    warp_sums[lane] = s;  // inclusive
+  }
+  __syncthreads();
+  uint32_t excl = (warp > 0 ? warp_sums[warp - 1] : 0u) + x - v;
+  if (total) *total = warp_sums[31];
+  return excl;
+}
+
+// local exclusive scan of each chunk of SC_CHUNK entries; chunk totals out
+__global__ void __launch_bounds__(SC_THREADS) rs_scan_local(uint32_t *__restrict__ hist, int total,
+                                                            uint32_t *__restrict__ chunk_sum) {
+  __shared__ uint32_t ws[32];
+  const int base = blockIdx.x * SC_CHUNK;
+  const int i0 = base + 2 * threadIdx.x;
+  uint32_t a = i0 < total ? hist[i0] : 0u;
+  uint32_t b = i0 + 1 < total ? hist[i0 + 1] : 0u;
+  uint32_t tot = 0;
+  uint32_t ex = block_exclusive_scan(a + b, ws, &tot);
+  if (i0 < total) hist[i0] = ex;
+  if (i0 + 1 < total) hist[i0 + 1] = ex + a;
+  if (threadIdx.x == 0) chunk_sum[blockIdx.x] = tot;
+}
+
+// exclusive scan of the chunk totals (any count), one block
+__global__ void __launch_bounds__(SC_THREADS) rs_scan_chunks(uint32_t *__restrict__ chunk_sum, int nchunks) {
+  __shared__ uint32_t ws[32];
   __shared__ uint32_t carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int base = 0; base < total; base += 1024) {
+  for (int base = 0; base < nchunks; base += SC_THREADS) {
     int i = base + threadIdx.x;
-    uint32_t v = i < total ? hist[i] : 0u;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[warp] = x;
+    uint32_t v = i < nchunks ? chunk_sum[i] : 0u;
+    uint32_t tot = 0;
+    uint32_t ex = block_exclusive_scan(v, ws, &tot);
+    uint32_t c = carry;
+    if (i < nchunks) chunk_sum[i] = c + ex;
     __syncthreads();
-    if (warp == 0) {
-      uint32_t s = warp_sums[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-        if (lane >= o) s += y;
-      }
-      warp_sums[lane] = s;  // inclusive
-    }
-    __syncthreads();
-    uint32_t excl = carry + (warp > 0 ? warp_sums[warp - 1] : 0u) + x - v;
-    if (i < total) hist[i] = excl;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry = excl + v;
+    if (threadIdx.x == 0) carry = c + tot;
     __syncthreads();
   }
 }
 
+template <int RB>
 __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const int32_t *__restrict__ d_count,
-    int shift, const uint32_t *__restrict__ hist, int nblocks) {
+    int shift, const uint32_t *__restrict__ hist, const uint32_t *__restrict__ chunk_off, int nblocks) {
+  constexpr int RADIX = 1 << RB;
   __shared__ uint32_t wh[RS_WARPS][RADIX];
   const int n = *d_count;
   const int base = blockIdx.x * RS_TILE;
@@ -105,7 +140,6 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(
     __syncwarp();
   }
   __syncthreads();
-  // per digit, exclusive prefix over warps
   for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) {
     uint32_t run = 0;
 #pragma unroll
@@ -121,27 +155,71 @@ __global__ void __launch_bounds__(RS_THREADS) rs_downsweep(
     int i = base + warp * (RS_ROUNDS * 32) + r * 32 + lane;
     if (i < n) {
       uint32_t d = (key[r] >> shift) & (RADIX - 1);
-      uint32_t pos = hist[d * nblocks + blockIdx.x] + wh[warp][d] + rank[r];
+      uint32_t h = d * nblocks + blockIdx.x;
+      uint32_t pos = hist[h] + chunk_off[h / SC_CHUNK] + wh[warp][d] + rank[r];
       keys_out[pos] = key[r];
       vals_out[pos] = val[r];
     }
   }
 }
 
-void radix_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
-                const int32_t *d_count, int max_count, int bits, const SortTemp &tmp, cudaStream_t st,
-                uint32_t **keys_result, uint32_t **vals_result) {
-  int nblocks = (max_count + RS_TILE - 1) / RS_TILE;
+static int digit_bits(int bits, int *passes) {
+  int p = (bits + 9) / 10;  // passes of at most 10 bits
+  if (p < 1) p = 1;
+  int rb = (bits + p - 1) / p;
+  if (rb < 8) rb = 8;
+  *passes = p;
+  return rb;
+}
+
+int radix_passes(int bits) {
+  int p;
+  digit_bits(bits, &p);
+  return p;
+}
+
+size_t radix_hist_words(int max_count, int bits) {
+  int p;
+  int rb = digit_bits(bits, &p);
+  size_t nblocks = (size_t)((max_count + RS_TILE - 1) / RS_TILE);
   if (nblocks < 1) nblocks = 1;
-  uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
-  for (int shift = 0; shift < bits; shift += 8) {
-    rs_upsweep<<<nblocks, RS_THREADS, 0, st>>>(ki, d_count, shift, tmp.hist, nblocks);
-    rs_scan<<<1, 1024, 0, st>>>(tmp.hist, RADIX * nblocks);
-    rs_downsweep<<<nblocks, RS_THREADS, 0, st>>>(ki, vi, ko, vo, d_count, shift, tmp.hist, nblocks);
+  size_t total = ((size_t)1 << rb) * nblocks;
+  size_t nchunks = (total + SC_CHUNK - 1) / SC_CHUNK;
+  return total + nchunks;
+}
+
+template <int RB>
+static void sort_passes(uint32_t *&ki, uint32_t *&vi, uint32_t *&ko, uint32_t *&vo, const int32_t *d_count,
+                        int nblocks, int passes, const SortTemp &tmp, cudaStream_t st) {
+  const int total = (1 << RB) * nblocks;
+  const int nchunks = (total + SC_CHUNK - 1) / SC_CHUNK;
+  uint32_t *hist = tmp.hist, *chunks = tmp.hist + total;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = p * RB;
+    rs_upsweep<RB><<<nblocks, RS_THREADS, 0, st>>>(ki, d_count, shift, hist, nblocks);
+    rs_scan_local<<<nchunks, SC_THREADS, 0, st>>>(hist, total, chunks);
+    rs_scan_chunks<<<1, SC_THREADS, 0, st>>>(chunks, nchunks);
+    rs_downsweep<RB><<<nblocks, RS_THREADS, 0, st>>>(ki, vi, ko, vo, d_count, shift, hist, chunks, nblocks);
     uint32_t *t;
     t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
   }
+}
+
+void radix_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, const int32_t *d_count,
+                int max_count, int bits, const SortTemp &tmp, cudaStream_t st, uint32_t **keys_result,
+                uint32_t **vals_result) {
+  int nblocks = (max_count + RS_TILE - 1) / RS_TILE;
+  if (nblocks < 1) nblocks = 1;
+  int passes;
+  const int rb = digit_bits(bits, &passes);
+  uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
+  if (rb <= 8)
+    sort_passes<8>(ki, vi, ko, vo, d_count, nblocks, passes, tmp, st);
+  else if (rb == 9)
+    sort_passes<9>(ki, vi, ko, vo, d_count, nblocks, passes, tmp, st);
+  else
+    sort_passes<10>(ki, vi, ko, vo, d_count, nblocks, passes, tmp, st);
   *keys_result = ki;
   *vals_result = vi;
 }
@@ -164,8 +242,8 @@ __global__ void k_cell_offsets(const uint32_t *__restrict__ keys, const int32_t 
   if (c == ncell) *d_nlive = lo;
 }
 
-void cell_offsets(const uint32_t *keys, const int32_t *d_count, uint32_t ncell, uint32_t *off,
-                  int32_t *d_nlive, cudaStream_t st) {
+void cell_offsets(const uint32_t *keys, const int32_t *d_count, uint32_t ncell, uint32_t *off, int32_t *d_nlive,
+                  cudaStream_t st) {
   uint32_t n = ncell + 1;
   k_cell_offsets<<<(n + 255) / 256, 256, 0, st>>>(keys, d_count, ncell, off, d_nlive);
 }

@@ -12,13 +12,26 @@
 //         density half update, buffer boundary values (a11) and the first
 //         half of the next sub-step.
 //
-// One thread per particle in cell order; the neighbours of a particle are
-// the particles of the 3^d cells around its cell, and because particles
-// are sorted by cell key the cells of one row form one contiguous index
-// range, so a 2D sweep walks three ranges (nine in 3D) of the packs.
-// Neighbouring threads read overlapping ranges, which L1/L2 serve.
-// R is the sweep precision (float or double); every accumulation that ends
-// in a master field is converted to FP64 in the epilogue.
+//  k_list (once per advection step, first): the neighbour list of the
+//         frozen configuration (the dual-criteria scheme of Sec. 2.3 keeps
+//         the configuration of an advection step), read by all the sweeps.
+//
+// Work mapping: one thread per particle in cell order, grid-stride over a
+// grid sized to the resident blocks of the GPU (so a sub-step that no
+// instance takes costs one pass over ~1k blocks).  The list builder visits
+// the 3^d cells around a particle's cell; because particles are sorted by
+// cell key the cells of one row form one contiguous index range.  Candidates
+// are fetched four at a time (independent loads in flight) and tested
+// against the cut-off.  The sweeps then walk the list (entry k of particle
+// i at k * stride + i, so a warp's reads of one k are coalesced), without
+// any candidate tests.
+//
+// Precision: R is the sweep precision.  Pair sums, forces, k-epsilon sources,
+// volumes and pressures are evaluated in R; FP64 is used only to update the
+// FP64 master state (x, v, rho, k, eps) and to invert B.  On GB300 FP64
+// issues at a small fraction of the FP32 rate, so with R = float the FP64
+// work per particle is a few fused multiply-adds and divisions are the fast
+// reciprocal form.  With R = double every operation is FP64 and IEEE.
 #include "sph_internal.cuh"
 
 namespace sphk {
@@ -30,12 +43,16 @@ struct Ex<double> {
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ void len(double rr, double &r) { r = sqrt(rr); }
 };
 template <>
 struct Ex<float> {
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ void len(float rr, float &r) { r = rr * rsqrtf(rr); }
 };
 
 // per-thread copy of the instance geometry in sweep precision
@@ -43,7 +60,7 @@ template <typename R>
 struct Geo {
   R L[3];
   int per[3];
-  R cut2, inv_h, alpha_h, reg;
+  R cut2, inv_h, c5, reg;
 };
 
 template <typename R, int D>
@@ -54,22 +71,22 @@ __device__ __forceinline__ Geo<R> make_geo(const InstDev &I) {
     g.per[a] = (a < D) ? I.periodic[a] : 0;
   }
   g.cut2 = (R)I.cut2;
-  g.inv_h = (R)(1.0 / I.h);
-  g.alpha_h = (R)I.alpha_h;
+  g.inv_h = (R)I.inv_h;
+  g.c5 = (R)(-5.0) * (R)I.alpha_h * (R)I.inv_h;
   g.reg = (R)I.reg;
   return g;
 }
 
-// r_ij = x_i - x_j with the minimum image; returns |r_ij|^2 summed left to
-// right without contraction (the cut-off test decides membership)
-template <typename R, int D>
+// r_ij = x_i - x_j (minimum image when PER); returns |r_ij|^2 summed left
+// to right without contraction (the cut-off test decides membership)
+template <typename R, int D, bool PER>
 __device__ __forceinline__ R pair_vec(const Geo<R> &g, const V4<R> &pi, const V4<R> &pj, R d[3]) {
   R xi[3] = {pi.x, pi.y, pi.z}, xj[3] = {pj.x, pj.y, pj.z};
   R rr = (R)0;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     R v = Ex<R>::sub(xi[a], xj[a]);
-    if (g.per[a]) {
+    if (PER && g.per[a]) {
       R h = (R)0.5 * g.L[a];
       if (v > h)
         v = Ex<R>::sub(v, g.L[a]);
@@ -83,12 +100,12 @@ __device__ __forceinline__ R pair_vec(const Geo<R> &g, const V4<R> &pi, const V4
   return rr;
 }
 
-// Wendland C2 derivative dW/dr (Sec. 2.2 kernel, support 2h)
+// Wendland C2 (Sec. 2.2 kernel, support 2h): F = (dW/dr) / r
+// = -5 (alpha / h^2) (1 - q/2)^3, evaluated without a division
 template <typename R>
-__device__ __forceinline__ R kernel_dW(const Geo<R> &g, R r) {
-  R q = r * g.inv_h;
-  R w = (R)1 - (R)0.5 * q;
-  return g.alpha_h * ((R)-5 * q) * w * w * w;
+__device__ __forceinline__ R kernel_F(const Geo<R> &g, R r) {
+  R w = (R)1 - (R)0.5 * (r * g.inv_h);
+  return g.c5 * w * w * w;
 }
 
 // buffer-frame coordinate 0 of a point, in sweep precision, plain order
@@ -100,53 +117,76 @@ __device__ __forceinline__ R local0(const R o[3], const R n[3], R x, R y, R z) {
   return s;
 }
 
-// distinct cell coordinates c-span..c+span along one axis (wrapped when
-// periodic, dropped when outside a non-periodic grid)
-__device__ __forceinline__ int axis_list(int c, int span, int n, int per, int out[5]) {
-  int cnt = 0;
-  for (int cc = c - span; cc <= c + span; ++cc) {
-    int w = cc;
-    if (cc < 0 || cc >= n) {
-      if (!per) continue;
-      w = ((cc % n) + n) % n;
-    }
-    bool dup = false;
-    for (int t = 0; t < cnt; ++t) dup |= (out[t] == w);
-    if (!dup) out[cnt++] = w;
-  }
-  return cnt;
-}
-
-// visit the index ranges of the cells within +-span of (cx, cy, cz); the
-// clamped part of each x row is one contiguous range, wrapped x cells are
-// extra single-cell ranges
-template <int D, typename F>
+// visit the index ranges of the cells within +-span of (cx, cy, cz): the
+// clamped part of each x row is one contiguous range; periodic axes hold at
+// least 2 span + 1 cells (checked at creation), so wrapped coordinates are
+// distinct and the wrapped x cells of a row form at most two more ranges.
+// f has one call site so that it stays inlined.
+template <int D, bool PER, typename F>
 __device__ __forceinline__ void visit_cells(const InstDev &I, int cx, int cy, int cz, int span,
                                             const uint32_t *__restrict__ off, F &&f) {
   const int nx = I.nc[0], ny = I.nc[1];
-  int ys[5], zs[5];
-  const int nys = axis_list(cy, span, ny, I.periodic[1], ys);
-  int nzs = 1;
-  zs[0] = 0;
-  if (D == 3) nzs = axis_list(cz, span, I.nc[2], I.periodic[2], zs);
+  const int nz = (D == 3) ? I.nc[2] : 1;
+  const int zspan = (D == 3) ? span : 0;
   const int a0 = max(cx - span, 0), a1 = min(cx + span, nx - 1);
-  int xw[4], nxw = 0;
-  if (I.periodic[0]) {
-    for (int xx = cx - span; xx <= cx + span; ++xx) {
-      if (xx >= 0 && xx < nx) continue;
-      int w = ((xx % nx) + nx) % nx;
-      if (w >= a0 && w <= a1) continue;
-      bool dup = false;
-      for (int t = 0; t < nxw; ++t) dup |= (xw[t] == w);
-      if (!dup && nxw < 4) xw[nxw++] = w;
+  const int nparts = (PER && I.periodic[0]) ? 3 : 1;
+  for (int dz = -zspan; dz <= zspan; ++dz) {
+    int zz = cz + dz;
+    if (zz < 0 || zz >= nz) {
+      if (!PER || D != 3 || !I.periodic[2]) continue;
+      zz = zz < 0 ? zz + nz : zz - nz;
+    }
+    for (int dy = -span; dy <= span; ++dy) {
+      int yy = cy + dy;
+      if (yy < 0 || yy >= ny) {
+        if (!PER || !I.periodic[1]) continue;
+        yy = yy < 0 ? yy + ny : yy - ny;
+      }
+      const uint32_t row = I.cell_base + ((uint32_t)zz * (uint32_t)ny + (uint32_t)yy) * (uint32_t)nx;
+      for (int part = 0; part < nparts; ++part) {
+        int c0 = a0, c1 = a1;
+        if (part == 1) {  // cells wrapped from the left edge
+          if (cx - span >= 0) continue;
+          c0 = cx - span + nx;
+          c1 = nx - 1;
+        } else if (part == 2) {  // cells wrapped from the right edge
+          if (cx + span < nx) continue;
+          c0 = 0;
+          c1 = cx + span - nx;
+        }
+        f(off[row + c0], off[row + c1 + 1]);
+      }
     }
   }
-  for (int zi = 0; zi < nzs; ++zi)
-    for (int yi = 0; yi < nys; ++yi) {
-      const uint32_t row = I.cell_base + ((uint32_t)zs[zi] * (uint32_t)ny + (uint32_t)ys[yi]) * (uint32_t)nx;
-      f(off[row + a0], off[row + a1 + 1]);
-      for (int t = 0; t < nxw; ++t) f(off[row + xw[t]], off[row + xw[t] + 1]);
+}
+
+// candidates j in [jb, je) of records P, four loads in flight; hit(j, Pj)
+// is called for every j with 0 < |r_ij|^2 < (2h)^2
+template <typename R, int D, bool PER, typename H>
+__device__ __forceinline__ void scan_range(const Geo<R> &g, const V4<R> &Pi, const V4<R> *__restrict__ P,
+                                           uint32_t jb, uint32_t je, H &&hit) {
+  for (uint32_t j = jb; j < je; j += 4) {
+    V4<R> q0 = P[j];
+    V4<R> q1 = (j + 1 < je) ? P[j + 1] : q0;
+    V4<R> q2 = (j + 2 < je) ? P[j + 2] : q0;
+    V4<R> q3 = (j + 3 < je) ? P[j + 3] : q0;
+    R d[3];
+    unsigned mask = 0;
+    R rr = pair_vec<R, D, PER>(g, Pi, q0, d);
+    mask |= (rr > (R)0 && rr < g.cut2) ? 1u : 0u;
+    rr = pair_vec<R, D, PER>(g, Pi, q1, d);
+    mask |= (j + 1 < je && rr > (R)0 && rr < g.cut2) ? 2u : 0u;
+    rr = pair_vec<R, D, PER>(g, Pi, q2, d);
+    mask |= (j + 2 < je && rr > (R)0 && rr < g.cut2) ? 4u : 0u;
+    rr = pair_vec<R, D, PER>(g, Pi, q3, d);
+    mask |= (j + 3 < je && rr > (R)0 && rr < g.cut2) ? 8u : 0u;
+    while (mask) {
+      const int k = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const V4<R> q = (k == 0) ? q0 : (k == 1) ? q1 : (k == 2) ? q2 : q3;
+      hit(j + (uint32_t)k, q);
     }
+  }
 }
 
 __device__ __forceinline__ void decode_cell(const InstDev &I, uint32_t key, int &cx, int &cy, int &cz) {
@@ -159,16 +199,15 @@ __device__ __forceinline__ void decode_cell(const InstDev &I, uint32_t key, int 
 
 // symmetric 3x3 stored as (xx, yy, zz, xy, xz, yz)
 template <typename R, int D>
-__device__ __forceinline__ void sym_add_outer(R A[6], const R d[3], const R gw[3], R V) {
-  // A += -d (x) gw V; the product is symmetric in exact arithmetic, the
-  // upper triangle is accumulated
-  A[0] += -d[0] * gw[0] * V;
-  A[1] += -d[1] * gw[1] * V;
-  A[3] += -d[0] * gw[1] * V;
+__device__ __forceinline__ void sym_add_outer(R A[6], const R d[3], R s) {
+  // A += s d (x) d; with s = -F V this is -r_ij (x) grad W V
+  A[0] += s * d[0] * d[0];
+  A[1] += s * d[1] * d[1];
+  A[3] += s * d[0] * d[1];
   if (D == 3) {
-    A[2] += -d[2] * gw[2] * V;
-    A[4] += -d[0] * gw[2] * V;
-    A[5] += -d[1] * gw[2] * V;
+    A[2] += s * d[2] * d[2];
+    A[4] += s * d[0] * d[2];
+    A[5] += s * d[1] * d[2];
   }
 }
 
@@ -183,26 +222,28 @@ __device__ __forceinline__ void invert_guarded(const double A[6], double B[6]) {
       B[0] = B[1] = 1.0;
       return;
     }
-    B[0] = A[1] / det;
-    B[1] = A[0] / det;
-    B[3] = -A[3] / det;
+    double inv = 1.0 / det;
+    B[0] = A[1] * inv;
+    B[1] = A[0] * inv;
+    B[3] = -A[3] * inv;
   } else {
     const double xx = A[0], yy = A[1], zz = A[2], xy = A[3], xz = A[4], yz = A[5];
     double c00 = yy * zz - yz * yz;
     double c01 = yz * xz - xy * zz;
     double c02 = xy * yz - yy * xz;
     double det = xx * c00 + xy * c01 + xz * c02;
-    double t = (xx + yy + zz) / 3.0;
+    double t = (xx + yy + zz) * (1.0 / 3.0);
     if (!(det > 1e-3 * t * t * t)) {
       B[0] = B[1] = B[2] = 1.0;
       return;
     }
-    B[0] = c00 / det;
-    B[1] = (xx * zz - xz * xz) / det;
-    B[2] = (xx * yy - xy * xy) / det;
-    B[3] = c01 / det;
-    B[4] = c02 / det;
-    B[5] = (xz * xy - xx * yz) / det;
+    double inv = 1.0 / det;
+    B[0] = c00 * inv;
+    B[1] = (xx * zz - xz * xz) * inv;
+    B[2] = (xx * yy - xy * xy) * inv;
+    B[3] = c01 * inv;
+    B[4] = c02 * inv;
+    B[5] = (xz * xy - xx * yz) * inv;
   }
 }
 
@@ -219,27 +260,106 @@ __device__ __forceinline__ void sym_matvec(const R B[6], const R x[3], R y[3]) {
   }
 }
 
+// own B_i in sweep precision from the neighbour-facing pack; particles of
+// pressure buffers carry a marker there and read their FP64 master instead.
+// kw returns 2/3 k_i (RANS effective pressure).
+template <typename R, int D>
+__device__ __forceinline__ void own_B(const Packs<R> &pk, const Derived &der, int i, R B[6], R &kw) {
+  const V4<R> b0 = pk.Bm0[i];
+  kw = b0.w;
+  if (b0.x < (R)0) {
+    for (int c = 0; c < 6; ++c) B[c] = (R)der.B[c][i];
+    if (D == 2) B[2] = B[4] = B[5] = (R)0;
+    return;
+  }
+  if (D == 2) {
+    B[0] = b0.x;
+    B[3] = b0.y;
+    B[1] = b0.z;
+    B[2] = B[4] = B[5] = (R)0;
+  } else {
+    const V4<R> b1 = pk.Bm1[i];
+    B[0] = b0.x;
+    B[1] = b0.y;
+    B[2] = b0.z;
+    B[3] = b1.x;
+    B[4] = b1.y;
+    B[5] = b1.z;
+  }
+}
+
+// effective pressure p + 2/3 rho k (Table 1) with rho = rho0 + p / c0^2,
+// the stiff EOS of Sec. 2.1 solved for the density
+template <typename R>
+__device__ __forceinline__ R p_eff(R p, R kw, R rho0, R inv_c0sq) {
+  return p + kw * (rho0 + p * inv_c0sq);
+}
+
+// =========================================================================
+// neighbour list of the frozen configuration (once per advection step)
+// =========================================================================
+template <typename R, int D, bool PER>
+__device__ __forceinline__ void list_one(const SweepArgs &a, const Packs<R> &pk, const int i) {
+  const InstDev &I = a.inst[a.m.inst[i]];
+  const Geo<R> g = make_geo<R, D>(I);
+  int cx, cy, cz;
+  decode_cell(I, a.keys[i], cx, cy, cz);
+  const V4<R> Pi = pk.P[0][i];
+  uint32_t *__restrict__ out = a.nl.nbr + i;
+  const size_t LS = (size_t)a.nl.stride;
+  const int K = a.nl.kmax;
+  int nr = 0, nw = 0;
+  // real neighbours, then wall dummies; 0 < |r|^2 < (2h)^2 excludes i itself
+  for (int set = 0; set < 2; ++set) {
+    const uint32_t *offs = set == 0 ? a.off : a.woff;
+    const V4<R> *recs = set == 0 ? pk.P[0] : pk.WP;
+    visit_cells<D, PER>(I, cx, cy, cz, 1, offs, [&](uint32_t jb, uint32_t je) {
+      scan_range<R, D, PER>(g, Pi, recs, jb, je, [&](uint32_t j, const V4<R> &) {
+        const int k = nr + nw;
+        if (k < K) out[(size_t)k * LS] = j;
+        if (set == 0)
+          ++nr;
+        else
+          ++nw;
+      });
+    });
+  }
+  if (nr + nw > K) {  // more neighbours than the list holds
+    set_status(a.status, SPH_ERR_CAPACITY);
+    nr = nr < K ? nr : K;
+    nw = K - nr < nw ? K - nr : nw;
+  }
+  a.nl.n_real[i] = (uint16_t)nr;
+  a.nl.n_wall[i] = (uint16_t)nw;
+}
+
 // =========================================================================
 // advection sweep: B (+ mirror), viscous acceleration, k-epsilon, half 1
 // =========================================================================
-template <typename R, int D>
-__global__ void __launch_bounds__(kBlock) k_adv(SweepArgs a, Packs<R> pk) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.cnt->n_live) return;
-  const Masters m = a.m;
+template <typename R, int D, bool PER>
+__device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, const int i) {
+  const Masters &m = a.m;
   const int ii = m.inst[i];
   const InstDev &I = a.inst[ii];
   const Geo<R> g = make_geo<R, D>(I);
   int cx, cy, cz;
   decode_cell(I, a.keys[i], cx, cy, cz);
+  const uint32_t *__restrict__ Lst = a.nl.nbr + i;
+  const size_t LS = (size_t)a.nl.stride;
+  const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
   const V4<R> Pi = pk.P[0][i];
   const V4<R> Qi = pk.Q[0][i];
   const bool rans = I.rans != 0;
   const R rho0 = (R)I.rho0, nu_l = (R)I.nu_l, c0 = (R)I.c0, eta = (R)I.eta, muRk = (R)I.muR_k;
-  const R nut_i = rans ? (R)m.nut[i] : (R)0;
-  const R k_i = rans ? (R)m.k[i] : (R)0, e_i = rans ? (R)m.eps[i] : (R)0;
+  R nut_i = (R)0, k_i = (R)0, e_i = (R)0;
+  if (rans) {
+    const V4<R> Ti = pk.T[i];
+    k_i = Ti.x;
+    e_i = Ti.y;
+    nut_i = Ti.z;
+  }
   const R mu_i = rho0 * (nu_l + nut_i);
-  const R Dk_i = nu_l + nut_i / (R)kSigK, De_i = nu_l + nut_i / (R)kSigE;
+  const R Dk_i = nu_l + nut_i * (R)(1.0 / kSigK), De_i = nu_l + nut_i * (R)(1.0 / kSigE);
 
   const int lab = m.label[i];
   const BufDev *mb = (lab > 0 && lab <= I.nbuf) ? &a.buf[I.buf0 + lab - 1] : nullptr;
@@ -256,91 +376,83 @@ __global__ void __launch_bounds__(kBlock) k_adv(SweepArgs a, Packs<R> pk) {
   R G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   R dk = 0, de = 0;
 
-  auto real_range = [&](uint32_t jb, uint32_t je) {
-    for (uint32_t j = jb; j < je; ++j) {
-      if ((int)j == i) continue;
+  // real neighbours
+  {
+#pragma unroll 4
+    for (int kk = 0; kk < nr; ++kk) {
+      const uint32_t j = Lst[(size_t)kk * LS];
       const V4<R> Pj = pk.P[0][j];
       R d[3];
-      const R rr = pair_vec<R, D>(g, Pi, Pj, d);
-      if (!(rr > (R)0 && rr < g.cut2)) continue;
-      const R r = sqrt(rr);
-      const R dw = kernel_dW(g, r);
-      const R inv_r = (R)1 / r;
-      R gw[3] = {dw * d[0] * inv_r, dw * d[1] * inv_r, dw * d[2] * inv_r};
+      const R rr = pair_vec<R, D, PER>(g, Pi, Pj, d);
+      R r;
+      Ex<R>::len(rr, r);
+      const R F = kernel_F(g, r);  // dW/dr / r
       const R V = Pj.w;
-      if (!mirror || !(local0<R, D>(mo, mn, Pj.x, Pj.y, Pj.z) < (R)0)) sym_add_outer<R, D>(A, d, gw, V);
+      if (!mirror || !(local0<R, D>(mo, mn, Pj.x, Pj.y, Pj.z) < (R)0)) sym_add_outer<R, D>(A, d, -F * V);
       const V4<R> Qj = pk.Q[0][j];
       R vij[3] = {Qi.x - Qj.x, Qi.y - Qj.y, Qi.z - Qj.z};
-      R nut_j = (R)0, k_j = (R)0, e_j = (R)0;
+      const R f = Ex<R>::div(F * r, r + g.reg) * V;  // dW/dr / (r + 0.01h) V
+      R mu_ad = mu_i;                                // laminar: harmonic mean of equal values
       if (rans) {
         const V4<R> Tj = pk.T[j];
-        k_j = Tj.x;
-        e_j = Tj.y;
-        nut_j = Tj.z;
-      }
-      const R mu_j = rho0 * (nu_l + nut_j);
-      const R mut = (R)2 * mu_i * mu_j / (mu_i + mu_j);
-      R mu_ad = mut;
-      if (rans) {
-        R ve = -(vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2]) * inv_r;
+        const R k_j = Tj.x, e_j = Tj.y, nut_j = Tj.z;
+        const R mu_j = rho0 * (nu_l + nut_j);
+        const R mut = Ex<R>::div((R)2 * mu_i * mu_j, mu_i + mu_j);
+        R ve = -(vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2]) * Ex<R>::div((R)1, r);
         R lim = eta * (ve > (R)0 ? ve : (R)0);
         R muR = muRk * (lim < c0 ? lim : c0);
         mu_ad = mut > muR ? mut : muR;
-      }
-      const R f = dw / (r + g.reg) * V;
-#pragma unroll
-      for (int c = 0; c < D; ++c) sv[c] += mu_ad * f * vij[c];
-      if (rans) {
+        const R FV = F * V;
 #pragma unroll
         for (int p = 0; p < D; ++p)
 #pragma unroll
-          for (int q = 0; q < D; ++q) G[p][q] += vij[p] * gw[q] * V;
-        const R Dk_j = nu_l + nut_j / (R)kSigK, De_j = nu_l + nut_j / (R)kSigE;
-        dk += rho0 * ((R)2 * Dk_i * Dk_j / (Dk_i + Dk_j)) * (k_i - k_j) * f;
-        de += rho0 * ((R)2 * De_i * De_j / (De_i + De_j)) * (e_i - e_j) * f;
+          for (int q = 0; q < D; ++q) G[p][q] += vij[p] * d[q] * FV;
+        const R Dk_j = nu_l + nut_j * (R)(1.0 / kSigK), De_j = nu_l + nut_j * (R)(1.0 / kSigE);
+        dk += rho0 * Ex<R>::div((R)2 * Dk_i * Dk_j, Dk_i + Dk_j) * (k_i - k_j) * f;
+        de += rho0 * Ex<R>::div((R)2 * De_i * De_j, De_i + De_j) * (e_i - e_j) * f;
       }
+#pragma unroll
+      for (int c = 0; c < D; ++c) sv[c] += mu_ad * f * vij[c];
     }
-  };
-  visit_cells<D>(I, cx, cy, cz, 1, a.off, real_range);
+  }
 
-  auto wall_range = [&](uint32_t jb, uint32_t je) {
-    for (uint32_t w = jb; w < je; ++w) {
+  // wall dummies
+  {
+#pragma unroll 4
+    for (int kk = nr; kk < nr + nw; ++kk) {
+      const uint32_t w = Lst[(size_t)kk * LS];
       const V4<R> Wp = pk.WP[w];
       R d[3];
-      const R rr = pair_vec<R, D>(g, Pi, Wp, d);
-      if (!(rr > (R)0 && rr < g.cut2)) continue;
-      const R r = sqrt(rr);
-      const R dw = kernel_dW(g, r);
-      const R inv_r = (R)1 / r;
-      R gw[3] = {dw * d[0] * inv_r, dw * d[1] * inv_r, dw * d[2] * inv_r};
+      const R rr = pair_vec<R, D, PER>(g, Pi, Wp, d);
+      R r;
+      Ex<R>::len(rr, r);
+      const R F = kernel_F(g, r);
       const R V = Wp.w;
-      if (!mirror || !(local0<R, D>(mo, mn, Wp.x, Wp.y, Wp.z) < (R)0)) sym_add_outer<R, D>(A, d, gw, V);
+      if (!mirror || !(local0<R, D>(mo, mn, Wp.x, Wp.y, Wp.z) < (R)0)) sym_add_outer<R, D>(A, d, -F * V);
       const V4<R> Wv = pk.WV[w];
       // no-slip: the dummy carries 2 v_wall - v_i
       R vij[3] = {(R)2 * (Qi.x - Wv.x), (R)2 * (Qi.y - Wv.y), (R)2 * (Qi.z - Wv.z)};
       R mu_ad = mu_i;
       if (rans) {
-        R ve = -(vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2]) * inv_r;
+        R ve = -(vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2]) * Ex<R>::div((R)1, r);
         R lim = eta * (ve > (R)0 ? ve : (R)0);
         R muR = muRk * (lim < c0 ? lim : c0);
         mu_ad = mu_i > muR ? mu_i : muR;
-      }
-      const R f = dw / (r + g.reg) * V;
-#pragma unroll
-      for (int c = 0; c < D; ++c) sv[c] += mu_ad * f * vij[c];
-      if (rans) {
+        const R FV = F * V;
 #pragma unroll
         for (int p = 0; p < D; ++p)
 #pragma unroll
-          for (int q = 0; q < D; ++q) G[p][q] += vij[p] * gw[q] * V;
+          for (int q = 0; q < D; ++q) G[p][q] += vij[p] * d[q] * FV;
       }
+      const R f = Ex<R>::div(F * r, r + g.reg) * V;
+#pragma unroll
+      for (int c = 0; c < D; ++c) sv[c] += mu_ad * f * vij[c];
     }
-  };
-  visit_cells<D>(I, cx, cy, cz, 1, a.woff, wall_range);
+  }
 
   if (mirror) {
     // images m_j = x_j - 2 x'_0(x_j) n_b of every particle on the fluid side
-    // of the open face; searched around the image of x_i (two-cell margin)
+    // of the open face, searched around the image of x_i (two-cell margin)
     const R si = local0<R, D>(mo, mn, Pi.x, Pi.y, Pi.z);
     const double q0 = (double)Pi.x - 2.0 * (double)si * mb->frame[0];
     const double q1 = (double)Pi.y - 2.0 * (double)si * mb->frame[1];
@@ -360,78 +472,102 @@ __global__ void __launch_bounds__(kBlock) k_adv(SweepArgs a, Packs<R> pk) {
         dd = (c == 0) ? Ex<R>::mul(d[c], d[c]) : Ex<R>::add(dd, Ex<R>::mul(d[c], d[c]));
       }
       if (!(dd > (R)0 && dd < g.cut2)) return;
-      const R r = sqrt(dd);
-      const R dw = kernel_dW(g, r);
-      const R inv_r = (R)1 / r;
-      R gw[3] = {dw * d[0] * inv_r, dw * d[1] * inv_r, dw * d[2] * inv_r};
-      sym_add_outer<R, D>(A, d, gw, Pj.w);
+      R r;
+      Ex<R>::len(dd, r);
+      sym_add_outer<R, D>(A, d, -kernel_F(g, r) * Pj.w);
     };
-    visit_cells<D>(I, qx, qy, qz, 2, a.off, [&](uint32_t jb, uint32_t je) {
-      for (uint32_t j = jb; j < je; ++j) mirror_one(pk.P[0][j]);
-    });
-    visit_cells<D>(I, qx, qy, qz, 2, a.woff, [&](uint32_t jb, uint32_t je) {
-      for (uint32_t w = jb; w < je; ++w) mirror_one(pk.WP[w]);
-    });
+    for (int set = 0; set < 2; ++set) {
+      const uint32_t *offs = set == 0 ? a.off : a.woff;
+      const V4<R> *recs = set == 0 ? pk.P[0] : pk.WP;
+      visit_cells<D, PER>(I, qx, qy, qz, 2, offs, [&](uint32_t jb, uint32_t je) {
+        for (uint32_t j = jb; j < je; ++j) mirror_one(recs[j]);
+      });
+    }
   }
 
-  // ---------------- epilogue (FP64) ----------------
+  // ---------------- epilogue ----------------
   double Ad[6], B[6];
   for (int c = 0; c < 6; ++c) Ad[c] = (double)A[c];
-  invert_guarded<D>(Ad, B);
-  for (int c = 0; c < 6; ++c) a.der.B[c][i] = B[c];
+  invert_guarded<D>(Ad, B);  // FP64 inversion (one reciprocal)
+  a.der.B[0][i] = B[0];
+  a.der.B[1][i] = B[1];
+  a.der.B[3][i] = B[3];
+  if (D == 3) {
+    a.der.B[2][i] = B[2];
+    a.der.B[4][i] = B[4];
+    a.der.B[5][i] = B[5];
+  }
+  R BR[6];
+  for (int c = 0; c < 6; ++c) BR[c] = (R)B[c];
   const double rho_i = m.rho[i], mass_i = m.mass[i];
-  for (int c = 0; c < 3; ++c) a.der.an[c][i] = (c < D) ? 2.0 * (double)sv[c] / rho_i : 0.0;
+  const R inv_rho = Ex<R>::div((R)1, (R)rho_i);
+  R an[3] = {0, 0, 0};
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    an[c] = (R)2 * sv[c] * inv_rho;
+    a.der.an[c][i] = (double)an[c];
+  }
+  V4<R> ap = {an[0] + (R)I.g[0], an[1] + (R)I.g[1], D == 3 ? an[2] + (R)I.g[2] : (R)0, (R)0};
+  pk.Ap[i] = ap;
 
-  double kap = 0.0;
+  R kw = (R)0;
   if (rans) {
     // grad v = -(sum v_ij (x) grad W V) B^T, (p, q) = dv_p / dx_q
-    double Bf[3][3] = {{B[0], B[3], B[4]}, {B[3], B[1], B[5]}, {B[4], B[5], B[2]}};
-    double gv[3][3];
+    R Bf[3][3] = {{BR[0], BR[3], BR[4]}, {BR[3], BR[1], BR[5]}, {BR[4], BR[5], BR[2]}};
+    R tr = 0, prod = 0;
+    R gv[3][3];
+#pragma unroll
     for (int p = 0; p < D; ++p)
+#pragma unroll
       for (int q = 0; q < D; ++q) {
-        double s = 0.0;
-        for (int c = 0; c < D; ++c) s += (double)G[p][c] * Bf[q][c];
+        R s = 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) s += G[p][c] * Bf[q][c];
         gv[p][q] = -s;
       }
-    double tr = 0.0, prod = 0.0;
+#pragma unroll
     for (int p = 0; p < D; ++p) {
       tr += gv[p][p];
+#pragma unroll
       for (int q = 0; q < D; ++q) prod += (gv[p][q] + gv[q][p]) * gv[p][q];
     }
-    const double kd = m.k[i], ed = m.eps[i], nutd = m.nut[i];
-    const double Gk = nutd * prod - (2.0 / 3.0) * kd * tr;
-    const double dkdt = Gk - ed + 2.0 * (double)dk / rho_i;
-    const double dedt = kC1 * (ed / kd) * Gk - kC2 * ed * ed / kd + 2.0 * (double)de / rho_i;
-    double k1 = kd + I.dt_ad * dkdt, e1 = ed + I.dt_ad * dedt;
+    const R inv_k = Ex<R>::div((R)1, k_i);
+    const R Gk = nut_i * prod - (R)(2.0 / 3.0) * k_i * tr;
+    const R dkdt = Gk - e_i + (R)2 * dk * inv_rho;
+    const R dedt = (R)kC1 * e_i * inv_k * Gk - (R)kC2 * e_i * e_i * inv_k + (R)2 * de * inv_rho;
+    double k1 = m.k[i] + I.dt_ad * (double)dkdt, e1 = m.eps[i] + I.dt_ad * (double)dedt;
     k1 = k1 > kFloor ? k1 : kFloor;
     e1 = e1 > kFloor ? e1 : kFloor;
     m.k[i] = k1;
     m.eps[i] = e1;
-    m.nut[i] = kCmu * k1 * k1 / e1;
-    kap = (2.0 / 3.0) * k1 * mass_i;
+    const R k1r = (R)k1, e1r = (R)e1;
+    m.nut[i] = (double)Ex<R>::div((R)kCmu * k1r * k1r, e1r);
+    kw = (R)(2.0 / 3.0) * k1r;
   }
   // neighbour-facing B pack; pressure-buffer particles are marked so that
   // neighbours use their own B_i (the condition B_k = B_i, Sec. 3.3)
   if (D == 2) {
-    V4<R> b0 = {(R)B[0], (R)B[3], (R)B[1], (R)kap};
+    V4<R> b0 = {BR[0], BR[3], BR[1], kw};
     if (mirror) b0.x = (R)-1;
     pk.Bm0[i] = b0;
   } else {
-    V4<R> b0 = {(R)B[0], (R)B[1], (R)B[2], (R)kap};
-    V4<R> b1 = {(R)B[3], (R)B[4], (R)B[5], (R)0};
+    V4<R> b0 = {BR[0], BR[1], BR[2], kw};
+    V4<R> b1 = {BR[3], BR[4], BR[5], (R)0};
     if (mirror) b0.x = (R)-1;
     pk.Bm0[i] = b0;
     pk.Bm1[i] = b1;
   }
-  // first half of sub-step 0 (a8)
-  const double dt = I.dt;
-  double rho = rho_i + 0.5 * dt * m.drho[i];
-  double p = I.eos_k * (rho / I.rho0 - 1.0);
+  // first half of sub-step 0 (a8): rho += dt/2 drho; p = c0^2 (rho - rho0);
+  // x += dt/2 v
+  const double hdt = 0.5 * I.dt;
+  const double rho = rho_i + hdt * m.drho[i];
+  const R p = (R)(rho - I.rho0) * (R)I.c0sq;
   m.rho[i] = rho;
-  m.p[i] = p;
-  for (int c = 0; c < D; ++c) m.x[c][i] = m.x[c][i] + 0.5 * dt * m.v[c][i];
-  V4<R> P1 = {Pi.x, Pi.y, Pi.z, (R)(mass_i / rho)};
-  V4<R> Q1 = {Qi.x, Qi.y, Qi.z, (R)p};
+  m.p[i] = (double)p;
+#pragma unroll
+  for (int c = 0; c < D; ++c) m.x[c][i] = m.x[c][i] + hdt * m.v[c][i];
+  V4<R> P1 = {Pi.x, Pi.y, Pi.z, Ex<R>::div((R)mass_i, (R)rho)};
+  V4<R> Q1 = {Qi.x, Qi.y, Qi.z, p};
   pk.P[1][i] = P1;
   pk.Q[1][i] = Q1;
 }
@@ -439,177 +575,183 @@ __global__ void __launch_bounds__(kBlock) k_adv(SweepArgs a, Packs<R> pk) {
 // =========================================================================
 // momentum sweep (a9)
 // =========================================================================
-template <typename R, int D>
-__global__ void __launch_bounds__(kBlock) k_mom(SweepArgs a, Packs<R> pk, int pin, int qin, int qout) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.cnt->n_live) return;
-  const Masters m = a.m;
+template <typename R, int D, bool PER>
+__device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, const V4<R> *__restrict__ P,
+                                        const V4<R> *__restrict__ Q, V4<R> *__restrict__ Qout, const int i) {
+  const Masters &m = a.m;
   const int ii = m.inst[i];
   const InstDev &I = a.inst[ii];
   if (a.sub >= I.n_ac) return;
   const Geo<R> g = make_geo<R, D>(I);
-  int cx, cy, cz;
-  decode_cell(I, a.keys[i], cx, cy, cz);
-  const V4<R> *__restrict__ P = pk.P[pin];
-  const V4<R> *__restrict__ Q = pk.Q[qin];
+  const uint32_t *__restrict__ Lst = a.nl.nbr + i;
+  const size_t LS = (size_t)a.nl.stride;
+  const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
   const V4<R> Pi = P[i];
   const R p_i = Q[i].w;
   const bool rans = I.rans != 0;
-  const double rho_i = m.rho[i];
-  double Bd[6];
-  for (int c = 0; c < 6; ++c) Bd[c] = a.der.B[c][i];
-  R Bi[6];
-  for (int c = 0; c < 6; ++c) Bi[c] = (R)Bd[c];
-  const R pe_i = rans ? p_i + (R)((2.0 / 3.0) * m.k[i] * m.mass[i]) / Pi.w : p_i;
+  const R rho0 = (R)I.rho0, inv_c0sq = (R)(1.0 / I.c0sq);
+  R Bi[6], kw_i;
+  own_B<R, D>(pk, a.der, i, Bi, kw_i);
+  const R pe_i = rans ? p_eff(p_i, kw_i, rho0, inv_c0sq) : p_i;
 
   R S1[3] = {0, 0, 0}, Cb[3] = {0, 0, 0}, S2[3] = {0, 0, 0}, Ct[3] = {0, 0, 0};
-  visit_cells<D>(I, cx, cy, cz, 1, a.off, [&](uint32_t jb, uint32_t je) {
-    for (uint32_t j = jb; j < je; ++j) {
-      if ((int)j == i) continue;
+  {
+#pragma unroll 4
+    for (int kk = 0; kk < nr; ++kk) {
+      const uint32_t j = Lst[(size_t)kk * LS];
       const V4<R> Pj = P[j];
       R d[3];
-      const R rr = pair_vec<R, D>(g, Pi, Pj, d);
-      if (!(rr > (R)0 && rr < g.cut2)) continue;
-      const R r = sqrt(rr);
-      const R dw = kernel_dW(g, r) / r;
-      const R V = Pj.w;
-      R gw[3] = {dw * d[0], dw * d[1], dw * d[2]};
+      const R rr = pair_vec<R, D, PER>(g, Pi, Pj, d);
+      R r;
+      Ex<R>::len(rr, r);
+      const R FV = kernel_F(g, r) * Pj.w;  // V_j dW/dr / r
+      R gw[3] = {FV * d[0], FV * d[1], FV * d[2]};  // V_j grad_i W_ij
       const R p_j = Q[j].w;
       const V4<R> b0 = pk.Bm0[j];
-      const R pe_j = rans ? p_j + b0.w / V : p_j;
+      const R pe_j = rans ? p_eff(p_j, b0.w, rho0, inv_c0sq) : p_j;
       if (b0.x < (R)0) {
 #pragma unroll
-        for (int c = 0; c < D; ++c) Cb[c] += V * gw[c];
+        for (int c = 0; c < D; ++c) Cb[c] += gw[c];
       } else {
         R Bj[6];
         if (D == 2) {
-          Bj[0] = b0.x; Bj[3] = b0.y; Bj[1] = b0.z;
+          Bj[0] = b0.x;
+          Bj[3] = b0.y;
+          Bj[1] = b0.z;
           Bj[2] = Bj[4] = Bj[5] = (R)0;
         } else {
           const V4<R> b1 = pk.Bm1[j];
-          Bj[0] = b0.x; Bj[1] = b0.y; Bj[2] = b0.z;
-          Bj[3] = b1.x; Bj[4] = b1.y; Bj[5] = b1.z;
+          Bj[0] = b0.x;
+          Bj[1] = b0.y;
+          Bj[2] = b0.z;
+          Bj[3] = b1.x;
+          Bj[4] = b1.y;
+          Bj[5] = b1.z;
         }
         R bg[3];
         sym_matvec<R, D>(Bj, gw, bg);
 #pragma unroll
-        for (int c = 0; c < D; ++c) S1[c] += V * bg[c];
+        for (int c = 0; c < D; ++c) S1[c] += bg[c];
       }
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        S2[c] += V * pe_j * gw[c];
-        Ct[c] += V * gw[c];
+        S2[c] += pe_j * gw[c];
+        Ct[c] += gw[c];
       }
     }
-  });
-  visit_cells<D>(I, cx, cy, cz, 1, a.woff, [&](uint32_t jb, uint32_t je) {
-    for (uint32_t w = jb; w < je; ++w) {
+  }
+  {
+#pragma unroll 4
+    for (int kk = nr; kk < nr + nw; ++kk) {
+      const uint32_t w = Lst[(size_t)kk * LS];
       const V4<R> Wp = pk.WP[w];
       R d[3];
-      const R rr = pair_vec<R, D>(g, Pi, Wp, d);
-      if (!(rr > (R)0 && rr < g.cut2)) continue;
-      const R r = sqrt(rr);
-      const R dw = kernel_dW(g, r) / r;
-      const R V = Wp.w;
+      const R rr = pair_vec<R, D, PER>(g, Pi, Wp, d);
+      R r;
+      Ex<R>::len(rr, r);
+      const R FV = kernel_F(g, r) * Wp.w;
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        const R gv = V * dw * d[c];
-        Cb[c] += gv;       // wall dummy: B^_j = B_i
-        S2[c] += pe_i * gv; // wall dummy: p_j = p_i
+        const R gv = FV * d[c];
+        Cb[c] += gv;         // wall dummy: B^_j = B_i
+        S2[c] += pe_i * gv;  // wall dummy: p_j = p_i
         Ct[c] += gv;
       }
     }
-  });
-  double acc[3] = {0, 0, 0};
-  {
-    double s1[3], cb[3], s2[3], ct[3], bcb[3], bs2[3], bct[3];
-    for (int c = 0; c < 3; ++c) {
-      s1[c] = (double)S1[c];
-      cb[c] = (double)Cb[c];
-      s2[c] = (double)S2[c];
-      ct[c] = (double)Ct[c];
-    }
-    sym_matvec<double, D>(Bd, cb, bcb);
-    sym_matvec<double, D>(Bd, s2, bs2);
-    sym_matvec<double, D>(Bd, ct, bct);
-    const double pe = (double)pe_i;
-    for (int c = 0; c < D; ++c) acc[c] = -(pe * (s1[c] + bcb[c]) + bs2[c]) / rho_i;
-    const int lab = m.label[i];
-    if (lab > 0 && lab <= I.nbuf) {
-      const BufDev &b = a.buf[I.buf0 + lab - 1];
-      if (b.type == SPH_BUF_PRESSURE) {
-        double pob = b.p_ob;
-        if (rans) pob += (2.0 / 3.0) * rho_i * m.k[i];
-        for (int c = 0; c < D; ++c) acc[c] += 2.0 * pob / rho_i * bct[c];
-      }
+  }
+  // a = -(1/rho_i) (p_i (S1 + B_i Cb) + B_i S2) [+ (2 p_ob / rho_i) B_i Ct]
+  const double rho_i = m.rho[i];
+  const R inv_rho = Ex<R>::div((R)1, (R)rho_i);
+  R bcb[3], bs2[3];
+  sym_matvec<R, D>(Bi, Cb, bcb);
+  sym_matvec<R, D>(Bi, S2, bs2);
+  R acc[3] = {0, 0, 0};
+#pragma unroll
+  for (int c = 0; c < D; ++c) acc[c] = -(pe_i * (S1[c] + bcb[c]) + bs2[c]) * inv_rho;
+  const int lab = m.label[i];
+  if (lab > 0 && lab <= I.nbuf) {
+    const BufDev &b = a.buf[I.buf0 + lab - 1];
+    if (b.type == SPH_BUF_PRESSURE) {
+      R pob = (R)b.p_ob;
+      if (rans) pob += (R)(2.0 / 3.0) * (R)rho_i * (R)m.k[i];
+      R bct[3];
+      sym_matvec<R, D>(Bi, Ct, bct);
+#pragma unroll
+      for (int c = 0; c < D; ++c) acc[c] += (R)2 * pob * inv_rho * bct[c];
     }
   }
-  const double dt = I.dt;
-  double v[3];
-  for (int c = 0; c < 3; ++c) v[c] = m.v[c][i];
+  // FP64 kick and half drift
+  const V4<R> ap = pk.Ap[i];
+  const R apr[3] = {ap.x, ap.y, ap.z};
+  const double dt = I.dt, hdt = 0.5 * I.dt;
+  R vo[3] = {(R)0, (R)0, (R)0};
+#pragma unroll
   for (int c = 0; c < D; ++c) {
-    v[c] = v[c] + dt * (acc[c] + a.der.an[c][i] + I.g[c]);
-    m.v[c][i] = v[c];
-    m.x[c][i] = m.x[c][i] + 0.5 * dt * v[c];
+    const double v = m.v[c][i] + dt * (double)(acc[c] + apr[c]);
+    m.v[c][i] = v;
+    m.x[c][i] = m.x[c][i] + hdt * v;
+    vo[c] = (R)v;
   }
-  V4<R> Qo = {(R)v[0], (R)v[1], (R)v[2], p_i};
-  pk.Q[qout][i] = Qo;
+  V4<R> Qo = {vo[0], vo[1], vo[2], p_i};
+  Qout[i] = Qo;
 }
 
 // =========================================================================
 // continuity sweep (a10) + density update + boundary values (a11) + next
 // half step (a8)
 // =========================================================================
-template <typename R, int D>
-__global__ void __launch_bounds__(kBlock) k_cont(SweepArgs a, Packs<R> pk, int pin, int qin, int pout,
-                                                 int qout) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.cnt->n_live) return;
-  const Masters m = a.m;
+template <typename R, int D, bool PER>
+__device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk, const V4<R> *__restrict__ P,
+                                         const V4<R> *__restrict__ Q, V4<R> *__restrict__ Pout,
+                                         V4<R> *__restrict__ Qout, const int i) {
+  const Masters &m = a.m;
   const int ii = m.inst[i];
   const InstDev &I = a.inst[ii];
   if (a.sub >= I.n_ac) return;
   const Geo<R> g = make_geo<R, D>(I);
-  int cx, cy, cz;
-  decode_cell(I, a.keys[i], cx, cy, cz);
-  const V4<R> *__restrict__ P = pk.P[pin];
-  const V4<R> *__restrict__ Q = pk.Q[qin];
+  const uint32_t *__restrict__ Lst = a.nl.nbr + i;
+  const size_t LS = (size_t)a.nl.stride;
+  const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
   const V4<R> Pi = P[i];
   const V4<R> Qi = Q[i];
-  const R inv_rc = (R)(1.0 / I.rc0);
+  const R inv_rc = (R)I.inv_rc0;
+  // drho_i / rho_i = sum_j [v_ij . r_ij / r + (p_i - p_j) / (rho0 c0)] dW/dr V_j
   R sum = 0;
-  visit_cells<D>(I, cx, cy, cz, 1, a.off, [&](uint32_t jb, uint32_t je) {
-    for (uint32_t j = jb; j < je; ++j) {
-      if ((int)j == i) continue;
+  {
+#pragma unroll 4
+    for (int kk = 0; kk < nr; ++kk) {
+      const uint32_t j = Lst[(size_t)kk * LS];
       const V4<R> Pj = P[j];
       R d[3];
-      const R rr = pair_vec<R, D>(g, Pi, Pj, d);
-      if (!(rr > (R)0 && rr < g.cut2)) continue;
-      const R r = sqrt(rr);
-      const R dw = kernel_dW(g, r);
+      const R rr = pair_vec<R, D, PER>(g, Pi, Pj, d);
+      R r;
+      Ex<R>::len(rr, r);
+      const R FV = kernel_F(g, r) * Pj.w;
       const V4<R> Qj = Q[j];
       const R vd = (Qi.x - Qj.x) * d[0] + (Qi.y - Qj.y) * d[1] + (Qi.z - Qj.z) * d[2];
-      sum += (vd / r + (Qi.w - Qj.w) * inv_rc) * dw * Pj.w;
+      sum += (vd + (Qi.w - Qj.w) * inv_rc * r) * FV;
     }
-  });
-  visit_cells<D>(I, cx, cy, cz, 1, a.woff, [&](uint32_t jb, uint32_t je) {
-    for (uint32_t w = jb; w < je; ++w) {
+  }
+  {
+#pragma unroll 4
+    for (int kk = nr; kk < nr + nw; ++kk) {
+      const uint32_t w = Lst[(size_t)kk * LS];
       const V4<R> Wp = pk.WP[w];
       R d[3];
-      const R rr = pair_vec<R, D>(g, Pi, Wp, d);
-      if (!(rr > (R)0 && rr < g.cut2)) continue;
-      const R r = sqrt(rr);
-      const R dw = kernel_dW(g, r);
+      const R rr = pair_vec<R, D, PER>(g, Pi, Wp, d);
+      R r;
+      Ex<R>::len(rr, r);
       const V4<R> Wv = pk.WV[w];
       // dummy velocity 2 v_wall - v_i, dummy pressure p_i
       const R vd = (R)2 * ((Qi.x - Wv.x) * d[0] + (Qi.y - Wv.y) * d[1] + (Qi.z - Wv.z) * d[2]);
-      sum += vd / r * dw * Wp.w;
+      sum += vd * kernel_F(g, r) * Wp.w;
     }
-  });
-  const double dt = I.dt;
-  const double drho = m.rho[i] * (double)sum;
+  }
+  const double hdt = 0.5 * I.dt;
+  const double rho_i = m.rho[i];
+  const double drho = rho_i * (double)sum;
   m.drho[i] = drho;
-  double rho = m.rho[i] + 0.5 * dt * drho;
+  double rho = rho_i + hdt * drho;
   m.rho[i] = rho;
   const int lab = m.label[i];
   if (lab > 0 && lab <= I.nbuf) {
@@ -618,25 +760,61 @@ __global__ void __launch_bounds__(kBlock) k_cont(SweepArgs a, Packs<R> pk, int p
     rho = m.rho[i];
     if (I.rans && b.turb == SPH_TURB_FREESTREAM) {
       V4<R> b0 = pk.Bm0[i];
-      b0.w = (R)((2.0 / 3.0) * b.k_in * m.mass[i]);
+      b0.w = (R)((2.0 / 3.0) * b.k_in);
       pk.Bm0[i] = b0;
     }
   }
-  double v0 = m.v[0][i], v1 = m.v[1][i], v2 = m.v[2][i];
-  if (!isfinite(rho) || !isfinite(v0) || !isfinite(v1) || !isfinite(v2)) set_status(a.status, SPH_ERR_NONFINITE);
+  double v[3] = {m.v[0][i], m.v[1][i], D == 3 ? m.v[2][i] : 0.0};
+  bool bad = !isfinite(rho);
+#pragma unroll
+  for (int c = 0; c < D; ++c) bad |= !isfinite(v[c]);
+  if (bad) set_status(a.status, SPH_ERR_NONFINITE);
   if (a.sub + 1 < I.n_ac) {
     // first half of the next sub-step
-    rho = rho + 0.5 * dt * drho;
-    const double p = I.eos_k * (rho / I.rho0 - 1.0);
+    rho = rho + hdt * drho;
+    const R p = (R)(rho - I.rho0) * (R)I.c0sq;
     m.rho[i] = rho;
-    m.p[i] = p;
-    double v[3] = {v0, v1, v2};
-    for (int c = 0; c < D; ++c) m.x[c][i] = m.x[c][i] + 0.5 * dt * v[c];
-    V4<R> Po = {Pi.x, Pi.y, Pi.z, (R)(m.mass[i] / rho)};
-    V4<R> Qo = {(R)v0, (R)v1, (R)v2, (R)p};
-    pk.P[pout][i] = Po;
-    pk.Q[qout][i] = Qo;
+    m.p[i] = (double)p;
+#pragma unroll
+    for (int c = 0; c < D; ++c) m.x[c][i] = m.x[c][i] + hdt * v[c];
+    V4<R> Po = {Pi.x, Pi.y, Pi.z, Ex<R>::div((R)m.mass[i], (R)rho)};
+    V4<R> Qo = {(R)v[0], (R)v[1], (R)v[2], p};
+    Pout[i] = Po;
+    Qout[i] = Qo;
   }
+}
+
+// ------------------------------------------------------------------------
+// kernels: grid-stride over the live particles
+// ------------------------------------------------------------------------
+template <typename R, int D, bool PER>
+__global__ void __launch_bounds__(kBlock) k_list(SweepArgs a, Packs<R> pk) {
+  const int n = a.cnt->n_live;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    list_one<R, D, PER>(a, pk, i);
+}
+
+template <typename R, int D, bool PER>
+__global__ void __launch_bounds__(kBlock) k_adv(SweepArgs a, Packs<R> pk) {
+  const int n = a.cnt->n_live;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    adv_one<R, D, PER>(a, pk, i);
+}
+
+template <typename R, int D, bool PER>
+__global__ void __launch_bounds__(kBlock) k_mom(SweepArgs a, Packs<R> pk, int pin, int qin, int qout) {
+  if (a.sub >= a.cnt->n_ac_all) return;  // no instance takes this sub-step
+  const int n = a.cnt->n_live;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    mom_one<R, D, PER>(a, pk, pk.P[pin], pk.Q[qin], pk.Q[qout], i);
+}
+
+template <typename R, int D, bool PER>
+__global__ void __launch_bounds__(kBlock) k_cont(SweepArgs a, Packs<R> pk, int pin, int qin, int pout, int qout) {
+  if (a.sub >= a.cnt->n_ac_all) return;
+  const int n = a.cnt->n_live;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    cont_one<R, D, PER>(a, pk, pk.P[pin], pk.Q[qin], pk.P[pout], pk.Q[qout], i);
 }
 
 // =========================================================================
@@ -678,95 +856,118 @@ __global__ void __launch_bounds__(kBlock) k_pairs(SweepArgs a, const double *__r
       out[4 * t + 3] = ii;
     }
   };
-  auto body = [&](uint32_t jb, uint32_t je) {
-    for (uint32_t j = jb; j < je; ++j) {
-      if ((int)j == i) continue;
-      const double xj[3] = {m.x[0][j], m.x[1][j], m.x[2][j]};
-      if (test(xj)) emit(m.uid[j], 0);
-    }
-  };
-  auto wbody = [&](uint32_t jb, uint32_t je) {
-    for (uint32_t w = jb; w < je; ++w) {
-      const double xj[3] = {wx[w], wy[w], wz[w]};
-      if (test(xj)) emit(wall_index[w], 1);
-    }
-  };
-  if (I.dim == 2) {
-    visit_cells<2>(I, cx, cy, cz, 1, a.off, body);
-    visit_cells<2>(I, cx, cy, cz, 1, a.woff, wbody);
-  } else {
-    visit_cells<3>(I, cx, cy, cz, 1, a.off, body);
-    visit_cells<3>(I, cx, cy, cz, 1, a.woff, wbody);
+  for (int set = 0; set < 2; ++set) {
+    auto body = [&](uint32_t jb, uint32_t je) {
+      for (uint32_t j = jb; j < je; ++j) {
+        if (set == 0) {
+          if ((int)j == i) continue;
+          const double xj[3] = {m.x[0][j], m.x[1][j], m.x[2][j]};
+          if (test(xj)) emit(m.uid[j], 0);
+        } else {
+          const double xj[3] = {wx[j], wy[j], wz[j]};
+          if (test(xj)) emit(wall_index[j], 1);
+        }
+      }
+    };
+    if (I.dim == 2)
+      visit_cells<2, true>(I, cx, cy, cz, 1, set == 0 ? a.off : a.woff, body);
+    else
+      visit_cells<3, true>(I, cx, cy, cz, 1, set == 0 ? a.off : a.woff, body);
   }
 }
 
 // ------------------------------------------------------------------------
 // launch wrappers
 // ------------------------------------------------------------------------
-static inline int grid_for(int max_n) {
-  int g = (max_n + kBlock - 1) / kBlock;
-  return g < 1 ? 1 : g;
+// blocks to launch: all resident blocks of the GPU, or fewer when the
+// particles need fewer; the occupancy query runs once per kernel
+template <typename K>
+static int resident_grid(K kernel, int max_n) {
+  static int per_gpu = 0;
+  if (per_gpu == 0) {
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+    per_gpu = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  int need = (max_n + kBlock - 1) / kBlock;
+  if (need < 1) need = 1;
+  return need < per_gpu ? need : per_gpu;
 }
 
-template <typename R>
-static void adv_dispatch(const SweepArgs &a, void *packs, int dim, int max_n, cudaStream_t st) {
-  Packs<R> &pk = *(Packs<R> *)packs;
-  if (dim == 2)
-    k_adv<R, 2><<<grid_for(max_n), kBlock, 0, st>>>(a, pk);
-  else
-    k_adv<R, 3><<<grid_for(max_n), kBlock, 0, st>>>(a, pk);
-}
-
-void launch_advection_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n, cudaStream_t st) {
-  if (prec == SPH_PREC_FP32)
-    adv_dispatch<float>(a, packs, dim, max_n, st);
-  else
-    adv_dispatch<double>(a, packs, dim, max_n, st);
+template <typename R, int D, bool PER>
+static void launch_sweeps_impl(int which, const SweepArgs &a, Packs<R> &pk, int max_n, int sub, cudaStream_t st) {
+  const int pc = (sub % 2 == 0) ? 1 : 0;
+  if (which == 3) {
+    auto k = k_list<R, D, PER>;
+    k<<<resident_grid(k, max_n), kBlock, 0, st>>>(a, pk);
+  } else if (which == 0) {
+    auto k = k_adv<R, D, PER>;
+    k<<<resident_grid(k, max_n), kBlock, 0, st>>>(a, pk);
+  } else if (which == 1) {
+    auto k = k_mom<R, D, PER>;
+    k<<<resident_grid(k, max_n), kBlock, 0, st>>>(a, pk, pc, 1, 0);
+  } else {
+    auto k = k_cont<R, D, PER>;
+    k<<<resident_grid(k, max_n), kBlock, 0, st>>>(a, pk, pc, 0, 1 - pc, 1);
+  }
 }
 
 // Pack ping-pong: the advection sweep leaves P[1], Q[1].  Sub-step s reads
 // P[pc] with pc = 1 for even s, 0 for odd s; momentum reads Q[1] and writes
 // Q[0]; continuity reads Q[0], writes P[1 - pc] and Q[1].
 template <typename R>
-static void mom_dispatch(const SweepArgs &a, void *packs, int dim, int max_n, int sub, cudaStream_t st) {
+static void launch_sweeps(int which, const SweepArgs &a, void *packs, int dim, int max_n, int sub, cudaStream_t st) {
   Packs<R> &pk = *(Packs<R> *)packs;
-  const int pc = (sub % 2 == 0) ? 1 : 0;
-  if (dim == 2)
-    k_mom<R, 2><<<grid_for(max_n), kBlock, 0, st>>>(a, pk, pc, 1, 0);
-  else
-    k_mom<R, 3><<<grid_for(max_n), kBlock, 0, st>>>(a, pk, pc, 1, 0);
+  if (dim == 2) {
+    if (a.any_periodic)
+      launch_sweeps_impl<R, 2, true>(which, a, pk, max_n, sub, st);
+    else
+      launch_sweeps_impl<R, 2, false>(which, a, pk, max_n, sub, st);
+  } else {
+    if (a.any_periodic)
+      launch_sweeps_impl<R, 3, true>(which, a, pk, max_n, sub, st);
+    else
+      launch_sweeps_impl<R, 3, false>(which, a, pk, max_n, sub, st);
+  }
 }
 
-template <typename R>
-static void cont_dispatch(const SweepArgs &a, void *packs, int dim, int max_n, int sub, cudaStream_t st) {
-  Packs<R> &pk = *(Packs<R> *)packs;
-  const int pc = (sub % 2 == 0) ? 1 : 0;
-  if (dim == 2)
-    k_cont<R, 2><<<grid_for(max_n), kBlock, 0, st>>>(a, pk, pc, 0, 1 - pc, 1);
+void launch_neighbour_list(const SweepArgs &a, void *packs, int prec, int dim, int max_n, cudaStream_t st) {
+  if (prec == SPH_PREC_FP32)
+    launch_sweeps<float>(3, a, packs, dim, max_n, 0, st);
   else
-    k_cont<R, 3><<<grid_for(max_n), kBlock, 0, st>>>(a, pk, pc, 0, 1 - pc, 1);
+    launch_sweeps<double>(3, a, packs, dim, max_n, 0, st);
+}
+
+void launch_advection_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n, cudaStream_t st) {
+  if (prec == SPH_PREC_FP32)
+    launch_sweeps<float>(0, a, packs, dim, max_n, 0, st);
+  else
+    launch_sweeps<double>(0, a, packs, dim, max_n, 0, st);
 }
 
 void launch_momentum_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n, int sub,
                            cudaStream_t st) {
   if (prec == SPH_PREC_FP32)
-    mom_dispatch<float>(a, packs, dim, max_n, sub, st);
+    launch_sweeps<float>(1, a, packs, dim, max_n, sub, st);
   else
-    mom_dispatch<double>(a, packs, dim, max_n, sub, st);
+    launch_sweeps<double>(1, a, packs, dim, max_n, sub, st);
 }
 
 void launch_continuity_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n, int sub,
                              cudaStream_t st) {
   if (prec == SPH_PREC_FP32)
-    cont_dispatch<float>(a, packs, dim, max_n, sub, st);
+    launch_sweeps<float>(2, a, packs, dim, max_n, sub, st);
   else
-    cont_dispatch<double>(a, packs, dim, max_n, sub, st);
+    launch_sweeps<double>(2, a, packs, dim, max_n, sub, st);
 }
 
 void launch_debug_pairs(const SweepArgs &a, const double *wx, const double *wy, const double *wz,
                         const uint32_t *wall_index, int64_t *out, int64_t max, unsigned long long *counter,
                         int max_n, cudaStream_t st) {
-  k_pairs<<<grid_for(max_n), kBlock, 0, st>>>(a, wx, wy, wz, wall_index, out, max, counter);
+  int g = (max_n + kBlock - 1) / kBlock;
+  k_pairs<<<g < 1 ? 1 : g, kBlock, 0, st>>>(a, wx, wy, wz, wall_index, out, max, counter);
 }
 
 }  // namespace sphk

@@ -21,10 +21,36 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *slot, doub
 }
 
 template <typename R>
+__device__ __forceinline__ void permute_one(const TopoArgs &a, const Packs<R> &pk, int t, int s_ii,
+                                            unsigned long long *s_v2, unsigned long long *s_nu);
+
+template <typename R>
 __global__ void __launch_bounds__(kBlock) k_permute(TopoArgs a, Packs<R> pk) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = a.cnt->n_live;
-  if (t >= n) return;
+  // time-step maxima are reduced in shared memory for the instance of the
+  // block's first particle (particles are instance-sorted, so almost every
+  // block has one) and go straight to global memory otherwise
+  __shared__ int s_ii;
+  __shared__ unsigned long long s_v2, s_nu;
+  const int base = blockIdx.x * blockDim.x;
+  if (threadIdx.x == 0) {
+    s_ii = base < n ? (int)a.src.inst[a.sorted_vals[base]] : -1;
+    s_v2 = 0ull;
+    s_nu = 0ull;
+  }
+  __syncthreads();
+  if (t < n) permute_one<R>(a, pk, t, s_ii, &s_v2, &s_nu);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_ii >= 0) {
+    atomicMax(&a.v2max[s_ii], s_v2);
+    atomicMax(&a.nutmax[s_ii], s_nu);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void permute_one(const TopoArgs &a, const Packs<R> &pk, int t, int s_ii,
+                                            unsigned long long *s_v2, unsigned long long *s_nu) {
   const int s = (int)a.sorted_vals[t];
   const Masters S = a.src, D = a.dst;
   const int ii = S.inst[s];
@@ -54,7 +80,7 @@ __global__ void __launch_bounds__(kBlock) k_permute(TopoArgs a, Packs<R> pk) {
     if (box_contains(B, I.dim, x, y, z)) lab = B.local_id + 1;
   }
   D.label[t] = lab;
-  V4<R> P = {(R)x, (R)y, (R)z, (R)(mass / rho)};
+  V4<R> P = {(R)x, (R)y, (R)z, (R)mass / (R)rho};
   V4<R> Q = {(R)vx, (R)vy, (R)vz, (R)S.p[s]};
   pk.P[0][t] = P;
   pk.Q[0][t] = Q;
@@ -66,8 +92,13 @@ __global__ void __launch_bounds__(kBlock) k_permute(TopoArgs a, Packs<R> pk) {
   double v2 = dmul(vx, vx);
   v2 = dadd(v2, dmul(vy, vy));
   if (I.dim == 3) v2 = dadd(v2, dmul(vz, vz));
-  atomic_max_nonneg(&a.v2max[ii], v2);
-  if (I.rans) atomic_max_nonneg(&a.nutmax[ii], nut);
+  if (ii == s_ii) {
+    atomicMax(s_v2, (unsigned long long)__double_as_longlong(v2));
+    if (I.rans) atomicMax(s_nu, (unsigned long long)__double_as_longlong(nut));
+  } else {
+    atomic_max_nonneg(&a.v2max[ii], v2);
+    if (I.rans) atomic_max_nonneg(&a.nutmax[ii], nut);
+  }
 }
 
 void launch_permute(const TopoArgs &a, int max_n, int prec, cudaStream_t st, void *packs) {
@@ -115,6 +146,7 @@ __global__ void k_time_step(TopoArgs a) {
   I.n_ac = n;
   I.dt = ddiv(dt_ad, (double)n);
   I.t = dadd(I.t, dt_ad);
+  atomicMax(&a.cnt->n_ac_all, n);
 }
 
 void launch_time_step(const TopoArgs &a, cudaStream_t st) {
@@ -218,8 +250,9 @@ __global__ void __launch_bounds__(1024) k_spawn_scan(TopoArgs a, int nblocks, ui
 // definition), then the cell key of the wrapped position
 __device__ __forceinline__ void wrap_and_key(const InstDev &I, const Masters &m, int i, uint32_t *keys) {
   double p[3] = {m.x[0][i], m.x[1][i], m.x[2][i]};
-  for (int d = 0; d < I.dim; ++d) {
-    if (!I.periodic[d]) continue;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (d >= I.dim || !I.periodic[d]) continue;
     if (p[d] >= I.hi[d])
       p[d] = dsub(p[d], I.L[d]);
     else if (p[d] < I.lo[d])
@@ -278,7 +311,9 @@ __global__ void __launch_bounds__(kBlock) k_spawn(TopoArgs a, const uint32_t *ui
   a.idx[dst] = (uint32_t)dst;
   wrap_and_key(I, m, dst, a.keys);
   const BufDev &B = a.buf[I.buf0 + m.label[i] - 1];
-  for (int d = 0; d < I.dim; ++d) m.x[d][i] = dsub(m.x[d][i], dmul(B.length, B.frame[d]));
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    if (d < I.dim) m.x[d][i] = dsub(m.x[d][i], dmul(B.length, B.frame[d]));
   apply_bc(I, B, m, i, a.step, kSubRecycle);
   wrap_and_key(I, m, i, a.keys);
 }

@@ -96,7 +96,7 @@ EXPORTS = ("sph_create", "sph_add_buffer", "sph_set_profile", "sph_step", "sph_r
            "sph_last_error", "sph_abi_version", "sph_set_profiling", "sph_get_stage_times", "sph_stage_name",
            "sph_cell_sort_noalloc")
 NOALLOC_MAX_POINTS = 1 << 19
-N_STAGES = 8
+N_STAGES = 9
 
 
 def library_path() -> str:
