@@ -273,3 +273,240 @@ def lattice_block(n_per_axis=21, dim=2, dp=0.1, rho0=1.0, c0=10.0, nu=0.01, h_fa
     return Case(name=f"lattice_{dim}d_{n_per_axis}", dim=dim, dp=dp, h=h, rho0=rho0, c0=c0, nu_l=nu,
                 rans=rans, U_ref=1.0, lo=lo, hi=hi, periodic=(0, 0, 0), wpos=np.zeros((0, 3)),
                 wvel=np.zeros((0, 3)), capacity=pos.shape[0] + 16, **arr)
+
+
+# --------------------------------------------------------------------------
+# U-shaped channel and the batch of independent channels (Sec. 4.2 shape)
+# --------------------------------------------------------------------------
+def _arc_points(centre, radius, theta0, theta1, dp):
+    """Points spaced ~dp along the arc of `radius` about `centre` from theta0 to theta1."""
+    n = max(1, int(round(abs(theta1 - theta0) * radius / dp)))
+    th = theta0 + (np.arange(n) + 0.5) * (theta1 - theta0) / n
+    return np.stack([centre[0] + radius * np.cos(th), centre[1] + radius * np.sin(th), np.zeros(n)], 1)
+
+
+def u_channel(dp=0.05, width=1.0, r_inner=0.5, leg=1.5, nu=0.01, p_in=2.3, p_out=2.25, c0=15.0,
+              rho0=1.0, jitter_frac=0.01, seed=7, buffer_cells=4, capacity_factor=1.5) -> Case:
+    """Pressure-driven U-shaped channel: two straight legs of length `leg`
+    joined by a half annulus (inner radius r_inner, outer r_inner + width).
+
+    The lower leg occupies 0 <= y <= width, the upper leg
+    width + 2 r_inner <= y <= 2 (width + r_inner), both for 0 <= x <= leg;
+    the bend is centred at (leg, width + r_inner).  Inlet (lower leg) and
+    outlet (upper leg) are pressure buffers at x = 0 with n_b = +x; four
+    wall-dummy layers line every wall, straight walls extending 4 dp beyond
+    the open faces.  The initial state is at rest with the density of the
+    mean pressure.
+    """
+    Ro = r_inner + width
+    cx, cy = leg, width + r_inner
+    top = 2.0 * (width + r_inner)
+    nx, ny = int(round((leg + Ro) / dp)), int(round(top / dp))
+    pts = lattice((nx, ny), dp)
+    x, y = pts[:, 0], pts[:, 1]
+    rr = np.hypot(x - cx, y - cy)
+    in_legs = (x < leg) & (((y > 0) & (y < width)) | ((y > width + 2 * r_inner) & (y < top)))
+    in_bend = (x >= leg) & (rr > r_inner) & (rr < Ro)
+    pos = jitter(pts[in_legs | in_bend], 2, jitter_frac * dp, seed)
+    h = H_FAC * dp
+    walls = []
+    x0 = -WALL_LAYERS * dp
+    ncol = int(round((leg - x0) / dp))
+    xs = x0 + (np.arange(ncol) + 0.5) * dp
+    for l in range(WALL_LAYERS):
+        off = (l + 0.5) * dp
+        for yy in (-off, width + off, width + 2 * r_inner - off, top + off):
+            walls.append(np.stack([xs, np.full(ncol, yy), np.zeros(ncol)], 1))
+        walls.append(_arc_points((cx, cy), Ro + off, -0.5 * np.pi, 0.5 * np.pi, dp))
+        walls.append(_arc_points((cx, cy), r_inner - off, -0.5 * np.pi, 0.5 * np.pi, dp))
+    wpos = np.concatenate(walls, 0)
+    Lb = buffer_cells * dp
+    bufs = [
+        BufferSpec("pressure", (0.0, 0.5 * width, 0.0), frame_2d((1, 0)), Lb, (0.5 * width, 0.0), p_ob=p_in),
+        BufferSpec("pressure", (0.0, top - 0.5 * width, 0.0), frame_2d((1, 0)), Lb, (0.5 * width, 0.0),
+                   p_ob=p_out),
+    ]
+    margin = WALL_LAYERS * dp + 2 * h
+    arr = _fluid_arrays(pos, 2, dp, rho0)
+    arr["rho"][:] = rho0 * (1.0 + 0.5 * (p_in + p_out) / (rho0 * c0 * c0))
+    return Case(name=f"u_channel_2d_dp{dp:g}", dim=2, dp=dp, h=h, rho0=rho0, c0=c0, nu_l=nu, rans=False,
+                U_ref=c0 / 10.0, lo=np.array([-margin, -margin, 0.0]),
+                hi=np.array([leg + Ro + margin, top + margin, 0.0]), periodic=(0, 0, 0), wpos=wpos,
+                wvel=np.zeros_like(wpos), buffers=bufs, seed=seed,
+                capacity=int(capacity_factor * pos.shape[0]) + 64, **arr)
+
+
+def batched_channels(n_instances=64, seed=3, dps=(0.05, 0.025, 0.0125), re_range=(10.0, 200.0),
+                     U=1.0, dt_mode="single") -> List[Case]:
+    """Independent laminar channels for one batched context: half straight
+    2 x 1 channels, half U-channels (inner radius 0.5, width 1, legs 1.5),
+    dp drawn from `dps` and Re uniform in `re_range`, nu = U W / Re.
+
+    The pressure drop is the one of plane Poiseuille flow with mean velocity
+    U over the centre-line length (dp/dx = 12 nu U / W^2); the outlet
+    pressure is 0.01 rho0 c0^2 with c0 = 10 U_max = 15 U, the background that
+    keeps the open boundaries free of tensile instability.
+    """
+    rng = np.random.default_rng(seed)
+    kinds = np.array([0, 1] * (n_instances // 2) + [0] * (n_instances % 2))
+    rng.shuffle(kinds)
+    out = []
+    for q in range(n_instances):
+        dp = float(rng.choice(np.asarray(dps)))
+        Re = float(rng.uniform(*re_range))
+        nu = U * 1.0 / Re
+        c0 = 15.0 * U
+        p_out = 0.01 * c0 * c0
+        if kinds[q] == 0:
+            c = poiseuille_channel(length=2.0, height=1.0, dp=dp, p_in=p_out + 12 * nu * U * 2.0, p_out=p_out,
+                                   nu=nu, seed=seed * 1000 + q)
+        else:
+            path = 2 * 1.5 + np.pi * 1.0
+            c = u_channel(dp=dp, nu=nu, p_in=p_out + 12 * nu * U * path, p_out=p_out, c0=c0,
+                          seed=seed * 1000 + q)
+        c.name = f"batch{q:02d}_{c.name}_Re{Re:.0f}"
+        c.dt_mode = dt_mode
+        out.append(c)
+    return out
+
+
+# --------------------------------------------------------------------------
+# plane jet with bidirectional buffers on the open sides (Sec. 4.3 shape)
+# --------------------------------------------------------------------------
+def plane_jet(dp=0.002, box=2.0, slot=0.1, U=1.0, Re=2.0e4, rho0=1.0, c0=10.0, n_theta=32,
+              theta=None, rans=True, seed=4, buffer_cells=4, jitter_frac=0.0,
+              capacity_factor=1.25) -> Case:
+    """Turbulent plane jet entering a box x, y in [0, box] through a slot of
+    width `slot` centred on the bottom side.
+
+    Bottom side: a velocity buffer over the slot (profile theta, n_theta
+    points across the slot, default uniform U; freestream k, eps) and
+    zero-velocity inflow buffers over the rest.  Left, right and top sides:
+    zero-pressure buffers (zero-gradient k, eps) that carry inflow and
+    outflow.  No walls.  nu = U slot / Re.  Initial state at rest with the
+    ambient k, eps.
+    """
+    n = int(round(box / dp))
+    pos = lattice((n, n), dp)
+    if jitter_frac:
+        pos = jitter(pos, 2, jitter_frac * dp, seed)
+    h = H_FAC * dp
+    Lb = buffer_cells * dp
+    k_in, eps_in = inlet_turbulence(U, slot)
+    k_a, eps_a = inlet_turbulence(U, box, intensity=0.01)
+    th = np.full(n_theta, U) if theta is None else np.asarray(theta, np.float64)
+    s0, s1 = 0.5 * (box - slot), 0.5 * (box + slot)
+    up = frame_2d((0, 1))
+    bufs = [
+        BufferSpec("velocity", (0.5 * box, 0.0, 0.0), up, Lb, (0.5 * slot, 0.0), theta=tuple(th),
+                   turb="freestream", k_in=k_in, eps_in=eps_in),
+        BufferSpec("velocity", (0.5 * s0, 0.0, 0.0), up, Lb, (0.5 * s0, 0.0), theta=(0.0,),
+                   turb="freestream", k_in=k_a, eps_in=eps_a),
+        BufferSpec("velocity", (0.5 * (s1 + box), 0.0, 0.0), up, Lb, (0.5 * (box - s1), 0.0), theta=(0.0,),
+                   turb="freestream", k_in=k_a, eps_in=eps_a),
+        BufferSpec("pressure", (0.0, 0.5 * box, 0.0), frame_2d((1, 0)), Lb, (0.5 * box - Lb, 0.0), p_ob=0.0),
+        BufferSpec("pressure", (box, 0.5 * box, 0.0), frame_2d((-1, 0)), Lb, (0.5 * box - Lb, 0.0), p_ob=0.0),
+        BufferSpec("pressure", (0.5 * box, box, 0.0), frame_2d((0, -1)), Lb, (0.5 * box, 0.0), p_ob=0.0),
+    ]
+    margin = 2 * h + Lb
+    arr = _fluid_arrays(pos, 2, dp, rho0, k=k_a, eps=eps_a)
+    return Case(name=f"plane_jet_2d_{box:g}_dp{dp:g}", dim=2, dp=dp, h=h, rho0=rho0, c0=c0,
+                nu_l=U * slot / Re, rans=rans, U_ref=U, lo=np.array([-margin, -margin, 0.0]),
+                hi=np.array([box + margin, box + margin, 0.0]), periodic=(0, 0, 0), wpos=np.zeros((0, 3)),
+                wvel=np.zeros((0, 3)), buffers=bufs, seed=seed,
+                capacity=int(capacity_factor * pos.shape[0]) + 1024, **arr)
+
+
+# --------------------------------------------------------------------------
+# 3D rotating-wall mixer (Sec. 4.4 shape)
+# --------------------------------------------------------------------------
+def _rings(R, z_levels, dp, centre=(0.0, 0.0)):
+    """Wall points on the cylinder of radius R at the given heights, ~dp apart."""
+    n = max(1, int(round(2 * np.pi * R / dp)))
+    th = (np.arange(n) + 0.5) * 2 * np.pi / n
+    xy = np.stack([centre[0] + R * np.cos(th), centre[1] + R * np.sin(th)], 1)
+    z = np.asarray(z_levels, np.float64)
+    out = np.zeros((n * z.size, 3))
+    out[:, :2] = np.tile(xy, (z.size, 1))
+    out[:, 2] = np.repeat(z, n)
+    return out
+
+
+def mixer_3d(dp=0.01, R=1.0, H=1.0, omega=2.0, r_in=0.15, x_in=0.5, U_in=0.5, r_out=0.3, stub_cells=8,
+             Re=100.0, rho0=1.0, seed=6, buffer_cells=4, capacity_factor=1.25) -> Case:
+    """Cylindrical chamber (radius R, height H) whose side wall rotates at
+    omega about the axis, fed by two axial inlet stubs of radius r_in on the
+    bottom at (+-x_in, 0) and drained by one outlet stub of radius r_out at
+    the top centre; stubs are stub_cells * dp long.
+
+    Inlets are velocity buffers (U_in along +z) whose boxes are the cuboids
+    bounding the circular stubs, so region-constrained labelling sees
+    corners outside the fluid; the outlet is a zero-pressure buffer.  Four
+    wall layers line every wall.  nu = U_in (2 r_in) / Re; c0 = 10 max(U_in,
+    omega R).  Initial state at rest.
+    """
+    Ls = stub_cells * dp
+    n_xy = int(round(2 * R / dp))
+    nz = int(round(H / dp))
+    pts = lattice((n_xy, n_xy, nz), dp, origin=(-R, -R, 0.0))
+    keep = np.hypot(pts[:, 0], pts[:, 1]) < R
+    fluid = [pts[keep]]
+    n_st = int(round(Ls / dp))
+    for (cx, rs, z0) in ((x_in, r_in, -Ls), (-x_in, r_in, -Ls), (0.0, r_out, H)):
+        m = int(np.ceil(rs / dp)) + 1
+        sp = lattice((2 * m, 2 * m, n_st), dp, origin=(cx - m * dp, -m * dp, z0))
+        fluid.append(sp[np.hypot(sp[:, 0] - cx, sp[:, 1]) < rs])
+    pos = np.concatenate(fluid, 0)
+    walls, wv = [], []
+    Lw = WALL_LAYERS * dp
+    # rotating side wall
+    zs = (np.arange(nz) + 0.5) * dp
+    for l in range(WALL_LAYERS):
+        ring = _rings(R + (l + 0.5) * dp, zs, dp)
+        walls.append(ring)
+        v = np.zeros_like(ring)
+        v[:, 0] = -omega * ring[:, 1]
+        v[:, 1] = omega * ring[:, 0]
+        wv.append(v)
+    # bottom and top plates with holes around the stubs, stub walls
+    m = int(np.ceil((R + Lw) / dp))
+    plate = lattice((2 * m, 2 * m), dp, origin=(-m * dp, -m * dp, 0.0))
+    plate = plate[np.hypot(plate[:, 0], plate[:, 1]) < R + Lw]
+    bot_ok = (np.hypot(plate[:, 0] - x_in, plate[:, 1]) >= r_in + Lw) & \
+             (np.hypot(plate[:, 0] + x_in, plate[:, 1]) >= r_in + Lw)
+    top_ok = np.hypot(plate[:, 0], plate[:, 1]) >= r_out + Lw
+    for l in range(WALL_LAYERS):
+        b = plate[bot_ok].copy()
+        b[:, 2] = -(l + 0.5) * dp
+        t = plate[top_ok].copy()
+        t[:, 2] = H + (l + 0.5) * dp
+        walls += [b, t]
+        wv += [np.zeros_like(b), np.zeros_like(t)]
+    n_sw = n_st + WALL_LAYERS
+    for (cx, rs, zlev) in ((x_in, r_in, -(np.arange(n_sw) + 0.5) * dp),
+                           (-x_in, r_in, -(np.arange(n_sw) + 0.5) * dp),
+                           (0.0, r_out, H + (np.arange(n_sw) + 0.5) * dp)):
+        for l in range(WALL_LAYERS):
+            ring = _rings(rs + (l + 0.5) * dp, zlev, dp, centre=(cx, 0.0))
+            walls.append(ring)
+            wv.append(np.zeros_like(ring))
+    wpos = np.concatenate(walls, 0)
+    wvel = np.concatenate(wv, 0)
+    h = H_FAC * dp
+    Lb = buffer_cells * dp
+    up = frame_3d((0, 0, 1), (1, 0, 0))
+    down = frame_3d((0, 0, -1), (1, 0, 0))
+    bufs = [
+        BufferSpec("velocity", (x_in, 0.0, -Ls), up, Lb, (r_in, r_in), theta=(U_in,)),
+        BufferSpec("velocity", (-x_in, 0.0, -Ls), up, Lb, (r_in, r_in), theta=(U_in,)),
+        BufferSpec("pressure", (0.0, 0.0, H + Ls), down, Lb, (r_out, r_out), p_ob=0.0),
+    ]
+    c0 = 10.0 * max(U_in, omega * R)
+    margin = Lw + 2 * h
+    arr = _fluid_arrays(pos, 3, dp, rho0)
+    lo = np.array([-R - margin, -R - margin, -Ls - margin])
+    hi = np.array([R + margin, R + margin, H + Ls + margin])
+    return Case(name=f"mixer_3d_R{R:g}_dp{dp:g}", dim=3, dp=dp, h=h, rho0=rho0, c0=c0,
+                nu_l=U_in * 2 * r_in / Re, rans=False, U_ref=max(U_in, omega * R), lo=lo, hi=hi,
+                periodic=(0, 0, 0), wpos=wpos, wvel=wvel, buffers=bufs, seed=seed,
+                capacity=int(capacity_factor * pos.shape[0]) + 1024, **arr)

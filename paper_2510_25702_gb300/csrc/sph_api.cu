@@ -301,19 +301,14 @@ static T *alloc_arr(sph_ctx *c, int64_t n) {
 
 template <typename R>
 static int alloc_packs(sph_ctx *c, Packs<R> &pk, int64_t cap, int64_t nw) {
-  for (int s = 0; s < 2; ++s) {
-    pk.P[s] = alloc_arr<V4<R>>(c, cap);
-    pk.Q[s] = alloc_arr<V4<R>>(c, cap);
-    if (!pk.P[s] || !pk.Q[s]) return -1;
-  }
-  pk.Bm0 = alloc_arr<V4<R>>(c, cap);
-  pk.Bm1 = alloc_arr<V4<R>>(c, c->dim == 3 ? cap : 1);
-  pk.T = alloc_arr<V4<R>>(c, cap);
+  const int d3 = c->dim == 3;
+  pk.adv = alloc_arr<V4<R>>(c, cap * (d3 ? RecLayout<3>::adv : RecLayout<2>::adv));
+  pk.mom = alloc_arr<V4<R>>(c, cap * (d3 ? RecLayout<3>::mom : RecLayout<2>::mom));
+  pk.cont = alloc_arr<V4<R>>(c, cap * (d3 ? RecLayout<3>::cont : RecLayout<2>::cont));
   pk.Ap = alloc_arr<V4<R>>(c, cap);
-  if (!pk.Ap) return -1;
   pk.WP = alloc_arr<V4<R>>(c, nw);
   pk.WV = alloc_arr<V4<R>>(c, nw);
-  if (!pk.Bm0 || !pk.Bm1 || !pk.T || !pk.WP || !pk.WV) return -1;
+  if (!pk.adv || !pk.mom || !pk.cont || !pk.Ap || !pk.WP || !pk.WV) return -1;
   return 0;
 }
 

@@ -4,11 +4,9 @@
 // Layout in HBM (one context):
 //  * master particle state, FP64 structure-of-arrays, two copies (the cell
 //    sort gathers one into the other every advection step);
-//  * per-step "packs": 4-wide vectors in the sweep precision R (float or
-//    double) that the pair sweeps read for neighbours -- P = (x, y, z, V),
-//    Q = (vx, vy, vz, p), Bm0/Bm1 = symmetric B and kappa = 2/3 k m,
-//    T = (k, eps, nu_t, -).  P and Q are double-buffered across the
-//    acoustic sub-steps so a sweep never reads what it writes;
+//  * per-sweep neighbour records in the sweep precision R (float or double):
+//    one record per particle holding what one sweep reads of a neighbour,
+//    written by the kernel that runs before that sweep (layout at Packs);
 //  * sorted cell keys, cell offsets (exclusive prefix over all cells of
 //    all instances) and the same for the fixed wall dummies;
 //  * a device status word (first error wins) and counters.
@@ -88,12 +86,31 @@ struct alignas(4 * sizeof(R)) V4 {
   R x, y, z, w;
 };
 
+// Neighbour records: what one sweep reads of a neighbour j, packed into
+// RV consecutive 4-vectors (32 B per record in 2D FP32, one sector), so
+// that a neighbour costs one gather.  Written by the kernel before the
+// sweep that reads them:
+//   adv  (permute -> advection sweep)   2D (x y V vx)(vy k eps nut)
+//                                       3D (x y z V)(vx vy vz k)(eps nut - -)
+//   mom  (advection / continuity -> momentum)
+//                                       2D (x y V p)(Bxx Bxy Byy kw)
+//                                       3D (x y z V)(p kw Bxx Byy)(Bzz Bxy Bxz Byz)
+//   cont (momentum -> continuity)       2D (x y V p)(vx vy - -)
+//                                       3D (x y z V)(p vx vy vz)
+// kw = 2/3 k (effective pressure); Bxx < 0 marks a pressure-buffer
+// particle whose neighbours use their own B (the condition B_k = B_i).
 template <typename R>
 struct Packs {
-  V4<R> *P[2], *Q[2];
-  V4<R> *Bm0, *Bm1, *T;
-  V4<R> *Ap;       // a_nu + g of the advection step (sweep precision)
-  V4<R> *WP, *WV;  // walls: (x, y, z, V) and (vx, vy, vz, 0)
+  V4<R> *adv, *mom, *cont;  // records, RV 4-vectors per particle
+  V4<R> *Ap;                // a_nu + g of the advection step
+  V4<R> *WP, *WV;           // walls: (x, y, z, V) and (vx, vy, vz, 0)
+};
+
+template <int D>
+struct RecLayout {
+  static constexpr int adv = (D == 2) ? 2 : 3;
+  static constexpr int mom = (D == 2) ? 2 : 3;
+  static constexpr int cont = 2;
 };
 
 struct Counters {

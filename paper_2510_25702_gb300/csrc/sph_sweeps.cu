@@ -1,5 +1,8 @@
 // sph_sweeps.cu -- the pair sweeps of one advection step.
 //
+//  k_list (first, once per advection step): the neighbour list of the frozen
+//         configuration -- the dual-criteria scheme of Sec. 2.3 keeps the
+//         configuration of an advection step -- read by all the sweeps.
 //  k_adv  (once per advection step): correction matrix B_i with the mirror
 //         condition at pressure buffers (a5; Sec. 2.2, 3.3), ARD viscous
 //         acceleration (a6; Sec. 2.2), k-epsilon sources and diffusion with
@@ -12,25 +15,22 @@
 //         density half update, buffer boundary values (a11) and the first
 //         half of the next sub-step.
 //
-//  k_list (once per advection step, first): the neighbour list of the
-//         frozen configuration (the dual-criteria scheme of Sec. 2.3 keeps
-//         the configuration of an advection step), read by all the sweeps.
-//
 // Work mapping: one thread per particle in cell order, grid-stride over a
-// grid sized to the resident blocks of the GPU (so a sub-step that no
-// instance takes costs one pass over ~1k blocks).  The list builder visits
-// the 3^d cells around a particle's cell; because particles are sorted by
-// cell key the cells of one row form one contiguous index range.  Candidates
-// are fetched four at a time (independent loads in flight) and tested
-// against the cut-off.  The sweeps then walk the list (entry k of particle
-// i at k * stride + i, so a warp's reads of one k are coalesced), without
-// any candidate tests.
+// grid sized to the resident blocks of the GPU (a sub-step that no instance
+// takes costs one pass over ~1k blocks).  The list builder visits the 3^d
+// cells around a particle's cell; because particles are sorted by cell key
+// the cells of one row form one contiguous index range; candidates are
+// fetched four at a time and tested against the cut-off.  The sweeps walk the
+// list (entry k of particle i at k * stride + i, so a warp's reads of one k
+// are coalesced) and gather one record per neighbour: everything a sweep
+// needs of neighbour j, written by the kernel before it (32 B in 2D FP32,
+// one sector).
 //
 // Precision: R is the sweep precision.  Pair sums, forces, k-epsilon sources,
-// volumes and pressures are evaluated in R; FP64 is used only to update the
-// FP64 master state (x, v, rho, k, eps) and to invert B.  On GB300 FP64
-// issues at a small fraction of the FP32 rate, so with R = float the FP64
-// work per particle is a few fused multiply-adds and divisions are the fast
+// volumes and pressures are evaluated in R; FP64 is used to update the FP64
+// master state (x, v, rho, k, eps) and to invert B.  On GB300 FP64 issues at a
+// small fraction of the FP32 rate, so with R = float the FP64 work per
+// particle is a few adds and conversions, and divisions are the fast
 // reciprocal form.  With R = double every operation is FP64 and IEEE.
 #include "sph_internal.cuh"
 
@@ -77,8 +77,10 @@ __device__ __forceinline__ Geo<R> make_geo(const InstDev &I) {
   return g;
 }
 
-// r_ij = x_i - x_j (minimum image when PER); returns |r_ij|^2 summed left
-// to right without contraction (the cut-off test decides membership)
+// r_ij = x_i - x_j (minimum image when PER) from the leading 4-vectors of two
+// records, whose first D components are the position; returns |r_ij|^2
+// summed left to right without contraction (the cut-off test decides
+// membership)
 template <typename R, int D, bool PER>
 __device__ __forceinline__ R pair_vec(const Geo<R> &g, const V4<R> &pi, const V4<R> &pj, R d[3]) {
   R xi[3] = {pi.x, pi.y, pi.z}, xj[3] = {pj.x, pj.y, pj.z};
@@ -98,6 +100,12 @@ __device__ __forceinline__ R pair_vec(const Geo<R> &g, const V4<R> &pi, const V4
   }
   if (D == 2) d[2] = (R)0;
   return rr;
+}
+
+// volume slot of a record's leading 4-vector: (x y V .) in 2D, (x y z V) in 3D
+template <typename R, int D>
+__device__ __forceinline__ R vol(const V4<R> &r0) {
+  return (D == 2) ? r0.z : r0.w;
 }
 
 // Wendland C2 (Sec. 2.2 kernel, support 2h): F = (dW/dr) / r
@@ -160,16 +168,17 @@ __device__ __forceinline__ void visit_cells(const InstDev &I, int cx, int cy, in
   }
 }
 
-// candidates j in [jb, je) of records P, four loads in flight; hit(j, Pj)
-// is called for every j with 0 < |r_ij|^2 < (2h)^2
+// candidates j in [jb, je) whose position leads the 4-vector P[j * stride],
+// four loads in flight; hit(j) is called for every j with
+// 0 < |r_ij|^2 < (2h)^2
 template <typename R, int D, bool PER, typename H>
 __device__ __forceinline__ void scan_range(const Geo<R> &g, const V4<R> &Pi, const V4<R> *__restrict__ P,
-                                           uint32_t jb, uint32_t je, H &&hit) {
+                                           int stride, uint32_t jb, uint32_t je, H &&hit) {
   for (uint32_t j = jb; j < je; j += 4) {
-    V4<R> q0 = P[j];
-    V4<R> q1 = (j + 1 < je) ? P[j + 1] : q0;
-    V4<R> q2 = (j + 2 < je) ? P[j + 2] : q0;
-    V4<R> q3 = (j + 3 < je) ? P[j + 3] : q0;
+    const V4<R> q0 = P[(size_t)j * stride];
+    const V4<R> q1 = (j + 1 < je) ? P[(size_t)(j + 1) * stride] : q0;
+    const V4<R> q2 = (j + 2 < je) ? P[(size_t)(j + 2) * stride] : q0;
+    const V4<R> q3 = (j + 3 < je) ? P[(size_t)(j + 3) * stride] : q0;
     R d[3];
     unsigned mask = 0;
     R rr = pair_vec<R, D, PER>(g, Pi, q0, d);
@@ -183,8 +192,7 @@ __device__ __forceinline__ void scan_range(const Geo<R> &g, const V4<R> &Pi, con
     while (mask) {
       const int k = __ffs(mask) - 1;
       mask &= mask - 1;
-      const V4<R> q = (k == 0) ? q0 : (k == 1) ? q1 : (k == 2) ? q2 : q3;
-      hit(j + (uint32_t)k, q);
+      hit(j + (uint32_t)k);
     }
   }
 }
@@ -260,31 +268,29 @@ __device__ __forceinline__ void sym_matvec(const R B[6], const R x[3], R y[3]) {
   }
 }
 
-// own B_i in sweep precision from the neighbour-facing pack; particles of
-// pressure buffers carry a marker there and read their FP64 master instead.
-// kw returns 2/3 k_i (RANS effective pressure).
+// B, kw = 2/3 k and (3D) p from a momentum record; false for the marker of a
+// pressure-buffer particle, whose B is then not in the record
 template <typename R, int D>
-__device__ __forceinline__ void own_B(const Packs<R> &pk, const Derived &der, int i, R B[6], R &kw) {
-  const V4<R> b0 = pk.Bm0[i];
-  kw = b0.w;
-  if (b0.x < (R)0) {
-    for (int c = 0; c < 6; ++c) B[c] = (R)der.B[c][i];
-    if (D == 2) B[2] = B[4] = B[5] = (R)0;
-    return;
-  }
+__device__ __forceinline__ bool mom_B(const V4<R> &m1, const V4<R> &m2, R B[6], R &kw, R &p) {
   if (D == 2) {
-    B[0] = b0.x;
-    B[3] = b0.y;
-    B[1] = b0.z;
+    // (x y V p)(Bxx Bxy Byy kw)
+    B[0] = m1.x;
+    B[3] = m1.y;
+    B[1] = m1.z;
     B[2] = B[4] = B[5] = (R)0;
+    kw = m1.w;
+    return m1.x >= (R)0;
   } else {
-    const V4<R> b1 = pk.Bm1[i];
-    B[0] = b0.x;
-    B[1] = b0.y;
-    B[2] = b0.z;
-    B[3] = b1.x;
-    B[4] = b1.y;
-    B[5] = b1.z;
+    // (x y z V)(p kw Bxx Byy)(Bzz Bxy Bxz Byz)
+    p = m1.x;
+    kw = m1.y;
+    B[0] = m1.z;
+    B[1] = m1.w;
+    B[2] = m2.x;
+    B[3] = m2.y;
+    B[4] = m2.z;
+    B[5] = m2.w;
+    return m1.z >= (R)0;
   }
 }
 
@@ -300,11 +306,12 @@ __device__ __forceinline__ R p_eff(R p, R kw, R rho0, R inv_c0sq) {
 // =========================================================================
 template <typename R, int D, bool PER>
 __device__ __forceinline__ void list_one(const SweepArgs &a, const Packs<R> &pk, const int i) {
+  constexpr int RA = RecLayout<D>::adv;
   const InstDev &I = a.inst[a.m.inst[i]];
   const Geo<R> g = make_geo<R, D>(I);
   int cx, cy, cz;
   decode_cell(I, a.keys[i], cx, cy, cz);
-  const V4<R> Pi = pk.P[0][i];
+  const V4<R> Pi = pk.adv[RA * (size_t)i];
   uint32_t *__restrict__ out = a.nl.nbr + i;
   const size_t LS = (size_t)a.nl.stride;
   const int K = a.nl.kmax;
@@ -312,9 +319,10 @@ __device__ __forceinline__ void list_one(const SweepArgs &a, const Packs<R> &pk,
   // real neighbours, then wall dummies; 0 < |r|^2 < (2h)^2 excludes i itself
   for (int set = 0; set < 2; ++set) {
     const uint32_t *offs = set == 0 ? a.off : a.woff;
-    const V4<R> *recs = set == 0 ? pk.P[0] : pk.WP;
+    const V4<R> *recs = set == 0 ? pk.adv : pk.WP;
+    const int stride = set == 0 ? RA : 1;
     visit_cells<D, PER>(I, cx, cy, cz, 1, offs, [&](uint32_t jb, uint32_t je) {
-      scan_range<R, D, PER>(g, Pi, recs, jb, je, [&](uint32_t j, const V4<R> &) {
+      scan_range<R, D, PER>(g, Pi, recs, stride, jb, je, [&](uint32_t j) {
         const int k = nr + nw;
         if (k < K) out[(size_t)k * LS] = j;
         if (set == 0)
@@ -338,25 +346,26 @@ __device__ __forceinline__ void list_one(const SweepArgs &a, const Packs<R> &pk,
 // =========================================================================
 template <typename R, int D, bool PER>
 __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, const int i) {
+  constexpr int RA = RecLayout<D>::adv;
   const Masters &m = a.m;
   const int ii = m.inst[i];
   const InstDev &I = a.inst[ii];
   const Geo<R> g = make_geo<R, D>(I);
-  int cx, cy, cz;
-  decode_cell(I, a.keys[i], cx, cy, cz);
   const uint32_t *__restrict__ Lst = a.nl.nbr + i;
   const size_t LS = (size_t)a.nl.stride;
   const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
-  const V4<R> Pi = pk.P[0][i];
-  const V4<R> Qi = pk.Q[0][i];
   const bool rans = I.rans != 0;
+  // own record: 2D (x y V vx)(vy k eps nut), 3D (x y z V)(vx vy vz k)(eps nut - -)
+  const V4<R> A0 = pk.adv[RA * (size_t)i], A1 = pk.adv[RA * (size_t)i + 1];
+  V4<R> A2 = A1;
+  if (D == 3 && rans) A2 = pk.adv[RA * (size_t)i + 2];
+  const R vi[3] = {D == 2 ? A0.w : A1.x, D == 2 ? A1.x : A1.y, D == 2 ? (R)0 : A1.z};
   const R rho0 = (R)I.rho0, nu_l = (R)I.nu_l, c0 = (R)I.c0, eta = (R)I.eta, muRk = (R)I.muR_k;
-  R nut_i = (R)0, k_i = (R)0, e_i = (R)0;
+  R k_i = (R)0, e_i = (R)0, nut_i = (R)0;
   if (rans) {
-    const V4<R> Ti = pk.T[i];
-    k_i = Ti.x;
-    e_i = Ti.y;
-    nut_i = Ti.z;
+    k_i = D == 2 ? A1.y : A1.w;
+    e_i = D == 2 ? A1.z : A2.x;
+    nut_i = D == 2 ? A1.w : A2.y;
   }
   const R mu_i = rho0 * (nu_l + nut_i);
   const R Dk_i = nu_l + nut_i * (R)(1.0 / kSigK), De_i = nu_l + nut_i * (R)(1.0 / kSigE);
@@ -377,92 +386,88 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   R dk = 0, de = 0;
 
   // real neighbours
-  {
-#pragma unroll 4
-    for (int kk = 0; kk < nr; ++kk) {
-      const uint32_t j = Lst[(size_t)kk * LS];
-      const V4<R> Pj = pk.P[0][j];
-      R d[3];
-      const R rr = pair_vec<R, D, PER>(g, Pi, Pj, d);
-      R r;
-      Ex<R>::len(rr, r);
-      const R F = kernel_F(g, r);  // dW/dr / r
-      const R V = Pj.w;
-      if (!mirror || !(local0<R, D>(mo, mn, Pj.x, Pj.y, Pj.z) < (R)0)) sym_add_outer<R, D>(A, d, -F * V);
-      const V4<R> Qj = pk.Q[0][j];
-      R vij[3] = {Qi.x - Qj.x, Qi.y - Qj.y, Qi.z - Qj.z};
-      const R f = Ex<R>::div(F * r, r + g.reg) * V;  // dW/dr / (r + 0.01h) V
-      R mu_ad = mu_i;                                // laminar: harmonic mean of equal values
-      if (rans) {
-        const V4<R> Tj = pk.T[j];
-        const R k_j = Tj.x, e_j = Tj.y, nut_j = Tj.z;
-        const R mu_j = rho0 * (nu_l + nut_j);
-        const R mut = Ex<R>::div((R)2 * mu_i * mu_j, mu_i + mu_j);
-        R ve = -(vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2]) * Ex<R>::div((R)1, r);
-        R lim = eta * (ve > (R)0 ? ve : (R)0);
-        R muR = muRk * (lim < c0 ? lim : c0);
-        mu_ad = mut > muR ? mut : muR;
-        const R FV = F * V;
+#pragma unroll 2
+  for (int kk = 0; kk < nr; ++kk) {
+    const uint32_t j = Lst[(size_t)kk * LS];
+    const V4<R> B0 = pk.adv[RA * (size_t)j], B1 = pk.adv[RA * (size_t)j + 1];
+    V4<R> B2 = B1;
+    if (D == 3 && rans) B2 = pk.adv[RA * (size_t)j + 2];
+    R d[3];
+    const R rr = pair_vec<R, D, PER>(g, A0, B0, d);
+    R r;
+    Ex<R>::len(rr, r);
+    const R F = kernel_F(g, r);  // dW/dr / r
+    const R V = vol<R, D>(B0);
+    if (!mirror || !(local0<R, D>(mo, mn, B0.x, B0.y, B0.z) < (R)0)) sym_add_outer<R, D>(A, d, -F * V);
+    const R vj[3] = {D == 2 ? B0.w : B1.x, D == 2 ? B1.x : B1.y, D == 2 ? (R)0 : B1.z};
+    const R vij[3] = {vi[0] - vj[0], vi[1] - vj[1], vi[2] - vj[2]};
+    const R f = Ex<R>::div(F * r, r + g.reg) * V;  // dW/dr / (r + 0.01h) V
+    R mu_ad = mu_i;                                // laminar: harmonic mean of equal values
+    if (rans) {
+      const R k_j = D == 2 ? B1.y : B1.w, e_j = D == 2 ? B1.z : B2.x, nut_j = D == 2 ? B1.w : B2.y;
+      const R mu_j = rho0 * (nu_l + nut_j);
+      const R mut = Ex<R>::div((R)2 * mu_i * mu_j, mu_i + mu_j);
+      R ve = -(vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2]) * Ex<R>::div((R)1, r);
+      R lim = eta * (ve > (R)0 ? ve : (R)0);
+      R muR = muRk * (lim < c0 ? lim : c0);
+      mu_ad = mut > muR ? mut : muR;
+      const R FV = F * V;
 #pragma unroll
-        for (int p = 0; p < D; ++p)
+      for (int p = 0; p < D; ++p)
 #pragma unroll
-          for (int q = 0; q < D; ++q) G[p][q] += vij[p] * d[q] * FV;
-        const R Dk_j = nu_l + nut_j * (R)(1.0 / kSigK), De_j = nu_l + nut_j * (R)(1.0 / kSigE);
-        dk += rho0 * Ex<R>::div((R)2 * Dk_i * Dk_j, Dk_i + Dk_j) * (k_i - k_j) * f;
-        de += rho0 * Ex<R>::div((R)2 * De_i * De_j, De_i + De_j) * (e_i - e_j) * f;
-      }
-#pragma unroll
-      for (int c = 0; c < D; ++c) sv[c] += mu_ad * f * vij[c];
+        for (int q = 0; q < D; ++q) G[p][q] += vij[p] * d[q] * FV;
+      const R Dk_j = nu_l + nut_j * (R)(1.0 / kSigK), De_j = nu_l + nut_j * (R)(1.0 / kSigE);
+      dk += rho0 * Ex<R>::div((R)2 * Dk_i * Dk_j, Dk_i + Dk_j) * (k_i - k_j) * f;
+      de += rho0 * Ex<R>::div((R)2 * De_i * De_j, De_i + De_j) * (e_i - e_j) * f;
     }
+#pragma unroll
+    for (int c = 0; c < D; ++c) sv[c] += mu_ad * f * vij[c];
   }
 
   // wall dummies
-  {
-#pragma unroll 4
-    for (int kk = nr; kk < nr + nw; ++kk) {
-      const uint32_t w = Lst[(size_t)kk * LS];
-      const V4<R> Wp = pk.WP[w];
-      R d[3];
-      const R rr = pair_vec<R, D, PER>(g, Pi, Wp, d);
-      R r;
-      Ex<R>::len(rr, r);
-      const R F = kernel_F(g, r);
-      const R V = Wp.w;
-      if (!mirror || !(local0<R, D>(mo, mn, Wp.x, Wp.y, Wp.z) < (R)0)) sym_add_outer<R, D>(A, d, -F * V);
-      const V4<R> Wv = pk.WV[w];
-      // no-slip: the dummy carries 2 v_wall - v_i
-      R vij[3] = {(R)2 * (Qi.x - Wv.x), (R)2 * (Qi.y - Wv.y), (R)2 * (Qi.z - Wv.z)};
-      R mu_ad = mu_i;
-      if (rans) {
-        R ve = -(vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2]) * Ex<R>::div((R)1, r);
-        R lim = eta * (ve > (R)0 ? ve : (R)0);
-        R muR = muRk * (lim < c0 ? lim : c0);
-        mu_ad = mu_i > muR ? mu_i : muR;
-        const R FV = F * V;
+  for (int kk = nr; kk < nr + nw; ++kk) {
+    const uint32_t w = Lst[(size_t)kk * LS];
+    const V4<R> Wp = pk.WP[w];
+    R d[3];
+    const R rr = pair_vec<R, D, PER>(g, A0, Wp, d);
+    R r;
+    Ex<R>::len(rr, r);
+    const R F = kernel_F(g, r);
+    const R V = Wp.w;
+    if (!mirror || !(local0<R, D>(mo, mn, Wp.x, Wp.y, Wp.z) < (R)0)) sym_add_outer<R, D>(A, d, -F * V);
+    const V4<R> Wv = pk.WV[w];
+    // no-slip: the dummy carries 2 v_wall - v_i
+    const R vij[3] = {(R)2 * (vi[0] - Wv.x), (R)2 * (vi[1] - Wv.y), (R)2 * (vi[2] - Wv.z)};
+    R mu_ad = mu_i;
+    if (rans) {
+      R ve = -(vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2]) * Ex<R>::div((R)1, r);
+      R lim = eta * (ve > (R)0 ? ve : (R)0);
+      R muR = muRk * (lim < c0 ? lim : c0);
+      mu_ad = mu_i > muR ? mu_i : muR;
+      const R FV = F * V;
 #pragma unroll
-        for (int p = 0; p < D; ++p)
+      for (int p = 0; p < D; ++p)
 #pragma unroll
-          for (int q = 0; q < D; ++q) G[p][q] += vij[p] * d[q] * FV;
-      }
-      const R f = Ex<R>::div(F * r, r + g.reg) * V;
-#pragma unroll
-      for (int c = 0; c < D; ++c) sv[c] += mu_ad * f * vij[c];
+        for (int q = 0; q < D; ++q) G[p][q] += vij[p] * d[q] * FV;
     }
+    const R f = Ex<R>::div(F * r, r + g.reg) * V;
+#pragma unroll
+    for (int c = 0; c < D; ++c) sv[c] += mu_ad * f * vij[c];
   }
 
   if (mirror) {
     // images m_j = x_j - 2 x'_0(x_j) n_b of every particle on the fluid side
     // of the open face, searched around the image of x_i (two-cell margin)
-    const R si = local0<R, D>(mo, mn, Pi.x, Pi.y, Pi.z);
-    const double q0 = (double)Pi.x - 2.0 * (double)si * mb->frame[0];
-    const double q1 = (double)Pi.y - 2.0 * (double)si * mb->frame[1];
-    const double q2 = (double)Pi.z - 2.0 * (double)si * mb->frame[2];
+    const R si = local0<R, D>(mo, mn, A0.x, A0.y, A0.z);
+    const double q0 = (double)A0.x - 2.0 * (double)si * mb->frame[0];
+    const double q1 = (double)A0.y - 2.0 * (double)si * mb->frame[1];
+    const double q2 = D == 3 ? (double)A0.z - 2.0 * (double)si * mb->frame[2] : 0.0;
     const int qx = cell_coord(I, q0, 0), qy = cell_coord(I, q1, 1), qz = D == 3 ? cell_coord(I, q2, 2) : 0;
-    auto mirror_one = [&](const V4<R> &Pj) {
+    auto mirror_one = [&](const V4<R> &Pj, R Vj) {
       const R sj = local0<R, D>(mo, mn, Pj.x, Pj.y, Pj.z);
       if (sj < (R)0) return;
       const R two_s = Ex<R>::mul((R)2, sj);
-      R xj[3] = {Pj.x, Pj.y, Pj.z}, xi[3] = {Pi.x, Pi.y, Pi.z};
+      R xj[3] = {Pj.x, Pj.y, Pj.z}, xi[3] = {A0.x, A0.y, A0.z};
       R d[3] = {0, 0, 0};
       R dd = 0;
 #pragma unroll
@@ -474,32 +479,43 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
       if (!(dd > (R)0 && dd < g.cut2)) return;
       R r;
       Ex<R>::len(dd, r);
-      sym_add_outer<R, D>(A, d, -kernel_F(g, r) * Pj.w);
+      sym_add_outer<R, D>(A, d, -kernel_F(g, r) * Vj);
     };
     for (int set = 0; set < 2; ++set) {
       const uint32_t *offs = set == 0 ? a.off : a.woff;
-      const V4<R> *recs = set == 0 ? pk.P[0] : pk.WP;
+      const V4<R> *recs = set == 0 ? pk.adv : pk.WP;
+      const int stride = set == 0 ? RA : 1;
       visit_cells<D, PER>(I, qx, qy, qz, 2, offs, [&](uint32_t jb, uint32_t je) {
-        for (uint32_t j = jb; j < je; ++j) mirror_one(recs[j]);
+        for (uint32_t j = jb; j < je; ++j) {
+          const V4<R> Pj = recs[(size_t)j * stride];
+          mirror_one(Pj, set == 0 ? vol<R, D>(Pj) : Pj.w);
+        }
       });
     }
   }
 
   // ---------------- epilogue ----------------
-  double Ad[6], B[6];
-  for (int c = 0; c < 6; ++c) Ad[c] = (double)A[c];
+  double Ad[6] = {(double)A[0], (double)A[1], 0.0, (double)A[3], 0.0, 0.0};
+  if (D == 3) {
+    Ad[2] = (double)A[2];
+    Ad[4] = (double)A[4];
+    Ad[5] = (double)A[5];
+  }
+  double B[6];
   invert_guarded<D>(Ad, B);  // FP64 inversion (one reciprocal)
   a.der.B[0][i] = B[0];
   a.der.B[1][i] = B[1];
   a.der.B[3][i] = B[3];
+  R BR[6] = {(R)B[0], (R)B[1], (R)0, (R)B[3], (R)0, (R)0};
   if (D == 3) {
     a.der.B[2][i] = B[2];
     a.der.B[4][i] = B[4];
     a.der.B[5][i] = B[5];
+    BR[2] = (R)B[2];
+    BR[4] = (R)B[4];
+    BR[5] = (R)B[5];
   }
-  R BR[6];
-  for (int c = 0; c < 6; ++c) BR[c] = (R)B[c];
-  const double rho_i = m.rho[i], mass_i = m.mass[i];
+  const double rho_i = m.rho[i];
   const R inv_rho = Ex<R>::div((R)1, (R)rho_i);
   R an[3] = {0, 0, 0};
 #pragma unroll
@@ -507,13 +523,12 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
     an[c] = (R)2 * sv[c] * inv_rho;
     a.der.an[c][i] = (double)an[c];
   }
-  V4<R> ap = {an[0] + (R)I.g[0], an[1] + (R)I.g[1], D == 3 ? an[2] + (R)I.g[2] : (R)0, (R)0};
-  pk.Ap[i] = ap;
+  pk.Ap[i] = V4<R>{an[0] + (R)I.g[0], an[1] + (R)I.g[1], D == 3 ? an[2] + (R)I.g[2] : (R)0, (R)0};
 
   R kw = (R)0;
   if (rans) {
     // grad v = -(sum v_ij (x) grad W V) B^T, (p, q) = dv_p / dx_q
-    R Bf[3][3] = {{BR[0], BR[3], BR[4]}, {BR[3], BR[1], BR[5]}, {BR[4], BR[5], BR[2]}};
+    const R Bf[3][3] = {{BR[0], BR[3], BR[4]}, {BR[3], BR[1], BR[5]}, {BR[4], BR[5], BR[2]}};
     R tr = 0, prod = 0;
     R gv[3][3];
 #pragma unroll
@@ -544,40 +559,36 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
     m.nut[i] = (double)Ex<R>::div((R)kCmu * k1r * k1r, e1r);
     kw = (R)(2.0 / 3.0) * k1r;
   }
-  // neighbour-facing B pack; pressure-buffer particles are marked so that
-  // neighbours use their own B_i (the condition B_k = B_i, Sec. 3.3)
-  if (D == 2) {
-    V4<R> b0 = {BR[0], BR[3], BR[1], kw};
-    if (mirror) b0.x = (R)-1;
-    pk.Bm0[i] = b0;
-  } else {
-    V4<R> b0 = {BR[0], BR[1], BR[2], kw};
-    V4<R> b1 = {BR[3], BR[4], BR[5], (R)0};
-    if (mirror) b0.x = (R)-1;
-    pk.Bm0[i] = b0;
-    pk.Bm1[i] = b1;
-  }
   // first half of sub-step 0 (a8): rho += dt/2 drho; p = c0^2 (rho - rho0);
-  // x += dt/2 v
+  // x += dt/2 v.  The pressure master keeps the value of the step's last
+  // first half, so only that one is stored.
   const double hdt = 0.5 * I.dt;
   const double rho = rho_i + hdt * m.drho[i];
   const R p = (R)(rho - I.rho0) * (R)I.c0sq;
   m.rho[i] = rho;
-  m.p[i] = (double)p;
+  if (I.n_ac == 1) m.p[i] = (double)p;
 #pragma unroll
   for (int c = 0; c < D; ++c) m.x[c][i] = m.x[c][i] + hdt * m.v[c][i];
-  V4<R> P1 = {Pi.x, Pi.y, Pi.z, Ex<R>::div((R)mass_i, (R)rho)};
-  V4<R> Q1 = {Qi.x, Qi.y, Qi.z, p};
-  pk.P[1][i] = P1;
-  pk.Q[1][i] = Q1;
+  // momentum record; pressure-buffer particles are marked so that their
+  // neighbours use their own B (the condition B_k = B_i, Sec. 3.3)
+  const R V = Ex<R>::div((R)m.mass[i], (R)rho);
+  const R bxx = mirror ? (R)-1 : BR[0];
+  if (D == 2) {
+    pk.mom[2 * (size_t)i] = V4<R>{A0.x, A0.y, V, p};
+    pk.mom[2 * (size_t)i + 1] = V4<R>{bxx, BR[3], BR[1], kw};
+  } else {
+    pk.mom[3 * (size_t)i] = V4<R>{A0.x, A0.y, A0.z, V};
+    pk.mom[3 * (size_t)i + 1] = V4<R>{p, kw, bxx, BR[1]};
+    pk.mom[3 * (size_t)i + 2] = V4<R>{BR[2], BR[3], BR[4], BR[5]};
+  }
 }
 
 // =========================================================================
 // momentum sweep (a9)
 // =========================================================================
 template <typename R, int D, bool PER>
-__device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, const V4<R> *__restrict__ P,
-                                        const V4<R> *__restrict__ Q, V4<R> *__restrict__ Qout, const int i) {
+__device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, const int i) {
+  constexpr int RM = RecLayout<D>::mom;
   const Masters &m = a.m;
   const int ii = m.inst[i];
   const InstDev &I = a.inst[ii];
@@ -586,77 +597,63 @@ __device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, 
   const uint32_t *__restrict__ Lst = a.nl.nbr + i;
   const size_t LS = (size_t)a.nl.stride;
   const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
-  const V4<R> Pi = P[i];
-  const R p_i = Q[i].w;
   const bool rans = I.rans != 0;
   const R rho0 = (R)I.rho0, inv_c0sq = (R)(1.0 / I.c0sq);
-  R Bi[6], kw_i;
-  own_B<R, D>(pk, a.der, i, Bi, kw_i);
+  const V4<R> M0 = pk.mom[RM * (size_t)i], M1 = pk.mom[RM * (size_t)i + 1];
+  V4<R> M2 = M1;
+  if (D == 3) M2 = pk.mom[RM * (size_t)i + 2];
+  R Bi[6], kw_i, p_i = M0.w;
+  if (!mom_B<R, D>(M1, M2, Bi, kw_i, p_i)) {  // pressure-buffer particle: FP64 master B
+    for (int c = 0; c < 6; ++c) Bi[c] = (R)a.der.B[c][i];
+    if (D == 2) Bi[2] = Bi[4] = Bi[5] = (R)0;
+  }
   const R pe_i = rans ? p_eff(p_i, kw_i, rho0, inv_c0sq) : p_i;
 
   R S1[3] = {0, 0, 0}, Cb[3] = {0, 0, 0}, S2[3] = {0, 0, 0}, Ct[3] = {0, 0, 0};
-  {
-#pragma unroll 4
-    for (int kk = 0; kk < nr; ++kk) {
-      const uint32_t j = Lst[(size_t)kk * LS];
-      const V4<R> Pj = P[j];
-      R d[3];
-      const R rr = pair_vec<R, D, PER>(g, Pi, Pj, d);
-      R r;
-      Ex<R>::len(rr, r);
-      const R FV = kernel_F(g, r) * Pj.w;  // V_j dW/dr / r
-      R gw[3] = {FV * d[0], FV * d[1], FV * d[2]};  // V_j grad_i W_ij
-      const R p_j = Q[j].w;
-      const V4<R> b0 = pk.Bm0[j];
-      const R pe_j = rans ? p_eff(p_j, b0.w, rho0, inv_c0sq) : p_j;
-      if (b0.x < (R)0) {
+#pragma unroll 2
+  for (int kk = 0; kk < nr; ++kk) {
+    const uint32_t j = Lst[(size_t)kk * LS];
+    const V4<R> N0 = pk.mom[RM * (size_t)j], N1 = pk.mom[RM * (size_t)j + 1];
+    V4<R> N2 = N1;
+    if (D == 3) N2 = pk.mom[RM * (size_t)j + 2];
+    R d[3];
+    const R rr = pair_vec<R, D, PER>(g, M0, N0, d);
+    R r;
+    Ex<R>::len(rr, r);
+    const R FV = kernel_F(g, r) * vol<R, D>(N0);       // V_j dW/dr / r
+    const R gw[3] = {FV * d[0], FV * d[1], FV * d[2]};  // V_j grad_i W_ij
+    R Bj[6], kw_j, p_j = N0.w;
+    const bool own = mom_B<R, D>(N1, N2, Bj, kw_j, p_j);
+    const R pe_j = rans ? p_eff(p_j, kw_j, rho0, inv_c0sq) : p_j;
+    if (own) {
+      R bg[3];
+      sym_matvec<R, D>(Bj, gw, bg);
 #pragma unroll
-        for (int c = 0; c < D; ++c) Cb[c] += gw[c];
-      } else {
-        R Bj[6];
-        if (D == 2) {
-          Bj[0] = b0.x;
-          Bj[3] = b0.y;
-          Bj[1] = b0.z;
-          Bj[2] = Bj[4] = Bj[5] = (R)0;
-        } else {
-          const V4<R> b1 = pk.Bm1[j];
-          Bj[0] = b0.x;
-          Bj[1] = b0.y;
-          Bj[2] = b0.z;
-          Bj[3] = b1.x;
-          Bj[4] = b1.y;
-          Bj[5] = b1.z;
-        }
-        R bg[3];
-        sym_matvec<R, D>(Bj, gw, bg);
+      for (int c = 0; c < D; ++c) S1[c] += bg[c];
+    } else {
 #pragma unroll
-        for (int c = 0; c < D; ++c) S1[c] += bg[c];
-      }
+      for (int c = 0; c < D; ++c) Cb[c] += gw[c];  // pressure-buffer neighbour: B^_j = B_i
+    }
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        S2[c] += pe_j * gw[c];
-        Ct[c] += gw[c];
-      }
+    for (int c = 0; c < D; ++c) {
+      S2[c] += pe_j * gw[c];
+      Ct[c] += gw[c];
     }
   }
-  {
-#pragma unroll 4
-    for (int kk = nr; kk < nr + nw; ++kk) {
-      const uint32_t w = Lst[(size_t)kk * LS];
-      const V4<R> Wp = pk.WP[w];
-      R d[3];
-      const R rr = pair_vec<R, D, PER>(g, Pi, Wp, d);
-      R r;
-      Ex<R>::len(rr, r);
-      const R FV = kernel_F(g, r) * Wp.w;
+  for (int kk = nr; kk < nr + nw; ++kk) {
+    const uint32_t w = Lst[(size_t)kk * LS];
+    const V4<R> Wp = pk.WP[w];
+    R d[3];
+    const R rr = pair_vec<R, D, PER>(g, M0, Wp, d);
+    R r;
+    Ex<R>::len(rr, r);
+    const R FV = kernel_F(g, r) * Wp.w;
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        const R gv = FV * d[c];
-        Cb[c] += gv;         // wall dummy: B^_j = B_i
-        S2[c] += pe_i * gv;  // wall dummy: p_j = p_i
-        Ct[c] += gv;
-      }
+    for (int c = 0; c < D; ++c) {
+      const R gv = FV * d[c];
+      Cb[c] += gv;         // wall dummy: B^_j = B_i
+      S2[c] += pe_i * gv;  // wall dummy: p_j = p_i
+      Ct[c] += gv;
     }
   }
   // a = -(1/rho_i) (p_i (S1 + B_i Cb) + B_i S2) [+ (2 p_ob / rho_i) B_i Ct]
@@ -692,8 +689,12 @@ __device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, 
     m.x[c][i] = m.x[c][i] + hdt * v;
     vo[c] = (R)v;
   }
-  V4<R> Qo = {vo[0], vo[1], vo[2], p_i};
-  Qout[i] = Qo;
+  // continuity record: 2D (x y V p)(vx vy - -), 3D (x y z V)(p vx vy vz)
+  pk.cont[2 * (size_t)i] = M0;
+  if (D == 2)
+    pk.cont[2 * (size_t)i + 1] = V4<R>{vo[0], vo[1], (R)0, (R)0};
+  else
+    pk.cont[2 * (size_t)i + 1] = V4<R>{p_i, vo[0], vo[1], vo[2]};
 }
 
 // =========================================================================
@@ -701,9 +702,8 @@ __device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, 
 // half step (a8)
 // =========================================================================
 template <typename R, int D, bool PER>
-__device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk, const V4<R> *__restrict__ P,
-                                         const V4<R> *__restrict__ Q, V4<R> *__restrict__ Pout,
-                                         V4<R> *__restrict__ Qout, const int i) {
+__device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk, const int i) {
+  constexpr int RM = RecLayout<D>::mom;
   const Masters &m = a.m;
   const int ii = m.inst[i];
   const InstDev &I = a.inst[ii];
@@ -712,40 +712,37 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
   const uint32_t *__restrict__ Lst = a.nl.nbr + i;
   const size_t LS = (size_t)a.nl.stride;
   const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
-  const V4<R> Pi = P[i];
-  const V4<R> Qi = Q[i];
+  const V4<R> C0 = pk.cont[2 * (size_t)i], C1 = pk.cont[2 * (size_t)i + 1];
+  const R vi[3] = {D == 2 ? C1.x : C1.y, D == 2 ? C1.y : C1.z, D == 2 ? (R)0 : C1.w};
+  const R p_i = D == 2 ? C0.w : C1.x;
   const R inv_rc = (R)I.inv_rc0;
   // drho_i / rho_i = sum_j [v_ij . r_ij / r + (p_i - p_j) / (rho0 c0)] dW/dr V_j
   R sum = 0;
-  {
-#pragma unroll 4
-    for (int kk = 0; kk < nr; ++kk) {
-      const uint32_t j = Lst[(size_t)kk * LS];
-      const V4<R> Pj = P[j];
-      R d[3];
-      const R rr = pair_vec<R, D, PER>(g, Pi, Pj, d);
-      R r;
-      Ex<R>::len(rr, r);
-      const R FV = kernel_F(g, r) * Pj.w;
-      const V4<R> Qj = Q[j];
-      const R vd = (Qi.x - Qj.x) * d[0] + (Qi.y - Qj.y) * d[1] + (Qi.z - Qj.z) * d[2];
-      sum += (vd + (Qi.w - Qj.w) * inv_rc * r) * FV;
-    }
+#pragma unroll 2
+  for (int kk = 0; kk < nr; ++kk) {
+    const uint32_t j = Lst[(size_t)kk * LS];
+    const V4<R> N0 = pk.cont[2 * (size_t)j], N1 = pk.cont[2 * (size_t)j + 1];
+    R d[3];
+    const R rr = pair_vec<R, D, PER>(g, C0, N0, d);
+    R r;
+    Ex<R>::len(rr, r);
+    const R FV = kernel_F(g, r) * vol<R, D>(N0);
+    const R vj[3] = {D == 2 ? N1.x : N1.y, D == 2 ? N1.y : N1.z, D == 2 ? (R)0 : N1.w};
+    const R p_j = D == 2 ? N0.w : N1.x;
+    const R vd = (vi[0] - vj[0]) * d[0] + (vi[1] - vj[1]) * d[1] + (vi[2] - vj[2]) * d[2];
+    sum += (vd + (p_i - p_j) * inv_rc * r) * FV;
   }
-  {
-#pragma unroll 4
-    for (int kk = nr; kk < nr + nw; ++kk) {
-      const uint32_t w = Lst[(size_t)kk * LS];
-      const V4<R> Wp = pk.WP[w];
-      R d[3];
-      const R rr = pair_vec<R, D, PER>(g, Pi, Wp, d);
-      R r;
-      Ex<R>::len(rr, r);
-      const V4<R> Wv = pk.WV[w];
-      // dummy velocity 2 v_wall - v_i, dummy pressure p_i
-      const R vd = (R)2 * ((Qi.x - Wv.x) * d[0] + (Qi.y - Wv.y) * d[1] + (Qi.z - Wv.z) * d[2]);
-      sum += vd * kernel_F(g, r) * Wp.w;
-    }
+  for (int kk = nr; kk < nr + nw; ++kk) {
+    const uint32_t w = Lst[(size_t)kk * LS];
+    const V4<R> Wp = pk.WP[w];
+    R d[3];
+    const R rr = pair_vec<R, D, PER>(g, C0, Wp, d);
+    R r;
+    Ex<R>::len(rr, r);
+    const V4<R> Wv = pk.WV[w];
+    // dummy velocity 2 v_wall - v_i, dummy pressure p_i
+    const R vd = (R)2 * ((vi[0] - Wv.x) * d[0] + (vi[1] - Wv.y) * d[1] + (vi[2] - Wv.z) * d[2]);
+    sum += vd * kernel_F(g, r) * Wp.w;
   }
   const double hdt = 0.5 * I.dt;
   const double rho_i = m.rho[i];
@@ -754,14 +751,15 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
   double rho = rho_i + hdt * drho;
   m.rho[i] = rho;
   const int lab = m.label[i];
+  bool kw_reset = false;
+  R kw_bc = (R)0;
   if (lab > 0 && lab <= I.nbuf) {
     const BufDev &b = a.buf[I.buf0 + lab - 1];
     apply_bc(I, b, m, i, a.step, (uint32_t)a.sub);
     rho = m.rho[i];
     if (I.rans && b.turb == SPH_TURB_FREESTREAM) {
-      V4<R> b0 = pk.Bm0[i];
-      b0.w = (R)((2.0 / 3.0) * b.k_in);
-      pk.Bm0[i] = b0;
+      kw_reset = true;
+      kw_bc = (R)((2.0 / 3.0) * b.k_in);
     }
   }
   double v[3] = {m.v[0][i], m.v[1][i], D == 3 ? m.v[2][i] : 0.0};
@@ -770,17 +768,30 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
   for (int c = 0; c < D; ++c) bad |= !isfinite(v[c]);
   if (bad) set_status(a.status, SPH_ERR_NONFINITE);
   if (a.sub + 1 < I.n_ac) {
-    // first half of the next sub-step
+    // first half of the next sub-step and the momentum record it reads
+    // (B and kw stay from the advection sweep unless a free-stream buffer
+    // reset k)
     rho = rho + hdt * drho;
     const R p = (R)(rho - I.rho0) * (R)I.c0sq;
     m.rho[i] = rho;
-    m.p[i] = (double)p;
+    if (a.sub + 2 == I.n_ac) m.p[i] = (double)p;  // the step's last first half
 #pragma unroll
     for (int c = 0; c < D; ++c) m.x[c][i] = m.x[c][i] + hdt * v[c];
-    V4<R> Po = {Pi.x, Pi.y, Pi.z, Ex<R>::div((R)m.mass[i], (R)rho)};
-    V4<R> Qo = {(R)v[0], (R)v[1], (R)v[2], p};
-    Pout[i] = Po;
-    Qout[i] = Qo;
+    const R Vn = Ex<R>::div((R)m.mass[i], (R)rho);
+    if (D == 2) {
+      pk.mom[2 * (size_t)i] = V4<R>{C0.x, C0.y, Vn, p};
+      if (kw_reset) {
+        V4<R> r1 = pk.mom[2 * (size_t)i + 1];
+        r1.w = kw_bc;
+        pk.mom[2 * (size_t)i + 1] = r1;
+      }
+    } else {
+      pk.mom[RM * (size_t)i] = V4<R>{C0.x, C0.y, C0.z, Vn};
+      V4<R> r1 = pk.mom[RM * (size_t)i + 1];
+      r1.x = p;
+      if (kw_reset) r1.y = kw_bc;
+      pk.mom[RM * (size_t)i + 1] = r1;
+    }
   }
 }
 
@@ -802,19 +813,19 @@ __global__ void __launch_bounds__(kBlock) k_adv(SweepArgs a, Packs<R> pk) {
 }
 
 template <typename R, int D, bool PER>
-__global__ void __launch_bounds__(kBlock) k_mom(SweepArgs a, Packs<R> pk, int pin, int qin, int qout) {
+__global__ void __launch_bounds__(kBlock) k_mom(SweepArgs a, Packs<R> pk) {
   if (a.sub >= a.cnt->n_ac_all) return;  // no instance takes this sub-step
   const int n = a.cnt->n_live;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    mom_one<R, D, PER>(a, pk, pk.P[pin], pk.Q[qin], pk.Q[qout], i);
+    mom_one<R, D, PER>(a, pk, i);
 }
 
 template <typename R, int D, bool PER>
-__global__ void __launch_bounds__(kBlock) k_cont(SweepArgs a, Packs<R> pk, int pin, int qin, int pout, int qout) {
+__global__ void __launch_bounds__(kBlock) k_cont(SweepArgs a, Packs<R> pk) {
   if (a.sub >= a.cnt->n_ac_all) return;
   const int n = a.cnt->n_live;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    cont_one<R, D, PER>(a, pk, pk.P[pin], pk.Q[qin], pk.P[pout], pk.Q[qout], i);
+    cont_one<R, D, PER>(a, pk, i);
 }
 
 // =========================================================================
@@ -896,9 +907,9 @@ static int resident_grid(K kernel, int max_n) {
   return need < per_gpu ? need : per_gpu;
 }
 
+// which: 0 advection, 1 momentum, 2 continuity, 3 neighbour list
 template <typename R, int D, bool PER>
-static void launch_sweeps_impl(int which, const SweepArgs &a, Packs<R> &pk, int max_n, int sub, cudaStream_t st) {
-  const int pc = (sub % 2 == 0) ? 1 : 0;
+static void launch_sweeps_impl(int which, const SweepArgs &a, Packs<R> &pk, int max_n, cudaStream_t st) {
   if (which == 3) {
     auto k = k_list<R, D, PER>;
     k<<<resident_grid(k, max_n), kBlock, 0, st>>>(a, pk);
@@ -907,60 +918,58 @@ static void launch_sweeps_impl(int which, const SweepArgs &a, Packs<R> &pk, int 
     k<<<resident_grid(k, max_n), kBlock, 0, st>>>(a, pk);
   } else if (which == 1) {
     auto k = k_mom<R, D, PER>;
-    k<<<resident_grid(k, max_n), kBlock, 0, st>>>(a, pk, pc, 1, 0);
+    k<<<resident_grid(k, max_n), kBlock, 0, st>>>(a, pk);
   } else {
     auto k = k_cont<R, D, PER>;
-    k<<<resident_grid(k, max_n), kBlock, 0, st>>>(a, pk, pc, 0, 1 - pc, 1);
+    k<<<resident_grid(k, max_n), kBlock, 0, st>>>(a, pk);
   }
 }
 
-// Pack ping-pong: the advection sweep leaves P[1], Q[1].  Sub-step s reads
-// P[pc] with pc = 1 for even s, 0 for odd s; momentum reads Q[1] and writes
-// Q[0]; continuity reads Q[0], writes P[1 - pc] and Q[1].
 template <typename R>
-static void launch_sweeps(int which, const SweepArgs &a, void *packs, int dim, int max_n, int sub, cudaStream_t st) {
+static void launch_sweeps(int which, const SweepArgs &a, void *packs, int dim, int max_n, cudaStream_t st) {
   Packs<R> &pk = *(Packs<R> *)packs;
   if (dim == 2) {
     if (a.any_periodic)
-      launch_sweeps_impl<R, 2, true>(which, a, pk, max_n, sub, st);
+      launch_sweeps_impl<R, 2, true>(which, a, pk, max_n, st);
     else
-      launch_sweeps_impl<R, 2, false>(which, a, pk, max_n, sub, st);
+      launch_sweeps_impl<R, 2, false>(which, a, pk, max_n, st);
   } else {
     if (a.any_periodic)
-      launch_sweeps_impl<R, 3, true>(which, a, pk, max_n, sub, st);
+      launch_sweeps_impl<R, 3, true>(which, a, pk, max_n, st);
     else
-      launch_sweeps_impl<R, 3, false>(which, a, pk, max_n, sub, st);
+      launch_sweeps_impl<R, 3, false>(which, a, pk, max_n, st);
   }
 }
 
 void launch_neighbour_list(const SweepArgs &a, void *packs, int prec, int dim, int max_n, cudaStream_t st) {
   if (prec == SPH_PREC_FP32)
-    launch_sweeps<float>(3, a, packs, dim, max_n, 0, st);
+    launch_sweeps<float>(3, a, packs, dim, max_n, st);
   else
-    launch_sweeps<double>(3, a, packs, dim, max_n, 0, st);
+    launch_sweeps<double>(3, a, packs, dim, max_n, st);
 }
 
 void launch_advection_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n, cudaStream_t st) {
   if (prec == SPH_PREC_FP32)
-    launch_sweeps<float>(0, a, packs, dim, max_n, 0, st);
+    launch_sweeps<float>(0, a, packs, dim, max_n, st);
   else
-    launch_sweeps<double>(0, a, packs, dim, max_n, 0, st);
+    launch_sweeps<double>(0, a, packs, dim, max_n, st);
 }
 
-void launch_momentum_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n, int sub,
+// the sub-step index travels in SweepArgs::sub
+void launch_momentum_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n, int,
                            cudaStream_t st) {
   if (prec == SPH_PREC_FP32)
-    launch_sweeps<float>(1, a, packs, dim, max_n, sub, st);
+    launch_sweeps<float>(1, a, packs, dim, max_n, st);
   else
-    launch_sweeps<double>(1, a, packs, dim, max_n, sub, st);
+    launch_sweeps<double>(1, a, packs, dim, max_n, st);
 }
 
-void launch_continuity_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n, int sub,
+void launch_continuity_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n, int,
                              cudaStream_t st) {
   if (prec == SPH_PREC_FP32)
-    launch_sweeps<float>(2, a, packs, dim, max_n, sub, st);
+    launch_sweeps<float>(2, a, packs, dim, max_n, st);
   else
-    launch_sweeps<double>(2, a, packs, dim, max_n, sub, st);
+    launch_sweeps<double>(2, a, packs, dim, max_n, st);
 }
 
 void launch_debug_pairs(const SweepArgs &a, const double *wx, const double *wy, const double *wz,

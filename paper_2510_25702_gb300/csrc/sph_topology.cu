@@ -80,13 +80,15 @@ __device__ __forceinline__ void permute_one(const TopoArgs &a, const Packs<R> &p
     if (box_contains(B, I.dim, x, y, z)) lab = B.local_id + 1;
   }
   D.label[t] = lab;
-  V4<R> P = {(R)x, (R)y, (R)z, (R)mass / (R)rho};
-  V4<R> Q = {(R)vx, (R)vy, (R)vz, (R)S.p[s]};
-  pk.P[0][t] = P;
-  pk.Q[0][t] = Q;
-  if (I.rans) {
-    V4<R> T = {(R)k, (R)eps, (R)nut, (R)0};
-    pk.T[t] = T;
+  // advection-sweep record of this particle
+  const R V = (R)mass / (R)rho;
+  if (I.dim == 2) {
+    pk.adv[2 * (size_t)t] = V4<R>{(R)x, (R)y, V, (R)vx};
+    pk.adv[2 * (size_t)t + 1] = V4<R>{(R)vy, (R)k, (R)eps, (R)nut};
+  } else {
+    pk.adv[3 * (size_t)t] = V4<R>{(R)x, (R)y, (R)z, V};
+    pk.adv[3 * (size_t)t + 1] = V4<R>{(R)vx, (R)vy, (R)vz, (R)k};
+    pk.adv[3 * (size_t)t + 2] = V4<R>{(R)eps, (R)nut, (R)0, (R)0};
   }
   // |v|^2 with the plain left-to-right sum, nu_t
   double v2 = dmul(vx, vx);
