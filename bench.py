@@ -40,7 +40,24 @@ def workload(name: str, seed: int = 2):
         return cases.turbulent_channel(length=0.6, height=0.2, dp=0.005, seed=seed)
     if name == "poiseuille":
         return cases.poiseuille_channel(seed=seed)
+    if name == "batched_channels":
+        return cases.batched_channels(seed=3 + 100 * (seed - 2))
+    if name == "plane_jet":
+        return cases.plane_jet(dp=0.002, seed=seed + 2)
+    if name == "mixer_3d":
+        return cases.mixer_3d(dp=0.01, seed=seed + 4)
     raise ValueError(name)
+
+
+def as_list(case):
+    return list(case) if isinstance(case, (list, tuple)) else [case]
+
+
+def describe(case):
+    """(name, dim, rans, walls) of a workload that may be a batch of instances."""
+    cs = as_list(case)
+    name = cs[0].name if len(cs) == 1 else f"batched_channels_{len(cs)}x ({sum(c.n for c in cs)} particles)"
+    return name, cs[0].dim, any(c.rans for c in cs), sum(c.nw for c in cs)
 
 
 def peaks():
@@ -134,6 +151,12 @@ def sample_case(work: str):
 
     if work == "turbulent_channel":
         return cases.turbulent_channel(length=0.75, height=2.0, dp=0.005, seed=2)
+    if work == "batched_channels":
+        return cases.batched_channels()[5]
+    if work == "plane_jet":
+        return cases.plane_jet(dp=0.002, box=0.4)
+    if work == "mixer_3d":
+        return cases.mixer_3d(dp=0.02)
     return workload(work)
 
 
@@ -175,8 +198,8 @@ def run_reference(args, rank: int):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": workload(args.workload).name, "sample": case.name, "particles": case.n,
-                       "rans": True},
+            "config": {"workload": describe(workload(args.workload))[0], "sample": case.name,
+                       "particles": case.n, "rans": bool(case.rans)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -192,6 +215,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison run")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default sweep block sizes")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -225,7 +249,13 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    wname, wdim, wrans, wwalls = describe(case)
     sim.step(args.warmup)
+    tuned = None
+    if not args.no_tune:
+        # sweep block sizes, cached per (GPU, workload shape) next to the build
+        tuned, hit = sim.autotune(steps=3, cache_path=os.path.join(os.path.dirname(_b.LIB), "autotune.txt"))
+        tuned = {"blocks": dict(zip(("list", "adv", "mom", "cont"), tuned)), "from_cache": hit}
     s0 = sim.stats()
     n0 = s0["n"]
     sim.set_profiling(2)
@@ -256,10 +286,25 @@ def main():
     dom = max(("advection_sweep", "momentum_sweep", "continuity_sweep"), key=lambda s: stages[s][0])
     dom_ms, dom_n = stages[dom]
     R = 4 if args.precision == "fp32" else 8
-    per_particle = algorithmic_bytes(dom, case.dim, R, case.rans)
+    per_particle = algorithmic_bytes(dom, wdim, R, wrans)
     nbar = 0.5 * (n0 + n1)
     achieved = per_particle * nbar / (dom_ms / dom_n * 1e-3) / 1e9
     peak, peak_kind = peaks()
+
+    # the same steps replayed from captured CUDA graphs (no stage events)
+    sim.set_graph(True)
+    sim.step(2)
+    torch.cuda.synchronize()
+    ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0 = sim.stats()
+    ga.record(stream)
+    sim.step(args.steps)
+    gb.record(stream)
+    torch.cuda.synchronize()
+    g_ms = ga.elapsed_time(gb)
+    g1 = sim.stats()
+    graph = {"value": 0.5 * (g0["n"] + g1["n"]) * args.steps / (g_ms * 1e-3), "ms_per_step": g_ms / args.steps}
+    sim.set_graph(False)
 
     # end to end through the C ABI: per step the inlet profile goes host ->
     # device (sph_set_profile), the step runs, the statistics come back
@@ -279,6 +324,8 @@ def main():
     fp64 = None
     if not args.no_fp64 and args.precision == "fp32" and rank == 0:
         sim64 = sph.Simulation(case, precision="fp64")
+        if tuned:
+            sim64.autotune(steps=3, cache_path=os.path.join(os.path.dirname(_b.LIB), "autotune.txt"))
         sim64.step(args.warmup)
         k64 = max(5, args.steps // 4)
         torch.cuda.synchronize()
@@ -301,7 +348,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
             "data": "synthetic",
-            "config": {"workload": case.name, "particles": int(nbar), "walls": case.nw, "rans": bool(case.rans),
+            "config": {"workload": wname, "particles": int(nbar), "walls": wwalls, "rans": bool(wrans),
                        "sweeps": args.precision, "integration": "f64", "sub_steps": st["n_ac"],
                        "l2": f"working set {st['device_bytes'] / 2**20:.0f} MiB > 129 MB L2, no flush",
                        "parallelism": f"replicas x{world}"},
@@ -310,7 +357,7 @@ def main():
                          "bytes_per_particle": per_particle, "avg_launch_ms": dom_ms / dom_n},
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "fp64_value": fp64, "fp32_over_fp64": (value / fp64) if fp64 else None,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "graph": graph, "autotune": tuned,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -236,6 +236,52 @@ int sph_get_stage_times(sph_ctx *ctx, double *ms_total, int64_t *launches, int32
                         int32_t *n_stages);
 const char *sph_stage_name(int32_t stage);
 
+/* CUDA-graph stepping (batching pattern; no counterpart in the paper).
+   With enable != 0, sph_step replays one captured graph per advection step
+   instead of enqueuing its kernels one by one: two graphs are captured on
+   first use (the FP64 master arrays alternate between two copies from step
+   to step), on a private capture stream, and launched on the context's
+   stream.  The first step after enabling runs uncaptured.  Results are
+   identical to uncaptured stepping; stage timing is not recorded for
+   replayed steps.  enable = 0 returns to uncaptured stepping (the graphs
+   are kept).  Errors: SPH_ERR_CUDA if capture or instantiation fails. */
+int sph_set_graph(sph_ctx *ctx, int32_t enable);
+
+/* Threads per block of the four pair-sweep kernels, in the order
+   SPH_SWEEP_LIST, SPH_SWEEP_ADV, SPH_SWEEP_MOM, SPH_SWEEP_CONT; each 64, 128
+   (the default) or 256, else SPH_ERR_ARG.  Drops captured graphs. */
+#define SPH_SWEEP_LIST 0
+#define SPH_SWEEP_ADV 1
+#define SPH_SWEEP_MOM 2
+#define SPH_SWEEP_CONT 3
+int sph_set_launch(sph_ctx *ctx, const int32_t block[4]);
+int sph_get_launch(sph_ctx *ctx, int32_t block[4]);
+
+/* Autotuner of the sweep block sizes (no counterpart in the paper).  Looks
+   up the key (GPU name and SM count, dimension, precision, instances, live
+   particles, walls, RANS, sub-step bound) in the text file cache_path (may
+   be NULL: no cache); on a miss it saves the state, times each sweep kernel
+   at 64, 128 and 256 threads per block over `steps` advection steps per
+   trial (one more untimed), restores the state, applies the fastest choice
+   and appends "key b_list b_adv b_mom b_cont" to the file.  The state after
+   the call equals the state before it.  block_out (may be NULL) receives
+   the four block sizes; *from_cache (may be NULL) 1 on a cache hit. */
+int sph_autotune(sph_ctx *ctx, int32_t steps, const char *cache_path, int32_t block_out[4],
+                 int32_t *from_cache);
+
+/* Snapshots of the particle state in device memory (checkpointing; no
+   counterpart in the paper).  sph_save_state copies the live state (FP64
+   masters, pending cell keys, counters, instance table incl. time and step
+   counter, uid counters, B and viscous acceleration of the last step) into
+   a new device allocation and returns its slot; sph_restore_state copies it
+   back (stream-ordered), after which stepping reproduces the steps taken
+   from the saved state bit for bit.  Buffer descriptions and profiles are
+   not part of a snapshot.  sph_drop_state frees a slot; sph_destroy frees
+   all.  Errors: SPH_ERR_ALLOC, SPH_ERR_ARG (unknown slot). */
+int sph_save_state(sph_ctx *ctx, int32_t *slot_out);
+int sph_restore_state(sph_ctx *ctx, int32_t slot);
+int sph_drop_state(sph_ctx *ctx, int32_t slot);
+
 /* Neighbour pairs of the configuration at the current positions
    (0 < |r_ij|^2 < (2h)^2 in FP64, Sec. 2.4.1 cell-linked list): rows
    (uid_i, uid_j or wall index, is_wall, instance).  Writes up to max rows

@@ -14,7 +14,10 @@
 #include <array>
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -86,6 +89,29 @@ struct sph_ctx {
   size_t ev_used = 0;
   double stage_ms[SPH_N_STAGES] = {0};
   int64_t stage_n[SPH_N_STAGES] = {0};
+  // threads per block of the sweeps: list, advection, momentum, continuity
+  int32_t blk[4] = {128, 128, 128, 128};
+  // CUDA-graph stepping: one executable graph per master-copy parity
+  bool use_graph = false;
+  bool graph_warm = false;  // an uncaptured step ran since the last change
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int64_t graph_kernels[2] = {0, 0};
+  // state snapshots: one device allocation each
+  struct Snap {
+    void *mem = nullptr;
+    size_t bytes = 0;
+    int64_t step = 0;
+  };
+  std::vector<Snap> snaps;
+
+  void drop_graphs() {
+    for (int q = 0; q < 2; ++q) {
+      if (gexec[q]) cudaGraphExecDestroy(gexec[q]);
+      gexec[q] = nullptr;
+    }
+    graph_warm = false;
+  }
 
   int prof_begin(int stage) {
     if (!prof) return -1;
@@ -166,13 +192,13 @@ struct sph_ctx {
     a.sentinel = ncell;
     a.ninst = ninst;
     a.n_ac_max = n_ac_max;
-    a.step = step;
     a.capacity = cap;
     return a;
   }
 
-  SweepArgs sweep(int sub) {
+  SweepArgs sweep(int sub, int which) {
     SweepArgs a{};
+    a.block = blk[which];
     a.inst = d_inst;
     a.buf = d_buf;
     a.m = M[cur];
@@ -183,7 +209,6 @@ struct sph_ctx {
     a.woff = woff;
     a.cnt = cnt;
     a.status = &cnt->status;
-    a.step = step;
     a.sub = sub;
     a.any_periodic = 0;
     for (const InstDev &I : inst) a.any_periodic |= I.periodic[0] | I.periodic[1] | I.periodic[2];
@@ -196,6 +221,26 @@ struct sph_ctx {
 // cell size, cut-off, lengths and boundary values match the plain
 // definitions bit for bit)
 // ------------------------------------------------------------------------
+template <typename R>
+static void fill_sweep_const(const InstDev &I, SweepConst<R> &k) {
+  for (int a = 0; a < 3; ++a) {
+    k.L[a] = (R)I.L[a];
+    k.g[a] = (R)I.g[a];
+  }
+  k.cut2 = (R)I.cut2;
+  k.inv_h = (R)I.inv_h;
+  k.c5 = (R)(-5.0) * (R)I.alpha_h * (R)I.inv_h;
+  k.reg = (R)I.reg;
+  k.rho0 = (R)I.rho0;
+  k.nu_l = (R)I.nu_l;
+  k.c0 = (R)I.c0;
+  k.eta = (R)I.eta;
+  k.muR_k = (R)I.muR_k;
+  k.inv_c0sq = (R)(1.0 / I.c0sq);
+  k.inv_rc0 = (R)I.inv_rc0;
+  k.c0sq = (R)I.c0sq;
+}
+
 static int build_inst(const sph_config &c, InstDev &I, std::string &why) {
   memset(&I, 0, sizeof(I));
   if (c.dim != 2 && c.dim != 3) return why = "dim must be 2 or 3", -1;
@@ -253,6 +298,8 @@ static int build_inst(const sph_config &c, InstDev &I, std::string &why) {
   I.inv_cs = 1.0 / I.cs;
   I.inv_rc0 = 1.0 / (c.rho0 * c.c0);
   I.c0sq = c.c0 * c.c0;
+  fill_sweep_const(I, I.kf);
+  fill_sweep_const(I, I.kd);
   I.n_ac = 1;
   return 0;
 }
@@ -630,6 +677,10 @@ int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *
 void sph_destroy(sph_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  for (size_t q = 0; q < c->snaps.size(); ++q)
+    if (c->snaps[q].mem) sph_drop_state(c, (int32_t)q);
+  c->drop_graphs();
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   c->release();
   delete c;
@@ -845,17 +896,17 @@ static void enqueue_step(sph_ctx *c) {
     launch_time_step(c->topo(), c->stream);
     c->prof_end(ev);
     ev = c->prof_begin(8);
-    launch_neighbour_list(c->sweep(0), c->packs(), c->prec, c->dim, maxn, c->stream);
+    launch_neighbour_list(c->sweep(0, 0), c->packs(), c->prec, c->dim, maxn, c->stream);
     c->prof_end(ev);
     ev = c->prof_begin(4);
-    launch_advection_sweep(c->sweep(0), c->packs(), c->prec, c->dim, maxn, c->stream);
+    launch_advection_sweep(c->sweep(0, 1), c->packs(), c->prec, c->dim, maxn, c->stream);
     c->prof_end(ev);
     for (int s = 0; s < c->n_ac_max; ++s) {
       ev = c->prof_begin(5);
-      launch_momentum_sweep(c->sweep(s), c->packs(), c->prec, c->dim, maxn, s, c->stream);
+      launch_momentum_sweep(c->sweep(s, 2), c->packs(), c->prec, c->dim, maxn, s, c->stream);
       c->prof_end(ev);
       ev = c->prof_begin(6);
-      launch_continuity_sweep(c->sweep(s), c->packs(), c->prec, c->dim, maxn, s, c->stream);
+      launch_continuity_sweep(c->sweep(s, 3), c->packs(), c->prec, c->dim, maxn, s, c->stream);
       c->prof_end(ev);
     }
   }
@@ -873,6 +924,39 @@ static int read_status(sph_ctx *c, int32_t *status) {
   return 0;
 }
 
+// capture one advection step whose masters start in copy `parity` into an
+// executable graph (nothing runs; host counters are left as they were)
+static int capture_graph(sph_ctx *c, int parity) {
+  if (!c->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t user = c->stream;
+  const bool prof = c->prof;
+  const int64_t step = c->step, launches = c->launches;
+  const int cur = c->cur;
+  c->stream = c->cap_stream;
+  c->prof = false;
+  c->cur = parity;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    enqueue_step(c);
+    e = cudaStreamEndCapture(c->cap_stream, &g);
+  }
+  c->graph_kernels[parity] = c->launches - launches;
+  c->stream = user;
+  c->prof = prof;
+  c->step = step;
+  c->launches = launches;
+  c->cur = cur;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec[parity], g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->gexec[parity] = nullptr;
+    cudaGetLastError();
+    return fail(SPH_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  return 0;
+}
+
 int sph_step(sph_ctx *c, int32_t nsteps, double *t_out) {
   if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
   if (nsteps < 0) return fail(SPH_ERR_ARG, "nsteps < 0");
@@ -881,13 +965,251 @@ int sph_step(sph_ctx *c, int32_t nsteps, double *t_out) {
     if (rc) return rc;
     c->started = true;
   }
-  for (int s = 0; s < nsteps; ++s) enqueue_step(c);
+  for (int s = 0; s < nsteps; ++s) {
+    if (!c->use_graph || !c->graph_warm) {
+      // uncaptured; also the first step after graphs were enabled or the
+      // launch configuration changed, so that every lazily initialised
+      // launch parameter is set before a capture
+      enqueue_step(c);
+      c->graph_warm = c->use_graph;
+      continue;
+    }
+    if (!c->gexec[c->cur]) {
+      int rc = capture_graph(c, c->cur);
+      if (rc) return rc;
+    }
+    CUDA_TRY(cudaGraphLaunch(c->gexec[c->cur], c->stream));
+    c->launches += c->graph_kernels[c->cur];
+    c->cur = 1 - c->cur;
+    c->step += 1;
+  }
   CUDA_TRY(cudaGetLastError());
   int32_t status = 0;
   int rc = read_status(c, &status);
   if (rc) return rc;
   if (t_out) CUDA_TRY(cudaMemcpy(t_out, &c->d_inst[0].t, sizeof(double), cudaMemcpyDeviceToHost));
   return status;
+}
+
+int sph_set_graph(sph_ctx *c, int32_t enable) {
+  if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
+  c->use_graph = enable != 0;
+  return SPH_OK;
+}
+
+int sph_set_launch(sph_ctx *c, const int32_t block[4]) {
+  if (!c || !block) return fail(SPH_ERR_ARG, "NULL argument");
+  for (int q = 0; q < 4; ++q)
+    if (block[q] != 64 && block[q] != 128 && block[q] != 256)
+      return fail(SPH_ERR_ARG, "block sizes must be 64, 128 or 256");
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  for (int q = 0; q < 4; ++q) c->blk[q] = block[q];
+  c->drop_graphs();
+  return SPH_OK;
+}
+
+int sph_get_launch(sph_ctx *c, int32_t block[4]) {
+  if (!c || !block) return fail(SPH_ERR_ARG, "NULL argument");
+  for (int q = 0; q < 4; ++q) block[q] = c->blk[q];
+  return SPH_OK;
+}
+
+// ------------------------------------------------------------------------
+// snapshots
+// ------------------------------------------------------------------------
+// (device pointer, bytes) of every array a snapshot holds, in a fixed order
+static void snap_parts(sph_ctx *c, std::vector<std::pair<void *, size_t>> &parts) {
+  parts.clear();
+  const size_t cap = (size_t)c->cap, d8 = 8 * cap;
+  Masters &M = c->M[c->cur];
+  for (int a = 0; a < 3; ++a) {
+    parts.push_back({M.x[a], d8});
+    parts.push_back({M.v[a], d8});
+  }
+  for (double *q : {M.rho, M.mass, M.drho, M.p, M.k, M.eps, M.nut}) parts.push_back({q, d8});
+  parts.push_back({M.label, 4 * cap});
+  parts.push_back({M.uid, 4 * cap});
+  parts.push_back({M.inst, 2 * cap});
+  parts.push_back({c->K[0], 4 * cap});
+  parts.push_back({c->Vv[0], 4 * cap});
+  for (int q = 0; q < 6; ++q) parts.push_back({c->der.B[q], d8});
+  for (int a = 0; a < 3; ++a) parts.push_back({c->der.an[a], d8});
+  parts.push_back({c->cnt, sizeof(Counters)});
+  parts.push_back({c->d_inst, sizeof(InstDev) * (size_t)c->ninst});
+  parts.push_back({c->next_uid, 4 * (size_t)c->ninst});
+  parts.push_back({c->inst_spawn, 8 * (size_t)c->ninst});
+}
+
+static size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+int sph_save_state(sph_ctx *c, int32_t *slot_out) {
+  if (!c || !slot_out) return fail(SPH_ERR_ARG, "NULL argument");
+  std::vector<std::pair<void *, size_t>> parts;
+  snap_parts(c, parts);
+  size_t total = 0;
+  for (auto &p : parts) total += align256(p.second);
+  void *mem = nullptr;
+  if (c->alloc.alloc)
+    mem = c->alloc.alloc(c->alloc.user, total, c->alloc.stream);
+  else if (cudaMalloc(&mem, total) != cudaSuccess)
+    mem = nullptr;
+  if (!mem) return fail(SPH_ERR_ALLOC, "snapshot allocation failed");
+  size_t off = 0;
+  for (auto &p : parts) {
+    CUDA_TRY(cudaMemcpyAsync((char *)mem + off, p.first, p.second, cudaMemcpyDeviceToDevice, c->stream));
+    off += align256(p.second);
+  }
+  sph_ctx::Snap sn;
+  sn.mem = mem;
+  sn.bytes = total;
+  sn.step = c->step;
+  int slot = -1;
+  for (size_t q = 0; q < c->snaps.size(); ++q)
+    if (!c->snaps[q].mem) {
+      slot = (int)q;
+      break;
+    }
+  if (slot < 0) {
+    slot = (int)c->snaps.size();
+    c->snaps.push_back(sn);
+  } else {
+    c->snaps[slot] = sn;
+  }
+  *slot_out = slot;
+  return SPH_OK;
+}
+
+int sph_restore_state(sph_ctx *c, int32_t slot) {
+  if (!c || slot < 0 || slot >= (int32_t)c->snaps.size() || !c->snaps[slot].mem)
+    return fail(SPH_ERR_ARG, "unknown snapshot slot");
+  std::vector<std::pair<void *, size_t>> parts;
+  snap_parts(c, parts);
+  const sph_ctx::Snap &sn = c->snaps[slot];
+  size_t off = 0;
+  for (auto &p : parts) {
+    CUDA_TRY(cudaMemcpyAsync(p.first, (char *)sn.mem + off, p.second, cudaMemcpyDeviceToDevice, c->stream));
+    off += align256(p.second);
+  }
+  c->step = sn.step;
+  return SPH_OK;
+}
+
+int sph_drop_state(sph_ctx *c, int32_t slot) {
+  if (!c || slot < 0 || slot >= (int32_t)c->snaps.size() || !c->snaps[slot].mem)
+    return fail(SPH_ERR_ARG, "unknown snapshot slot");
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  sph_ctx::Snap &sn = c->snaps[slot];
+  if (c->alloc.free)
+    c->alloc.free(c->alloc.user, sn.mem, c->alloc.stream);
+  else
+    cudaFree(sn.mem);
+  sn = sph_ctx::Snap();
+  return SPH_OK;
+}
+
+// ------------------------------------------------------------------------
+// autotuner of the sweep block sizes
+// ------------------------------------------------------------------------
+static std::string tune_key(sph_ctx *c) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  std::string name = "gpu";
+  if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+    name = prop.name;
+    sms = prop.multiProcessorCount;
+  }
+  for (char &ch : name)
+    if (ch == ' ' || ch == '\t') ch = '_';
+  Counters h;
+  int64_t n = 0;
+  if (cudaMemcpy(&h, c->cnt, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess) n = h.m_pending - h.n_del_step;
+  int rans = 0;
+  for (const InstDev &I : c->inst) rans |= I.rans;
+  return name + "|sm" + std::to_string(sms) + "|d" + std::to_string(c->dim) + "|p" + std::to_string(c->prec) +
+         "|i" + std::to_string(c->ninst) + "|n" + std::to_string(n) + "|w" + std::to_string(c->nw) + "|r" +
+         std::to_string(rans) + "|s" + std::to_string(c->n_ac_max);
+}
+
+int sph_autotune(sph_ctx *c, int32_t steps, const char *cache_path, int32_t block_out[4], int32_t *from_cache) {
+  if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
+  if (steps < 1) return fail(SPH_ERR_ARG, "steps must be >= 1");
+  if (from_cache) *from_cache = 0;
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  const std::string key = tune_key(c);
+  if (cache_path) {
+    std::ifstream in(cache_path);
+    std::string line;
+    while (std::getline(in, line)) {
+      std::istringstream ls(line);
+      std::string k;
+      int32_t b[4];
+      if (!(ls >> k >> b[0] >> b[1] >> b[2] >> b[3]) || k != key) continue;
+      int rc = sph_set_launch(c, b);
+      if (rc) continue;
+      if (block_out)
+        for (int q = 0; q < 4; ++q) block_out[q] = b[q];
+      if (from_cache) *from_cache = 1;
+      return SPH_OK;
+    }
+  }
+  if (!c->started) {
+    int rc = upload_buffers(c);
+    if (rc) return rc;
+    c->started = true;
+  }
+  int32_t slot = -1;
+  int rc = sph_save_state(c, &slot);
+  if (rc) return rc;
+  const bool prof = c->prof, graph = c->use_graph;
+  double keep_ms[SPH_N_STAGES];
+  int64_t keep_n[SPH_N_STAGES];
+  memcpy(keep_ms, c->stage_ms, sizeof(keep_ms));
+  memcpy(keep_n, c->stage_n, sizeof(keep_n));
+  const int stage_of[4] = {8, 4, 5, 6};  // profiling stage of each sweep
+  const int cand[3] = {64, 128, 256};
+  int32_t best[4];
+  for (int q = 0; q < 4; ++q) best[q] = c->blk[q];
+  c->use_graph = false;
+  c->prof = true;
+  for (int q = 0; q < 4 && !rc; ++q) {
+    double best_ms = 1e300;
+    for (int t = 0; t < 3 && !rc; ++t) {
+      int32_t trial[4];
+      for (int u = 0; u < 4; ++u) trial[u] = best[u];
+      trial[q] = cand[t];
+      if ((rc = sph_set_launch(c, trial)) || (rc = sph_restore_state(c, slot))) break;
+      enqueue_step(c);  // untimed
+      int32_t st = 0;
+      if ((rc = read_status(c, &st))) break;
+      for (int k = 0; k < SPH_N_STAGES; ++k) c->stage_ms[k] = 0, c->stage_n[k] = 0;
+      for (int k = 0; k < steps; ++k) enqueue_step(c);
+      if ((rc = read_status(c, &st))) break;
+      const int sg = stage_of[q];
+      const double ms = c->stage_n[sg] ? c->stage_ms[sg] / (double)c->stage_n[sg] : 1e300;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best[q] = cand[t];
+      }
+    }
+  }
+  c->prof = prof;
+  c->use_graph = graph;
+  memcpy(c->stage_ms, keep_ms, sizeof(keep_ms));
+  memcpy(c->stage_n, keep_n, sizeof(keep_n));
+  int rc2 = sph_restore_state(c, slot);
+  if (!rc) rc = rc2;
+  rc2 = sph_drop_state(c, slot);
+  if (!rc) rc = rc2;
+  if (!rc) rc = sph_set_launch(c, best);
+  if (rc) return rc;
+  if (block_out)
+    for (int q = 0; q < 4; ++q) block_out[q] = best[q];
+  if (cache_path) {
+    std::ofstream o(cache_path, std::ios::app);
+    if (o) o << key << " " << best[0] << " " << best[1] << " " << best[2] << " " << best[3] << "\n";
+  }
+  return SPH_OK;
 }
 
 }  // extern "C"
@@ -1120,7 +1442,7 @@ int sph_debug_pairs(sph_ctx *c, int64_t *out, int64_t max, int64_t *count) {
   int64_t *dout = nullptr;
   if (max > 0 && cudaMalloc(&dout, sizeof(int64_t) * 4 * (size_t)max) != cudaSuccess)
     return fail(SPH_ERR_ALLOC, "pair buffer");
-  launch_debug_pairs(c->sweep(0), c->wx[0], c->wx[1], c->wx[2], c->wall_index, dout, max, c->pair_counter, (int)c->cap,
+  launch_debug_pairs(c->sweep(0, 0), c->wx[0], c->wx[1], c->wx[2], c->wall_index, dout, max, c->pair_counter, (int)c->cap,
                      c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess) e = cudaGetLastError();

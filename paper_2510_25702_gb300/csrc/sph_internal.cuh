@@ -20,11 +20,21 @@
 namespace sphk {
 
 constexpr uint32_t kSubRecycle = 0xFFFFFFFFu;
-constexpr int kBlock = 128;
+constexpr int kBlock = 128;     // topology kernels
+constexpr int kMaxBlock = 256;  // largest block size of the sweeps
 
 // k-epsilon constants (App. A table)
 constexpr double kC1 = 1.44, kC2 = 1.92, kCmu = 0.09, kSigK = 1.0, kSigE = 1.3;
 constexpr double kFloor = 1e-12;
+
+// constants of the pair sweeps in the sweep precision, converted once on
+// the host (the conversions match the ones the device would make)
+template <typename R>
+struct SweepConst {
+  R L[3], g[3];
+  R cut2, inv_h, c5, reg;  // c5 = -5 alpha_d / h^2: F = c5 (1 - q/2)^3
+  R rho0, nu_l, c0, eta, muR_k, inv_c0sq, inv_rc0, c0sq;
+};
 
 struct InstDev {
   int32_t dim, rans, dt_mode, n_ac_fixed;
@@ -49,11 +59,24 @@ struct InstDev {
   double inv_cs;   // 1 / (2h)
   double inv_rc0;  // 1 / (rho0 c0)
   double c0sq;     // c0^2: p = c0^2 (rho - rho0), the stiff EOS of Sec. 2.1
+  SweepConst<float> kf;
+  SweepConst<double> kd;
   // written every advection step by the time-step kernel
   double dt_ad, dt_ac, dt, t;
   int32_t n_ac;
   int32_t pad1;
 };
+
+template <typename R>
+__host__ __device__ __forceinline__ const SweepConst<R> &sweep_const(const InstDev &I);
+template <>
+__host__ __device__ __forceinline__ const SweepConst<float> &sweep_const<float>(const InstDev &I) {
+  return I.kf;
+}
+template <>
+__host__ __device__ __forceinline__ const SweepConst<double> &sweep_const<double>(const InstDev &I) {
+  return I.kd;
+}
 
 struct BufDev {
   int32_t type, turb, n_theta, inst;
@@ -123,6 +146,10 @@ struct Counters {
   int32_t n_ac_all;    // largest sub-step count of any instance this step
   int32_t pad2;
   unsigned long long spawned, deleted;
+  // advection steps completed (the Philox step counter of the boundary
+  // noise); advanced by the buffer update, which keeps the index of the step
+  // it closes in spawn_step for the recycled particles
+  long long step, spawn_step;
 };
 
 // ------------------------------------------------------------------------
@@ -292,7 +319,6 @@ struct TopoArgs {
   int32_t *block_cnt;
   uint32_t sentinel;
   int32_t ninst, n_ac_max;
-  int64_t step;
   int64_t capacity;
 };
 
@@ -323,9 +349,9 @@ struct SweepArgs {
   const uint32_t *woff;  // wall cell offsets
   const Counters *cnt;
   int32_t *status;
-  int64_t step;
   int32_t sub;
   int32_t any_periodic;  // some instance has a periodic axis
+  int32_t block;         // threads per block of the launch
 };
 
 // sweeps: prec 0 -> double packs, 1 -> float packs; dim 2 / 3

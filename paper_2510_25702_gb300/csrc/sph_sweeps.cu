@@ -65,15 +65,16 @@ struct Geo {
 
 template <typename R, int D>
 __device__ __forceinline__ Geo<R> make_geo(const InstDev &I) {
+  const SweepConst<R> &k = sweep_const<R>(I);
   Geo<R> g;
   for (int a = 0; a < 3; ++a) {
-    g.L[a] = (R)I.L[a];
+    g.L[a] = k.L[a];
     g.per[a] = (a < D) ? I.periodic[a] : 0;
   }
-  g.cut2 = (R)I.cut2;
-  g.inv_h = (R)I.inv_h;
-  g.c5 = (R)(-5.0) * (R)I.alpha_h * (R)I.inv_h;
-  g.reg = (R)I.reg;
+  g.cut2 = k.cut2;
+  g.inv_h = k.inv_h;
+  g.c5 = k.c5;
+  g.reg = k.reg;
   return g;
 }
 
@@ -360,7 +361,8 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   V4<R> A2 = A1;
   if (D == 3 && rans) A2 = pk.adv[RA * (size_t)i + 2];
   const R vi[3] = {D == 2 ? A0.w : A1.x, D == 2 ? A1.x : A1.y, D == 2 ? (R)0 : A1.z};
-  const R rho0 = (R)I.rho0, nu_l = (R)I.nu_l, c0 = (R)I.c0, eta = (R)I.eta, muRk = (R)I.muR_k;
+  const SweepConst<R> &kc = sweep_const<R>(I);
+  const R rho0 = kc.rho0, nu_l = kc.nu_l, c0 = kc.c0, eta = kc.eta, muRk = kc.muR_k;
   R k_i = (R)0, e_i = (R)0, nut_i = (R)0;
   if (rans) {
     k_i = D == 2 ? A1.y : A1.w;
@@ -386,7 +388,7 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   R dk = 0, de = 0;
 
   // real neighbours
-#pragma unroll 2
+#pragma unroll 4
   for (int kk = 0; kk < nr; ++kk) {
     const uint32_t j = Lst[(size_t)kk * LS];
     const V4<R> B0 = pk.adv[RA * (size_t)j], B1 = pk.adv[RA * (size_t)j + 1];
@@ -523,7 +525,7 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
     an[c] = (R)2 * sv[c] * inv_rho;
     a.der.an[c][i] = (double)an[c];
   }
-  pk.Ap[i] = V4<R>{an[0] + (R)I.g[0], an[1] + (R)I.g[1], D == 3 ? an[2] + (R)I.g[2] : (R)0, (R)0};
+  pk.Ap[i] = V4<R>{an[0] + kc.g[0], an[1] + kc.g[1], D == 3 ? an[2] + kc.g[2] : (R)0, (R)0};
 
   R kw = (R)0;
   if (rans) {
@@ -564,7 +566,7 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   // first half, so only that one is stored.
   const double hdt = 0.5 * I.dt;
   const double rho = rho_i + hdt * m.drho[i];
-  const R p = (R)(rho - I.rho0) * (R)I.c0sq;
+  const R p = (R)(rho - I.rho0) * sweep_const<R>(I).c0sq;
   m.rho[i] = rho;
   if (I.n_ac == 1) m.p[i] = (double)p;
 #pragma unroll
@@ -598,7 +600,7 @@ __device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, 
   const size_t LS = (size_t)a.nl.stride;
   const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
   const bool rans = I.rans != 0;
-  const R rho0 = (R)I.rho0, inv_c0sq = (R)(1.0 / I.c0sq);
+  const R rho0 = sweep_const<R>(I).rho0, inv_c0sq = sweep_const<R>(I).inv_c0sq;
   const V4<R> M0 = pk.mom[RM * (size_t)i], M1 = pk.mom[RM * (size_t)i + 1];
   V4<R> M2 = M1;
   if (D == 3) M2 = pk.mom[RM * (size_t)i + 2];
@@ -610,7 +612,7 @@ __device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, 
   const R pe_i = rans ? p_eff(p_i, kw_i, rho0, inv_c0sq) : p_i;
 
   R S1[3] = {0, 0, 0}, Cb[3] = {0, 0, 0}, S2[3] = {0, 0, 0}, Ct[3] = {0, 0, 0};
-#pragma unroll 2
+#pragma unroll 4
   for (int kk = 0; kk < nr; ++kk) {
     const uint32_t j = Lst[(size_t)kk * LS];
     const V4<R> N0 = pk.mom[RM * (size_t)j], N1 = pk.mom[RM * (size_t)j + 1];
@@ -715,10 +717,10 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
   const V4<R> C0 = pk.cont[2 * (size_t)i], C1 = pk.cont[2 * (size_t)i + 1];
   const R vi[3] = {D == 2 ? C1.x : C1.y, D == 2 ? C1.y : C1.z, D == 2 ? (R)0 : C1.w};
   const R p_i = D == 2 ? C0.w : C1.x;
-  const R inv_rc = (R)I.inv_rc0;
+  const R inv_rc = sweep_const<R>(I).inv_rc0;
   // drho_i / rho_i = sum_j [v_ij . r_ij / r + (p_i - p_j) / (rho0 c0)] dW/dr V_j
   R sum = 0;
-#pragma unroll 2
+#pragma unroll 4
   for (int kk = 0; kk < nr; ++kk) {
     const uint32_t j = Lst[(size_t)kk * LS];
     const V4<R> N0 = pk.cont[2 * (size_t)j], N1 = pk.cont[2 * (size_t)j + 1];
@@ -755,7 +757,7 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
   R kw_bc = (R)0;
   if (lab > 0 && lab <= I.nbuf) {
     const BufDev &b = a.buf[I.buf0 + lab - 1];
-    apply_bc(I, b, m, i, a.step, (uint32_t)a.sub);
+    apply_bc(I, b, m, i, a.cnt->step, (uint32_t)a.sub);
     rho = m.rho[i];
     if (I.rans && b.turb == SPH_TURB_FREESTREAM) {
       kw_reset = true;
@@ -772,7 +774,7 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
     // (B and kw stay from the advection sweep unless a free-stream buffer
     // reset k)
     rho = rho + hdt * drho;
-    const R p = (R)(rho - I.rho0) * (R)I.c0sq;
+    const R p = (R)(rho - I.rho0) * sweep_const<R>(I).c0sq;
     m.rho[i] = rho;
     if (a.sub + 2 == I.n_ac) m.p[i] = (double)p;  // the step's last first half
 #pragma unroll
@@ -799,21 +801,21 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
 // kernels: grid-stride over the live particles
 // ------------------------------------------------------------------------
 template <typename R, int D, bool PER>
-__global__ void __launch_bounds__(kBlock) k_list(SweepArgs a, Packs<R> pk) {
+__global__ void __launch_bounds__(kMaxBlock) k_list(SweepArgs a, Packs<R> pk) {
   const int n = a.cnt->n_live;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     list_one<R, D, PER>(a, pk, i);
 }
 
 template <typename R, int D, bool PER>
-__global__ void __launch_bounds__(kBlock) k_adv(SweepArgs a, Packs<R> pk) {
+__global__ void __launch_bounds__(kMaxBlock) k_adv(SweepArgs a, Packs<R> pk) {
   const int n = a.cnt->n_live;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     adv_one<R, D, PER>(a, pk, i);
 }
 
 template <typename R, int D, bool PER>
-__global__ void __launch_bounds__(kBlock) k_mom(SweepArgs a, Packs<R> pk) {
+__global__ void __launch_bounds__(kMaxBlock) k_mom(SweepArgs a, Packs<R> pk) {
   if (a.sub >= a.cnt->n_ac_all) return;  // no instance takes this sub-step
   const int n = a.cnt->n_live;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -821,7 +823,7 @@ __global__ void __launch_bounds__(kBlock) k_mom(SweepArgs a, Packs<R> pk) {
 }
 
 template <typename R, int D, bool PER>
-__global__ void __launch_bounds__(kBlock) k_cont(SweepArgs a, Packs<R> pk) {
+__global__ void __launch_bounds__(kMaxBlock) k_cont(SweepArgs a, Packs<R> pk) {
   if (a.sub >= a.cnt->n_ac_all) return;
   const int n = a.cnt->n_live;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -890,38 +892,41 @@ __global__ void __launch_bounds__(kBlock) k_pairs(SweepArgs a, const double *__r
 // ------------------------------------------------------------------------
 // launch wrappers
 // ------------------------------------------------------------------------
-// blocks to launch: all resident blocks of the GPU, or fewer when the
-// particles need fewer; the occupancy query runs once per kernel
+// blocks to launch: all resident blocks of the GPU at the chosen block size,
+// or fewer when the particles need fewer.  The occupancy query runs once per
+// kernel and block size (64, 128 or 256 threads).
 template <typename K>
-static int resident_grid(K kernel, int max_n) {
-  static int per_gpu = 0;
-  if (per_gpu == 0) {
+static int resident_grid(K kernel, int block, int max_n) {
+  static int per_gpu[3] = {0, 0, 0};
+  const int slot = block <= 64 ? 0 : (block <= 128 ? 1 : 2);
+  if (per_gpu[slot] == 0) {
     int dev = 0, sms = 1, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
-    per_gpu = sms * (per_sm > 0 ? per_sm : 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
+    per_gpu[slot] = sms * (per_sm > 0 ? per_sm : 1);
   }
-  int need = (max_n + kBlock - 1) / kBlock;
+  int need = (max_n + block - 1) / block;
   if (need < 1) need = 1;
-  return need < per_gpu ? need : per_gpu;
+  return need < per_gpu[slot] ? need : per_gpu[slot];
 }
 
 // which: 0 advection, 1 momentum, 2 continuity, 3 neighbour list
 template <typename R, int D, bool PER>
 static void launch_sweeps_impl(int which, const SweepArgs &a, Packs<R> &pk, int max_n, cudaStream_t st) {
+  const int b = (a.block == 64 || a.block == 256) ? a.block : 128;
   if (which == 3) {
     auto k = k_list<R, D, PER>;
-    k<<<resident_grid(k, max_n), kBlock, 0, st>>>(a, pk);
+    k<<<resident_grid(k, b, max_n), b, 0, st>>>(a, pk);
   } else if (which == 0) {
     auto k = k_adv<R, D, PER>;
-    k<<<resident_grid(k, max_n), kBlock, 0, st>>>(a, pk);
+    k<<<resident_grid(k, b, max_n), b, 0, st>>>(a, pk);
   } else if (which == 1) {
     auto k = k_mom<R, D, PER>;
-    k<<<resident_grid(k, max_n), kBlock, 0, st>>>(a, pk);
+    k<<<resident_grid(k, b, max_n), b, 0, st>>>(a, pk);
   } else {
     auto k = k_cont<R, D, PER>;
-    k<<<resident_grid(k, max_n), kBlock, 0, st>>>(a, pk);
+    k<<<resident_grid(k, b, max_n), b, 0, st>>>(a, pk);
   }
 }
 

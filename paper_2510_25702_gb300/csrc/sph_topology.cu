@@ -235,6 +235,8 @@ __global__ void __launch_bounds__(1024) k_spawn_scan(TopoArgs a, int nblocks, ui
     a.cnt->m_pending = n + S;
     a.cnt->n_del_step = 0;
     a.cnt->spawned += (unsigned long long)S;
+    a.cnt->spawn_step = a.cnt->step;
+    a.cnt->step += 1;
     // per-instance uid bases: copy number r (global rank) of instance ii gets
     // uid next_uid[ii] + (r - first global rank of ii)
     int32_t run = 0;
@@ -316,7 +318,7 @@ __global__ void __launch_bounds__(kBlock) k_spawn(TopoArgs a, const uint32_t *ui
 #pragma unroll
   for (int d = 0; d < 3; ++d)
     if (d < I.dim) m.x[d][i] = dsub(m.x[d][i], dmul(B.length, B.frame[d]));
-  apply_bc(I, B, m, i, a.step, kSubRecycle);
+  apply_bc(I, B, m, i, a.cnt->spawn_step, kSubRecycle);
   wrap_and_key(I, m, i, a.keys);
 }
 

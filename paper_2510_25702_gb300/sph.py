@@ -94,7 +94,8 @@ _lib = None
 EXPORTS = ("sph_create", "sph_add_buffer", "sph_set_profile", "sph_step", "sph_read_fields",
            "sph_write_fields", "sph_get_stats", "sph_debug_pairs", "sph_destroy", "sph_error_string",
            "sph_last_error", "sph_abi_version", "sph_set_profiling", "sph_get_stage_times", "sph_stage_name",
-           "sph_cell_sort_noalloc")
+           "sph_cell_sort_noalloc", "sph_set_graph", "sph_set_launch", "sph_get_launch", "sph_autotune",
+           "sph_save_state", "sph_restore_state", "sph_drop_state")
 NOALLOC_MAX_POINTS = 1 << 19
 N_STAGES = 9
 
@@ -129,6 +130,13 @@ def lib():
         L.sph_stage_name.restype = C.c_char_p
         L.sph_cell_sort_noalloc.argtypes = [C.POINTER(Config), vp, C.c_int32, vp, vp, C.c_int64,
                                             C.POINTER(C.c_int64), vp]
+        L.sph_set_graph.argtypes = [vp, C.c_int32]
+        L.sph_set_launch.argtypes = [vp, C.POINTER(C.c_int32)]
+        L.sph_get_launch.argtypes = [vp, C.POINTER(C.c_int32)]
+        L.sph_autotune.argtypes = [vp, C.c_int32, C.c_char_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.sph_save_state.argtypes = [vp, C.POINTER(C.c_int32)]
+        L.sph_restore_state.argtypes = [vp, C.c_int32]
+        L.sph_drop_state.argtypes = [vp, C.c_int32]
         L.sph_error_string.restype = C.c_char_p
         L.sph_last_error.restype = C.c_char_p
         _lib = L
@@ -339,6 +347,38 @@ class Simulation:
         th = np.ascontiguousarray(theta, np.float64)
         _check(lib().sph_set_profile(self.ctx, instance, buffer_id, th.ctypes.data_as(C.POINTER(C.c_double)),
                                      th.size), "sph_set_profile")
+
+    def set_graph(self, enable: bool = True):
+        _check(lib().sph_set_graph(self.ctx, int(bool(enable))), "sph_set_graph")
+
+    def set_launch(self, blocks: Sequence[int]):
+        b = (C.c_int32 * 4)(*[int(x) for x in blocks])
+        _check(lib().sph_set_launch(self.ctx, b), "sph_set_launch")
+
+    def get_launch(self) -> List[int]:
+        b = (C.c_int32 * 4)()
+        _check(lib().sph_get_launch(self.ctx, b), "sph_get_launch")
+        return list(b)
+
+    def autotune(self, steps: int = 3, cache_path: Optional[str] = None):
+        """Pick the sweep block sizes (list, advection, momentum, continuity);
+        returns (blocks, from_cache).  The simulation state is unchanged."""
+        b = (C.c_int32 * 4)()
+        hit = C.c_int32()
+        path = cache_path.encode() if cache_path else None
+        _check(lib().sph_autotune(self.ctx, int(steps), path, b, C.byref(hit)), "sph_autotune")
+        return list(b), bool(hit.value)
+
+    def save_state(self) -> int:
+        slot = C.c_int32()
+        _check(lib().sph_save_state(self.ctx, C.byref(slot)), "sph_save_state")
+        return slot.value
+
+    def restore_state(self, slot: int):
+        _check(lib().sph_restore_state(self.ctx, int(slot)), "sph_restore_state")
+
+    def drop_state(self, slot: int):
+        _check(lib().sph_drop_state(self.ctx, int(slot)), "sph_drop_state")
 
     def debug_pairs(self, max_pairs: Optional[int] = None) -> np.ndarray:
         cnt = C.c_int64()

@@ -44,7 +44,11 @@ def small_cases():
     lat3.buffers = [cases.BufferSpec("pressure", (0.0, 0.45, 0.45), cases.frame_3d((1, 0, 0), (0, 1, 0)),
                                      0.4, (0.5, 0.5), p_ob=0.05)]
     lat3.vel[:, 0] = 0.1
-    return {"channel": c1, "rans_channel": c2, "box2": box, "box2_rans": boxr, "box3": box3, "lattice3_buf": lat3}
+    uch = cases.u_channel(dp=0.05, nu=0.02)
+    jet = cases.plane_jet(dp=0.02, jitter_frac=0.05)
+    mix = cases.mixer_3d(dp=0.05)
+    return {"channel": c1, "rans_channel": c2, "box2": box, "box2_rans": boxr, "box3": box3, "lattice3_buf": lat3,
+            "u_channel": uch, "plane_jet": jet, "mixer3d": mix}
 
 
 CASES = small_cases()
