@@ -185,6 +185,58 @@ def cpu_baseline(work: str, steps: int = 20):
                       f"({case.n} particles, a section of the workload), {dt:.1f} s single-threaded FP64"}
 
 
+def adjoint_bench(steps: int = 200, every: int = 20, dp: float = 0.002):
+    """Differentiated window on the plane jet (2 x 2, slot 0.1, dp 0.002,
+    about 1M particles, k-eps with frozen turbulence, fixed dt, FP64):
+    times of the plain forward, the checkpointed forward and the reverse
+    pass over `steps` steps, and a finite-difference check of the gradient
+    along one random direction of the 32-point inlet profile."""
+    import math
+
+    import torch
+
+    from paper_2510_25702_gb300 import cases, sph
+    from paper_2510_25702_gb300.adjoint import Window
+
+    th = 1.0 + 0.1 * np.cos(np.linspace(0.0, 2.0 * np.pi, 32))
+    c = cases.plane_jet(dp=dp, theta=th)
+    dt_ad = 0.25 * c.h / c.U_ref
+    n_ac = max(1, math.ceil(dt_ad / (0.6 * c.h / (c.c0 + c.U_ref))))
+    c = c.replace(dt_mode="fixed", dt_ad_fixed=dt_ad, n_ac_fixed=n_ac)
+    sim = sph.Simulation(c, precision="fp64")
+    sim.step(2)
+    start = sim.save_state()
+    win = Window(sim, 0, 0, [3, 4, 5], steps, every, 4 * c.dp)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    _, t_plain = timed(lambda: sim.step(steps))
+    sim.restore_state(start)
+    J, t_fwd = timed(lambda: win.forward(th))
+    g, t_bwd = timed(lambda: win.backward())
+    u = np.random.default_rng(11).normal(size=th.size)
+    u /= np.linalg.norm(u)
+    h = 1e-6
+    once = Window(sim, 0, 0, [3, 4, 5], steps, steps, 4 * c.dp)
+    sim.restore_state(start)
+    jp = once.forward(th + h * u)
+    sim.restore_state(start)
+    jm = once.forward(th - h * u)
+    fd = (jp - jm) / (2 * h)
+    sim.adjoint_release()
+    sim.close()
+    return {"workload": c.name, "particles": c.n, "window_steps": steps, "checkpoint_every": every,
+            "sub_steps": n_ac, "J": J, "forward_plain_s": t_plain, "forward_checkpointed_s": t_fwd,
+            "backward_s": t_bwd, "adjoint_over_forward": t_bwd / t_plain,
+            "fd_directional": fd, "adjoint_directional": float(g @ u),
+            "fd_rel_err": abs(float(g @ u) - fd) / max(abs(fd), 1e-300), "dtype": "f64"}
+
+
 def run_reference(args, rank: int):
     """--impl reference: the oracle on the host cores, each step one oracle
     advection step of the bounded sample; rank 0 only."""
@@ -216,6 +268,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison run")
     ap.add_argument("--no-tune", action="store_true", help="keep the default sweep block sizes")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiated-window timing")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -337,6 +390,10 @@ def main():
         fp64 = sim64.stats()["n"] * k64 / (a.elapsed_time(b) * 1e-3)
         sim64.close()
 
+    adj = None
+    if rank == 0 and not args.no_adjoint:
+        adj = adjoint_bench()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)
@@ -357,7 +414,7 @@ def main():
                          "bytes_per_particle": per_particle, "avg_launch_ms": dom_ms / dom_n},
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "fp64_value": fp64, "fp32_over_fp64": (value / fp64) if fp64 else None,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "graph": graph, "autotune": tuned,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "graph": graph, "autotune": tuned, "adjoint": adj,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

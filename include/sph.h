@@ -282,6 +282,43 @@ int sph_save_state(sph_ctx *ctx, int32_t *slot_out);
 int sph_restore_state(sph_ctx *ctx, int32_t slot);
 int sph_drop_state(sph_ctx *ctx, int32_t slot);
 
+/* Differentiated windows (adjoint; no counterpart in the paper).  A window
+   of `steps` advection steps from the current state is differentiated with
+   respect to the velocity profile theta of one velocity buffer, for the
+   outlet mass flux
+       J = sum over the window's steps of dt * sum_{i in S} m_i v_i . n_out / slab,
+   S = the particles of `instance` labelled in one of the `outlets` buffers
+   when the window starts (followed by uid), n_out = -n_b of that buffer, v
+   the velocity after each step's buffer update.  Inside the window every
+   instance needs SPH_DT_FIXED (dt is not differentiated), and RANS
+   instances hold k, eps and nu_t at their values (frozen turbulence); the
+   discrete decisions of each step (cell order, neighbour lists, labels,
+   injection and deletion) are those the forward took.
+   sph_adjoint_forward sets theta (n_theta values, the profile of
+   profile_buffer), advances the window, keeps a state snapshot every
+   checkpoint_every steps and the final state, and returns J.
+   sph_adjoint_backward recomputes each segment from its snapshot, runs the
+   hand-written reverse of every step in reverse order and writes dJ/dtheta
+   (n_theta values); the context is left in the state after the window.
+   sph_adjoint_release frees the snapshots and work arrays.
+   Errors: SPH_ERR_ARG (FP32 context, dt mode, buffer kinds, sizes),
+   SPH_ERR_STATE (backward without forward), SPH_ERR_ALLOC, device errors
+   of the steps. */
+typedef struct sph_adjoint_desc {
+  int32_t instance;
+  int32_t profile_buffer;  /* a velocity buffer of instance */
+  int32_t steps;
+  int32_t checkpoint_every;
+  int32_t n_outlets;
+  int32_t outlets[SPH_MAX_BUFFERS];
+  int32_t n_theta;
+  double slab;  /* w_s, the slab width that normalises the flux */
+  double theta[SPH_MAX_THETA];
+} sph_adjoint_desc;
+int sph_adjoint_forward(sph_ctx *ctx, const sph_adjoint_desc *d, double *J_out);
+int sph_adjoint_backward(sph_ctx *ctx, double *grad_out, int32_t n_theta);
+int sph_adjoint_release(sph_ctx *ctx);
+
 /* Neighbour pairs of the configuration at the current positions
    (0 < |r_ij|^2 < (2h)^2 in FP64, Sec. 2.4.1 cell-linked list): rows
    (uid_i, uid_j or wall index, is_wall, instance).  Writes up to max rows

@@ -47,7 +47,7 @@ class OrcConfig(C.Structure):
         ("hi", C.c_double * 3), ("periodic", C.c_int * 3), ("seed", C.c_uint32),
         ("gen_offset", C.c_double), ("id_check", C.c_int), ("contain_check", C.c_int),
         ("mirror_B", C.c_int), ("compensation", C.c_int), ("neighbor_mode", C.c_int),
-        ("rkgc", C.c_int),
+        ("rkgc", C.c_int), ("freeze_turb", C.c_int),
     ]
 
 
@@ -143,7 +143,7 @@ class OracleSim:
 
     def __init__(self, case, capacity: Optional[int] = None, neighbor_mode: int = 1,
                  gen_offset: float = 0.5, id_check: int = 1, contain_check: int = 1,
-                 mirror_B: int = 1, compensation: int = 1, rkgc: int = 1):
+                 mirror_B: int = 1, compensation: int = 1, rkgc: int = 1, freeze_turb: int = 0):
         self.case = case
         cap = int(capacity or case.capacity or case.n + 16)
         n, nw = case.n, case.nw
@@ -167,6 +167,7 @@ class OracleSim:
         c.mirror_B, c.compensation = mirror_B, compensation
         c.neighbor_mode = neighbor_mode
         c.rkgc = rkgc
+        c.freeze_turb = freeze_turb
 
         z3 = lambda m: np.zeros((m, 3))
         self.a: Dict[str, np.ndarray] = dict(
@@ -232,6 +233,16 @@ class OracleSim:
 
     def step(self, nsteps: int = 1):
         _check(lib().orc_step(self._cp, self._sp, int(nsteps)), "orc_step")
+
+    def set_profile(self, buffer_id: int, theta):
+        """Replace the velocity profile of a buffer (theta across the width)."""
+        th = np.asarray(theta, np.float64).reshape(-1)
+        if not 1 <= th.size <= MAX_THETA:
+            raise ValueError("theta length")
+        b = self.st.buf[buffer_id]
+        b.n_theta = th.size
+        for q, v in enumerate(th):
+            b.theta[q] = float(v)
 
     def compact_sort(self):
         _check(lib().orc_compact_sort(self._cp, self._sp), "orc_compact_sort")

@@ -1115,7 +1115,7 @@ static void apply_bc_one(const orc_config *c, orc_state *s, int64_t i, int64_t s
     s->p[i] = b->p_ob;
     s->rho[i] = c->rho0 * (1.0 + b->p_ob / (c->rho0 * c->c0 * c->c0));
   }
-  if (c->rans && b->turb_bc == ORC_TURB_FREESTREAM) {
+  if (c->rans && !c->freeze_turb && b->turb_bc == ORC_TURB_FREESTREAM) {
     s->k[i] = b->k_in;
     s->eps[i] = b->eps_in;
     s->nut[i] = KE_CMU * b->k_in * b->k_in / b->eps_in;
@@ -1226,7 +1226,7 @@ int orc_step(const orc_config *c, orc_state *s, int nsteps) {
     if (build_pairs(c, s, &L)) return ORC_ERR_NOMEM;
     rc = orc_bmatrix_impl(c, s, NULL, &L);
     if (!rc) rc = orc_viscous_impl(c, s, &L);
-    if (!rc && c->rans) rc = orc_rans_impl(c, s, s->dt_ad, &L);
+    if (!rc && c->rans && !c->freeze_turb) rc = orc_rans_impl(c, s, s->dt_ad, &L);
     for (int sub = 0; sub < s->n_ac && !rc; ++sub) {
       double dt = s->dt;
       rc = orc_half1(c, s, dt);

@@ -68,6 +68,7 @@ typedef struct orc_config {
   int compensation;  /* compensated pressure term (Sec. 3.3, final Eq.) */
   int neighbor_mode; /* 0 brute force, 1 cell grid */
   int rkgc;          /* 1: kernel correction B (Sec. 2.2); 0: B = I (Case 1) */
+  int freeze_turb;   /* 1: k, eps, nu_t held (frozen-turbulence gradient windows) */
 } orc_config;
 
 typedef struct orc_buffer {

@@ -1,0 +1,925 @@
+// sph_adjoint.cu -- reverse (adjoint) of one advection step for
+// differentiated windows, FP64.
+//
+// The differentiated map is the step as the forward kernels compute it,
+// with the discrete decisions of that step held: cell order, neighbour
+// lists, labels, the buffer-update decisions, the guard of the B inverse,
+// the time step (fixed) and, in RANS instances, k, eps and nu_t (held over
+// the window).  Everything continuous is differentiated: positions enter
+// through the pair geometry of every sweep (kernel gradient, the
+// correction matrix B with dB = -B dA B, the mirror images at pressure
+// buffers), densities through volumes and pressures, velocities through
+// the viscous, momentum and continuity sums, and the inlet profile theta
+// through the velocity boundary values and the recycling of injected
+// particles (Sec. 2.4.2, 3.1).
+//
+// Reverse of a pair sum O_i = sum_j T(q_i, q_j, x_i - x_j) in gather form:
+// thread i adds, over its list, the derivative of its own term T_ij with
+// respect to its quantities (seeded by the adjoint of O_i) and of the
+// neighbour's term T_ji (seeded by the adjoint of O_j), so no two threads
+// write the same particle.  The mirror images of the B sum are not in the
+// lists; their source terms are scattered with atomics into separate
+// arrays.
+#include "sph_pair.cuh"
+
+namespace sphk {
+
+namespace {
+
+using G = Geo<double>;
+
+// F = W'(r) / r and its r derivative
+__device__ __forceinline__ void kernel_FF(const G &g, double r, double &F, double &Fr) {
+  const double w = 1.0 - 0.5 * (r * g.inv_h);
+  F = g.c5 * w * w * w;
+  Fr = -1.5 * g.c5 * g.inv_h * w * w;
+}
+
+__device__ __forceinline__ double dot3(const double a[3], const double b[3]) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// symmetric (xx, yy, zz, xy, xz, yz) -> full
+__device__ __forceinline__ void sym_full(const double s[6], double M[3][3]) {
+  M[0][0] = s[0];
+  M[1][1] = s[1];
+  M[2][2] = s[2];
+  M[0][1] = M[1][0] = s[3];
+  M[0][2] = M[2][0] = s[4];
+  M[1][2] = M[2][1] = s[5];
+}
+
+__device__ __forceinline__ void matvec3(const double M[3][3], const double x[3], double y[3]) {
+  for (int a = 0; a < 3; ++a) y[a] = M[a][0] * x[0] + M[a][1] * x[1] + M[a][2] * x[2];
+}
+
+// add the symmetric part of u (x) w to the stored symmetric adjoint
+__device__ __forceinline__ void sym_acc(double s[6], const double u[3], const double w[3], double c) {
+  s[0] += c * u[0] * w[0];
+  s[1] += c * u[1] * w[1];
+  s[2] += c * u[2] * w[2];
+  s[3] += c * 0.5 * (u[0] * w[1] + u[1] * w[0]);
+  s[4] += c * 0.5 * (u[0] * w[2] + u[2] * w[0]);
+  s[5] += c * 0.5 * (u[1] * w[2] + u[2] * w[1]);
+}
+
+__device__ __forceinline__ int buffer_of(const AdjArgs &a, const InstDev &I, int i) {
+  const int lab = a.m.label[i];
+  return (lab > 0 && lab <= I.nbuf) ? I.buf0 + lab - 1 : -1;
+}
+
+__device__ __forceinline__ bool is_pressure(const AdjArgs &a, const InstDev &I, int i) {
+  const int b = buffer_of(a, I, i);
+  return b >= 0 && a.buf[b].type == SPH_BUF_PRESSURE;
+}
+
+__device__ __forceinline__ double rho_s(const AdjArgs &a, int s, int i) { return a.T.rho_s[(size_t)s * a.T.cap + i]; }
+
+__device__ __forceinline__ void load_x0(const AdjArgs &a, int i, double x[3]) {
+  x[0] = a.T.x0[0][i];
+  x[1] = a.T.x0[1][i];
+  x[2] = a.T.x0[2][i];
+}
+
+__device__ __forceinline__ void load_B(const AdjArgs &a, int i, int dim, double B[6]) {
+  B[0] = a.der.B[0][i];
+  B[1] = a.der.B[1][i];
+  B[3] = a.der.B[3][i];
+  if (dim == 3) {
+    B[2] = a.der.B[2][i];
+    B[4] = a.der.B[4][i];
+    B[5] = a.der.B[5][i];
+  } else {
+    B[2] = B[4] = B[5] = 0.0;
+  }
+}
+
+// minimum-image pair vector in FP64 (same rule as the forward)
+template <int D, bool PER>
+__device__ __forceinline__ double pvec(const G &g, const double xi[3], const double xj[3], double d[3]) {
+  V4<double> pi{xi[0], xi[1], xi[2], 0.0}, pj{xj[0], xj[1], xj[2], 0.0};
+  return pair_vec<double, D, PER>(g, pi, pj, d);
+}
+
+// velocity profile U(s1) of a buffer with its theta and s1 derivatives
+__device__ __forceinline__ double profile_dU(const BufDev &b, double s1, int &k0, double &w0, int &k1, double &w1,
+                                             double &dU_ds1) {
+  k0 = 0;
+  w0 = 1.0;
+  k1 = 0;
+  w1 = 0.0;
+  dU_ds1 = 0.0;
+  if (b.n_theta <= 1) return b.theta[0];
+  const double w = b.half[0];
+  const double u = (s1 + w) / (2.0 * w) * (double)(b.n_theta - 1);
+  if (!(u > 0.0)) return b.theta[0];
+  if (u >= (double)(b.n_theta - 1)) {
+    k0 = b.n_theta - 1;
+    return b.theta[k0];
+  }
+  const int k = (int)floor(u);
+  const double f = u - (double)k;
+  k0 = k;
+  w0 = 1.0 - f;
+  k1 = k + 1;
+  w1 = f;
+  dU_ds1 = (b.theta[k + 1] - b.theta[k]) * (double)(b.n_theta - 1) / (2.0 * w);
+  return b.theta[k] + f * (b.theta[k + 1] - b.theta[k]);
+}
+
+// reverse of the velocity boundary value v = U(s1(x)) (n_b + noise xi) at
+// position x: theta gradient (profile of the differentiated buffer only),
+// position adjoint, and the velocity adjoint is consumed
+__device__ void velocity_bc_rev(const AdjArgs &a, const InstDev &I, int bidx, int i, const double x[3],
+                                int64_t step, uint32_t sub, double lv[3], double lx[3]) {
+  const BufDev &b = a.buf[bidx];
+  const double s1 = local_coord(b, I.dim, x[0], x[1], x[2], 1);
+  int k0, k1;
+  double w0, w1, dU;
+  profile_dU(b, s1, k0, w0, k1, w1, dU);
+  double xi[3] = {0.0, 0.0, 0.0};
+  if (b.noise != 0.0) {
+    uint32_t c[4] = {(uint32_t)step, sub, 0u, 0u};
+    philox4x32_10(c, I.seed, a.m.uid[i]);
+    xi[0] = uniform_pm1(c[0], c[1]);
+    xi[1] = uniform_pm1(c[2], c[3]);
+    if (I.dim == 3) {
+      uint32_t c2[4] = {(uint32_t)step, sub, 1u, 0u};
+      philox4x32_10(c2, I.seed, a.m.uid[i]);
+      xi[2] = uniform_pm1(c2[0], c2[1]);
+    }
+  }
+  double ld = 0.0;
+  for (int c = 0; c < I.dim; ++c) ld += lv[c] * (b.frame[c] + b.noise * xi[c]);
+  const int ii = a.m.inst[i];
+  if (ii == a.g_inst && bidx == I.buf0 + a.g_buf) {
+    atomicAdd(&a.grad[k0], ld * w0);
+    if (w1 != 0.0) atomicAdd(&a.grad[k1], ld * w1);
+  }
+  for (int c = 0; c < I.dim; ++c) {
+    lx[c] += ld * dU * b.frame[3 + c];
+    lv[c] = 0.0;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------
+// tape kernels (run inside the recomputed forward step)
+// ------------------------------------------------------------------------
+__global__ void k_adj_tape_start(AdjArgs a) {
+  const int n = a.cnt->n_live;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int c = 0; c < 3; ++c) {
+      a.T.x0[c][i] = a.m.x[c][i];
+      a.T.v0[c][i] = a.m.v[c][i];
+    }
+    a.T.rho0[i] = a.m.rho[i];
+    a.T.drho0[i] = a.m.drho[i];
+  }
+}
+
+__global__ void k_adj_tape_sub(AdjArgs a, int s) {
+  const int n = a.cnt->n_live;
+  const size_t o = (size_t)s * a.T.cap;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    a.T.rho_s[o + i] = a.m.rho[i];
+    for (int c = 0; c < 3; ++c) {
+      a.T.v1[c][o + i] = a.m.v[c][i];
+      a.T.xbc[c][o + i] = a.m.x[c][i];
+    }
+  }
+}
+
+__global__ void k_adj_tape_drho(AdjArgs a, int s) {
+  const int n = a.cnt->n_live;
+  const size_t o = (size_t)s * a.T.cap;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    a.T.drho_s[o + i] = a.m.drho[i];
+}
+
+// ------------------------------------------------------------------------
+// objective: J = sum over steps dt sum_{i in S} m_i v_i . n_out / w_s,
+// S = particles of the objective instance labelled in one of the chosen
+// buffers at window start (by uid), n_out = -n_b; evaluated on the state
+// after each step's buffer update (deleted entries excluded)
+// ------------------------------------------------------------------------
+__global__ void k_adj_region(AdjArgs a, uint8_t *region, const int32_t *obj_mask) {
+  const int n = a.cnt->m_pending;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (a.m.inst[i] != a.o_inst || a.pending_keys[i] == a.sentinel) continue;
+    const InstDev &I = a.inst[a.o_inst];
+    const int lab = a.m.label[i];
+    if (lab < 1 || lab > I.nbuf || !obj_mask[lab - 1]) continue;
+    const uint32_t u = a.m.uid[i];
+    if ((int64_t)u < a.n_region) region[u] = (uint8_t)lab;
+  }
+}
+
+__device__ __forceinline__ double member_weight(const AdjArgs &a, int i, double nout[3]) {
+  if (a.m.inst[i] != a.o_inst || a.pending_keys[i] == a.sentinel) return 0.0;
+  const uint32_t u = a.m.uid[i];
+  if ((int64_t)u >= a.n_region) return 0.0;
+  const int lab = a.region[u];
+  if (!lab) return 0.0;
+  const InstDev &I = a.inst[a.o_inst];
+  const BufDev &b = a.buf[I.buf0 + lab - 1];
+  for (int c = 0; c < 3; ++c) nout[c] = c < I.dim ? -b.frame[c] : 0.0;
+  return a.dt_obj * a.m.mass[i] / a.w_s;
+}
+
+__global__ void k_adj_objective(AdjArgs a, int seed) {
+  const int n = a.cnt->m_pending;
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double nout[3];
+    const double w = member_weight(a, i, nout);
+    if (w == 0.0) continue;
+    if (seed) {
+      for (int c = 0; c < 3; ++c) a.lv[c][i] += w * nout[c];
+    } else {
+      acc += w * (a.m.v[0][i] * nout[0] + a.m.v[1][i] * nout[1] + a.m.v[2][i] * nout[2]);
+    }
+  }
+  if (!seed) {
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(a.J, acc);
+  }
+}
+
+// ------------------------------------------------------------------------
+// reverse of the buffer update: the injecting particle's copy inherited its
+// pre-recycle state; the particle itself was shifted by -L_b n_b and given
+// boundary values
+// ------------------------------------------------------------------------
+__global__ void k_adj_buffer_rev(AdjArgs a) {
+  if (a.cnt->overflow) return;  // nothing was committed
+  const int n = a.cnt->n_live;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (a.flag[i] != 1) continue;  // injection
+    const InstDev &I = a.inst[a.m.inst[i]];
+    const int b = buffer_of(a, I, i);
+    if (b < 0) continue;
+    double lv[3] = {a.lv[0][i], a.lv[1][i], a.lv[2][i]};
+    double lx[3] = {a.lx[0][i], a.lx[1][i], a.lx[2][i]};
+    if (a.buf[b].type == SPH_BUF_VELOCITY) {
+      const double x[3] = {a.m.x[0][i], a.m.x[1][i], a.m.x[2][i]};
+      velocity_bc_rev(a, I, b, i, x, a.cnt->spawn_step, kSubRecycle, lv, lx);
+    } else {
+      a.lrho[i] = 0.0;
+    }
+    const int d = a.T.spawn_dst[i];
+    if (d < n || (int64_t)d >= a.T.cap) continue;
+    for (int c = 0; c < 3; ++c) {
+      a.lv[c][i] = lv[c] + a.lv[c][d];
+      a.lx[c][i] = lx[c] + a.lx[c][d];
+    }
+    a.lrho[i] += a.lrho[d];
+    a.ldrho[i] += a.ldrho[d];
+  }
+}
+
+// ------------------------------------------------------------------------
+// reverse of one acoustic sub-step
+// ------------------------------------------------------------------------
+// R1: boundary values and the density update of sub-step s
+__global__ void k_adj_bc_density(AdjArgs a, int s) {
+  const int n = a.cnt->n_live;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const InstDev &I = a.inst[a.m.inst[i]];
+    if (s >= I.n_ac) continue;
+    const double hdt = 0.5 * I.dt;
+    const int b = buffer_of(a, I, i);
+    if (b >= 0) {
+      if (a.buf[b].type == SPH_BUF_VELOCITY) {
+        double lv[3] = {a.lv[0][i], a.lv[1][i], a.lv[2][i]};
+        double lx[3] = {a.lx[0][i], a.lx[1][i], a.lx[2][i]};
+        const size_t o = (size_t)s * a.T.cap + i;
+        const double x[3] = {a.T.xbc[0][o], a.T.xbc[1][o], a.T.xbc[2][o]};
+        velocity_bc_rev(a, I, b, i, x, a.cnt->spawn_step, (uint32_t)s, lv, lx);
+        for (int c = 0; c < 3; ++c) {
+          a.lv[c][i] = lv[c];
+          a.lx[c][i] = lx[c];
+        }
+      } else {
+        a.lrho[i] = 0.0;
+      }
+    }
+    // rho' = rho_s + hdt drho, drho = rho_s Sigma
+    const double rs = rho_s(a, s, i);
+    const double Sig = a.T.drho_s[(size_t)s * a.T.cap + i] / rs;
+    const double ltot = a.ldrho[i] + hdt * a.lrho[i];
+    a.sd[0][i] = ltot * rs;
+    a.lrho[i] += ltot * Sig;
+    a.ldrho[i] = 0.0;
+  }
+}
+
+// R2: continuity sum  Sigma_i = sum_j [v_ij . r_ij + (p_i - p_j) r / (rho0 c0)] F V_j
+template <int D, bool PER>
+__global__ void k_adj_cont(AdjArgs a, int s) {
+  const int n = a.cnt->n_live;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const InstDev &I = a.inst[a.m.inst[i]];
+    if (s >= I.n_ac) continue;
+    const G g = make_geo<double, D>(I);
+    const double kap = I.inv_rc0, c0sq = I.c0sq;
+    const size_t o = (size_t)s * a.T.cap;
+    double xi[3];
+    load_x0(a, i, xi);
+    const double rsi = a.T.rho_s[o + i], pi = c0sq * (rsi - I.rho0), Vi = a.m.mass[i] / rsi;
+    const double vi[3] = {a.T.v1[0][o + i], a.T.v1[1][o + i], a.T.v1[2][o + i]};
+    const double lsi = a.sd[0][i];
+    double lvi[3] = {0, 0, 0}, lxi[3] = {0, 0, 0}, lpi = 0.0, lVi = 0.0;
+    const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
+    const uint32_t *L = a.nl.nbr + i;
+    const size_t LS = (size_t)a.nl.stride;
+    for (int kk = 0; kk < nr; ++kk) {
+      const int j = (int)L[kk * LS];
+      double xj[3], d[3];
+      load_x0(a, j, xj);
+      const double rr = pvec<D, PER>(g, xi, xj, d);
+      const double r = sqrt(rr);
+      double F, Fr;
+      kernel_FF(g, r, F, Fr);
+      const double rsj = a.T.rho_s[o + j], pj = c0sq * (rsj - I.rho0), Vj = a.m.mass[j] / rsj;
+      const double vv[3] = {vi[0] - a.T.v1[0][o + j], vi[1] - a.T.v1[1][o + j], vi[2] - a.T.v1[2][o + j]};
+      const double lsj = a.sd[0][j];
+      const double vd = dot3(vv, d), dp = pi - pj;
+      // own term (seed lsi)
+      const double br = vd + dp * kap * r;
+      for (int c = 0; c < D; ++c) {
+        lvi[c] += lsi * F * Vj * d[c];
+        lxi[c] += lsi * Vj * (F * vv[c] + br * Fr * d[c] / r + dp * kap * F * d[c] / r);
+      }
+      lpi += lsi * kap * r * F * Vj;
+      // neighbour's term (seed lsj), i as its source
+      const double br2 = vd - dp * kap * r;
+      for (int c = 0; c < D; ++c) {
+        lvi[c] += lsj * F * Vi * d[c];
+        lxi[c] += lsj * Vi * (F * vv[c] + br2 * Fr * d[c] / r - dp * kap * F * d[c] / r);
+      }
+      lpi -= lsj * kap * r * F * Vi;
+      lVi += lsj * br2 * F;
+    }
+    for (int kk = nr; kk < nr + nw; ++kk) {
+      const int w = (int)L[kk * LS];
+      const double xw[3] = {a.wx[0][w], a.wx[1][w], a.wx[2][w]};
+      double d[3];
+      const double rr = pvec<D, PER>(g, xi, xw, d);
+      const double r = sqrt(rr);
+      double F, Fr;
+      kernel_FF(g, r, F, Fr);
+      const V4<double> Wv = a.WV[w];
+      const double vv[3] = {vi[0] - Wv.x, vi[1] - Wv.y, vi[2] - Wv.z};
+      const double vd = dot3(vv, d), Vw = I.Vw;
+      for (int c = 0; c < D; ++c) {
+        lvi[c] += lsi * 2.0 * F * Vw * d[c];
+        lxi[c] += lsi * 2.0 * Vw * (F * vv[c] + vd * Fr * d[c] / r);
+      }
+    }
+    for (int c = 0; c < D; ++c) {
+      a.lv[c][i] += lvi[c];
+      a.lxg[c][i] += lxi[c];
+    }
+    a.lrho[i] += c0sq * lpi - (Vi / rsi) * lVi;
+  }
+}
+
+// momentum sums of particle i at sub-step s (forward recomputation)
+template <int D, bool PER>
+__device__ void mom_sums(const AdjArgs &a, const InstDev &I, const G &g, int s, int i, const double xi[3],
+                         double pei, double S1[3], double Cb[3], double S2[3], double Ct[3]) {
+  const size_t o = (size_t)s * a.T.cap;
+  const double c0sq = I.c0sq;
+  for (int c = 0; c < 3; ++c) S1[c] = Cb[c] = S2[c] = Ct[c] = 0.0;
+  const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
+  const uint32_t *L = a.nl.nbr + i;
+  const size_t LS = (size_t)a.nl.stride;
+  for (int kk = 0; kk < nr; ++kk) {
+    const int j = (int)L[kk * LS];
+    double xj[3], d[3];
+    load_x0(a, j, xj);
+    const double r = sqrt(pvec<D, PER>(g, xi, xj, d));
+    double F, Fr;
+    kernel_FF(g, r, F, Fr);
+    const double rsj = a.T.rho_s[o + j], pj = c0sq * (rsj - I.rho0), Vj = a.m.mass[j] / rsj;
+    const double kwj = I.rans ? (2.0 / 3.0) * a.m.k[j] : 0.0;
+    const double pej = I.rans ? pj + kwj * (I.rho0 + pj / c0sq) : pj;
+    double gw[3] = {Vj * F * d[0], Vj * F * d[1], Vj * F * d[2]};
+    if (is_pressure(a, I, j)) {
+      for (int c = 0; c < D; ++c) Cb[c] += gw[c];
+    } else {
+      double Bj[6], bg[3];
+      load_B(a, j, D, Bj);
+      sym_matvec<double, D>(Bj, gw, bg);
+      for (int c = 0; c < D; ++c) S1[c] += bg[c];
+    }
+    for (int c = 0; c < D; ++c) {
+      S2[c] += pej * gw[c];
+      Ct[c] += gw[c];
+    }
+  }
+  for (int kk = nr; kk < nr + nw; ++kk) {
+    const int w = (int)L[kk * LS];
+    const double xw[3] = {a.wx[0][w], a.wx[1][w], a.wx[2][w]};
+    double d[3];
+    const double r = sqrt(pvec<D, PER>(g, xi, xw, d));
+    double F, Fr;
+    kernel_FF(g, r, F, Fr);
+    for (int c = 0; c < D; ++c) {
+      const double gv = I.Vw * F * d[c];
+      Cb[c] += gv;
+      S2[c] += pei * gv;
+      Ct[c] += gv;
+    }
+  }
+}
+
+// R3: reverse of the kick and half drift, then the per-particle part of the
+// momentum reverse: seeds a1 (S1), ab (Cb), a2 (S2), at (Ct) and the direct
+// dependence on rho_i (1/rho_i, p_i, compensation) and B_i
+template <int D, bool PER>
+__global__ void k_adj_mom_seed(AdjArgs a, int s) {
+  const int n = a.cnt->n_live;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const InstDev &I = a.inst[a.m.inst[i]];
+    if (s >= I.n_ac) continue;
+    const G g = make_geo<double, D>(I);
+    const double dt = I.dt, hdt = 0.5 * I.dt, c0sq = I.c0sq;
+    double la[3] = {0, 0, 0};
+    for (int c = 0; c < D; ++c) {
+      const double lv = a.lv[c][i] + hdt * a.lx[c][i];
+      a.lv[c][i] = lv;
+      la[c] = dt * lv;
+      a.lan[c][i] += dt * lv;
+    }
+    double xi[3];
+    load_x0(a, i, xi);
+    const double rsi = rho_s(a, s, i), pi = c0sq * (rsi - I.rho0);
+    const double kwi = I.rans ? (2.0 / 3.0) * a.m.k[i] : 0.0;
+    const double pei = I.rans ? pi + kwi * (I.rho0 + pi / c0sq) : pi;
+    double S1[3], Cb[3], S2[3], Ct[3];
+    mom_sums<D, PER>(a, I, g, s, i, xi, pei, S1, Cb, S2, Ct);
+    double B[6];
+    load_B(a, i, D, B);
+    const bool comp = is_pressure(a, I, i);
+    const int bi = buffer_of(a, I, i);
+    double pob = comp ? a.buf[bi].p_ob : 0.0;
+    if (comp && I.rans) pob += (2.0 / 3.0) * rsi * a.m.k[i];
+    double Bla[3], BCb[3], BS2[3], BCt[3];
+    sym_matvec<double, D>(B, la, Bla);
+    sym_matvec<double, D>(B, Cb, BCb);
+    sym_matvec<double, D>(B, S2, BS2);
+    sym_matvec<double, D>(B, Ct, BCt);
+    const double inv = 1.0 / rsi;
+    for (int c = 0; c < 3; ++c) {
+      a.sd[0 + c][i] = c < D ? -pei * inv * la[c] : 0.0;
+      a.sd[3 + c][i] = c < D ? -pei * inv * Bla[c] : 0.0;
+      a.sd[6 + c][i] = c < D ? -inv * Bla[c] : 0.0;
+      a.sd[9 + c][i] = (c < D && comp) ? 2.0 * pob * inv * Bla[c] : 0.0;
+    }
+    double accp = 0.0, accc = 0.0, lpe = 0.0;
+    for (int c = 0; c < D; ++c) {
+      accp += la[c] * (-(pei * (S1[c] + BCb[c]) + BS2[c]) * inv);
+      if (comp) accc += la[c] * 2.0 * pob * inv * BCt[c];
+      lpe += -inv * la[c] * (S1[c] + BCb[c]);
+    }
+    double lrho = -(accp + accc) * inv + lpe * (c0sq + kwi);
+    if (comp && I.rans) {
+      double t = 0.0;
+      for (int c = 0; c < D; ++c) t += la[c] * BCt[c];
+      lrho += 2.0 * inv * (2.0 / 3.0) * a.m.k[i] * t;
+    }
+    a.lrho[i] += lrho;
+    double lB[6] = {0, 0, 0, 0, 0, 0};
+    sym_acc(lB, la, Cb, -pei * inv);
+    sym_acc(lB, la, S2, -inv);
+    if (comp) sym_acc(lB, la, Ct, 2.0 * pob * inv);
+    for (int q = 0; q < 6; ++q) a.lB[q][i] += lB[q];
+  }
+}
+
+// R4: momentum pair reverse
+template <int D, bool PER>
+__global__ void k_adj_mom(AdjArgs a, int s) {
+  const int n = a.cnt->n_live;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const InstDev &I = a.inst[a.m.inst[i]];
+    if (s >= I.n_ac) continue;
+    const G g = make_geo<double, D>(I);
+    const size_t o = (size_t)s * a.T.cap;
+    const double c0sq = I.c0sq;
+    double xi[3];
+    load_x0(a, i, xi);
+    const double rsi = a.T.rho_s[o + i], pi = c0sq * (rsi - I.rho0), Vi = a.m.mass[i] / rsi;
+    const double kwi = I.rans ? (2.0 / 3.0) * a.m.k[i] : 0.0;
+    const double pei = I.rans ? pi + kwi * (I.rho0 + pi / c0sq) : pi;
+    const bool mk_i = is_pressure(a, I, i);
+    double Bi[6];
+    load_B(a, i, D, Bi);
+    const double a1i[3] = {a.sd[0][i], a.sd[1][i], a.sd[2][i]}, abi[3] = {a.sd[3][i], a.sd[4][i], a.sd[5][i]};
+    const double a2i[3] = {a.sd[6][i], a.sd[7][i], a.sd[8][i]}, ati[3] = {a.sd[9][i], a.sd[10][i], a.sd[11][i]};
+    double lxi[3] = {0, 0, 0}, lB[6] = {0, 0, 0, 0, 0, 0}, lpe = 0.0, lVi = 0.0;
+    const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
+    const uint32_t *L = a.nl.nbr + i;
+    const size_t LS = (size_t)a.nl.stride;
+    for (int kk = 0; kk < nr; ++kk) {
+      const int j = (int)L[kk * LS];
+      double xj[3], d[3];
+      load_x0(a, j, xj);
+      const double r = sqrt(pvec<D, PER>(g, xi, xj, d));
+      double F, Fr;
+      kernel_FF(g, r, F, Fr);
+      const double rsj = a.T.rho_s[o + j], pj = c0sq * (rsj - I.rho0), Vj = a.m.mass[j] / rsj;
+      const double kwj = I.rans ? (2.0 / 3.0) * a.m.k[j] : 0.0;
+      const double pej = I.rans ? pj + kwj * (I.rho0 + pj / c0sq) : pj;
+      const bool mk_j = is_pressure(a, I, j);
+      double Bj[6];
+      load_B(a, j, D, Bj);
+      // own term: L = G . gw, gw = V_j F d
+      double Gv[3];
+      if (mk_j) {
+        for (int c = 0; c < 3; ++c) Gv[c] = abi[c];
+      } else {
+        sym_matvec<double, D>(Bj, a1i, Gv);
+      }
+      for (int c = 0; c < D; ++c) Gv[c] += pej * a2i[c] + ati[c];
+      double Gd = 0.0;
+      for (int c = 0; c < D; ++c) Gd += Gv[c] * d[c];
+      for (int c = 0; c < D; ++c) lxi[c] += Vj * (F * Gv[c] + Gd * Fr * d[c] / r);
+      // neighbour's term with i as its source: gw' = -V_i F d
+      const double a1j[3] = {a.sd[0][j], a.sd[1][j], a.sd[2][j]}, abj[3] = {a.sd[3][j], a.sd[4][j], a.sd[5][j]};
+      const double a2j[3] = {a.sd[6][j], a.sd[7][j], a.sd[8][j]}, atj[3] = {a.sd[9][j], a.sd[10][j], a.sd[11][j]};
+      double Gp[3];
+      if (mk_i) {
+        for (int c = 0; c < 3; ++c) Gp[c] = abj[c];
+      } else {
+        sym_matvec<double, D>(Bi, a1j, Gp);
+      }
+      for (int c = 0; c < D; ++c) Gp[c] += pei * a2j[c] + atj[c];
+      double gwp[3] = {-Vi * F * d[0], -Vi * F * d[1], -Vi * F * d[2]};
+      if (!mk_i) sym_acc(lB, a1j, gwp, 1.0);
+      double Gpd = 0.0, a2g = 0.0;
+      for (int c = 0; c < D; ++c) {
+        Gpd += Gp[c] * d[c];
+        a2g += a2j[c] * gwp[c];
+      }
+      lpe += a2g;
+      lVi += -F * Gpd;
+      for (int c = 0; c < D; ++c) lxi[c] += -Vi * (F * Gp[c] + Gpd * Fr * d[c] / r);
+    }
+    for (int kk = nr; kk < nr + nw; ++kk) {
+      const int w = (int)L[kk * LS];
+      const double xw[3] = {a.wx[0][w], a.wx[1][w], a.wx[2][w]};
+      double d[3];
+      const double r = sqrt(pvec<D, PER>(g, xi, xw, d));
+      double F, Fr;
+      kernel_FF(g, r, F, Fr);
+      double Gv[3], Gd = 0.0, a2g = 0.0;
+      for (int c = 0; c < D; ++c) {
+        Gv[c] = abi[c] + pei * a2i[c] + ati[c];
+        Gd += Gv[c] * d[c];
+        a2g += a2i[c] * I.Vw * F * d[c];
+      }
+      lpe += a2g;
+      for (int c = 0; c < D; ++c) lxi[c] += I.Vw * (F * Gv[c] + Gd * Fr * d[c] / r);
+    }
+    for (int c = 0; c < D; ++c) a.lxg[c][i] += lxi[c];
+    for (int q = 0; q < 6; ++q) a.lB[q][i] += lB[q];
+    a.lrho[i] += lpe * (c0sq + kwi) - (Vi / rsi) * lVi;
+  }
+}
+
+// R5: reverse of the first half of sub-step s: rho_s = rho + hdt drho,
+// x += hdt v
+__global__ void k_adj_half1(AdjArgs a, int s) {
+  const int n = a.cnt->n_live;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const InstDev &I = a.inst[a.m.inst[i]];
+    if (s >= I.n_ac) continue;
+    const double hdt = 0.5 * I.dt;
+    a.ldrho[i] += hdt * a.lrho[i];
+    for (int c = 0; c < I.dim; ++c) a.lv[c][i] += hdt * a.lx[c][i];
+  }
+}
+
+// ------------------------------------------------------------------------
+// reverse of the advection sweep: B (with mirror images) and the viscous
+// acceleration, from the adjoints of B (lB) and a_nu (lan)
+// ------------------------------------------------------------------------
+__global__ void k_adj_adv_seed(AdjArgs a) {
+  const int n = a.cnt->n_live;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const InstDev &I = a.inst[a.m.inst[i]];
+    const double rho = a.T.rho0[i];
+    double t = 0.0;
+    for (int c = 0; c < I.dim; ++c) {
+      const double l = a.lan[c][i];
+      a.sd[6 + c][i] = 2.0 * l / rho;
+      t += a.der.an[c][i] * l;
+    }
+    if (I.dim == 2) a.sd[8][i] = 0.0;
+    a.lrho[i] -= t / rho;
+    // lambda_A = -B Lambda_B B unless the guard replaced B by I
+    double Bs[6];
+    load_B(a, i, I.dim, Bs);
+    const bool guard = Bs[0] == 1.0 && Bs[1] == 1.0 && Bs[3] == 0.0 &&
+                       (I.dim == 2 || (Bs[2] == 1.0 && Bs[4] == 0.0 && Bs[5] == 0.0));
+    double lA[6] = {0, 0, 0, 0, 0, 0};
+    if (!guard) {
+      double B[3][3], Lm[3][3], T[3][3], R[3][3];
+      sym_full(Bs, B);
+      const double lb[6] = {a.lB[0][i], a.lB[1][i], a.lB[2][i], a.lB[3][i], a.lB[4][i], a.lB[5][i]};
+      sym_full(lb, Lm);
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) T[p][q] = Lm[p][0] * B[0][q] + Lm[p][1] * B[1][q] + Lm[p][2] * B[2][q];
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) R[p][q] = -(B[p][0] * T[0][q] + B[p][1] * T[1][q] + B[p][2] * T[2][q]);
+      lA[0] = R[0][0];
+      lA[1] = R[1][1];
+      lA[2] = R[2][2];
+      lA[3] = 0.5 * (R[0][1] + R[1][0]);
+      lA[4] = 0.5 * (R[0][2] + R[2][0]);
+      lA[5] = 0.5 * (R[1][2] + R[2][1]);
+    }
+    for (int q = 0; q < 6; ++q) a.sd[q][i] = lA[q];
+  }
+}
+
+// viscous coefficient of a pair and whether the ARD term is the active one
+__device__ __forceinline__ double visc_mu(const InstDev &I, double mu_a, double mu_b, bool harmonic,
+                                          const double vv[3], const double d[3], double r, bool &ard) {
+  ard = false;
+  if (!I.rans) return mu_a;
+  const double mut = harmonic ? 2.0 * mu_a * mu_b / (mu_a + mu_b) : mu_a;
+  const double ve = -dot3(vv, d) / r;
+  const double lim = I.eta * (ve > 0.0 ? ve : 0.0);
+  const double muR = I.muR_k * (lim < I.c0 ? lim : I.c0);
+  if (mut > muR) return mut;
+  ard = ve > 0.0 && lim < I.c0;
+  return muR;
+}
+
+template <int D, bool PER>
+__global__ void k_adj_adv(AdjArgs a) {
+  const int n = a.cnt->n_live;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const InstDev &I = a.inst[a.m.inst[i]];
+    const G g = make_geo<double, D>(I);
+    const double reg = I.reg, kR = I.muR_k * I.eta;
+    double xi[3];
+    load_x0(a, i, xi);
+    const double vi[3] = {a.T.v0[0][i], a.T.v0[1][i], a.T.v0[2][i]};
+    const double rhoi = a.T.rho0[i], Vi = a.m.mass[i] / rhoi;
+    const double mui = I.rho0 * (I.nu_l + (I.rans ? a.m.nut[i] : 0.0));
+    double LAi[3][3];
+    {
+      const double s6[6] = {a.sd[0][i], a.sd[1][i], a.sd[2][i], a.sd[3][i], a.sd[4][i], a.sd[5][i]};
+      sym_full(s6, LAi);
+    }
+    const double sgi[3] = {a.sd[6][i], a.sd[7][i], a.sd[8][i]};
+    const int bi = buffer_of(a, I, i);
+    const bool mir_i = bi >= 0 && a.buf[bi].type == SPH_BUF_PRESSURE;
+    double lvi[3] = {0, 0, 0}, lxi[3] = {0, 0, 0}, lVi = 0.0;
+    const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
+    const uint32_t *L = a.nl.nbr + i;
+    const size_t LS = (size_t)a.nl.stride;
+    for (int kk = 0; kk < nr; ++kk) {
+      const int j = (int)L[kk * LS];
+      double xj[3], d[3];
+      load_x0(a, j, xj);
+      const double r = sqrt(pvec<D, PER>(g, xi, xj, d));
+      double F, Fr;
+      kernel_FF(g, r, F, Fr);
+      const double rhoj = a.T.rho0[j], Vj = a.m.mass[j] / rhoj;
+      const double vv[3] = {vi[0] - a.T.v0[0][j], vi[1] - a.T.v0[1][j], vi[2] - a.T.v0[2][j]};
+      const double muj = I.rans ? I.rho0 * (I.nu_l + a.m.nut[j]) : mui;
+      bool ard;
+      const double mu = visc_mu(I, mui, muj, true, vv, d, r, ard);
+      const double rf = r / (r + reg), dfr = Fr * rf + F * reg / ((r + reg) * (r + reg));
+      const double vd = dot3(vv, d);
+      // ---- own terms (seeds of i) ----
+      if (!mir_i || !(local_coord(a.buf[bi], D, xj[0], xj[1], xj[2], 0) < 0.0)) {
+        double u[3];
+        matvec3(LAi, d, u);
+        const double q = dot3(d, u);
+        for (int c = 0; c < D; ++c) lxi[c] += -Vj * (Fr * q * d[c] / r + 2.0 * F * u[c]);
+      }
+      {
+        const double f = F * rf * Vj, sv = dot3(sgi, vv);
+        for (int c = 0; c < D; ++c) {
+          lvi[c] += mu * f * sgi[c];
+          lxi[c] += mu * sv * Vj * dfr * d[c] / r;
+        }
+        if (ard) {
+          const double Lm = f * sv * kR;
+          for (int c = 0; c < D; ++c) {
+            lvi[c] += -Lm * d[c] / r;
+            lxi[c] += Lm * (-vv[c] / r + vd * d[c] / (r * r * r));
+          }
+        }
+      }
+      // ---- neighbour's terms (seeds of j), i as the source ----
+      const int bj = buffer_of(a, I, j);
+      const bool mir_j = bj >= 0 && a.buf[bj].type == SPH_BUF_PRESSURE;
+      if (!mir_j || !(local_coord(a.buf[bj], D, xi[0], xi[1], xi[2], 0) < 0.0)) {
+        double LAj[3][3], u[3];
+        const double s6[6] = {a.sd[0][j], a.sd[1][j], a.sd[2][j], a.sd[3][j], a.sd[4][j], a.sd[5][j]};
+        sym_full(s6, LAj);
+        matvec3(LAj, d, u);
+        const double q = dot3(d, u);
+        lVi += -F * q;
+        for (int c = 0; c < D; ++c) lxi[c] += -Vi * (Fr * q * d[c] / r + 2.0 * F * u[c]);
+      }
+      {
+        const double sgj[3] = {a.sd[6][j], a.sd[7][j], a.sd[8][j]};
+        const double fp = F * rf * Vi, svp = -dot3(sgj, vv);  // v_ji = -v_ij
+        for (int c = 0; c < D; ++c) {
+          lvi[c] += -mu * fp * sgj[c];
+          lxi[c] += mu * svp * Vi * dfr * d[c] / r;
+        }
+        lVi += mu * F * rf * svp;
+        if (ard) {
+          const double Lm = fp * svp * kR;
+          for (int c = 0; c < D; ++c) {
+            lvi[c] += -Lm * d[c] / r;
+            lxi[c] += Lm * (-vv[c] / r + vd * d[c] / (r * r * r));
+          }
+        }
+      }
+    }
+    for (int kk = nr; kk < nr + nw; ++kk) {
+      const int w = (int)L[kk * LS];
+      const double xw[3] = {a.wx[0][w], a.wx[1][w], a.wx[2][w]};
+      double d[3];
+      const double r = sqrt(pvec<D, PER>(g, xi, xw, d));
+      double F, Fr;
+      kernel_FF(g, r, F, Fr);
+      const double Vw = I.Vw;
+      if (!mir_i || !(local_coord(a.buf[bi], D, xw[0], xw[1], xw[2], 0) < 0.0)) {
+        double u[3];
+        matvec3(LAi, d, u);
+        const double q = dot3(d, u);
+        for (int c = 0; c < D; ++c) lxi[c] += -Vw * (Fr * q * d[c] / r + 2.0 * F * u[c]);
+      }
+      const V4<double> Wv = a.WV[w];
+      const double vv[3] = {2.0 * (vi[0] - Wv.x), 2.0 * (vi[1] - Wv.y), 2.0 * (vi[2] - Wv.z)};
+      bool ard;
+      const double mu = visc_mu(I, mui, mui, false, vv, d, r, ard);
+      const double rf = r / (r + reg), dfr = Fr * rf + F * reg / ((r + reg) * (r + reg));
+      const double f = F * rf * Vw, sv = dot3(sgi, vv), vd = dot3(vv, d);
+      for (int c = 0; c < D; ++c) {
+        lvi[c] += 2.0 * mu * f * sgi[c];
+        lxi[c] += mu * sv * Vw * dfr * d[c] / r;
+      }
+      if (ard) {
+        const double Lm = f * sv * kR;
+        for (int c = 0; c < D; ++c) {
+          lvi[c] += -2.0 * Lm * d[c] / r;
+          lxi[c] += Lm * (-vv[c] / r + vd * d[c] / (r * r * r));
+        }
+      }
+    }
+    if (mir_i) {
+      // images m_k = x_k - 2 s_k n of every particle with s_k >= 0 around the
+      // image of x_i (two-cell margin), as the forward sweep found them
+      const BufDev &b = a.buf[bi];
+      const double nb[3] = {b.frame[0], b.frame[1], b.frame[2]};
+      const double si = local_coord(b, D, xi[0], xi[1], xi[2], 0);
+      const double q0 = xi[0] - 2.0 * si * nb[0], q1 = xi[1] - 2.0 * si * nb[1];
+      const double q2 = D == 3 ? xi[2] - 2.0 * si * nb[2] : 0.0;
+      const int qx = cell_coord(I, q0, 0), qy = cell_coord(I, q1, 1), qz = D == 3 ? cell_coord(I, q2, 2) : 0;
+      for (int set = 0; set < 2; ++set) {
+        visit_cells<D, PER>(I, qx, qy, qz, 2, set == 0 ? a.off : a.woff, [&](uint32_t jb, uint32_t je) {
+          for (uint32_t k = jb; k < je; ++k) {
+            double xk[3];
+            double Vk;
+            if (set == 0) {
+              load_x0(a, (int)k, xk);
+              Vk = a.m.mass[k] / a.T.rho0[k];
+            } else {
+              xk[0] = a.wx[0][k];
+              xk[1] = a.wx[1][k];
+              xk[2] = a.wx[2][k];
+              Vk = I.Vw;
+            }
+            const double sk = local_coord(b, D, xk[0], xk[1], xk[2], 0);
+            if (sk < 0.0) continue;
+            double dd[3] = {0, 0, 0}, rr = 0.0;
+            for (int c = 0; c < D; ++c) {
+              dd[c] = xi[c] - (xk[c] - 2.0 * sk * nb[c]);
+              rr += dd[c] * dd[c];
+            }
+            if (!(rr > 0.0 && rr < g.cut2)) continue;
+            const double r = sqrt(rr);
+            double F, Fr;
+            kernel_FF(g, r, F, Fr);
+            double u[3];
+            matvec3(LAi, dd, u);
+            const double q = dot3(dd, u);
+            double gd[3] = {0, 0, 0};
+            for (int c = 0; c < D; ++c) {
+              gd[c] = -Vk * (Fr * q * dd[c] / r + 2.0 * F * u[c]);
+              lxi[c] += gd[c];
+            }
+            if (set == 0) {
+              double ng = 0.0;
+              for (int c = 0; c < D; ++c) ng += nb[c] * gd[c];
+              for (int c = 0; c < D; ++c) atomicAdd(&a.lxs[c][k], -(gd[c] - 2.0 * nb[c] * ng));
+              atomicAdd(&a.lrhos[k], (-F * q) * (-Vk / a.T.rho0[k]));
+            }
+          }
+        });
+      }
+    }
+    for (int c = 0; c < D; ++c) {
+      a.lv[c][i] += lvi[c];
+      a.lxg[c][i] += lxi[c];
+    }
+    a.lrho[i] += -(Vi / rhoi) * lVi;
+  }
+}
+
+// ------------------------------------------------------------------------
+// reverse of the cell sort: adjoint in the pending order of the step
+// ------------------------------------------------------------------------
+__global__ void k_adj_perm_rev(AdjArgs a) {
+  const int n = a.cnt->n_live;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int s = (int)a.T.perm[t];
+    for (int c = 0; c < 3; ++c) {
+      a.out[c][s] = a.lx[c][t] + a.lxg[c][t] + a.lxs[c][t];
+      a.out[3 + c][s] = a.lv[c][t];
+    }
+    a.out[6][s] = a.lrho[t] + a.lrhos[t];
+    a.out[7][s] = a.ldrho[t];
+  }
+}
+
+// ------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------
+static int grid_of(int max_n, int block) {
+  int g = (max_n + block - 1) / block;
+  return g < 1 ? 1 : (g > 65535 ? 65535 : g);
+}
+
+void launch_adj_tape_start(const AdjArgs &a, int max_n, cudaStream_t st) {
+  k_adj_tape_start<<<grid_of(max_n, 256), 256, 0, st>>>(a);
+}
+void launch_adj_tape_sub(const AdjArgs &a, int sub, int max_n, cudaStream_t st) {
+  k_adj_tape_sub<<<grid_of(max_n, 256), 256, 0, st>>>(a, sub);
+}
+void launch_adj_tape_drho(const AdjArgs &a, int sub, int max_n, cudaStream_t st) {
+  k_adj_tape_drho<<<grid_of(max_n, 256), 256, 0, st>>>(a, sub);
+}
+void launch_adj_region(const AdjArgs &a, uint8_t *region, const int32_t *obj_buf_mask, int max_n,
+                       cudaStream_t st) {
+  k_adj_region<<<grid_of(max_n, 256), 256, 0, st>>>(a, region, obj_buf_mask);
+}
+void launch_adj_objective(const AdjArgs &a, int seed, int max_n, cudaStream_t st) {
+  k_adj_objective<<<grid_of(max_n, 256), 256, 0, st>>>(a, seed);
+}
+void launch_adj_buffer_rev(const AdjArgs &a, int max_n, cudaStream_t st) {
+  k_adj_buffer_rev<<<grid_of(max_n, 256), 256, 0, st>>>(a);
+}
+
+template <int D, bool PER>
+static void substep_rev(const AdjArgs &a, int s, int max_n, cudaStream_t st) {
+  const int g = grid_of(max_n, kBlock);
+  k_adj_bc_density<<<g, kBlock, 0, st>>>(a, s);
+  k_adj_cont<D, PER><<<g, kBlock, 0, st>>>(a, s);
+  k_adj_mom_seed<D, PER><<<g, kBlock, 0, st>>>(a, s);
+  k_adj_mom<D, PER><<<g, kBlock, 0, st>>>(a, s);
+  k_adj_half1<<<g, kBlock, 0, st>>>(a, s);
+}
+
+void launch_adj_substep_rev(const AdjArgs &a, int dim, int any_periodic, int sub, int max_n, cudaStream_t st) {
+  if (dim == 2)
+    any_periodic ? substep_rev<2, true>(a, sub, max_n, st) : substep_rev<2, false>(a, sub, max_n, st);
+  else
+    any_periodic ? substep_rev<3, true>(a, sub, max_n, st) : substep_rev<3, false>(a, sub, max_n, st);
+}
+
+void launch_adj_adv_rev(const AdjArgs &a, int dim, int any_periodic, int max_n, cudaStream_t st) {
+  const int g = grid_of(max_n, kBlock);
+  k_adj_adv_seed<<<g, kBlock, 0, st>>>(a);
+  if (dim == 2) {
+    if (any_periodic)
+      k_adj_adv<2, true><<<g, kBlock, 0, st>>>(a);
+    else
+      k_adj_adv<2, false><<<g, kBlock, 0, st>>>(a);
+  } else {
+    if (any_periodic)
+      k_adj_adv<3, true><<<g, kBlock, 0, st>>>(a);
+    else
+      k_adj_adv<3, false><<<g, kBlock, 0, st>>>(a);
+  }
+}
+
+void launch_adj_perm_rev(const AdjArgs &a, int max_n, cudaStream_t st) {
+  k_adj_perm_rev<<<grid_of(max_n, 256), 256, 0, st>>>(a);
+}
+
+}  // namespace sphk

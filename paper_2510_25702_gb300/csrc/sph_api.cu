@@ -80,7 +80,7 @@ struct sph_ctx {
   uint8_t *flag = nullptr;
   int32_t *block_cnt = nullptr;
   SortTemp sort_tmp{};
-  uint32_t *sorted_keys = nullptr;
+  uint32_t *sorted_keys = nullptr, *sorted_vals = nullptr;
   NbrList nl{};
   // stage timing (CUDA event pairs on the context's stream)
   bool prof = false;
@@ -104,6 +104,23 @@ struct sph_ctx {
     int64_t step = 0;
   };
   std::vector<Snap> snaps;
+  // differentiated window (adjoint)
+  struct Adj {
+    bool fwd = false;
+    sph_adjoint_desc d{};
+    std::vector<int32_t> ckpt;
+    int32_t end_slot = -1;
+    void *mem = nullptr;
+    size_t bytes = 0;
+    AdjTape T{};
+    double *lam[8] = {}, *out[8] = {};  // x3, v3, rho, drho
+    double *lxg[3] = {}, *lxs[3] = {}, *lrhos = nullptr, *lB[6] = {}, *lan[3] = {}, *sd[12] = {};
+    double *grad = nullptr, *J = nullptr;
+    uint8_t *region = nullptr;
+    int32_t *mask = nullptr;
+    int64_t n_region = 0;
+    double dt = 0.0;
+  } adj;
 
   void drop_graphs() {
     for (int q = 0; q < 2; ++q) {
@@ -215,6 +232,10 @@ struct sph_ctx {
     return a;
   }
 };
+
+extern "C" {
+static void adj_free(sph_ctx *c);
+}
 
 // ------------------------------------------------------------------------
 // host-side derived constants (compiled without FP contraction so that the
@@ -677,6 +698,7 @@ int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *
 void sph_destroy(sph_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  adj_free(c);
   for (size_t q = 0; q < c->snaps.size(); ++q)
     if (c->snaps[q].mem) sph_drop_state(c, (int32_t)q);
   c->drop_graphs();
@@ -885,6 +907,7 @@ static void enqueue_topology(sph_ctx *c) {
   c->prof_end(ev);
   c->cur = 1 - c->cur;
   c->sorted_keys = ks;
+  c->sorted_vals = vs;
   c->launches += kSortKernelsPerPass * radix_passes(c->key_bits) + 2;
 }
 
@@ -1104,6 +1127,279 @@ int sph_drop_state(sph_ctx *c, int32_t slot) {
   else
     cudaFree(sn.mem);
   sn = sph_ctx::Snap();
+  return SPH_OK;
+}
+
+// ------------------------------------------------------------------------
+// differentiated windows
+// ------------------------------------------------------------------------
+static void adj_free(sph_ctx *c) {
+  sph_ctx::Adj &A = c->adj;
+  cudaStreamSynchronize(c->stream);
+  for (int32_t s : A.ckpt) sph_drop_state(c, s);
+  if (A.end_slot >= 0) sph_drop_state(c, A.end_slot);
+  if (A.mem) {
+    if (c->alloc.free)
+      c->alloc.free(c->alloc.user, A.mem, c->alloc.stream);
+    else
+      cudaFree(A.mem);
+  }
+  A = sph_ctx::Adj();
+}
+
+static void set_freeze(sph_ctx *c, int on) {
+  for (int i = 0; i < c->ninst; ++i) {
+    c->inst[i].freeze_turb = on;
+    cudaMemcpyAsync(&c->d_inst[i].freeze_turb, &c->inst[i].freeze_turb, sizeof(int32_t), cudaMemcpyHostToDevice,
+                    c->stream);
+  }
+}
+
+// carve the work arrays of the reverse pass out of one allocation
+static int adj_alloc(sph_ctx *c) {
+  sph_ctx::Adj &A = c->adj;
+  if (A.mem) return 0;
+  const size_t cap = (size_t)c->cap, ns = (size_t)c->n_ac_max;
+  const size_t nd = 8 + 8 + 3 + 3 + 1 + 6 + 3 + 12 + (3 + 3 + 1 + 1) + ns * (1 + 1 + 3 + 3);
+  const size_t bytes = nd * (cap * 8 + 256) + 2 * (cap * 4 + 256) + 2 * 256 + (size_t)A.d.n_theta * 8 + 8 +
+                       (size_t)A.n_region + 4096;
+  void *mem = nullptr;
+  if (c->alloc.alloc)
+    mem = c->alloc.alloc(c->alloc.user, bytes, c->alloc.stream);
+  else if (cudaMalloc(&mem, bytes) != cudaSuccess)
+    mem = nullptr;
+  if (!mem) return fail(SPH_ERR_ALLOC, "adjoint work arrays");
+  A.mem = mem;
+  A.bytes = bytes;
+  char *p = (char *)mem;
+  auto take = [&](size_t n) {
+    void *q = p;
+    p += (n + 255) & ~(size_t)255;
+    return q;
+  };
+  auto d = [&]() { return (double *)take(cap * 8); };
+  for (int k = 0; k < 8; ++k) A.lam[k] = d();
+  for (int k = 0; k < 8; ++k) A.out[k] = d();
+  for (int k = 0; k < 3; ++k) A.lxg[k] = d();
+  for (int k = 0; k < 3; ++k) A.lxs[k] = d();
+  A.lrhos = d();
+  for (int k = 0; k < 6; ++k) A.lB[k] = d();
+  for (int k = 0; k < 3; ++k) A.lan[k] = d();
+  for (int k = 0; k < 12; ++k) A.sd[k] = d();
+  AdjTape &T = A.T;
+  T.cap = (int64_t)cap;
+  for (int k = 0; k < 3; ++k) T.x0[k] = d();
+  for (int k = 0; k < 3; ++k) T.v0[k] = d();
+  T.rho0 = d();
+  T.drho0 = d();
+  T.rho_s = (double *)take(ns * cap * 8);
+  T.drho_s = (double *)take(ns * cap * 8);
+  for (int k = 0; k < 3; ++k) T.v1[k] = (double *)take(ns * cap * 8);
+  for (int k = 0; k < 3; ++k) T.xbc[k] = (double *)take(ns * cap * 8);
+  T.perm = (uint32_t *)take(cap * 4);
+  T.spawn_dst = (int32_t *)take(cap * 4);
+  A.grad = (double *)take((size_t)A.d.n_theta * 8);
+  A.J = (double *)take(8);
+  A.region = (uint8_t *)take((size_t)A.n_region + 1);
+  A.mask = (int32_t *)take(SPH_MAX_BUFFERS * 4);
+  return 0;
+}
+
+static AdjArgs adj_args(sph_ctx *c) {
+  sph_ctx::Adj &A = c->adj;
+  AdjArgs a{};
+  a.inst = c->d_inst;
+  a.buf = c->d_buf;
+  a.m = c->M[c->cur];
+  a.der = c->der;
+  a.nl = c->nl;
+  a.off = c->off;
+  a.woff = c->woff;
+  a.pending_keys = c->K[0];
+  for (int k = 0; k < 3; ++k) a.wx[k] = c->wx[k];
+  a.WV = c->pkd.WV;
+  a.cnt = c->cnt;
+  a.flag = c->flag;
+  a.T = A.T;
+  for (int k = 0; k < 3; ++k) {
+    a.lx[k] = A.lam[k];
+    a.lv[k] = A.lam[3 + k];
+    a.lxg[k] = A.lxg[k];
+    a.lxs[k] = A.lxs[k];
+    a.lan[k] = A.lan[k];
+  }
+  a.lrho = A.lam[6];
+  a.ldrho = A.lam[7];
+  a.lrhos = A.lrhos;
+  for (int k = 0; k < 6; ++k) a.lB[k] = A.lB[k];
+  for (int k = 0; k < 12; ++k) a.sd[k] = A.sd[k];
+  for (int k = 0; k < 8; ++k) a.out[k] = A.out[k];
+  a.grad = A.grad;
+  a.J = A.J;
+  a.region = A.region;
+  a.n_region = A.n_region;
+  a.g_inst = A.d.instance;
+  a.g_buf = A.d.profile_buffer;
+  a.o_inst = A.d.instance;
+  a.sentinel = c->ncell;
+  a.w_s = A.d.slab;
+  a.dt_obj = A.dt;
+  return a;
+}
+
+// one advection step with the records the reverse pass reads
+static void enqueue_step_taped(sph_ctx *c) {
+  enqueue_topology(c);
+  const int maxn = (int)c->cap;
+  AdjArgs a = adj_args(c);
+  cudaMemcpyAsync(c->adj.T.perm, c->sorted_vals, 4 * (size_t)c->cap, cudaMemcpyDeviceToDevice, c->stream);
+  launch_adj_tape_start(a, maxn, c->stream);
+  launch_time_step(c->topo(), c->stream);
+  launch_neighbour_list(c->sweep(0, 0), c->packs(), c->prec, c->dim, maxn, c->stream);
+  launch_advection_sweep(c->sweep(0, 1), c->packs(), c->prec, c->dim, maxn, c->stream);
+  for (int s = 0; s < c->n_ac_max; ++s) {
+    launch_momentum_sweep(c->sweep(s, 2), c->packs(), c->prec, c->dim, maxn, s, c->stream);
+    launch_adj_tape_sub(a, s, maxn, c->stream);
+    launch_continuity_sweep(c->sweep(s, 3), c->packs(), c->prec, c->dim, maxn, s, c->stream);
+    launch_adj_tape_drho(a, s, maxn, c->stream);
+  }
+  TopoArgs t = c->topo();
+  t.spawn_dst = c->adj.T.spawn_dst;
+  launch_buffer_update(t, maxn, c->stream);
+  c->launches += 3 + 3 + 4 * c->n_ac_max + 3;
+  c->step += 1;
+}
+
+// reverse of the step just recomputed by enqueue_step_taped; the adjoint
+// arrays go from the state after the step to the state before it
+static void enqueue_step_reverse(sph_ctx *c) {
+  sph_ctx::Adj &A = c->adj;
+  const int maxn = (int)c->cap;
+  const size_t b8 = 8 * (size_t)c->cap;
+  for (int k = 0; k < 3; ++k) {
+    cudaMemsetAsync(A.lxg[k], 0, b8, c->stream);
+    cudaMemsetAsync(A.lxs[k], 0, b8, c->stream);
+    cudaMemsetAsync(A.lan[k], 0, b8, c->stream);
+  }
+  cudaMemsetAsync(A.lrhos, 0, b8, c->stream);
+  for (int k = 0; k < 6; ++k) cudaMemsetAsync(A.lB[k], 0, b8, c->stream);
+  int any_per = 0;
+  for (const InstDev &I : c->inst) any_per |= I.periodic[0] | I.periodic[1] | I.periodic[2];
+  AdjArgs a = adj_args(c);
+  launch_adj_objective(a, 1, maxn, c->stream);
+  launch_adj_buffer_rev(a, maxn, c->stream);
+  for (int s = c->n_ac_max - 1; s >= 0; --s) launch_adj_substep_rev(a, c->dim, any_per, s, maxn, c->stream);
+  launch_adj_adv_rev(a, c->dim, any_per, maxn, c->stream);
+  for (int k = 0; k < 8; ++k) cudaMemsetAsync(A.out[k], 0, b8, c->stream);
+  launch_adj_perm_rev(a, maxn, c->stream);
+  for (int k = 0; k < 8; ++k) std::swap(A.lam[k], A.out[k]);
+  c->launches += 4 + 5 * c->n_ac_max + 3;
+}
+
+int sph_adjoint_forward(sph_ctx *c, const sph_adjoint_desc *d, double *J_out) {
+  if (!c || !d) return fail(SPH_ERR_ARG, "NULL argument");
+  if (c->prec != SPH_PREC_FP64) return fail(SPH_ERR_ARG, "differentiated windows need an FP64 context");
+  if (c->kinematic) return fail(SPH_ERR_ARG, "kinematic contexts have no dynamics to differentiate");
+  if (d->instance < 0 || d->instance >= c->ninst) return fail(SPH_ERR_ARG, "instance out of range");
+  if (d->steps < 1 || d->checkpoint_every < 1) return fail(SPH_ERR_ARG, "steps and checkpoint_every must be >= 1");
+  if (d->n_theta < 1 || d->n_theta > SPH_MAX_THETA) return fail(SPH_ERR_ARG, "n_theta must be 1..64");
+  if (!(d->slab > 0)) return fail(SPH_ERR_ARG, "slab must be > 0");
+  for (int i = 0; i < c->ninst; ++i)
+    if (c->cfg[i].dt_mode != SPH_DT_FIXED) return fail(SPH_ERR_ARG, "differentiated windows need SPH_DT_FIXED");
+  const auto &bufs = c->bufs[d->instance];
+  if (d->profile_buffer < 0 || d->profile_buffer >= (int32_t)bufs.size() ||
+      bufs[d->profile_buffer].type != SPH_BUF_VELOCITY)
+    return fail(SPH_ERR_ARG, "profile_buffer must be a velocity buffer of the instance");
+  if (d->n_outlets < 1 || d->n_outlets > SPH_MAX_BUFFERS) return fail(SPH_ERR_ARG, "need 1..16 outlets");
+  for (int q = 0; q < d->n_outlets; ++q)
+    if (d->outlets[q] < 0 || d->outlets[q] >= (int32_t)bufs.size()) return fail(SPH_ERR_ARG, "outlet out of range");
+  adj_free(c);
+  int rc = sph_set_profile(c, d->instance, d->profile_buffer, d->theta, d->n_theta);
+  if (rc) return rc;
+  if (!c->started) {
+    if ((rc = upload_buffers(c))) return rc;
+    c->started = true;
+  }
+  sph_ctx::Adj &A = c->adj;
+  A.d = *d;
+  A.dt = c->cfg[d->instance].dt_ad_fixed;
+  uint32_t nu = 0;
+  CUDA_TRY(cudaMemcpy(&nu, c->next_uid + d->instance, 4, cudaMemcpyDeviceToHost));
+  A.n_region = (int64_t)nu;
+  if ((rc = adj_alloc(c))) return rc;
+  int32_t mask[SPH_MAX_BUFFERS] = {0};
+  for (int q = 0; q < d->n_outlets; ++q) mask[d->outlets[q]] = 1;
+  CUDA_TRY(cudaMemcpyAsync(A.mask, mask, sizeof(mask), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(cudaMemsetAsync(A.region, 0, (size_t)A.n_region + 1, c->stream));
+  CUDA_TRY(cudaMemsetAsync(A.J, 0, 8, c->stream));
+  launch_adj_region(adj_args(c), A.region, A.mask, (int)c->cap, c->stream);
+  set_freeze(c, 1);
+  for (int n = 0; n < d->steps; ++n) {
+    if (n % d->checkpoint_every == 0) {
+      int32_t slot;
+      if ((rc = sph_save_state(c, &slot))) break;
+      A.ckpt.push_back(slot);
+    }
+    enqueue_step(c);
+    launch_adj_objective(adj_args(c), 0, (int)c->cap, c->stream);
+  }
+  if (!rc) rc = sph_save_state(c, &A.end_slot);
+  set_freeze(c, 0);
+  if (rc) return rc;
+  CUDA_TRY(cudaGetLastError());
+  int32_t status = 0;
+  if ((rc = read_status(c, &status))) return rc;
+  if (status) return status;
+  double J = 0.0;
+  CUDA_TRY(cudaMemcpy(&J, A.J, 8, cudaMemcpyDeviceToHost));
+  if (J_out) *J_out = J;
+  A.fwd = true;
+  return SPH_OK;
+}
+
+int sph_adjoint_backward(sph_ctx *c, double *grad_out, int32_t n_theta) {
+  if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
+  sph_ctx::Adj &A = c->adj;
+  if (!A.fwd) return fail(SPH_ERR_STATE, "sph_adjoint_backward needs a completed sph_adjoint_forward");
+  if (grad_out && n_theta != A.d.n_theta) return fail(SPH_ERR_ARG, "n_theta differs from the forward window");
+  const size_t b8 = 8 * (size_t)c->cap;
+  for (int k = 0; k < 8; ++k) CUDA_TRY(cudaMemsetAsync(A.lam[k], 0, b8, c->stream));
+  CUDA_TRY(cudaMemsetAsync(A.grad, 0, 8 * (size_t)A.d.n_theta, c->stream));
+  set_freeze(c, 1);
+  const int K = A.d.checkpoint_every, steps = A.d.steps;
+  const int nseg = (int)A.ckpt.size();
+  int rc = 0;
+  std::vector<int32_t> snap;
+  for (int seg = nseg - 1; seg >= 0 && !rc; --seg) {
+    const int s0 = seg * K, s1 = std::min(s0 + K, steps);
+    snap.assign(s1 - s0, -1);
+    snap[0] = A.ckpt[seg];
+    if ((rc = sph_restore_state(c, A.ckpt[seg]))) break;
+    for (int n = s0; n < s1 - 1 && !rc; ++n) {
+      enqueue_step(c);
+      rc = sph_save_state(c, &snap[n + 1 - s0]);
+    }
+    for (int n = s1 - 1; n >= s0 && !rc; --n) {
+      if ((rc = sph_restore_state(c, snap[n - s0]))) break;
+      enqueue_step_taped(c);
+      enqueue_step_reverse(c);
+      if (n > s0) rc = sph_drop_state(c, snap[n - s0]);
+    }
+  }
+  if (!rc) rc = sph_restore_state(c, A.end_slot);
+  set_freeze(c, 0);
+  if (rc) return rc;
+  CUDA_TRY(cudaGetLastError());
+  int32_t status = 0;
+  if ((rc = read_status(c, &status))) return rc;
+  if (status) return status;
+  if (grad_out) CUDA_TRY(cudaMemcpy(grad_out, A.grad, 8 * (size_t)A.d.n_theta, cudaMemcpyDeviceToHost));
+  return SPH_OK;
+}
+
+int sph_adjoint_release(sph_ctx *c) {
+  if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
+  adj_free(c);
   return SPH_OK;
 }
 

@@ -39,6 +39,7 @@ struct SweepConst {
 struct InstDev {
   int32_t dim, rans, dt_mode, n_ac_fixed;
   int32_t kinematic;
+  int32_t freeze_turb;  // k, eps, nu_t held (differentiated windows)
   int32_t periodic[3];
   int32_t nc[3];
   int32_t nbuf, buf0;
@@ -274,7 +275,7 @@ __device__ __forceinline__ void apply_bc(const InstDev &I, const BufDev &b, cons
     m.p[i] = b.p_ob;
     m.rho[i] = b.rho_ob;
   }
-  if (I.rans && b.turb == SPH_TURB_FREESTREAM) {
+  if (I.rans && !I.freeze_turb && b.turb == SPH_TURB_FREESTREAM) {
     m.k[i] = b.k_in;
     m.eps[i] = b.eps_in;
     m.nut[i] = b.nut_in;
@@ -320,6 +321,7 @@ struct TopoArgs {
   uint32_t sentinel;
   int32_t ninst, n_ac_max;
   int64_t capacity;
+  int32_t *spawn_dst;  // optional: index of the copy each injecting particle made
 };
 
 void launch_permute(const TopoArgs &a, int max_n, int prec, cudaStream_t st, void *packs);
@@ -362,6 +364,61 @@ void launch_momentum_sweep(const SweepArgs &a, void *packs, int prec, int dim, i
                            cudaStream_t st);
 void launch_continuity_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n, int sub,
                              cudaStream_t st);
+// ------------------------------------------------------------------------
+// adjoint of the step (differentiated windows, FP64 contexts)
+// ------------------------------------------------------------------------
+// What the reverse pass needs of one advection step, recorded while the
+// step is recomputed: the start-of-step state in cell order, per sub-step
+// the density of the first half, the velocity after the kick, the position
+// at the boundary-value time and the continuity rate, the sort permutation
+// and the copies of the buffer update.
+struct AdjTape {
+  double *x0[3], *v0[3], *rho0, *drho0;
+  double *rho_s, *drho_s, *v1[3], *xbc[3];  // [sub * cap + i]
+  uint32_t *perm;                           // cell-order index -> pending index
+  int32_t *spawn_dst;                       // injecting particle -> its copy
+  int64_t cap;
+};
+
+struct AdjArgs {
+  const InstDev *inst;
+  const BufDev *buf;
+  Masters m;    // masters after the recomputed step (cell order of the step)
+  Derived der;  // B and viscous acceleration of the step
+  NbrList nl;
+  const uint32_t *off, *woff, *pending_keys;
+  const double *wx[3];
+  const V4<double> *WV;  // wall velocities
+  const Counters *cnt;
+  const uint8_t *flag;  // buffer-update decisions of the step
+  AdjTape T;
+  double *lx[3], *lv[3], *lrho, *ldrho;  // adjoint of the particle state
+  double *lxg[3];                        // adjoint of the start position (pair geometry)
+  double *lxs[3], *lrhos;                // mirror-term contributions (scattered)
+  double *lB[6], *lan[3];
+  double *sd[12];                        // per-particle seeds of one pair reverse
+  double *out[8];                        // pending-order result of the permutation reverse
+  double *grad;                          // dJ/dtheta
+  double *J;                             // objective accumulator
+  const uint8_t *region;                 // per uid of the objective instance: buffer + 1
+  int64_t n_region;
+  int32_t g_inst, g_buf, o_inst;
+  int32_t sub;
+  uint32_t sentinel;
+  double w_s, dt_obj;
+};
+
+void launch_adj_tape_start(const AdjArgs &a, int max_n, cudaStream_t st);
+void launch_adj_tape_sub(const AdjArgs &a, int sub, int max_n, cudaStream_t st);
+void launch_adj_tape_drho(const AdjArgs &a, int sub, int max_n, cudaStream_t st);
+void launch_adj_region(const AdjArgs &a, uint8_t *region, const int32_t *obj_buf_mask, int max_n,
+                       cudaStream_t st);
+void launch_adj_objective(const AdjArgs &a, int seed, int max_n, cudaStream_t st);
+void launch_adj_buffer_rev(const AdjArgs &a, int max_n, cudaStream_t st);
+void launch_adj_substep_rev(const AdjArgs &a, int dim, int any_periodic, int sub, int max_n, cudaStream_t st);
+void launch_adj_adv_rev(const AdjArgs &a, int dim, int any_periodic, int max_n, cudaStream_t st);
+void launch_adj_perm_rev(const AdjArgs &a, int max_n, cudaStream_t st);
+
 void launch_debug_pairs(const SweepArgs &a, const double *wx, const double *wy, const double *wz,
                         const uint32_t *wall_index, int64_t *out, int64_t max, unsigned long long *counter,
                         int max_n, cudaStream_t st);

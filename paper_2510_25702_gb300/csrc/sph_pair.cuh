@@ -1,0 +1,277 @@
+// sph_pair.cuh -- pair geometry and small linear algebra shared by the
+// forward sweeps and their adjoint: exact/fast arithmetic per precision,
+// the Wendland C2 kernel factor, minimum-image pair vectors, cell-range
+// visiting, symmetric 2x2 / 3x3 helpers and the guarded inverse of B.
+#pragma once
+
+#include "sph_internal.cuh"
+
+namespace sphk {
+
+template <typename R>
+struct Ex;
+template <>
+struct Ex<double> {
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ void len(double rr, double &r) { r = sqrt(rr); }
+};
+template <>
+struct Ex<float> {
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ void len(float rr, float &r) { r = rr * rsqrtf(rr); }
+};
+
+// per-thread copy of the instance geometry in sweep precision
+template <typename R>
+struct Geo {
+  R L[3];
+  int per[3];
+  R cut2, inv_h, c5, reg;
+};
+
+template <typename R, int D>
+__device__ __forceinline__ Geo<R> make_geo(const InstDev &I) {
+  const SweepConst<R> &k = sweep_const<R>(I);
+  Geo<R> g;
+  for (int a = 0; a < 3; ++a) {
+    g.L[a] = k.L[a];
+    g.per[a] = (a < D) ? I.periodic[a] : 0;
+  }
+  g.cut2 = k.cut2;
+  g.inv_h = k.inv_h;
+  g.c5 = k.c5;
+  g.reg = k.reg;
+  return g;
+}
+
+// r_ij = x_i - x_j (minimum image when PER) from the leading 4-vectors of two
+// records, whose first D components are the position; returns |r_ij|^2
+// summed left to right without contraction (the cut-off test decides
+// membership)
+template <typename R, int D, bool PER>
+__device__ __forceinline__ R pair_vec(const Geo<R> &g, const V4<R> &pi, const V4<R> &pj, R d[3]) {
+  R xi[3] = {pi.x, pi.y, pi.z}, xj[3] = {pj.x, pj.y, pj.z};
+  R rr = (R)0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    R v = Ex<R>::sub(xi[a], xj[a]);
+    if (PER && g.per[a]) {
+      R h = (R)0.5 * g.L[a];
+      if (v > h)
+        v = Ex<R>::sub(v, g.L[a]);
+      else if (v < -h)
+        v = Ex<R>::add(v, g.L[a]);
+    }
+    d[a] = v;
+    rr = (a == 0) ? Ex<R>::mul(v, v) : Ex<R>::add(rr, Ex<R>::mul(v, v));
+  }
+  if (D == 2) d[2] = (R)0;
+  return rr;
+}
+
+// volume slot of a record's leading 4-vector: (x y V .) in 2D, (x y z V) in 3D
+template <typename R, int D>
+__device__ __forceinline__ R vol(const V4<R> &r0) {
+  return (D == 2) ? r0.z : r0.w;
+}
+
+// Wendland C2 (Sec. 2.2 kernel, support 2h): F = (dW/dr) / r
+// = -5 (alpha / h^2) (1 - q/2)^3, evaluated without a division
+template <typename R>
+__device__ __forceinline__ R kernel_F(const Geo<R> &g, R r) {
+  R w = (R)1 - (R)0.5 * (r * g.inv_h);
+  return g.c5 * w * w * w;
+}
+
+// buffer-frame coordinate 0 of a point, in sweep precision, plain order
+template <typename R, int D>
+__device__ __forceinline__ R local0(const R o[3], const R n[3], R x, R y, R z) {
+  R s = Ex<R>::mul(Ex<R>::sub(x, o[0]), n[0]);
+  s = Ex<R>::add(s, Ex<R>::mul(Ex<R>::sub(y, o[1]), n[1]));
+  if (D == 3) s = Ex<R>::add(s, Ex<R>::mul(Ex<R>::sub(z, o[2]), n[2]));
+  return s;
+}
+
+// visit the index ranges of the cells within +-span of (cx, cy, cz): the
+// clamped part of each x row is one contiguous range; periodic axes hold at
+// least 2 span + 1 cells (checked at creation), so wrapped coordinates are
+// distinct and the wrapped x cells of a row form at most two more ranges.
+// f has one call site so that it stays inlined.
+template <int D, bool PER, typename F>
+__device__ __forceinline__ void visit_cells(const InstDev &I, int cx, int cy, int cz, int span,
+                                            const uint32_t *__restrict__ off, F &&f) {
+  const int nx = I.nc[0], ny = I.nc[1];
+  const int nz = (D == 3) ? I.nc[2] : 1;
+  const int zspan = (D == 3) ? span : 0;
+  const int a0 = max(cx - span, 0), a1 = min(cx + span, nx - 1);
+  const int nparts = (PER && I.periodic[0]) ? 3 : 1;
+  for (int dz = -zspan; dz <= zspan; ++dz) {
+    int zz = cz + dz;
+    if (zz < 0 || zz >= nz) {
+      if (!PER || D != 3 || !I.periodic[2]) continue;
+      zz = zz < 0 ? zz + nz : zz - nz;
+    }
+    for (int dy = -span; dy <= span; ++dy) {
+      int yy = cy + dy;
+      if (yy < 0 || yy >= ny) {
+        if (!PER || !I.periodic[1]) continue;
+        yy = yy < 0 ? yy + ny : yy - ny;
+      }
+      const uint32_t row = I.cell_base + ((uint32_t)zz * (uint32_t)ny + (uint32_t)yy) * (uint32_t)nx;
+      for (int part = 0; part < nparts; ++part) {
+        int c0 = a0, c1 = a1;
+        if (part == 1) {  // cells wrapped from the left edge
+          if (cx - span >= 0) continue;
+          c0 = cx - span + nx;
+          c1 = nx - 1;
+        } else if (part == 2) {  // cells wrapped from the right edge
+          if (cx + span < nx) continue;
+          c0 = 0;
+          c1 = cx + span - nx;
+        }
+        f(off[row + c0], off[row + c1 + 1]);
+      }
+    }
+  }
+}
+
+// candidates j in [jb, je) whose position leads the 4-vector P[j * stride],
+// four loads in flight; hit(j) is called for every j with
+// 0 < |r_ij|^2 < (2h)^2
+template <typename R, int D, bool PER, typename H>
+__device__ __forceinline__ void scan_range(const Geo<R> &g, const V4<R> &Pi, const V4<R> *__restrict__ P,
+                                           int stride, uint32_t jb, uint32_t je, H &&hit) {
+  for (uint32_t j = jb; j < je; j += 4) {
+    const V4<R> q0 = P[(size_t)j * stride];
+    const V4<R> q1 = (j + 1 < je) ? P[(size_t)(j + 1) * stride] : q0;
+    const V4<R> q2 = (j + 2 < je) ? P[(size_t)(j + 2) * stride] : q0;
+    const V4<R> q3 = (j + 3 < je) ? P[(size_t)(j + 3) * stride] : q0;
+    R d[3];
+    unsigned mask = 0;
+    R rr = pair_vec<R, D, PER>(g, Pi, q0, d);
+    mask |= (rr > (R)0 && rr < g.cut2) ? 1u : 0u;
+    rr = pair_vec<R, D, PER>(g, Pi, q1, d);
+    mask |= (j + 1 < je && rr > (R)0 && rr < g.cut2) ? 2u : 0u;
+    rr = pair_vec<R, D, PER>(g, Pi, q2, d);
+    mask |= (j + 2 < je && rr > (R)0 && rr < g.cut2) ? 4u : 0u;
+    rr = pair_vec<R, D, PER>(g, Pi, q3, d);
+    mask |= (j + 3 < je && rr > (R)0 && rr < g.cut2) ? 8u : 0u;
+    while (mask) {
+      const int k = __ffs(mask) - 1;
+      mask &= mask - 1;
+      hit(j + (uint32_t)k);
+    }
+  }
+}
+
+__device__ __forceinline__ void decode_cell(const InstDev &I, uint32_t key, int &cx, int &cy, int &cz) {
+  uint32_t l = key - I.cell_base;
+  cx = (int)(l % (uint32_t)I.nc[0]);
+  uint32_t r = l / (uint32_t)I.nc[0];
+  cy = (int)(r % (uint32_t)I.nc[1]);
+  cz = (int)(r / (uint32_t)I.nc[1]);
+}
+
+// symmetric 3x3 stored as (xx, yy, zz, xy, xz, yz)
+template <typename R, int D>
+__device__ __forceinline__ void sym_add_outer(R A[6], const R d[3], R s) {
+  // A += s d (x) d; with s = -F V this is -r_ij (x) grad W V
+  A[0] += s * d[0] * d[0];
+  A[1] += s * d[1] * d[1];
+  A[3] += s * d[0] * d[1];
+  if (D == 3) {
+    A[2] += s * d[2] * d[2];
+    A[4] += s * d[0] * d[2];
+    A[5] += s * d[1] * d[2];
+  }
+}
+
+// B = A^-1 in FP64 with the guard det A <= 1e-3 (tr A / d)^d -> I
+template <int D>
+__device__ __forceinline__ void invert_guarded(const double A[6], double B[6]) {
+  for (int c = 0; c < 6; ++c) B[c] = 0.0;
+  if (D == 2) {
+    double t = 0.5 * (A[0] + A[1]);
+    double det = A[0] * A[1] - A[3] * A[3];
+    if (!(det > 1e-3 * t * t)) {
+      B[0] = B[1] = 1.0;
+      return;
+    }
+    double inv = 1.0 / det;
+    B[0] = A[1] * inv;
+    B[1] = A[0] * inv;
+    B[3] = -A[3] * inv;
+  } else {
+    const double xx = A[0], yy = A[1], zz = A[2], xy = A[3], xz = A[4], yz = A[5];
+    double c00 = yy * zz - yz * yz;
+    double c01 = yz * xz - xy * zz;
+    double c02 = xy * yz - yy * xz;
+    double det = xx * c00 + xy * c01 + xz * c02;
+    double t = (xx + yy + zz) * (1.0 / 3.0);
+    if (!(det > 1e-3 * t * t * t)) {
+      B[0] = B[1] = B[2] = 1.0;
+      return;
+    }
+    double inv = 1.0 / det;
+    B[0] = c00 * inv;
+    B[1] = (xx * zz - xz * xz) * inv;
+    B[2] = (xx * yy - xy * xy) * inv;
+    B[3] = c01 * inv;
+    B[4] = c02 * inv;
+    B[5] = (xz * xy - xx * yz) * inv;
+  }
+}
+
+template <typename R, int D>
+__device__ __forceinline__ void sym_matvec(const R B[6], const R x[3], R y[3]) {
+  if (D == 2) {
+    y[0] = B[0] * x[0] + B[3] * x[1];
+    y[1] = B[3] * x[0] + B[1] * x[1];
+    y[2] = (R)0;
+  } else {
+    y[0] = B[0] * x[0] + B[3] * x[1] + B[4] * x[2];
+    y[1] = B[3] * x[0] + B[1] * x[1] + B[5] * x[2];
+    y[2] = B[4] * x[0] + B[5] * x[1] + B[2] * x[2];
+  }
+}
+
+// B, kw = 2/3 k and (3D) p from a momentum record; false for the marker of a
+// pressure-buffer particle, whose B is then not in the record
+template <typename R, int D>
+__device__ __forceinline__ bool mom_B(const V4<R> &m1, const V4<R> &m2, R B[6], R &kw, R &p) {
+  if (D == 2) {
+    // (x y V p)(Bxx Bxy Byy kw)
+    B[0] = m1.x;
+    B[3] = m1.y;
+    B[1] = m1.z;
+    B[2] = B[4] = B[5] = (R)0;
+    kw = m1.w;
+    return m1.x >= (R)0;
+  } else {
+    // (x y z V)(p kw Bxx Byy)(Bzz Bxy Bxz Byz)
+    p = m1.x;
+    kw = m1.y;
+    B[0] = m1.z;
+    B[1] = m1.w;
+    B[2] = m2.x;
+    B[3] = m2.y;
+    B[4] = m2.z;
+    B[5] = m2.w;
+    return m1.z >= (R)0;
+  }
+}
+
+// effective pressure p + 2/3 rho k (Table 1) with rho = rho0 + p / c0^2,
+// the stiff EOS of Sec. 2.1 solved for the density
+template <typename R>
+__device__ __forceinline__ R p_eff(R p, R kw, R rho0, R inv_c0sq) {
+  return p + kw * (rho0 + p * inv_c0sq);
+}
+
+}  // namespace sphk

@@ -296,6 +296,7 @@ __global__ void __launch_bounds__(kBlock) k_spawn(TopoArgs a, const uint32_t *ui
   }
   // injection: copy at the parent's position, parent recycled by -L_b n_b
   const int dst = n + rank;
+  if (a.spawn_dst) a.spawn_dst[i] = dst;
   for (int d = 0; d < 3; ++d) {
     m.x[d][dst] = m.x[d][i];
     m.v[d][dst] = m.v[d][i];

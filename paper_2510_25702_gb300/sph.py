@@ -76,6 +76,12 @@ ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
 
+class AdjointDesc(C.Structure):
+    _fields_ = [("instance", C.c_int32), ("profile_buffer", C.c_int32), ("steps", C.c_int32),
+                ("checkpoint_every", C.c_int32), ("n_outlets", C.c_int32), ("outlets", C.c_int32 * 16),
+                ("n_theta", C.c_int32), ("slab", C.c_double), ("theta", C.c_double * 64)]
+
+
 class Alloc(C.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p), ("stream", C.c_void_p)]
 
@@ -95,7 +101,8 @@ EXPORTS = ("sph_create", "sph_add_buffer", "sph_set_profile", "sph_step", "sph_r
            "sph_write_fields", "sph_get_stats", "sph_debug_pairs", "sph_destroy", "sph_error_string",
            "sph_last_error", "sph_abi_version", "sph_set_profiling", "sph_get_stage_times", "sph_stage_name",
            "sph_cell_sort_noalloc", "sph_set_graph", "sph_set_launch", "sph_get_launch", "sph_autotune",
-           "sph_save_state", "sph_restore_state", "sph_drop_state")
+           "sph_save_state", "sph_restore_state", "sph_drop_state", "sph_adjoint_forward",
+           "sph_adjoint_backward", "sph_adjoint_release")
 NOALLOC_MAX_POINTS = 1 << 19
 N_STAGES = 9
 
@@ -137,6 +144,9 @@ def lib():
         L.sph_save_state.argtypes = [vp, C.POINTER(C.c_int32)]
         L.sph_restore_state.argtypes = [vp, C.c_int32]
         L.sph_drop_state.argtypes = [vp, C.c_int32]
+        L.sph_adjoint_forward.argtypes = [vp, C.POINTER(AdjointDesc), C.POINTER(C.c_double)]
+        L.sph_adjoint_backward.argtypes = [vp, C.POINTER(C.c_double), C.c_int32]
+        L.sph_adjoint_release.argtypes = [vp]
         L.sph_error_string.restype = C.c_char_p
         L.sph_last_error.restype = C.c_char_p
         _lib = L
@@ -379,6 +389,33 @@ class Simulation:
 
     def drop_state(self, slot: int):
         _check(lib().sph_drop_state(self.ctx, int(slot)), "sph_drop_state")
+
+    def adjoint_forward(self, theta, instance: int, profile_buffer: int, outlets: Sequence[int], steps: int,
+                        checkpoint_every: int, slab: float) -> float:
+        """Run a differentiated window (C ABI sph_adjoint_forward); returns J."""
+        th = np.ascontiguousarray(theta, np.float64).reshape(-1)
+        d = AdjointDesc()
+        d.instance, d.profile_buffer, d.steps, d.checkpoint_every = instance, profile_buffer, steps, checkpoint_every
+        d.n_outlets = len(outlets)
+        for q, b in enumerate(outlets):
+            d.outlets[q] = int(b)
+        d.n_theta = th.size
+        d.slab = float(slab)
+        for q, v in enumerate(th):
+            d.theta[q] = float(v)
+        J = C.c_double()
+        _check(lib().sph_adjoint_forward(self.ctx, C.byref(d), C.byref(J)), "sph_adjoint_forward")
+        self._adj_n = th.size
+        return J.value
+
+    def adjoint_backward(self) -> np.ndarray:
+        g = np.zeros(self._adj_n, np.float64)
+        _check(lib().sph_adjoint_backward(self.ctx, g.ctypes.data_as(C.POINTER(C.c_double)), g.size),
+               "sph_adjoint_backward")
+        return g
+
+    def adjoint_release(self):
+        _check(lib().sph_adjoint_release(self.ctx), "sph_adjoint_release")
 
     def debug_pairs(self, max_pairs: Optional[int] = None) -> np.ndarray:
         cnt = C.c_int64()

@@ -535,3 +535,34 @@ def test_uniform_map_range(orc):
     assert L.orc_uniform_pm1(0, 0) == -1.0
     assert L.orc_uniform_pm1(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 2.0 ** -52
     assert L.orc_uniform_pm1(0x80000000, 0) == 0.0
+
+
+def test_frozen_turbulence_holds_k_eps(orc):
+    """With turbulence held (differentiated windows), k, eps and nu_t ride
+    with the particles unchanged while the flow advances."""
+    from paper_2510_25702_gb300 import cases
+
+    c = cases.turbulent_channel(length=0.3, height=0.1, dp=0.005, jitter_frac=0.05)
+    o = orc.OracleSim(c, freeze_turb=1)
+    f0 = o.fields()
+    o.step(3)
+    f1 = o.fields()
+    keep = np.isin(f1["uid"], f0["uid"])
+    idx = np.searchsorted(f0["uid"], f1["uid"][keep])
+    for k in ("k", "eps", "nut"):
+        assert np.array_equal(f1[k][keep], f0[k][idx]), k
+    assert not np.allclose(f1["vel"][keep], f0["vel"][idx])
+
+
+def test_profile_replacement_moves_inlet_velocity(orc):
+    from paper_2510_25702_gb300 import cases
+
+    c = cases.turbulent_channel(length=0.3, height=0.1, dp=0.005, noise=0.0)
+    o = orc.OracleSim(c)
+    o.set_profile(0, [0.5, 1.5])
+    o.step(1)
+    f = o.fields()
+    inlet = f["label"] == 1
+    y = f["pos"][inlet, 1]
+    # linear profile across the width: U = 0.5 at the bottom, 1.5 at the top
+    assert np.allclose(f["vel"][inlet, 0], 0.5 + (y - 0.0) / 0.1, atol=1e-12)
