@@ -31,6 +31,15 @@ METRIC = "particle-steps/s vs plain FP64 at stated error; HBM GB/s; adjoint/forw
 UNIT = "particle-steps/s"
 
 
+_T0 = time.perf_counter()
+
+
+def log(msg: str):
+    """Progress on stderr (the JSON line goes to stdout)."""
+    sys.stderr.write(f"[bench {time.perf_counter() - _T0:7.1f}s] {msg}\n")
+    sys.stderr.flush()
+
+
 def workload(name: str, seed: int = 2):
     from paper_2510_25702_gb300 import cases
 
@@ -58,6 +67,28 @@ def describe(case):
     cs = as_list(case)
     name = cs[0].name if len(cs) == 1 else f"batched_channels_{len(cs)}x ({sum(c.n for c in cs)} particles)"
     return name, cs[0].dim, any(c.rans for c in cs), sum(c.nw for c in cs)
+
+
+# DRAM traffic per launch of the dominant kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum; the command and the summary
+# are in profiles/), keyed by the hash of the kernel sources it was taken
+# with: a changed source reports null.
+NCU_TRAFFIC = {
+    # (kernel stage, workload, csrc hash): bytes per launch
+}
+
+
+def csrc_hash() -> str:
+    import hashlib
+
+    d = os.path.join(ROOT, "paper_2510_25702_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def peaks():
@@ -187,8 +218,8 @@ def cpu_baseline(work: str, steps: int = 20):
 
 def adjoint_bench(steps: int = 200, every: int = 20, dp: float = 0.002):
     """Differentiated window on the plane jet (2 x 2, slot 0.1, dp 0.002,
-    about 1M particles, k-eps with frozen turbulence, fixed dt, FP64):
-    times of the plain forward, the checkpointed forward and the reverse
+    about 1M particles, k-eps held over the window, fixed dt, FP64): times
+    of the forward (one snapshot), the checkpointed forward and the reverse
     pass over `steps` steps, and a finite-difference check of the gradient
     along one random direction of the 32-point inlet profile."""
     import math
@@ -204,7 +235,13 @@ def adjoint_bench(steps: int = 200, every: int = 20, dp: float = 0.002):
     n_ac = max(1, math.ceil(dt_ad / (0.6 * c.h / (c.c0 + c.U_ref))))
     c = c.replace(dt_mode="fixed", dt_ad_fixed=dt_ad, n_ac_fixed=n_ac)
     sim = sph.Simulation(c, precision="fp64")
-    sim.step(2)
+    log(f"adjoint: created {c.name}")
+    # one step with the turbulence held labels the buffer particles (the
+    # outlet set S is taken from the labels at the window start); unfrozen
+    # k-eps steps at the impulsively started slot would raise nu_t at the
+    # slot edges within a few steps beyond what the fixed dt can carry
+    Window(sim, 0, 0, [3, 4, 5], 1, 1, 4 * c.dp).forward(th)
+    sim.adjoint_release()
     start = sim.save_state()
     win = Window(sim, 0, 0, [3, 4, 5], steps, every, 4 * c.dp)
 
@@ -215,14 +252,19 @@ def adjoint_bench(steps: int = 200, every: int = 20, dp: float = 0.002):
         torch.cuda.synchronize()
         return out, time.perf_counter() - t0
 
-    _, t_plain = timed(lambda: sim.step(steps))
+    # forward of the differentiated map (fixed dt, turbulence held) with one
+    # snapshot, then with a snapshot every `every` steps, then the reverse
+    once = Window(sim, 0, 0, [3, 4, 5], steps, steps, 4 * c.dp)
+    _, t_plain = timed(lambda: once.forward(th))
+    log(f"adjoint: forward {t_plain:.2f} s")
     sim.restore_state(start)
     J, t_fwd = timed(lambda: win.forward(th))
+    log(f"adjoint: checkpointed forward {t_fwd:.2f} s")
     g, t_bwd = timed(lambda: win.backward())
+    log(f"adjoint: backward {t_bwd:.2f} s")
     u = np.random.default_rng(11).normal(size=th.size)
     u /= np.linalg.norm(u)
     h = 1e-6
-    once = Window(sim, 0, 0, [3, 4, 5], steps, steps, 4 * c.dp)
     sim.restore_state(start)
     jp = once.forward(th + h * u)
     sim.restore_state(start)
@@ -233,6 +275,7 @@ def adjoint_bench(steps: int = 200, every: int = 20, dp: float = 0.002):
     return {"workload": c.name, "particles": c.n, "window_steps": steps, "checkpoint_every": every,
             "sub_steps": n_ac, "J": J, "forward_plain_s": t_plain, "forward_checkpointed_s": t_fwd,
             "backward_s": t_bwd, "adjoint_over_forward": t_bwd / t_plain,
+            "note": "turbulence held and dt fixed over the window in every pass",
             "fd_directional": fd, "adjoint_directional": float(g @ u),
             "fd_rel_err": abs(float(g @ u) - fd) / max(abs(fd), 1e-300), "dtype": "f64"}
 
@@ -269,6 +312,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison run")
     ap.add_argument("--no-tune", action="store_true", help="keep the default sweep block sizes")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiated-window timing")
+    ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--adjoint-dp", type=float, default=0.002)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -303,15 +348,20 @@ def main():
         torch.cuda.synchronize()
 
     wname, wdim, wrans, wwalls = describe(case)
+    log(f"created {wname}")
     sim.step(args.warmup)
+    log("warm-up done")
     tuned = None
     if not args.no_tune:
         # sweep block sizes, cached per (GPU, workload shape) next to the build
         tuned, hit = sim.autotune(steps=3, cache_path=os.path.join(os.path.dirname(_b.LIB), "autotune.txt"))
         tuned = {"blocks": dict(zip(("list", "adv", "mom", "cont"), tuned)), "from_cache": hit}
+    log(f"autotune {tuned}")
+    # timed region: K steps replayed from the two captured CUDA graphs
+    sim.set_graph(True)
+    sim.step(3)  # one uncaptured step, then both graphs are captured
     s0 = sim.stats()
     n0 = s0["n"]
-    sim.set_profiling(2)
     barrier()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -321,8 +371,6 @@ def main():
         torch.cuda.synchronize()
     barrier()
     ms = start.elapsed_time(end)
-    sim.set_profiling(0)
-    stages = sim.stage_times()
     s1 = sim.stats()
     n1 = s1["n"]
     launches = s1["kernel_launches"] - s0["kernel_launches"]
@@ -334,6 +382,25 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         ms, particle_steps = float(mx[0]), float(t[1])
     value = particle_steps / (ms * 1e-3)
+    log(f"timed region (graphs) {ms:.1f} ms")
+
+    # the same K steps launched one kernel at a time with CUDA events around
+    # every stage on the launching stream: per-kernel durations for the
+    # roofline (a graph replay has no per-kernel events)
+    sim.set_graph(False)
+    sim.set_profiling(2)
+    pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0 = sim.stats()
+    pa.record(stream)
+    sim.step(args.steps)
+    pb.record(stream)
+    torch.cuda.synchronize()
+    e_ms = pa.elapsed_time(pb)
+    e1 = sim.stats()
+    sim.set_profiling(0)
+    stages = sim.stage_times()
+    eager = {"value": 0.5 * (e0["n"] + e1["n"]) * args.steps / (e_ms * 1e-3), "ms_per_step": e_ms / args.steps}
+    log(f"profiled pass {e_ms:.1f} ms")
 
     # dominant kernel and its roofline
     dom = max(("advection_sweep", "momentum_sweep", "continuity_sweep"), key=lambda s: stages[s][0])
@@ -344,25 +411,11 @@ def main():
     achieved = per_particle * nbar / (dom_ms / dom_n * 1e-3) / 1e9
     peak, peak_kind = peaks()
 
-    # the same steps replayed from captured CUDA graphs (no stage events)
-    sim.set_graph(True)
-    sim.step(2)
-    torch.cuda.synchronize()
-    ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    g0 = sim.stats()
-    ga.record(stream)
-    sim.step(args.steps)
-    gb.record(stream)
-    torch.cuda.synchronize()
-    g_ms = ga.elapsed_time(gb)
-    g1 = sim.stats()
-    graph = {"value": 0.5 * (g0["n"] + g1["n"]) * args.steps / (g_ms * 1e-3), "ms_per_step": g_ms / args.steps}
-    sim.set_graph(False)
-
     # end to end through the C ABI: per step the inlet profile goes host ->
     # device (sph_set_profile), the step runs, the statistics come back
     e2e_steps = max(10, args.steps // 4)
     theta = np.array([1.0])
+    sim.set_graph(True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ps = 0.0
@@ -374,6 +427,7 @@ def main():
     e2e = {"value": ps / (t1 - t0) * (world if dist is not None else 1), "unit": UNIT,
            "h2d_bytes_per_step": 4 + 8 * theta.size, "d2h_bytes_per_step": 4 + 40 + 40}
 
+    log("e2e done")
     fp64 = None
     if not args.no_fp64 and args.precision == "fp32" and rank == 0:
         sim64 = sph.Simulation(case, precision="fp64")
@@ -390,9 +444,11 @@ def main():
         fp64 = sim64.stats()["n"] * k64 / (a.elapsed_time(b) * 1e-3)
         sim64.close()
 
+    log("fp64 done")
     adj = None
     if rank == 0 and not args.no_adjoint:
-        adj = adjoint_bench()
+        adj = adjoint_bench(steps=args.adjoint_steps, every=max(1, args.adjoint_steps // 10), dp=args.adjoint_dp)
+        log("adjoint done")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -410,11 +466,15 @@ def main():
                        "l2": f"working set {st['device_bytes'] / 2**20:.0f} MiB > 129 MB L2, no flush",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": NCU_TRAFFIC.get((dom, args.workload, csrc_hash())),
+                         "csrc": csrc_hash(),
                          "bytes_per_particle": per_particle, "avg_launch_ms": dom_ms / dom_n},
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+            "stage_timing": "CUDA events around each stage in a second pass of the same K steps launched "
+                            "kernel by kernel (value comes from graph replay)",
             "fp64_value": fp64, "fp32_over_fp64": (value / fp64) if fp64 else None,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "graph": graph, "autotune": tuned, "adjoint": adj,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "eager": eager, "autotune": tuned, "adjoint": adj,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -282,19 +282,176 @@ __global__ void k_adj_buffer_rev(AdjArgs a) {
 // ------------------------------------------------------------------------
 // reverse of one acoustic sub-step
 // ------------------------------------------------------------------------
-// R1: boundary values and the density update of sub-step s
+// Per-particle records of the reverse pair passes (FP64, V4 units), written
+// by the point kernel before each pass so that a neighbour costs one
+// contiguous read:
+//   C (continuity)  2D (x y V p)(vx vy ls -)        3D (x y z V)(p vx vy vz)(ls - - -)
+//   M (momentum)    2D (x y V pe)(Bxx Bxy Byy mk)   3D (x y z V)(pe mk Bxx Byy)(Bzz Bxy Bxz Byz)
+//   S (mom. seeds)  2D (a1 ab)(a2 at)               3D (a1 abx)(aby abz a2x a2y)(a2z at)
+//   A (advection)   2D (x y V mu)(vx vy mir Lxx)(Lyy Lxy sx sy)
+//                   3D (x y z V)(vx vy vz mu)(mir Lxx Lyy Lzz)(Lxy Lxz Lyz sx)(sy sz - -)
+// with ls the continuity seed, mk 1 for pressure-buffer particles, a1..at
+// the momentum seeds, L the adjoint of A and s the adjoint of the viscous
+// sum, mir the buffer index of a pressure-buffer particle or -1.
+template <int D>
+struct RecW {
+  static constexpr int C = D == 2 ? 2 : 3, M = D == 2 ? 2 : 3, S = D == 2 ? 2 : 3, A = D == 2 ? 3 : 5;
+};
+
+struct CRec {
+  double x[3], V, p, v[3], ls;
+};
+struct MRec {
+  double x[3], V, pe, B[6];
+  bool mk;
+};
+struct SRec {
+  double a1[3], ab[3], a2[3], at[3];
+};
+struct ARec {
+  double x[3], V, v[3], mu, L[6], sg[3];
+  int mir;
+};
+
+template <int D>
+__device__ __forceinline__ void put_c(V4<double> *r, int i, const CRec &c) {
+  V4<double> *p = r + (size_t)RecW<D>::C * i;
+  if (D == 2) {
+    p[0] = V4<double>{c.x[0], c.x[1], c.V, c.p};
+    p[1] = V4<double>{c.v[0], c.v[1], c.ls, 0.0};
+  } else {
+    p[0] = V4<double>{c.x[0], c.x[1], c.x[2], c.V};
+    p[1] = V4<double>{c.p, c.v[0], c.v[1], c.v[2]};
+    p[2] = V4<double>{c.ls, 0.0, 0.0, 0.0};
+  }
+}
+template <int D>
+__device__ __forceinline__ CRec get_c(const V4<double> *r, int i) {
+  const V4<double> *p = r + (size_t)RecW<D>::C * i;
+  CRec c;
+  const V4<double> q0 = p[0], q1 = p[1];
+  if (D == 2) {
+    c.x[0] = q0.x, c.x[1] = q0.y, c.x[2] = 0.0, c.V = q0.z, c.p = q0.w;
+    c.v[0] = q1.x, c.v[1] = q1.y, c.v[2] = 0.0, c.ls = q1.z;
+  } else {
+    const V4<double> q2 = p[2];
+    c.x[0] = q0.x, c.x[1] = q0.y, c.x[2] = q0.z, c.V = q0.w;
+    c.p = q1.x, c.v[0] = q1.y, c.v[1] = q1.z, c.v[2] = q1.w, c.ls = q2.x;
+  }
+  return c;
+}
+template <int D>
+__device__ __forceinline__ void put_m(V4<double> *r, int i, const MRec &m) {
+  V4<double> *p = r + (size_t)RecW<D>::M * i;
+  const double mk = m.mk ? 1.0 : 0.0;
+  if (D == 2) {
+    p[0] = V4<double>{m.x[0], m.x[1], m.V, m.pe};
+    p[1] = V4<double>{m.B[0], m.B[3], m.B[1], mk};
+  } else {
+    p[0] = V4<double>{m.x[0], m.x[1], m.x[2], m.V};
+    p[1] = V4<double>{m.pe, mk, m.B[0], m.B[1]};
+    p[2] = V4<double>{m.B[2], m.B[3], m.B[4], m.B[5]};
+  }
+}
+template <int D>
+__device__ __forceinline__ MRec get_m(const V4<double> *r, int i) {
+  const V4<double> *p = r + (size_t)RecW<D>::M * i;
+  MRec m;
+  const V4<double> q0 = p[0], q1 = p[1];
+  if (D == 2) {
+    m.x[0] = q0.x, m.x[1] = q0.y, m.x[2] = 0.0, m.V = q0.z, m.pe = q0.w;
+    m.B[0] = q1.x, m.B[3] = q1.y, m.B[1] = q1.z, m.mk = q1.w != 0.0;
+    m.B[2] = m.B[4] = m.B[5] = 0.0;
+  } else {
+    const V4<double> q2 = p[2];
+    m.x[0] = q0.x, m.x[1] = q0.y, m.x[2] = q0.z, m.V = q0.w;
+    m.pe = q1.x, m.mk = q1.y != 0.0, m.B[0] = q1.z, m.B[1] = q1.w;
+    m.B[2] = q2.x, m.B[3] = q2.y, m.B[4] = q2.z, m.B[5] = q2.w;
+  }
+  return m;
+}
+template <int D>
+__device__ __forceinline__ void put_s(V4<double> *r, int i, const SRec &s) {
+  V4<double> *p = r + (size_t)RecW<D>::S * i;
+  if (D == 2) {
+    p[0] = V4<double>{s.a1[0], s.a1[1], s.ab[0], s.ab[1]};
+    p[1] = V4<double>{s.a2[0], s.a2[1], s.at[0], s.at[1]};
+  } else {
+    p[0] = V4<double>{s.a1[0], s.a1[1], s.a1[2], s.ab[0]};
+    p[1] = V4<double>{s.ab[1], s.ab[2], s.a2[0], s.a2[1]};
+    p[2] = V4<double>{s.a2[2], s.at[0], s.at[1], s.at[2]};
+  }
+}
+template <int D>
+__device__ __forceinline__ SRec get_s(const V4<double> *r, int i) {
+  const V4<double> *p = r + (size_t)RecW<D>::S * i;
+  SRec s;
+  const V4<double> q0 = p[0], q1 = p[1];
+  if (D == 2) {
+    s.a1[0] = q0.x, s.a1[1] = q0.y, s.ab[0] = q0.z, s.ab[1] = q0.w;
+    s.a2[0] = q1.x, s.a2[1] = q1.y, s.at[0] = q1.z, s.at[1] = q1.w;
+    s.a1[2] = s.ab[2] = s.a2[2] = s.at[2] = 0.0;
+  } else {
+    const V4<double> q2 = p[2];
+    s.a1[0] = q0.x, s.a1[1] = q0.y, s.a1[2] = q0.z, s.ab[0] = q0.w;
+    s.ab[1] = q1.x, s.ab[2] = q1.y, s.a2[0] = q1.z, s.a2[1] = q1.w;
+    s.a2[2] = q2.x, s.at[0] = q2.y, s.at[1] = q2.z, s.at[2] = q2.w;
+  }
+  return s;
+}
+template <int D>
+__device__ __forceinline__ void put_a(V4<double> *r, int i, const ARec &q) {
+  V4<double> *p = r + (size_t)RecW<D>::A * i;
+  const double mir = (double)q.mir;
+  if (D == 2) {
+    p[0] = V4<double>{q.x[0], q.x[1], q.V, q.mu};
+    p[1] = V4<double>{q.v[0], q.v[1], mir, q.L[0]};
+    p[2] = V4<double>{q.L[1], q.L[3], q.sg[0], q.sg[1]};
+  } else {
+    p[0] = V4<double>{q.x[0], q.x[1], q.x[2], q.V};
+    p[1] = V4<double>{q.v[0], q.v[1], q.v[2], q.mu};
+    p[2] = V4<double>{mir, q.L[0], q.L[1], q.L[2]};
+    p[3] = V4<double>{q.L[3], q.L[4], q.L[5], q.sg[0]};
+    p[4] = V4<double>{q.sg[1], q.sg[2], 0.0, 0.0};
+  }
+}
+template <int D>
+__device__ __forceinline__ ARec get_a(const V4<double> *r, int i) {
+  const V4<double> *p = r + (size_t)RecW<D>::A * i;
+  ARec q;
+  const V4<double> q0 = p[0], q1 = p[1], q2 = p[2];
+  if (D == 2) {
+    q.x[0] = q0.x, q.x[1] = q0.y, q.x[2] = 0.0, q.V = q0.z, q.mu = q0.w;
+    q.v[0] = q1.x, q.v[1] = q1.y, q.v[2] = 0.0, q.mir = (int)q1.z, q.L[0] = q1.w;
+    q.L[1] = q2.x, q.L[3] = q2.y, q.sg[0] = q2.z, q.sg[1] = q2.w;
+    q.L[2] = q.L[4] = q.L[5] = 0.0;
+    q.sg[2] = 0.0;
+  } else {
+    const V4<double> q3 = p[3], q4 = p[4];
+    q.x[0] = q0.x, q.x[1] = q0.y, q.x[2] = q0.z, q.V = q0.w;
+    q.v[0] = q1.x, q.v[1] = q1.y, q.v[2] = q1.z, q.mu = q1.w;
+    q.mir = (int)q2.x, q.L[0] = q2.y, q.L[1] = q2.z, q.L[2] = q2.w;
+    q.L[3] = q3.x, q.L[4] = q3.y, q.L[5] = q3.z, q.sg[0] = q3.w;
+    q.sg[1] = q4.x, q.sg[2] = q4.y;
+  }
+  return q;
+}
+
+// R1: boundary values and the density update of sub-step s; writes the
+// continuity record
+template <int D>
 __global__ void k_adj_bc_density(AdjArgs a, int s) {
   const int n = a.cnt->n_live;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const InstDev &I = a.inst[a.m.inst[i]];
     if (s >= I.n_ac) continue;
     const double hdt = 0.5 * I.dt;
+    const size_t o = (size_t)s * a.T.cap + i;
     const int b = buffer_of(a, I, i);
     if (b >= 0) {
       if (a.buf[b].type == SPH_BUF_VELOCITY) {
         double lv[3] = {a.lv[0][i], a.lv[1][i], a.lv[2][i]};
         double lx[3] = {a.lx[0][i], a.lx[1][i], a.lx[2][i]};
-        const size_t o = (size_t)s * a.T.cap + i;
         const double x[3] = {a.T.xbc[0][o], a.T.xbc[1][o], a.T.xbc[2][o]};
         velocity_bc_rev(a, I, b, i, x, a.cnt->spawn_step, (uint32_t)s, lv, lx);
         for (int c = 0; c < 3; ++c) {
@@ -306,12 +463,18 @@ __global__ void k_adj_bc_density(AdjArgs a, int s) {
       }
     }
     // rho' = rho_s + hdt drho, drho = rho_s Sigma
-    const double rs = rho_s(a, s, i);
-    const double Sig = a.T.drho_s[(size_t)s * a.T.cap + i] / rs;
+    const double rs = a.T.rho_s[o];
+    const double Sig = a.T.drho_s[o] / rs;
     const double ltot = a.ldrho[i] + hdt * a.lrho[i];
-    a.sd[0][i] = ltot * rs;
     a.lrho[i] += ltot * Sig;
     a.ldrho[i] = 0.0;
+    CRec c;
+    load_x0(a, i, c.x);
+    c.V = a.m.mass[i] / rs;
+    c.p = I.c0sq * (rs - I.rho0);
+    for (int q = 0; q < 3; ++q) c.v[q] = a.T.v1[q][o];
+    c.ls = ltot * rs;
+    put_c<D>(a.rc, i, c);
   }
 }
 
@@ -323,55 +486,46 @@ __global__ void k_adj_cont(AdjArgs a, int s) {
     const InstDev &I = a.inst[a.m.inst[i]];
     if (s >= I.n_ac) continue;
     const G g = make_geo<double, D>(I);
-    const double kap = I.inv_rc0, c0sq = I.c0sq;
-    const size_t o = (size_t)s * a.T.cap;
-    double xi[3];
-    load_x0(a, i, xi);
-    const double rsi = a.T.rho_s[o + i], pi = c0sq * (rsi - I.rho0), Vi = a.m.mass[i] / rsi;
-    const double vi[3] = {a.T.v1[0][o + i], a.T.v1[1][o + i], a.T.v1[2][o + i]};
-    const double lsi = a.sd[0][i];
+    const double kap = I.inv_rc0;
+    const CRec ci = get_c<D>(a.rc, i);
+    const double lsi = ci.ls;
     double lvi[3] = {0, 0, 0}, lxi[3] = {0, 0, 0}, lpi = 0.0, lVi = 0.0;
     const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
-    const uint32_t *L = a.nl.nbr + i;
-    const size_t LS = (size_t)a.nl.stride;
+    const uint32_t *L = list_of(a.nl, i);
+    const size_t LS = kListTile;
+#pragma unroll 2
     for (int kk = 0; kk < nr; ++kk) {
       const int j = (int)L[kk * LS];
-      double xj[3], d[3];
-      load_x0(a, j, xj);
-      const double rr = pvec<D, PER>(g, xi, xj, d);
-      const double r = sqrt(rr);
+      const CRec cj = get_c<D>(a.rc, j);
+      double d[3];
+      const double r = sqrt(pvec<D, PER>(g, ci.x, cj.x, d));
       double F, Fr;
       kernel_FF(g, r, F, Fr);
-      const double rsj = a.T.rho_s[o + j], pj = c0sq * (rsj - I.rho0), Vj = a.m.mass[j] / rsj;
-      const double vv[3] = {vi[0] - a.T.v1[0][o + j], vi[1] - a.T.v1[1][o + j], vi[2] - a.T.v1[2][o + j]};
-      const double lsj = a.sd[0][j];
-      const double vd = dot3(vv, d), dp = pi - pj;
+      const double vv[3] = {ci.v[0] - cj.v[0], ci.v[1] - cj.v[1], ci.v[2] - cj.v[2]};
+      const double vd = dot3(vv, d), dp = ci.p - cj.p;
       // own term (seed lsi)
       const double br = vd + dp * kap * r;
-      for (int c = 0; c < D; ++c) {
-        lvi[c] += lsi * F * Vj * d[c];
-        lxi[c] += lsi * Vj * (F * vv[c] + br * Fr * d[c] / r + dp * kap * F * d[c] / r);
-      }
-      lpi += lsi * kap * r * F * Vj;
       // neighbour's term (seed lsj), i as its source
       const double br2 = vd - dp * kap * r;
+      const double lsj = cj.ls;
+#pragma unroll
       for (int c = 0; c < D; ++c) {
-        lvi[c] += lsj * F * Vi * d[c];
-        lxi[c] += lsj * Vi * (F * vv[c] + br2 * Fr * d[c] / r - dp * kap * F * d[c] / r);
+        lvi[c] += (lsi * cj.V + lsj * ci.V) * F * d[c];
+        lxi[c] += lsi * cj.V * (F * vv[c] + br * Fr * d[c] / r + dp * kap * F * d[c] / r) +
+                  lsj * ci.V * (F * vv[c] + br2 * Fr * d[c] / r - dp * kap * F * d[c] / r);
       }
-      lpi -= lsj * kap * r * F * Vi;
+      lpi += (lsi * cj.V - lsj * ci.V) * kap * r * F;
       lVi += lsj * br2 * F;
     }
     for (int kk = nr; kk < nr + nw; ++kk) {
       const int w = (int)L[kk * LS];
       const double xw[3] = {a.wx[0][w], a.wx[1][w], a.wx[2][w]};
       double d[3];
-      const double rr = pvec<D, PER>(g, xi, xw, d);
-      const double r = sqrt(rr);
+      const double r = sqrt(pvec<D, PER>(g, ci.x, xw, d));
       double F, Fr;
       kernel_FF(g, r, F, Fr);
       const V4<double> Wv = a.WV[w];
-      const double vv[3] = {vi[0] - Wv.x, vi[1] - Wv.y, vi[2] - Wv.z};
+      const double vv[3] = {ci.v[0] - Wv.x, ci.v[1] - Wv.y, ci.v[2] - Wv.z};
       const double vd = dot3(vv, d), Vw = I.Vw;
       for (int c = 0; c < D; ++c) {
         lvi[c] += lsi * 2.0 * F * Vw * d[c];
@@ -382,63 +536,39 @@ __global__ void k_adj_cont(AdjArgs a, int s) {
       a.lv[c][i] += lvi[c];
       a.lxg[c][i] += lxi[c];
     }
-    a.lrho[i] += c0sq * lpi - (Vi / rsi) * lVi;
+    a.lrho[i] += I.c0sq * lpi - (ci.V / a.T.rho_s[(size_t)s * a.T.cap + i]) * lVi;
   }
 }
 
-// momentum sums of particle i at sub-step s (forward recomputation)
-template <int D, bool PER>
-__device__ void mom_sums(const AdjArgs &a, const InstDev &I, const G &g, int s, int i, const double xi[3],
-                         double pei, double S1[3], double Cb[3], double S2[3], double Ct[3]) {
-  const size_t o = (size_t)s * a.T.cap;
-  const double c0sq = I.c0sq;
-  for (int c = 0; c < 3; ++c) S1[c] = Cb[c] = S2[c] = Ct[c] = 0.0;
-  const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
-  const uint32_t *L = a.nl.nbr + i;
-  const size_t LS = (size_t)a.nl.stride;
-  for (int kk = 0; kk < nr; ++kk) {
-    const int j = (int)L[kk * LS];
-    double xj[3], d[3];
-    load_x0(a, j, xj);
-    const double r = sqrt(pvec<D, PER>(g, xi, xj, d));
-    double F, Fr;
-    kernel_FF(g, r, F, Fr);
-    const double rsj = a.T.rho_s[o + j], pj = c0sq * (rsj - I.rho0), Vj = a.m.mass[j] / rsj;
-    const double kwj = I.rans ? (2.0 / 3.0) * a.m.k[j] : 0.0;
-    const double pej = I.rans ? pj + kwj * (I.rho0 + pj / c0sq) : pj;
-    double gw[3] = {Vj * F * d[0], Vj * F * d[1], Vj * F * d[2]};
-    if (is_pressure(a, I, j)) {
-      for (int c = 0; c < D; ++c) Cb[c] += gw[c];
-    } else {
-      double Bj[6], bg[3];
-      load_B(a, j, D, Bj);
-      sym_matvec<double, D>(Bj, gw, bg);
-      for (int c = 0; c < D; ++c) S1[c] += bg[c];
-    }
+// R3a: reverse of the kick and half drift; writes the momentum record
+template <int D>
+__global__ void k_adj_mom_rec(AdjArgs a, int s) {
+  const int n = a.cnt->n_live;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const InstDev &I = a.inst[a.m.inst[i]];
+    if (s >= I.n_ac) continue;
+    const double dt = I.dt, hdt = 0.5 * I.dt, c0sq = I.c0sq;
     for (int c = 0; c < D; ++c) {
-      S2[c] += pej * gw[c];
-      Ct[c] += gw[c];
+      const double lv = a.lv[c][i] + hdt * a.lx[c][i];
+      a.lv[c][i] = lv;
+      a.sd[c][i] = dt * lv;  // adjoint of the pressure acceleration
+      a.lan[c][i] += dt * lv;
     }
-  }
-  for (int kk = nr; kk < nr + nw; ++kk) {
-    const int w = (int)L[kk * LS];
-    const double xw[3] = {a.wx[0][w], a.wx[1][w], a.wx[2][w]};
-    double d[3];
-    const double r = sqrt(pvec<D, PER>(g, xi, xw, d));
-    double F, Fr;
-    kernel_FF(g, r, F, Fr);
-    for (int c = 0; c < D; ++c) {
-      const double gv = I.Vw * F * d[c];
-      Cb[c] += gv;
-      S2[c] += pei * gv;
-      Ct[c] += gv;
-    }
+    MRec m;
+    load_x0(a, i, m.x);
+    const double rs = rho_s(a, s, i), p = c0sq * (rs - I.rho0);
+    const double kw = I.rans ? (2.0 / 3.0) * a.m.k[i] : 0.0;
+    m.V = a.m.mass[i] / rs;
+    m.pe = I.rans ? p + kw * (I.rho0 + p / c0sq) : p;
+    load_B(a, i, D, m.B);
+    m.mk = is_pressure(a, I, i);
+    put_m<D>(a.rm, i, m);
   }
 }
 
-// R3: reverse of the kick and half drift, then the per-particle part of the
-// momentum reverse: seeds a1 (S1), ab (Cb), a2 (S2), at (Ct) and the direct
-// dependence on rho_i (1/rho_i, p_i, compensation) and B_i
+// R3b: momentum sums (forward recomputation from the records), the seeds
+// a1 (S1), ab (Cb), a2 (S2), at (Ct) and the direct dependence on rho_i
+// (1/rho_i, p_i, compensation) and B_i
 template <int D, bool PER>
 __global__ void k_adj_mom_seed(AdjArgs a, int s) {
   const int n = a.cnt->n_live;
@@ -446,42 +576,70 @@ __global__ void k_adj_mom_seed(AdjArgs a, int s) {
     const InstDev &I = a.inst[a.m.inst[i]];
     if (s >= I.n_ac) continue;
     const G g = make_geo<double, D>(I);
-    const double dt = I.dt, hdt = 0.5 * I.dt, c0sq = I.c0sq;
-    double la[3] = {0, 0, 0};
-    for (int c = 0; c < D; ++c) {
-      const double lv = a.lv[c][i] + hdt * a.lx[c][i];
-      a.lv[c][i] = lv;
-      la[c] = dt * lv;
-      a.lan[c][i] += dt * lv;
+    const double c0sq = I.c0sq;
+    const MRec mi = get_m<D>(a.rm, i);
+    const double la[3] = {a.sd[0][i], a.sd[1][i], D == 3 ? a.sd[2][i] : 0.0};
+    double S1[3] = {0, 0, 0}, Cb[3] = {0, 0, 0}, S2[3] = {0, 0, 0}, Ct[3] = {0, 0, 0};
+    const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
+    const uint32_t *L = list_of(a.nl, i);
+    const size_t LS = kListTile;
+#pragma unroll 2
+    for (int kk = 0; kk < nr; ++kk) {
+      const int j = (int)L[kk * LS];
+      const MRec mj = get_m<D>(a.rm, j);
+      double d[3];
+      const double r = sqrt(pvec<D, PER>(g, mi.x, mj.x, d));
+      double F, Fr;
+      kernel_FF(g, r, F, Fr);
+      const double gw[3] = {mj.V * F * d[0], mj.V * F * d[1], mj.V * F * d[2]};
+      if (mj.mk) {
+        for (int c = 0; c < D; ++c) Cb[c] += gw[c];
+      } else {
+        double bg[3];
+        sym_matvec<double, D>(mj.B, gw, bg);
+        for (int c = 0; c < D; ++c) S1[c] += bg[c];
+      }
+      for (int c = 0; c < D; ++c) {
+        S2[c] += mj.pe * gw[c];
+        Ct[c] += gw[c];
+      }
     }
-    double xi[3];
-    load_x0(a, i, xi);
-    const double rsi = rho_s(a, s, i), pi = c0sq * (rsi - I.rho0);
+    for (int kk = nr; kk < nr + nw; ++kk) {
+      const int w = (int)L[kk * LS];
+      const double xw[3] = {a.wx[0][w], a.wx[1][w], a.wx[2][w]};
+      double d[3];
+      const double r = sqrt(pvec<D, PER>(g, mi.x, xw, d));
+      double F, Fr;
+      kernel_FF(g, r, F, Fr);
+      for (int c = 0; c < D; ++c) {
+        const double gv = I.Vw * F * d[c];
+        Cb[c] += gv;
+        S2[c] += mi.pe * gv;
+        Ct[c] += gv;
+      }
+    }
+    const double rsi = rho_s(a, s, i);
     const double kwi = I.rans ? (2.0 / 3.0) * a.m.k[i] : 0.0;
-    const double pei = I.rans ? pi + kwi * (I.rho0 + pi / c0sq) : pi;
-    double S1[3], Cb[3], S2[3], Ct[3];
-    mom_sums<D, PER>(a, I, g, s, i, xi, pei, S1, Cb, S2, Ct);
-    double B[6];
-    load_B(a, i, D, B);
-    const bool comp = is_pressure(a, I, i);
-    const int bi = buffer_of(a, I, i);
-    double pob = comp ? a.buf[bi].p_ob : 0.0;
+    const bool comp = mi.mk;
+    double pob = comp ? a.buf[buffer_of(a, I, i)].p_ob : 0.0;
     if (comp && I.rans) pob += (2.0 / 3.0) * rsi * a.m.k[i];
     double Bla[3], BCb[3], BS2[3], BCt[3];
-    sym_matvec<double, D>(B, la, Bla);
-    sym_matvec<double, D>(B, Cb, BCb);
-    sym_matvec<double, D>(B, S2, BS2);
-    sym_matvec<double, D>(B, Ct, BCt);
+    sym_matvec<double, D>(mi.B, la, Bla);
+    sym_matvec<double, D>(mi.B, Cb, BCb);
+    sym_matvec<double, D>(mi.B, S2, BS2);
+    sym_matvec<double, D>(mi.B, Ct, BCt);
     const double inv = 1.0 / rsi;
+    SRec sr;
     for (int c = 0; c < 3; ++c) {
-      a.sd[0 + c][i] = c < D ? -pei * inv * la[c] : 0.0;
-      a.sd[3 + c][i] = c < D ? -pei * inv * Bla[c] : 0.0;
-      a.sd[6 + c][i] = c < D ? -inv * Bla[c] : 0.0;
-      a.sd[9 + c][i] = (c < D && comp) ? 2.0 * pob * inv * Bla[c] : 0.0;
+      sr.a1[c] = c < D ? -mi.pe * inv * la[c] : 0.0;
+      sr.ab[c] = c < D ? -mi.pe * inv * Bla[c] : 0.0;
+      sr.a2[c] = c < D ? -inv * Bla[c] : 0.0;
+      sr.at[c] = (c < D && comp) ? 2.0 * pob * inv * Bla[c] : 0.0;
     }
+    put_s<D>(a.rs, i, sr);
     double accp = 0.0, accc = 0.0, lpe = 0.0;
     for (int c = 0; c < D; ++c) {
-      accp += la[c] * (-(pei * (S1[c] + BCb[c]) + BS2[c]) * inv);
+      accp += la[c] * (-(mi.pe * (S1[c] + BCb[c]) + BS2[c]) * inv);
       if (comp) accc += la[c] * 2.0 * pob * inv * BCt[c];
       lpe += -inv * la[c] * (S1[c] + BCb[c]);
     }
@@ -493,7 +651,7 @@ __global__ void k_adj_mom_seed(AdjArgs a, int s) {
     }
     a.lrho[i] += lrho;
     double lB[6] = {0, 0, 0, 0, 0, 0};
-    sym_acc(lB, la, Cb, -pei * inv);
+    sym_acc(lB, la, Cb, -mi.pe * inv);
     sym_acc(lB, la, S2, -inv);
     if (comp) sym_acc(lB, la, Ct, 2.0 * pob * inv);
     for (int q = 0; q < 6; ++q) a.lB[q][i] += lB[q];
@@ -508,86 +666,71 @@ __global__ void k_adj_mom(AdjArgs a, int s) {
     const InstDev &I = a.inst[a.m.inst[i]];
     if (s >= I.n_ac) continue;
     const G g = make_geo<double, D>(I);
-    const size_t o = (size_t)s * a.T.cap;
-    const double c0sq = I.c0sq;
-    double xi[3];
-    load_x0(a, i, xi);
-    const double rsi = a.T.rho_s[o + i], pi = c0sq * (rsi - I.rho0), Vi = a.m.mass[i] / rsi;
-    const double kwi = I.rans ? (2.0 / 3.0) * a.m.k[i] : 0.0;
-    const double pei = I.rans ? pi + kwi * (I.rho0 + pi / c0sq) : pi;
-    const bool mk_i = is_pressure(a, I, i);
-    double Bi[6];
-    load_B(a, i, D, Bi);
-    const double a1i[3] = {a.sd[0][i], a.sd[1][i], a.sd[2][i]}, abi[3] = {a.sd[3][i], a.sd[4][i], a.sd[5][i]};
-    const double a2i[3] = {a.sd[6][i], a.sd[7][i], a.sd[8][i]}, ati[3] = {a.sd[9][i], a.sd[10][i], a.sd[11][i]};
+    const MRec mi = get_m<D>(a.rm, i);
+    const SRec si = get_s<D>(a.rs, i);
     double lxi[3] = {0, 0, 0}, lB[6] = {0, 0, 0, 0, 0, 0}, lpe = 0.0, lVi = 0.0;
     const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
-    const uint32_t *L = a.nl.nbr + i;
-    const size_t LS = (size_t)a.nl.stride;
+    const uint32_t *L = list_of(a.nl, i);
+    const size_t LS = kListTile;
+#pragma unroll 2
     for (int kk = 0; kk < nr; ++kk) {
       const int j = (int)L[kk * LS];
-      double xj[3], d[3];
-      load_x0(a, j, xj);
-      const double r = sqrt(pvec<D, PER>(g, xi, xj, d));
+      const MRec mj = get_m<D>(a.rm, j);
+      const SRec sj = get_s<D>(a.rs, j);
+      double d[3];
+      const double r = sqrt(pvec<D, PER>(g, mi.x, mj.x, d));
       double F, Fr;
       kernel_FF(g, r, F, Fr);
-      const double rsj = a.T.rho_s[o + j], pj = c0sq * (rsj - I.rho0), Vj = a.m.mass[j] / rsj;
-      const double kwj = I.rans ? (2.0 / 3.0) * a.m.k[j] : 0.0;
-      const double pej = I.rans ? pj + kwj * (I.rho0 + pj / c0sq) : pj;
-      const bool mk_j = is_pressure(a, I, j);
-      double Bj[6];
-      load_B(a, j, D, Bj);
       // own term: L = G . gw, gw = V_j F d
       double Gv[3];
-      if (mk_j) {
-        for (int c = 0; c < 3; ++c) Gv[c] = abi[c];
+      if (mj.mk) {
+        for (int c = 0; c < 3; ++c) Gv[c] = si.ab[c];
       } else {
-        sym_matvec<double, D>(Bj, a1i, Gv);
+        sym_matvec<double, D>(mj.B, si.a1, Gv);
       }
-      for (int c = 0; c < D; ++c) Gv[c] += pej * a2i[c] + ati[c];
-      double Gd = 0.0;
-      for (int c = 0; c < D; ++c) Gd += Gv[c] * d[c];
-      for (int c = 0; c < D; ++c) lxi[c] += Vj * (F * Gv[c] + Gd * Fr * d[c] / r);
+      for (int c = 0; c < D; ++c) Gv[c] += mj.pe * si.a2[c] + si.at[c];
       // neighbour's term with i as its source: gw' = -V_i F d
-      const double a1j[3] = {a.sd[0][j], a.sd[1][j], a.sd[2][j]}, abj[3] = {a.sd[3][j], a.sd[4][j], a.sd[5][j]};
-      const double a2j[3] = {a.sd[6][j], a.sd[7][j], a.sd[8][j]}, atj[3] = {a.sd[9][j], a.sd[10][j], a.sd[11][j]};
       double Gp[3];
-      if (mk_i) {
-        for (int c = 0; c < 3; ++c) Gp[c] = abj[c];
+      if (mi.mk) {
+        for (int c = 0; c < 3; ++c) Gp[c] = sj.ab[c];
       } else {
-        sym_matvec<double, D>(Bi, a1j, Gp);
+        sym_matvec<double, D>(mi.B, sj.a1, Gp);
       }
-      for (int c = 0; c < D; ++c) Gp[c] += pei * a2j[c] + atj[c];
-      double gwp[3] = {-Vi * F * d[0], -Vi * F * d[1], -Vi * F * d[2]};
-      if (!mk_i) sym_acc(lB, a1j, gwp, 1.0);
-      double Gpd = 0.0, a2g = 0.0;
+      for (int c = 0; c < D; ++c) Gp[c] += mi.pe * sj.a2[c] + sj.at[c];
+      const double gwp[3] = {-mi.V * F * d[0], -mi.V * F * d[1], -mi.V * F * d[2]};
+      if (!mi.mk) sym_acc(lB, sj.a1, gwp, 1.0);
+      double Gd = 0.0, Gpd = 0.0, a2g = 0.0;
       for (int c = 0; c < D; ++c) {
+        Gd += Gv[c] * d[c];
         Gpd += Gp[c] * d[c];
-        a2g += a2j[c] * gwp[c];
+        a2g += sj.a2[c] * gwp[c];
       }
       lpe += a2g;
       lVi += -F * Gpd;
-      for (int c = 0; c < D; ++c) lxi[c] += -Vi * (F * Gp[c] + Gpd * Fr * d[c] / r);
+      for (int c = 0; c < D; ++c)
+        lxi[c] += mj.V * (F * Gv[c] + Gd * Fr * d[c] / r) - mi.V * (F * Gp[c] + Gpd * Fr * d[c] / r);
     }
     for (int kk = nr; kk < nr + nw; ++kk) {
       const int w = (int)L[kk * LS];
       const double xw[3] = {a.wx[0][w], a.wx[1][w], a.wx[2][w]};
       double d[3];
-      const double r = sqrt(pvec<D, PER>(g, xi, xw, d));
+      const double r = sqrt(pvec<D, PER>(g, mi.x, xw, d));
       double F, Fr;
       kernel_FF(g, r, F, Fr);
       double Gv[3], Gd = 0.0, a2g = 0.0;
       for (int c = 0; c < D; ++c) {
-        Gv[c] = abi[c] + pei * a2i[c] + ati[c];
+        Gv[c] = si.ab[c] + mi.pe * si.a2[c] + si.at[c];
         Gd += Gv[c] * d[c];
-        a2g += a2i[c] * I.Vw * F * d[c];
+        a2g += si.a2[c] * I.Vw * F * d[c];
       }
       lpe += a2g;
       for (int c = 0; c < D; ++c) lxi[c] += I.Vw * (F * Gv[c] + Gd * Fr * d[c] / r);
     }
+    const double rsi = rho_s(a, s, i);
+    const double kwi = I.rans ? (2.0 / 3.0) * a.m.k[i] : 0.0;
     for (int c = 0; c < D; ++c) a.lxg[c][i] += lxi[c];
     for (int q = 0; q < 6; ++q) a.lB[q][i] += lB[q];
-    a.lrho[i] += lpe * (c0sq + kwi) - (Vi / rsi) * lVi;
+    a.lrho[i] += lpe * (I.c0sq + kwi) - (mi.V / rsi) * lVi;
   }
 }
 
@@ -608,42 +751,49 @@ __global__ void k_adj_half1(AdjArgs a, int s) {
 // reverse of the advection sweep: B (with mirror images) and the viscous
 // acceleration, from the adjoints of B (lB) and a_nu (lan)
 // ------------------------------------------------------------------------
+template <int D>
 __global__ void k_adj_adv_seed(AdjArgs a) {
   const int n = a.cnt->n_live;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const InstDev &I = a.inst[a.m.inst[i]];
     const double rho = a.T.rho0[i];
+    ARec q;
     double t = 0.0;
-    for (int c = 0; c < I.dim; ++c) {
-      const double l = a.lan[c][i];
-      a.sd[6 + c][i] = 2.0 * l / rho;
-      t += a.der.an[c][i] * l;
+    for (int c = 0; c < 3; ++c) {
+      const double l = c < D ? a.lan[c][i] : 0.0;
+      q.sg[c] = 2.0 * l / rho;
+      if (c < D) t += a.der.an[c][i] * l;
     }
-    if (I.dim == 2) a.sd[8][i] = 0.0;
     a.lrho[i] -= t / rho;
     // lambda_A = -B Lambda_B B unless the guard replaced B by I
     double Bs[6];
-    load_B(a, i, I.dim, Bs);
+    load_B(a, i, D, Bs);
     const bool guard = Bs[0] == 1.0 && Bs[1] == 1.0 && Bs[3] == 0.0 &&
-                       (I.dim == 2 || (Bs[2] == 1.0 && Bs[4] == 0.0 && Bs[5] == 0.0));
-    double lA[6] = {0, 0, 0, 0, 0, 0};
+                       (D == 2 || (Bs[2] == 1.0 && Bs[4] == 0.0 && Bs[5] == 0.0));
+    for (int c = 0; c < 6; ++c) q.L[c] = 0.0;
     if (!guard) {
       double B[3][3], Lm[3][3], T[3][3], R[3][3];
       sym_full(Bs, B);
       const double lb[6] = {a.lB[0][i], a.lB[1][i], a.lB[2][i], a.lB[3][i], a.lB[4][i], a.lB[5][i]};
       sym_full(lb, Lm);
       for (int p = 0; p < 3; ++p)
-        for (int q = 0; q < 3; ++q) T[p][q] = Lm[p][0] * B[0][q] + Lm[p][1] * B[1][q] + Lm[p][2] * B[2][q];
+        for (int r = 0; r < 3; ++r) T[p][r] = Lm[p][0] * B[0][r] + Lm[p][1] * B[1][r] + Lm[p][2] * B[2][r];
       for (int p = 0; p < 3; ++p)
-        for (int q = 0; q < 3; ++q) R[p][q] = -(B[p][0] * T[0][q] + B[p][1] * T[1][q] + B[p][2] * T[2][q]);
-      lA[0] = R[0][0];
-      lA[1] = R[1][1];
-      lA[2] = R[2][2];
-      lA[3] = 0.5 * (R[0][1] + R[1][0]);
-      lA[4] = 0.5 * (R[0][2] + R[2][0]);
-      lA[5] = 0.5 * (R[1][2] + R[2][1]);
+        for (int r = 0; r < 3; ++r) R[p][r] = -(B[p][0] * T[0][r] + B[p][1] * T[1][r] + B[p][2] * T[2][r]);
+      q.L[0] = R[0][0];
+      q.L[1] = R[1][1];
+      q.L[2] = R[2][2];
+      q.L[3] = 0.5 * (R[0][1] + R[1][0]);
+      q.L[4] = 0.5 * (R[0][2] + R[2][0]);
+      q.L[5] = 0.5 * (R[1][2] + R[2][1]);
     }
-    for (int q = 0; q < 6; ++q) a.sd[q][i] = lA[q];
+    load_x0(a, i, q.x);
+    q.V = a.m.mass[i] / rho;
+    for (int c = 0; c < 3; ++c) q.v[c] = a.T.v0[c][i];
+    q.mu = I.rho0 * (I.nu_l + (I.rans ? a.m.nut[i] : 0.0));
+    const int b = buffer_of(a, I, i);
+    q.mir = (b >= 0 && a.buf[b].type == SPH_BUF_PRESSURE) ? b : -1;
+    put_a<D>(a.ra, i, q);
   }
 }
 
@@ -661,6 +811,13 @@ __device__ __forceinline__ double visc_mu(const InstDev &I, double mu_a, double 
   return muR;
 }
 
+template <int D>
+__device__ __forceinline__ void sym_apply(const double L[6], const double d[3], double u[3]) {
+  u[0] = L[0] * d[0] + L[3] * d[1] + L[4] * d[2];
+  u[1] = L[3] * d[0] + L[1] * d[1] + L[5] * d[2];
+  u[2] = L[4] * d[0] + L[5] * d[1] + L[2] * d[2];
+}
+
 template <int D, bool PER>
 __global__ void k_adj_adv(AdjArgs a) {
   const int n = a.cnt->n_live;
@@ -668,49 +825,37 @@ __global__ void k_adj_adv(AdjArgs a) {
     const InstDev &I = a.inst[a.m.inst[i]];
     const G g = make_geo<double, D>(I);
     const double reg = I.reg, kR = I.muR_k * I.eta;
-    double xi[3];
-    load_x0(a, i, xi);
-    const double vi[3] = {a.T.v0[0][i], a.T.v0[1][i], a.T.v0[2][i]};
-    const double rhoi = a.T.rho0[i], Vi = a.m.mass[i] / rhoi;
-    const double mui = I.rho0 * (I.nu_l + (I.rans ? a.m.nut[i] : 0.0));
-    double LAi[3][3];
-    {
-      const double s6[6] = {a.sd[0][i], a.sd[1][i], a.sd[2][i], a.sd[3][i], a.sd[4][i], a.sd[5][i]};
-      sym_full(s6, LAi);
-    }
-    const double sgi[3] = {a.sd[6][i], a.sd[7][i], a.sd[8][i]};
-    const int bi = buffer_of(a, I, i);
-    const bool mir_i = bi >= 0 && a.buf[bi].type == SPH_BUF_PRESSURE;
+    const ARec qi = get_a<D>(a.ra, i);
+    const bool mir_i = qi.mir >= 0;
     double lvi[3] = {0, 0, 0}, lxi[3] = {0, 0, 0}, lVi = 0.0;
     const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
-    const uint32_t *L = a.nl.nbr + i;
-    const size_t LS = (size_t)a.nl.stride;
+    const uint32_t *L = list_of(a.nl, i);
+    const size_t LS = kListTile;
+#pragma unroll 2
     for (int kk = 0; kk < nr; ++kk) {
       const int j = (int)L[kk * LS];
-      double xj[3], d[3];
-      load_x0(a, j, xj);
-      const double r = sqrt(pvec<D, PER>(g, xi, xj, d));
+      const ARec qj = get_a<D>(a.ra, j);
+      double d[3];
+      const double r = sqrt(pvec<D, PER>(g, qi.x, qj.x, d));
       double F, Fr;
       kernel_FF(g, r, F, Fr);
-      const double rhoj = a.T.rho0[j], Vj = a.m.mass[j] / rhoj;
-      const double vv[3] = {vi[0] - a.T.v0[0][j], vi[1] - a.T.v0[1][j], vi[2] - a.T.v0[2][j]};
-      const double muj = I.rans ? I.rho0 * (I.nu_l + a.m.nut[j]) : mui;
+      const double vv[3] = {qi.v[0] - qj.v[0], qi.v[1] - qj.v[1], qi.v[2] - qj.v[2]};
       bool ard;
-      const double mu = visc_mu(I, mui, muj, true, vv, d, r, ard);
+      const double mu = visc_mu(I, qi.mu, qj.mu, true, vv, d, r, ard);
       const double rf = r / (r + reg), dfr = Fr * rf + F * reg / ((r + reg) * (r + reg));
       const double vd = dot3(vv, d);
       // ---- own terms (seeds of i) ----
-      if (!mir_i || !(local_coord(a.buf[bi], D, xj[0], xj[1], xj[2], 0) < 0.0)) {
+      if (!mir_i || !(local_coord(a.buf[qi.mir], D, qj.x[0], qj.x[1], qj.x[2], 0) < 0.0)) {
         double u[3];
-        matvec3(LAi, d, u);
+        sym_apply<D>(qi.L, d, u);
         const double q = dot3(d, u);
-        for (int c = 0; c < D; ++c) lxi[c] += -Vj * (Fr * q * d[c] / r + 2.0 * F * u[c]);
+        for (int c = 0; c < D; ++c) lxi[c] += -qj.V * (Fr * q * d[c] / r + 2.0 * F * u[c]);
       }
       {
-        const double f = F * rf * Vj, sv = dot3(sgi, vv);
+        const double f = F * rf * qj.V, sv = dot3(qi.sg, vv);
         for (int c = 0; c < D; ++c) {
-          lvi[c] += mu * f * sgi[c];
-          lxi[c] += mu * sv * Vj * dfr * d[c] / r;
+          lvi[c] += mu * f * qi.sg[c];
+          lxi[c] += mu * sv * qj.V * dfr * d[c] / r;
         }
         if (ard) {
           const double Lm = f * sv * kR;
@@ -721,23 +866,18 @@ __global__ void k_adj_adv(AdjArgs a) {
         }
       }
       // ---- neighbour's terms (seeds of j), i as the source ----
-      const int bj = buffer_of(a, I, j);
-      const bool mir_j = bj >= 0 && a.buf[bj].type == SPH_BUF_PRESSURE;
-      if (!mir_j || !(local_coord(a.buf[bj], D, xi[0], xi[1], xi[2], 0) < 0.0)) {
-        double LAj[3][3], u[3];
-        const double s6[6] = {a.sd[0][j], a.sd[1][j], a.sd[2][j], a.sd[3][j], a.sd[4][j], a.sd[5][j]};
-        sym_full(s6, LAj);
-        matvec3(LAj, d, u);
+      if (!(qj.mir >= 0) || !(local_coord(a.buf[qj.mir], D, qi.x[0], qi.x[1], qi.x[2], 0) < 0.0)) {
+        double u[3];
+        sym_apply<D>(qj.L, d, u);
         const double q = dot3(d, u);
         lVi += -F * q;
-        for (int c = 0; c < D; ++c) lxi[c] += -Vi * (Fr * q * d[c] / r + 2.0 * F * u[c]);
+        for (int c = 0; c < D; ++c) lxi[c] += -qi.V * (Fr * q * d[c] / r + 2.0 * F * u[c]);
       }
       {
-        const double sgj[3] = {a.sd[6][j], a.sd[7][j], a.sd[8][j]};
-        const double fp = F * rf * Vi, svp = -dot3(sgj, vv);  // v_ji = -v_ij
+        const double fp = F * rf * qi.V, svp = -dot3(qj.sg, vv);  // v_ji = -v_ij
         for (int c = 0; c < D; ++c) {
-          lvi[c] += -mu * fp * sgj[c];
-          lxi[c] += mu * svp * Vi * dfr * d[c] / r;
+          lvi[c] += -mu * fp * qj.sg[c];
+          lxi[c] += mu * svp * qi.V * dfr * d[c] / r;
         }
         lVi += mu * F * rf * svp;
         if (ard) {
@@ -753,24 +893,24 @@ __global__ void k_adj_adv(AdjArgs a) {
       const int w = (int)L[kk * LS];
       const double xw[3] = {a.wx[0][w], a.wx[1][w], a.wx[2][w]};
       double d[3];
-      const double r = sqrt(pvec<D, PER>(g, xi, xw, d));
+      const double r = sqrt(pvec<D, PER>(g, qi.x, xw, d));
       double F, Fr;
       kernel_FF(g, r, F, Fr);
       const double Vw = I.Vw;
-      if (!mir_i || !(local_coord(a.buf[bi], D, xw[0], xw[1], xw[2], 0) < 0.0)) {
+      if (!mir_i || !(local_coord(a.buf[qi.mir], D, xw[0], xw[1], xw[2], 0) < 0.0)) {
         double u[3];
-        matvec3(LAi, d, u);
+        sym_apply<D>(qi.L, d, u);
         const double q = dot3(d, u);
         for (int c = 0; c < D; ++c) lxi[c] += -Vw * (Fr * q * d[c] / r + 2.0 * F * u[c]);
       }
       const V4<double> Wv = a.WV[w];
-      const double vv[3] = {2.0 * (vi[0] - Wv.x), 2.0 * (vi[1] - Wv.y), 2.0 * (vi[2] - Wv.z)};
+      const double vv[3] = {2.0 * (qi.v[0] - Wv.x), 2.0 * (qi.v[1] - Wv.y), 2.0 * (qi.v[2] - Wv.z)};
       bool ard;
-      const double mu = visc_mu(I, mui, mui, false, vv, d, r, ard);
+      const double mu = visc_mu(I, qi.mu, qi.mu, false, vv, d, r, ard);
       const double rf = r / (r + reg), dfr = Fr * rf + F * reg / ((r + reg) * (r + reg));
-      const double f = F * rf * Vw, sv = dot3(sgi, vv), vd = dot3(vv, d);
+      const double f = F * rf * Vw, sv = dot3(qi.sg, vv), vd = dot3(vv, d);
       for (int c = 0; c < D; ++c) {
-        lvi[c] += 2.0 * mu * f * sgi[c];
+        lvi[c] += 2.0 * mu * f * qi.sg[c];
         lxi[c] += mu * sv * Vw * dfr * d[c] / r;
       }
       if (ard) {
@@ -784,11 +924,11 @@ __global__ void k_adj_adv(AdjArgs a) {
     if (mir_i) {
       // images m_k = x_k - 2 s_k n of every particle with s_k >= 0 around the
       // image of x_i (two-cell margin), as the forward sweep found them
-      const BufDev &b = a.buf[bi];
+      const BufDev &b = a.buf[qi.mir];
       const double nb[3] = {b.frame[0], b.frame[1], b.frame[2]};
-      const double si = local_coord(b, D, xi[0], xi[1], xi[2], 0);
-      const double q0 = xi[0] - 2.0 * si * nb[0], q1 = xi[1] - 2.0 * si * nb[1];
-      const double q2 = D == 3 ? xi[2] - 2.0 * si * nb[2] : 0.0;
+      const double si = local_coord(b, D, qi.x[0], qi.x[1], qi.x[2], 0);
+      const double q0 = qi.x[0] - 2.0 * si * nb[0], q1 = qi.x[1] - 2.0 * si * nb[1];
+      const double q2 = D == 3 ? qi.x[2] - 2.0 * si * nb[2] : 0.0;
       const int qx = cell_coord(I, q0, 0), qy = cell_coord(I, q1, 1), qz = D == 3 ? cell_coord(I, q2, 2) : 0;
       for (int set = 0; set < 2; ++set) {
         visit_cells<D, PER>(I, qx, qy, qz, 2, set == 0 ? a.off : a.woff, [&](uint32_t jb, uint32_t je) {
@@ -796,8 +936,9 @@ __global__ void k_adj_adv(AdjArgs a) {
             double xk[3];
             double Vk;
             if (set == 0) {
-              load_x0(a, (int)k, xk);
-              Vk = a.m.mass[k] / a.T.rho0[k];
+              const ARec qk = get_a<D>(a.ra, (int)k);
+              for (int c = 0; c < 3; ++c) xk[c] = qk.x[c];
+              Vk = qk.V;
             } else {
               xk[0] = a.wx[0][k];
               xk[1] = a.wx[1][k];
@@ -808,7 +949,7 @@ __global__ void k_adj_adv(AdjArgs a) {
             if (sk < 0.0) continue;
             double dd[3] = {0, 0, 0}, rr = 0.0;
             for (int c = 0; c < D; ++c) {
-              dd[c] = xi[c] - (xk[c] - 2.0 * sk * nb[c]);
+              dd[c] = qi.x[c] - (xk[c] - 2.0 * sk * nb[c]);
               rr += dd[c] * dd[c];
             }
             if (!(rr > 0.0 && rr < g.cut2)) continue;
@@ -816,7 +957,7 @@ __global__ void k_adj_adv(AdjArgs a) {
             double F, Fr;
             kernel_FF(g, r, F, Fr);
             double u[3];
-            matvec3(LAi, dd, u);
+            sym_apply<D>(qi.L, dd, u);
             const double q = dot3(dd, u);
             double gd[3] = {0, 0, 0};
             for (int c = 0; c < D; ++c) {
@@ -837,7 +978,7 @@ __global__ void k_adj_adv(AdjArgs a) {
       a.lv[c][i] += lvi[c];
       a.lxg[c][i] += lxi[c];
     }
-    a.lrho[i] += -(Vi / rhoi) * lVi;
+    a.lrho[i] += -(qi.V / a.T.rho0[i]) * lVi;
   }
 }
 
@@ -888,8 +1029,9 @@ void launch_adj_buffer_rev(const AdjArgs &a, int max_n, cudaStream_t st) {
 template <int D, bool PER>
 static void substep_rev(const AdjArgs &a, int s, int max_n, cudaStream_t st) {
   const int g = grid_of(max_n, kBlock);
-  k_adj_bc_density<<<g, kBlock, 0, st>>>(a, s);
+  k_adj_bc_density<D><<<g, kBlock, 0, st>>>(a, s);
   k_adj_cont<D, PER><<<g, kBlock, 0, st>>>(a, s);
+  k_adj_mom_rec<D><<<g, kBlock, 0, st>>>(a, s);
   k_adj_mom_seed<D, PER><<<g, kBlock, 0, st>>>(a, s);
   k_adj_mom<D, PER><<<g, kBlock, 0, st>>>(a, s);
   k_adj_half1<<<g, kBlock, 0, st>>>(a, s);
@@ -904,13 +1046,14 @@ void launch_adj_substep_rev(const AdjArgs &a, int dim, int any_periodic, int sub
 
 void launch_adj_adv_rev(const AdjArgs &a, int dim, int any_periodic, int max_n, cudaStream_t st) {
   const int g = grid_of(max_n, kBlock);
-  k_adj_adv_seed<<<g, kBlock, 0, st>>>(a);
   if (dim == 2) {
+    k_adj_adv_seed<2><<<g, kBlock, 0, st>>>(a);
     if (any_periodic)
       k_adj_adv<2, true><<<g, kBlock, 0, st>>>(a);
     else
       k_adj_adv<2, false><<<g, kBlock, 0, st>>>(a);
   } else {
+    k_adj_adv_seed<3><<<g, kBlock, 0, st>>>(a);
     if (any_periodic)
       k_adj_adv<3, true><<<g, kBlock, 0, st>>>(a);
     else

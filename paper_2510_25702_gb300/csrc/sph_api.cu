@@ -116,6 +116,7 @@ struct sph_ctx {
     double *lam[8] = {}, *out[8] = {};  // x3, v3, rho, drho
     double *lxg[3] = {}, *lxs[3] = {}, *lrhos = nullptr, *lB[6] = {}, *lan[3] = {}, *sd[12] = {};
     double *grad = nullptr, *J = nullptr;
+    V4<double> *rc = nullptr, *rm = nullptr, *rs = nullptr, *ra = nullptr;
     uint8_t *region = nullptr;
     int32_t *mask = nullptr;
     int64_t n_region = 0;
@@ -614,7 +615,9 @@ int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *
     kmax = std::max(16, std::min(kmax, 4096));
     c->nl.kmax = kmax;
     c->nl.stride = (int32_t)cap;
-    ok &= (c->nl.nbr = alloc_arr<uint32_t>(c, cap * (int64_t)kmax)) != nullptr;
+    const int64_t tiles = (cap + kListTile - 1) / kListTile;
+    ok &= (c->nl.nbr = alloc_arr<uint32_t>(c, tiles * kListTile * (int64_t)kmax)) != nullptr;
+    ok &= (c->nl.rows = alloc_arr<uint16_t>(c, tiles)) != nullptr;
     ok &= (c->nl.n_real = alloc_arr<uint16_t>(c, cap)) != nullptr;
     ok &= (c->nl.n_wall = alloc_arr<uint16_t>(c, cap)) != nullptr;
   }
@@ -1162,6 +1165,7 @@ static int adj_alloc(sph_ctx *c) {
   const size_t cap = (size_t)c->cap, ns = (size_t)c->n_ac_max;
   const size_t nd = 8 + 8 + 3 + 3 + 1 + 6 + 3 + 12 + (3 + 3 + 1 + 1) + ns * (1 + 1 + 3 + 3);
   const size_t bytes = nd * (cap * 8 + 256) + 2 * (cap * 4 + 256) + 2 * 256 + (size_t)A.d.n_theta * 8 + 8 +
+                       (3 + 3 + 3 + 5) * (cap * 32 + 256) +
                        (size_t)A.n_region + 4096;
   void *mem = nullptr;
   if (c->alloc.alloc)
@@ -1198,6 +1202,10 @@ static int adj_alloc(sph_ctx *c) {
   for (int k = 0; k < 3; ++k) T.xbc[k] = (double *)take(ns * cap * 8);
   T.perm = (uint32_t *)take(cap * 4);
   T.spawn_dst = (int32_t *)take(cap * 4);
+  A.rc = (V4<double> *)take(3 * cap * 32);
+  A.rm = (V4<double> *)take(3 * cap * 32);
+  A.rs = (V4<double> *)take(3 * cap * 32);
+  A.ra = (V4<double> *)take(5 * cap * 32);
   A.grad = (double *)take((size_t)A.d.n_theta * 8);
   A.J = (double *)take(8);
   A.region = (uint8_t *)take((size_t)A.n_region + 1);
@@ -1234,6 +1242,10 @@ static AdjArgs adj_args(sph_ctx *c) {
   for (int k = 0; k < 6; ++k) a.lB[k] = A.lB[k];
   for (int k = 0; k < 12; ++k) a.sd[k] = A.sd[k];
   for (int k = 0; k < 8; ++k) a.out[k] = A.out[k];
+  a.rc = A.rc;
+  a.rm = A.rm;
+  a.rs = A.rs;
+  a.ra = A.ra;
   a.grad = A.grad;
   a.J = A.J;
   a.region = A.region;
@@ -1293,7 +1305,7 @@ static void enqueue_step_reverse(sph_ctx *c) {
   for (int k = 0; k < 8; ++k) cudaMemsetAsync(A.out[k], 0, b8, c->stream);
   launch_adj_perm_rev(a, maxn, c->stream);
   for (int k = 0; k < 8; ++k) std::swap(A.lam[k], A.out[k]);
-  c->launches += 4 + 5 * c->n_ac_max + 3;
+  c->launches += 4 + 6 * c->n_ac_max + 3;
 }
 
 int sph_adjoint_forward(sph_ctx *c, const sph_adjoint_desc *d, double *J_out) {

@@ -331,14 +331,35 @@ void launch_keys(const TopoArgs &a, int max_n, int all_live, cudaStream_t st);
 void launch_iota(uint32_t *idx, int max_n, cudaStream_t st);
 
 // Neighbour list of the frozen configuration (rebuilt every advection
-// step): entry k of particle i at nbr[k * stride + i], the n_real[i] real
-// neighbours first, then n_wall[i] wall dummies.
+// step), in warp tiles: the entries of the 32 particles of warp tile w form
+// one contiguous block of kmax rows of 32 (entry k of particle i at
+// nbr[((i / 32) * kmax + k) * 32 + i % 32]), so a warp reads row k as one
+// 128-byte line and its whole list as one contiguous range; the n_real[i]
+// real neighbours come first, then n_wall[i] wall dummies; rows[w] is the
+// longest list of tile w (rows worth prefetching).
 struct NbrList {
   uint32_t *nbr;
   uint16_t *n_real, *n_wall;
+  uint16_t *rows;
   int32_t stride;  // particle capacity
   int32_t kmax;    // entries per particle
 };
+
+constexpr int kListTile = 32;
+
+__host__ __device__ __forceinline__ uint32_t *list_of(const NbrList &nl, int i) {
+  return nl.nbr + ((size_t)(i / kListTile) * (size_t)nl.kmax) * kListTile + (i % kListTile);
+}
+
+// asynchronous L2 prefetch of the list tile that particle i belongs to
+__device__ __forceinline__ void prefetch_list_tile(const NbrList &nl, int i) {
+  const int w = i / kListTile;
+  const unsigned rows = nl.rows[w];
+  if (rows == 0) return;
+  const uint32_t *p = nl.nbr + (size_t)w * (size_t)nl.kmax * kListTile;
+  const unsigned bytes = rows * kListTile * 4u;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 struct SweepArgs {
   const InstDev *inst;
@@ -396,7 +417,8 @@ struct AdjArgs {
   double *lxg[3];                        // adjoint of the start position (pair geometry)
   double *lxs[3], *lrhos;                // mirror-term contributions (scattered)
   double *lB[6], *lan[3];
-  double *sd[12];                        // per-particle seeds of one pair reverse
+  double *sd[12];                        // per-particle scratch of one pair reverse
+  V4<double> *rc, *rm, *rs, *ra;         // per-particle records of the pair reverses
   double *out[8];                        // pending-order result of the permutation reverse
   double *grad;                          // dJ/dtheta
   double *J;                             // objective accumulator

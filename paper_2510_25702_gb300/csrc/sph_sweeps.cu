@@ -40,15 +40,15 @@ namespace sphk {
 // neighbour list of the frozen configuration (once per advection step)
 // =========================================================================
 template <typename R, int D, bool PER>
-__device__ __forceinline__ void list_one(const SweepArgs &a, const Packs<R> &pk, const int i) {
+__device__ __forceinline__ int list_one(const SweepArgs &a, const Packs<R> &pk, const int i) {
   constexpr int RA = RecLayout<D>::adv;
   const InstDev &I = a.inst[a.m.inst[i]];
   const Geo<R> g = make_geo<R, D>(I);
   int cx, cy, cz;
   decode_cell(I, a.keys[i], cx, cy, cz);
   const V4<R> Pi = pk.adv[RA * (size_t)i];
-  uint32_t *__restrict__ out = a.nl.nbr + i;
-  const size_t LS = (size_t)a.nl.stride;
+  uint32_t *__restrict__ out = list_of(a.nl, i);
+  const size_t LS = kListTile;
   const int K = a.nl.kmax;
   int nr = 0, nw = 0;
   // real neighbours, then wall dummies; 0 < |r|^2 < (2h)^2 excludes i itself
@@ -74,6 +74,7 @@ __device__ __forceinline__ void list_one(const SweepArgs &a, const Packs<R> &pk,
   }
   a.nl.n_real[i] = (uint16_t)nr;
   a.nl.n_wall[i] = (uint16_t)nw;
+  return nr + nw;
 }
 
 // =========================================================================
@@ -86,8 +87,8 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   const int ii = m.inst[i];
   const InstDev &I = a.inst[ii];
   const Geo<R> g = make_geo<R, D>(I);
-  const uint32_t *__restrict__ Lst = a.nl.nbr + i;
-  const size_t LS = (size_t)a.nl.stride;
+  const uint32_t *__restrict__ Lst = list_of(a.nl, i);
+  const size_t LS = kListTile;
   const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
   const bool rans = I.rans != 0;
   // own record: 2D (x y V vx)(vy k eps nut), 3D (x y z V)(vx vy vz k)(eps nut - -)
@@ -332,8 +333,8 @@ __device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, 
   const InstDev &I = a.inst[ii];
   if (a.sub >= I.n_ac) return;
   const Geo<R> g = make_geo<R, D>(I);
-  const uint32_t *__restrict__ Lst = a.nl.nbr + i;
-  const size_t LS = (size_t)a.nl.stride;
+  const uint32_t *__restrict__ Lst = list_of(a.nl, i);
+  const size_t LS = kListTile;
   const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
   const bool rans = I.rans != 0;
   const R rho0 = sweep_const<R>(I).rho0, inv_c0sq = sweep_const<R>(I).inv_c0sq;
@@ -447,8 +448,8 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
   const InstDev &I = a.inst[ii];
   if (a.sub >= I.n_ac) return;
   const Geo<R> g = make_geo<R, D>(I);
-  const uint32_t *__restrict__ Lst = a.nl.nbr + i;
-  const size_t LS = (size_t)a.nl.stride;
+  const uint32_t *__restrict__ Lst = list_of(a.nl, i);
+  const size_t LS = kListTile;
   const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
   const V4<R> C0 = pk.cont[2 * (size_t)i], C1 = pk.cont[2 * (size_t)i + 1];
   const R vi[3] = {D == 2 ? C1.x : C1.y, D == 2 ? C1.y : C1.z, D == 2 ? (R)0 : C1.w};
@@ -538,32 +539,55 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
 // ------------------------------------------------------------------------
 template <typename R, int D, bool PER>
 __global__ void __launch_bounds__(kMaxBlock) k_list(SweepArgs a, Packs<R> pk) {
+  // after a device error (non-finite state, capacity) the state is not
+  // advanced further: non-finite positions would all fall into one edge
+  // cell and make the candidate scan quadratic
+  if (a.cnt->status) return;
   const int n = a.cnt->n_live;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    list_one<R, D, PER>(a, pk, i);
+  // whole blocks iterate together so that every lane of a warp takes part
+  // in the reduction of the tile's longest list
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int cnt = i < n ? list_one<R, D, PER>(a, pk, i) : 0;
+    const int rows = __reduce_max_sync(0xffffffffu, cnt);
+    if ((threadIdx.x & 31) == 0 && i < n) a.nl.rows[i / kListTile] = (uint16_t)rows;
+  }
 }
 
 template <typename R, int D, bool PER>
 __global__ void __launch_bounds__(kMaxBlock) k_adv(SweepArgs a, Packs<R> pk) {
+  if (a.cnt->status) return;
   const int n = a.cnt->n_live;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+  const int step = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+    // the next tile's neighbour list on its way to L2 while this one runs
+    if ((threadIdx.x & 31) == 0 && i + step < n) prefetch_list_tile(a.nl, i + step);
     adv_one<R, D, PER>(a, pk, i);
+  }
 }
 
 template <typename R, int D, bool PER>
 __global__ void __launch_bounds__(kMaxBlock) k_mom(SweepArgs a, Packs<R> pk) {
-  if (a.sub >= a.cnt->n_ac_all) return;  // no instance takes this sub-step
+  if (a.sub >= a.cnt->n_ac_all || a.cnt->status) return;  // no instance takes this sub-step
   const int n = a.cnt->n_live;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+  const int step = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+    // the next tile's neighbour list on its way to L2 while this one runs
+    if ((threadIdx.x & 31) == 0 && i + step < n) prefetch_list_tile(a.nl, i + step);
     mom_one<R, D, PER>(a, pk, i);
+  }
 }
 
 template <typename R, int D, bool PER>
 __global__ void __launch_bounds__(kMaxBlock) k_cont(SweepArgs a, Packs<R> pk) {
-  if (a.sub >= a.cnt->n_ac_all) return;
+  if (a.sub >= a.cnt->n_ac_all || a.cnt->status) return;
   const int n = a.cnt->n_live;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+  const int step = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+    // the next tile's neighbour list on its way to L2 while this one runs
+    if ((threadIdx.x & 31) == 0 && i + step < n) prefetch_list_tile(a.nl, i + step);
     cont_one<R, D, PER>(a, pk, i);
+  }
 }
 
 // =========================================================================
