@@ -566,57 +566,26 @@ __global__ void k_adj_mom_rec(AdjArgs a, int s) {
   }
 }
 
-// R3b: momentum sums (forward recomputation from the records), the seeds
-// a1 (S1), ab (Cb), a2 (S2), at (Ct) and the direct dependence on rho_i
-// (1/rho_i, p_i, compensation) and B_i
-template <int D, bool PER>
+// R3b: the seeds a1 (S1), ab (Cb), a2 (S2), at (Ct) from the momentum sums
+// the forward step recorded, and the direct dependence on rho_i (1/rho_i,
+// p_i, compensation) and B_i
+template <int D>
 __global__ void k_adj_mom_seed(AdjArgs a, int s) {
   const int n = a.cnt->n_live;
+  const size_t cap = (size_t)a.T.cap;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const InstDev &I = a.inst[a.m.inst[i]];
     if (s >= I.n_ac) continue;
-    const G g = make_geo<double, D>(I);
     const double c0sq = I.c0sq;
     const MRec mi = get_m<D>(a.rm, i);
     const double la[3] = {a.sd[0][i], a.sd[1][i], D == 3 ? a.sd[2][i] : 0.0};
-    double S1[3] = {0, 0, 0}, Cb[3] = {0, 0, 0}, S2[3] = {0, 0, 0}, Ct[3] = {0, 0, 0};
-    const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
-    const uint32_t *L = list_of(a.nl, i);
-    const size_t LS = kListTile;
-#pragma unroll 2
-    for (int kk = 0; kk < nr; ++kk) {
-      const int j = (int)L[kk * LS];
-      const MRec mj = get_m<D>(a.rm, j);
-      double d[3];
-      const double r = sqrt(pvec<D, PER>(g, mi.x, mj.x, d));
-      double F, Fr;
-      kernel_FF(g, r, F, Fr);
-      const double gw[3] = {mj.V * F * d[0], mj.V * F * d[1], mj.V * F * d[2]};
-      if (mj.mk) {
-        for (int c = 0; c < D; ++c) Cb[c] += gw[c];
-      } else {
-        double bg[3];
-        sym_matvec<double, D>(mj.B, gw, bg);
-        for (int c = 0; c < D; ++c) S1[c] += bg[c];
-      }
-      for (int c = 0; c < D; ++c) {
-        S2[c] += mj.pe * gw[c];
-        Ct[c] += gw[c];
-      }
-    }
-    for (int kk = nr; kk < nr + nw; ++kk) {
-      const int w = (int)L[kk * LS];
-      const double xw[3] = {a.wx[0][w], a.wx[1][w], a.wx[2][w]};
-      double d[3];
-      const double r = sqrt(pvec<D, PER>(g, mi.x, xw, d));
-      double F, Fr;
-      kernel_FF(g, r, F, Fr);
-      for (int c = 0; c < D; ++c) {
-        const double gv = I.Vw * F * d[c];
-        Cb[c] += gv;
-        S2[c] += mi.pe * gv;
-        Ct[c] += gv;
-      }
+    const double *t = a.T.S + (size_t)s * 12 * cap + i;
+    double S1[3], Cb[3], S2[3], Ct[3];
+    for (int c = 0; c < 3; ++c) {
+      S1[c] = t[(0 + c) * cap];
+      Cb[c] = t[(3 + c) * cap];
+      S2[c] = t[(6 + c) * cap];
+      Ct[c] = t[(9 + c) * cap];
     }
     const double rsi = rho_s(a, s, i);
     const double kwi = I.rans ? (2.0 / 3.0) * a.m.k[i] : 0.0;
@@ -645,9 +614,9 @@ __global__ void k_adj_mom_seed(AdjArgs a, int s) {
     }
     double lrho = -(accp + accc) * inv + lpe * (c0sq + kwi);
     if (comp && I.rans) {
-      double t = 0.0;
-      for (int c = 0; c < D; ++c) t += la[c] * BCt[c];
-      lrho += 2.0 * inv * (2.0 / 3.0) * a.m.k[i] * t;
+      double tt = 0.0;
+      for (int c = 0; c < D; ++c) tt += la[c] * BCt[c];
+      lrho += 2.0 * inv * (2.0 / 3.0) * a.m.k[i] * tt;
     }
     a.lrho[i] += lrho;
     double lB[6] = {0, 0, 0, 0, 0, 0};
@@ -1032,7 +1001,7 @@ static void substep_rev(const AdjArgs &a, int s, int max_n, cudaStream_t st) {
   k_adj_bc_density<D><<<g, kBlock, 0, st>>>(a, s);
   k_adj_cont<D, PER><<<g, kBlock, 0, st>>>(a, s);
   k_adj_mom_rec<D><<<g, kBlock, 0, st>>>(a, s);
-  k_adj_mom_seed<D, PER><<<g, kBlock, 0, st>>>(a, s);
+  k_adj_mom_seed<D><<<g, kBlock, 0, st>>>(a, s);
   k_adj_mom<D, PER><<<g, kBlock, 0, st>>>(a, s);
   k_adj_half1<<<g, kBlock, 0, st>>>(a, s);
 }

@@ -117,6 +117,21 @@ struct sph_ctx {
     double *lxg[3] = {}, *lxs[3] = {}, *lrhos = nullptr, *lB[6] = {}, *lan[3] = {}, *sd[12] = {};
     double *grad = nullptr, *J = nullptr;
     V4<double> *rc = nullptr, *rm = nullptr, *rs = nullptr, *ra = nullptr;
+    // what the reverse pass of one step reads, recorded while the segment
+    // is recomputed: the tape, the neighbour list, B and a_nu, the masters
+    // after the step that the reverse kernels index, the pending keys, the
+    // buffer-update flags, the cell offsets and the counters
+    struct Slot {
+      void *mem = nullptr;
+      AdjTape T{};
+      NbrList nl{};
+      Derived der{};
+      Masters m{};
+      uint32_t *keys = nullptr, *off = nullptr;
+      uint8_t *flag = nullptr;
+      Counters *cnt = nullptr;
+    };
+    std::vector<Slot> slots;
     uint8_t *region = nullptr;
     int32_t *mask = nullptr;
     int64_t n_region = 0;
@@ -1141,12 +1156,15 @@ static void adj_free(sph_ctx *c) {
   cudaStreamSynchronize(c->stream);
   for (int32_t s : A.ckpt) sph_drop_state(c, s);
   if (A.end_slot >= 0) sph_drop_state(c, A.end_slot);
-  if (A.mem) {
+  auto dfree = [&](void *p) {
+    if (!p) return;
     if (c->alloc.free)
-      c->alloc.free(c->alloc.user, A.mem, c->alloc.stream);
+      c->alloc.free(c->alloc.user, p, c->alloc.stream);
     else
-      cudaFree(A.mem);
-  }
+      cudaFree(p);
+  };
+  for (auto &sl : A.slots) dfree(sl.mem);
+  dfree(A.mem);
   A = sph_ctx::Adj();
 }
 
@@ -1163,7 +1181,8 @@ static int adj_alloc(sph_ctx *c) {
   sph_ctx::Adj &A = c->adj;
   if (A.mem) return 0;
   const size_t cap = (size_t)c->cap, ns = (size_t)c->n_ac_max;
-  const size_t nd = 8 + 8 + 3 + 3 + 1 + 6 + 3 + 12 + (3 + 3 + 1 + 1) + ns * (1 + 1 + 3 + 3);
+  const size_t nd = 8 + 8 + 3 + 3 + 1 + 6 + 3 + 12;
+  (void)ns;
   const size_t bytes = nd * (cap * 8 + 256) + 2 * (cap * 4 + 256) + 2 * 256 + (size_t)A.d.n_theta * 8 + 8 +
                        (3 + 3 + 3 + 5) * (cap * 32 + 256) +
                        (size_t)A.n_region + 4096;
@@ -1190,18 +1209,6 @@ static int adj_alloc(sph_ctx *c) {
   for (int k = 0; k < 6; ++k) A.lB[k] = d();
   for (int k = 0; k < 3; ++k) A.lan[k] = d();
   for (int k = 0; k < 12; ++k) A.sd[k] = d();
-  AdjTape &T = A.T;
-  T.cap = (int64_t)cap;
-  for (int k = 0; k < 3; ++k) T.x0[k] = d();
-  for (int k = 0; k < 3; ++k) T.v0[k] = d();
-  T.rho0 = d();
-  T.drho0 = d();
-  T.rho_s = (double *)take(ns * cap * 8);
-  T.drho_s = (double *)take(ns * cap * 8);
-  for (int k = 0; k < 3; ++k) T.v1[k] = (double *)take(ns * cap * 8);
-  for (int k = 0; k < 3; ++k) T.xbc[k] = (double *)take(ns * cap * 8);
-  T.perm = (uint32_t *)take(cap * 4);
-  T.spawn_dst = (int32_t *)take(cap * 4);
   A.rc = (V4<double> *)take(3 * cap * 32);
   A.rm = (V4<double> *)take(3 * cap * 32);
   A.rs = (V4<double> *)take(3 * cap * 32);
@@ -1213,7 +1220,65 @@ static int adj_alloc(sph_ctx *c) {
   return 0;
 }
 
-static AdjArgs adj_args(sph_ctx *c) {
+static int slot_alloc(sph_ctx *c, sph_ctx::Adj::Slot &sl) {
+  if (sl.mem) return 0;
+  const size_t cap = (size_t)c->cap, ns = (size_t)c->n_ac_max;
+  const size_t tiles = (cap + kListTile - 1) / kListTile;
+  const size_t nbr = tiles * kListTile * (size_t)c->nl.kmax;
+  const size_t ncell1 = (size_t)c->ncell + 1;
+  // doubles: tape 8 + ns (1 + 1 + 3 + 3 + 12); B 6, a_nu 3; masters mass, k, nut, x 3
+  const size_t nd = 8 + ns * 20 + 9 + 6;
+  const size_t bytes = nd * (cap * 8 + 256) + (nbr * 4 + 256) + 2 * (cap * 2 + 256) + 5 * (cap * 4 + 256) +
+                       (cap * 2 + 256) + (cap + 256) + (ncell1 * 4 + 256) + 512 + 4096;
+  void *mem = nullptr;
+  if (c->alloc.alloc)
+    mem = c->alloc.alloc(c->alloc.user, bytes, c->alloc.stream);
+  else if (cudaMalloc(&mem, bytes) != cudaSuccess)
+    mem = nullptr;
+  if (!mem) return fail(SPH_ERR_ALLOC, "adjoint step records");
+  sl.mem = mem;
+  char *p = (char *)mem;
+  auto take = [&](size_t n) {
+    void *q = p;
+    p += (n + 255) & ~(size_t)255;
+    return q;
+  };
+  auto d = [&]() { return (double *)take(cap * 8); };
+  AdjTape &T = sl.T;
+  T.cap = (int64_t)cap;
+  for (int k = 0; k < 3; ++k) T.x0[k] = d();
+  for (int k = 0; k < 3; ++k) T.v0[k] = d();
+  T.rho0 = d();
+  T.drho0 = d();
+  T.rho_s = (double *)take(ns * cap * 8);
+  T.drho_s = (double *)take(ns * cap * 8);
+  for (int k = 0; k < 3; ++k) T.v1[k] = (double *)take(ns * cap * 8);
+  for (int k = 0; k < 3; ++k) T.xbc[k] = (double *)take(ns * cap * 8);
+  T.S = (double *)take(ns * 12 * cap * 8);
+  T.perm = (uint32_t *)take(cap * 4);
+  T.spawn_dst = (int32_t *)take(cap * 4);
+  sl.nl = c->nl;
+  sl.nl.nbr = (uint32_t *)take(nbr * 4);
+  sl.nl.n_real = (uint16_t *)take(cap * 2);
+  sl.nl.n_wall = (uint16_t *)take(cap * 2);
+  sl.nl.rows = nullptr;
+  for (int q = 0; q < 6; ++q) sl.der.B[q] = d();
+  for (int k = 0; k < 3; ++k) sl.der.an[k] = d();
+  sl.m.mass = d();
+  sl.m.k = d();
+  sl.m.nut = d();
+  for (int k = 0; k < 3; ++k) sl.m.x[k] = d();
+  sl.m.label = (int32_t *)take(cap * 4);
+  sl.m.uid = (uint32_t *)take(cap * 4);
+  sl.m.inst = (uint16_t *)take(cap * 2);
+  sl.keys = (uint32_t *)take(cap * 4);
+  sl.flag = (uint8_t *)take(cap);
+  sl.off = (uint32_t *)take(ncell1 * 4);
+  sl.cnt = (Counters *)take(sizeof(Counters));
+  return 0;
+}
+
+static AdjArgs adj_args(sph_ctx *c, const sph_ctx::Adj::Slot *sl = nullptr) {
   sph_ctx::Adj &A = c->adj;
   AdjArgs a{};
   a.inst = c->d_inst;
@@ -1228,7 +1293,16 @@ static AdjArgs adj_args(sph_ctx *c) {
   a.WV = c->pkd.WV;
   a.cnt = c->cnt;
   a.flag = c->flag;
-  a.T = A.T;
+  if (sl) {
+    a.m = sl->m;
+    a.der = sl->der;
+    a.nl = sl->nl;
+    a.off = sl->off;
+    a.pending_keys = sl->keys;
+    a.cnt = sl->cnt;
+    a.flag = sl->flag;
+    a.T = sl->T;
+  }
   for (int k = 0; k < 3; ++k) {
     a.lx[k] = A.lam[k];
     a.lv[k] = A.lam[3 + k];
@@ -1259,32 +1333,57 @@ static AdjArgs adj_args(sph_ctx *c) {
   return a;
 }
 
-// one advection step with the records the reverse pass reads
-static void enqueue_step_taped(sph_ctx *c) {
+// one advection step, recording into slot sl what its reverse pass reads
+static void enqueue_step_taped(sph_ctx *c, sph_ctx::Adj::Slot &sl) {
   enqueue_topology(c);
   const int maxn = (int)c->cap;
+  const size_t cap = (size_t)c->cap;
+  cudaStream_t st = c->stream;
   AdjArgs a = adj_args(c);
-  cudaMemcpyAsync(c->adj.T.perm, c->sorted_vals, 4 * (size_t)c->cap, cudaMemcpyDeviceToDevice, c->stream);
-  launch_adj_tape_start(a, maxn, c->stream);
-  launch_time_step(c->topo(), c->stream);
-  launch_neighbour_list(c->sweep(0, 0), c->packs(), c->prec, c->dim, maxn, c->stream);
-  launch_advection_sweep(c->sweep(0, 1), c->packs(), c->prec, c->dim, maxn, c->stream);
+  a.T = sl.T;  // tape kernels read the live masters and write the slot
+  cudaMemcpyAsync(sl.T.perm, c->sorted_vals, 4 * cap, cudaMemcpyDeviceToDevice, st);
+  launch_adj_tape_start(a, maxn, st);
+  launch_time_step(c->topo(), st);
+  launch_neighbour_list(c->sweep(0, 0), c->packs(), c->prec, c->dim, maxn, st);
+  launch_advection_sweep(c->sweep(0, 1), c->packs(), c->prec, c->dim, maxn, st);
   for (int s = 0; s < c->n_ac_max; ++s) {
-    launch_momentum_sweep(c->sweep(s, 2), c->packs(), c->prec, c->dim, maxn, s, c->stream);
-    launch_adj_tape_sub(a, s, maxn, c->stream);
-    launch_continuity_sweep(c->sweep(s, 3), c->packs(), c->prec, c->dim, maxn, s, c->stream);
-    launch_adj_tape_drho(a, s, maxn, c->stream);
+    SweepArgs sm = c->sweep(s, 2);
+    sm.tape_S = sl.T.S;
+    launch_momentum_sweep(sm, c->packs(), c->prec, c->dim, maxn, s, st);
+    launch_adj_tape_sub(a, s, maxn, st);
+    launch_continuity_sweep(c->sweep(s, 3), c->packs(), c->prec, c->dim, maxn, s, st);
+    launch_adj_tape_drho(a, s, maxn, st);
   }
   TopoArgs t = c->topo();
-  t.spawn_dst = c->adj.T.spawn_dst;
-  launch_buffer_update(t, maxn, c->stream);
+  t.spawn_dst = sl.T.spawn_dst;
+  launch_buffer_update(t, maxn, st);
+  // the state the reverse kernels index
+  auto cp = [&](void *dst, const void *src, size_t n) { cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, st); };
+  const size_t tiles = (cap + kListTile - 1) / kListTile;
+  cp(sl.nl.nbr, c->nl.nbr, tiles * kListTile * (size_t)c->nl.kmax * 4);
+  cp(sl.nl.n_real, c->nl.n_real, cap * 2);
+  cp(sl.nl.n_wall, c->nl.n_wall, cap * 2);
+  for (int q = 0; q < 6; ++q) cp(sl.der.B[q], c->der.B[q], cap * 8);
+  for (int k = 0; k < 3; ++k) cp(sl.der.an[k], c->der.an[k], cap * 8);
+  const Masters &M = c->M[c->cur];
+  cp(sl.m.mass, M.mass, cap * 8);
+  cp(sl.m.k, M.k, cap * 8);
+  cp(sl.m.nut, M.nut, cap * 8);
+  for (int k = 0; k < 3; ++k) cp(sl.m.x[k], M.x[k], cap * 8);
+  cp(sl.m.label, M.label, cap * 4);
+  cp(sl.m.uid, M.uid, cap * 4);
+  cp(sl.m.inst, M.inst, cap * 2);
+  cp(sl.keys, c->K[0], cap * 4);
+  cp(sl.flag, c->flag, cap);
+  cp(sl.off, c->off, ((size_t)c->ncell + 1) * 4);
+  cp(sl.cnt, c->cnt, sizeof(Counters));
   c->launches += 3 + 3 + 4 * c->n_ac_max + 3;
   c->step += 1;
 }
 
-// reverse of the step just recomputed by enqueue_step_taped; the adjoint
-// arrays go from the state after the step to the state before it
-static void enqueue_step_reverse(sph_ctx *c) {
+// reverse of the step recorded in slot sl; the adjoint arrays go from the
+// state after the step to the state before it
+static void enqueue_step_reverse(sph_ctx *c, const sph_ctx::Adj::Slot &sl) {
   sph_ctx::Adj &A = c->adj;
   const int maxn = (int)c->cap;
   const size_t b8 = 8 * (size_t)c->cap;
@@ -1297,7 +1396,7 @@ static void enqueue_step_reverse(sph_ctx *c) {
   for (int k = 0; k < 6; ++k) cudaMemsetAsync(A.lB[k], 0, b8, c->stream);
   int any_per = 0;
   for (const InstDev &I : c->inst) any_per |= I.periodic[0] | I.periodic[1] | I.periodic[2];
-  AdjArgs a = adj_args(c);
+  AdjArgs a = adj_args(c, &sl);
   launch_adj_objective(a, 1, maxn, c->stream);
   launch_adj_buffer_rev(a, maxn, c->stream);
   for (int s = c->n_ac_max - 1; s >= 0; --s) launch_adj_substep_rev(a, c->dim, any_per, s, maxn, c->stream);
@@ -1381,22 +1480,13 @@ int sph_adjoint_backward(sph_ctx *c, double *grad_out, int32_t n_theta) {
   const int K = A.d.checkpoint_every, steps = A.d.steps;
   const int nseg = (int)A.ckpt.size();
   int rc = 0;
-  std::vector<int32_t> snap;
+  if ((int)A.slots.size() < K) A.slots.resize(K);
+  for (int q = 0; q < K && !rc; ++q) rc = slot_alloc(c, A.slots[q]);
   for (int seg = nseg - 1; seg >= 0 && !rc; --seg) {
     const int s0 = seg * K, s1 = std::min(s0 + K, steps);
-    snap.assign(s1 - s0, -1);
-    snap[0] = A.ckpt[seg];
     if ((rc = sph_restore_state(c, A.ckpt[seg]))) break;
-    for (int n = s0; n < s1 - 1 && !rc; ++n) {
-      enqueue_step(c);
-      rc = sph_save_state(c, &snap[n + 1 - s0]);
-    }
-    for (int n = s1 - 1; n >= s0 && !rc; --n) {
-      if ((rc = sph_restore_state(c, snap[n - s0]))) break;
-      enqueue_step_taped(c);
-      enqueue_step_reverse(c);
-      if (n > s0) rc = sph_drop_state(c, snap[n - s0]);
-    }
+    for (int n = s0; n < s1; ++n) enqueue_step_taped(c, A.slots[n - s0]);
+    for (int n = s1 - 1; n >= s0; --n) enqueue_step_reverse(c, A.slots[n - s0]);
   }
   if (!rc) rc = sph_restore_state(c, A.end_slot);
   set_freeze(c, 0);

@@ -375,6 +375,7 @@ struct SweepArgs {
   int32_t sub;
   int32_t any_periodic;  // some instance has a periodic axis
   int32_t block;         // threads per block of the launch
+  double *tape_S;        // optional: momentum sums S1, Cb, S2, Ct per sub-step
 };
 
 // sweeps: prec 0 -> double packs, 1 -> float packs; dim 2 / 3
@@ -395,6 +396,7 @@ void launch_continuity_sweep(const SweepArgs &a, void *packs, int prec, int dim,
 // and the copies of the buffer update.
 struct AdjTape {
   double *x0[3], *v0[3], *rho0, *drho0;
+  double *S;  // momentum sums [sub][12][cap]: S1, Cb, S2, Ct
   double *rho_s, *drho_s, *v1[3], *xbc[3];  // [sub * cap + i]
   uint32_t *perm;                           // cell-order index -> pending index
   int32_t *spawn_dst;                       // injecting particle -> its copy

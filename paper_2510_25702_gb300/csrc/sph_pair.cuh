@@ -69,7 +69,10 @@ __device__ __forceinline__ R pair_vec(const Geo<R> &g, const V4<R> &pi, const V4
         v = Ex<R>::add(v, g.L[a]);
     }
     d[a] = v;
-    rr = (a == 0) ? Ex<R>::mul(v, v) : Ex<R>::add(rr, Ex<R>::mul(v, v));
+    if (sizeof(R) == 4)
+      rr = (a == 0) ? v * v : fmaf((float)v, (float)v, (float)rr);  // FP32: contracted
+    else
+      rr = (a == 0) ? Ex<R>::mul(v, v) : Ex<R>::add(rr, Ex<R>::mul(v, v));
   }
   if (D == 2) d[2] = (R)0;
   return rr;
@@ -219,6 +222,40 @@ __device__ __forceinline__ void invert_guarded(const double A[6], double B[6]) {
       return;
     }
     double inv = 1.0 / det;
+    B[0] = c00 * inv;
+    B[1] = (xx * zz - xz * xz) * inv;
+    B[2] = (xx * yy - xy * xy) * inv;
+    B[3] = c01 * inv;
+    B[4] = c02 * inv;
+    B[5] = (xz * xy - xx * yz) * inv;
+  }
+}
+
+// the same guarded inverse in the sweep precision (fast reciprocal in FP32)
+template <typename R, int D>
+__device__ __forceinline__ void invert_guarded_fast(const R A[6], R B[6]) {
+  for (int c = 0; c < 6; ++c) B[c] = (R)0;
+  if (D == 2) {
+    const R t = (R)0.5 * (A[0] + A[1]);
+    const R det = A[0] * A[1] - A[3] * A[3];
+    if (!(det > (R)1e-3 * t * t)) {
+      B[0] = B[1] = (R)1;
+      return;
+    }
+    const R inv = Ex<R>::div((R)1, det);
+    B[0] = A[1] * inv;
+    B[1] = A[0] * inv;
+    B[3] = -A[3] * inv;
+  } else {
+    const R xx = A[0], yy = A[1], zz = A[2], xy = A[3], xz = A[4], yz = A[5];
+    const R c00 = yy * zz - yz * yz, c01 = yz * xz - xy * zz, c02 = xy * yz - yy * xz;
+    const R det = xx * c00 + xy * c01 + xz * c02;
+    const R t = (xx + yy + zz) * (R)(1.0 / 3.0);
+    if (!(det > (R)1e-3 * t * t * t)) {
+      B[0] = B[1] = B[2] = (R)1;
+      return;
+    }
+    const R inv = Ex<R>::div((R)1, det);
     B[0] = c00 * inv;
     B[1] = (xx * zz - xz * xz) * inv;
     B[2] = (xx * yy - xy * xy) * inv;

@@ -232,25 +232,43 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   }
 
   // ---------------- epilogue ----------------
-  double Ad[6] = {(double)A[0], (double)A[1], 0.0, (double)A[3], 0.0, 0.0};
-  if (D == 3) {
-    Ad[2] = (double)A[2];
-    Ad[4] = (double)A[4];
-    Ad[5] = (double)A[5];
+  // B = A^-1.  FP64 where the support is cut (wall dummies in the list,
+  // particles in a buffer): there A can be ill-conditioned.  Interior
+  // particles of the FP32 form, whose A is close to the full-support
+  // lattice value (about 0.97 I), invert in the sweep precision.
+  R BR[6] = {(R)0, (R)0, (R)0, (R)0, (R)0, (R)0};
+  if (sizeof(R) == 4 && nw == 0 && lab == 0) {
+    invert_guarded_fast<R, D>(A, BR);
+  } else {
+    double Ad[6] = {(double)A[0], (double)A[1], 0.0, (double)A[3], 0.0, 0.0};
+    if (D == 3) {
+      Ad[2] = (double)A[2];
+      Ad[4] = (double)A[4];
+      Ad[5] = (double)A[5];
+    }
+    double Bd[6];
+    invert_guarded<D>(Ad, Bd);  // FP64 inversion (one reciprocal)
+    for (int c = 0; c < 6; ++c) BR[c] = (R)Bd[c];
+    if (sizeof(R) == 8) {  // FP64 form: keep every bit of the FP64 inverse
+      a.der.B[0][i] = Bd[0];
+      a.der.B[1][i] = Bd[1];
+      a.der.B[3][i] = Bd[3];
+      if (D == 3) {
+        a.der.B[2][i] = Bd[2];
+        a.der.B[4][i] = Bd[4];
+        a.der.B[5][i] = Bd[5];
+      }
+    }
   }
-  double B[6];
-  invert_guarded<D>(Ad, B);  // FP64 inversion (one reciprocal)
-  a.der.B[0][i] = B[0];
-  a.der.B[1][i] = B[1];
-  a.der.B[3][i] = B[3];
-  R BR[6] = {(R)B[0], (R)B[1], (R)0, (R)B[3], (R)0, (R)0};
-  if (D == 3) {
-    a.der.B[2][i] = B[2];
-    a.der.B[4][i] = B[4];
-    a.der.B[5][i] = B[5];
-    BR[2] = (R)B[2];
-    BR[4] = (R)B[4];
-    BR[5] = (R)B[5];
+  if (sizeof(R) == 4) {
+    a.der.B[0][i] = (double)BR[0];
+    a.der.B[1][i] = (double)BR[1];
+    a.der.B[3][i] = (double)BR[3];
+    if (D == 3) {
+      a.der.B[2][i] = (double)BR[2];
+      a.der.B[4][i] = (double)BR[4];
+      a.der.B[5][i] = (double)BR[5];
+    }
   }
   const double rho_i = m.rho[i];
   const R inv_rho = Ex<R>::div((R)1, (R)rho_i);
@@ -416,6 +434,17 @@ __device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, 
       for (int c = 0; c < D; ++c) acc[c] += (R)2 * pob * inv_rho * bct[c];
     }
   }
+  if (a.tape_S) {
+    // the four sums for the reverse pass of a differentiated window
+    double *t = a.tape_S + (size_t)a.sub * 12 * a.nl.stride;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      t[(size_t)(0 + c) * a.nl.stride + i] = (double)S1[c];
+      t[(size_t)(3 + c) * a.nl.stride + i] = (double)Cb[c];
+      t[(size_t)(6 + c) * a.nl.stride + i] = (double)S2[c];
+      t[(size_t)(9 + c) * a.nl.stride + i] = (double)Ct[c];
+    }
+  }
   // FP64 kick and half drift
   const V4<R> ap = pk.Ap[i];
   const R apr[3] = {ap.x, ap.y, ap.z};
@@ -502,9 +531,11 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
     }
   }
   double v[3] = {m.v[0][i], m.v[1][i], D == 3 ? m.v[2][i] : 0.0};
-  bool bad = !isfinite(rho);
+  // non-finite test on the exponent bits (integer pipe)
+  auto nonfinite = [](double x) { return (__double2hiint(x) & 0x7ff00000) == 0x7ff00000; };
+  bool bad = nonfinite(rho);
 #pragma unroll
-  for (int c = 0; c < D; ++c) bad |= !isfinite(v[c]);
+  for (int c = 0; c < D; ++c) bad |= nonfinite(v[c]);
   if (bad) set_status(a.status, SPH_ERR_NONFINITE);
   if (a.sub + 1 < I.n_ac) {
     // first half of the next sub-step and the momentum record it reads
