@@ -492,10 +492,9 @@ __global__ void k_adj_cont(AdjArgs a, int s) {
     double lvi[3] = {0, 0, 0}, lxi[3] = {0, 0, 0}, lpi = 0.0, lVi = 0.0;
     const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
     const uint32_t *L = list_of(a.nl, i);
-    const size_t LS = kListTile;
 #pragma unroll 2
     for (int kk = 0; kk < nr; ++kk) {
-      const int j = (int)L[kk * LS];
+      const int j = (int)list_at(L, kk);
       const CRec cj = get_c<D>(a.rc, j);
       double d[3];
       const double r = sqrt(pvec<D, PER>(g, ci.x, cj.x, d));
@@ -518,7 +517,7 @@ __global__ void k_adj_cont(AdjArgs a, int s) {
       lVi += lsj * br2 * F;
     }
     for (int kk = nr; kk < nr + nw; ++kk) {
-      const int w = (int)L[kk * LS];
+      const int w = (int)list_at(L, kk);
       const double xw[3] = {a.wx[0][w], a.wx[1][w], a.wx[2][w]};
       double d[3];
       const double r = sqrt(pvec<D, PER>(g, ci.x, xw, d));
@@ -640,10 +639,9 @@ __global__ void k_adj_mom(AdjArgs a, int s) {
     double lxi[3] = {0, 0, 0}, lB[6] = {0, 0, 0, 0, 0, 0}, lpe = 0.0, lVi = 0.0;
     const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
     const uint32_t *L = list_of(a.nl, i);
-    const size_t LS = kListTile;
 #pragma unroll 2
     for (int kk = 0; kk < nr; ++kk) {
-      const int j = (int)L[kk * LS];
+      const int j = (int)list_at(L, kk);
       const MRec mj = get_m<D>(a.rm, j);
       const SRec sj = get_s<D>(a.rs, j);
       double d[3];
@@ -680,7 +678,7 @@ __global__ void k_adj_mom(AdjArgs a, int s) {
         lxi[c] += mj.V * (F * Gv[c] + Gd * Fr * d[c] / r) - mi.V * (F * Gp[c] + Gpd * Fr * d[c] / r);
     }
     for (int kk = nr; kk < nr + nw; ++kk) {
-      const int w = (int)L[kk * LS];
+      const int w = (int)list_at(L, kk);
       const double xw[3] = {a.wx[0][w], a.wx[1][w], a.wx[2][w]};
       double d[3];
       const double r = sqrt(pvec<D, PER>(g, mi.x, xw, d));
@@ -799,10 +797,9 @@ __global__ void k_adj_adv(AdjArgs a) {
     double lvi[3] = {0, 0, 0}, lxi[3] = {0, 0, 0}, lVi = 0.0;
     const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
     const uint32_t *L = list_of(a.nl, i);
-    const size_t LS = kListTile;
 #pragma unroll 2
     for (int kk = 0; kk < nr; ++kk) {
-      const int j = (int)L[kk * LS];
+      const int j = (int)list_at(L, kk);
       const ARec qj = get_a<D>(a.ra, j);
       double d[3];
       const double r = sqrt(pvec<D, PER>(g, qi.x, qj.x, d));
@@ -859,7 +856,7 @@ __global__ void k_adj_adv(AdjArgs a) {
       }
     }
     for (int kk = nr; kk < nr + nw; ++kk) {
-      const int w = (int)L[kk * LS];
+      const int w = (int)list_at(L, kk);
       const double xw[3] = {a.wx[0][w], a.wx[1][w], a.wx[2][w]};
       double d[3];
       const double r = sqrt(pvec<D, PER>(g, qi.x, xw, d));

@@ -331,24 +331,32 @@ void launch_keys(const TopoArgs &a, int max_n, int all_live, cudaStream_t st);
 void launch_iota(uint32_t *idx, int max_n, cudaStream_t st);
 
 // Neighbour list of the frozen configuration (rebuilt every advection
-// step), in warp tiles: the entries of the 32 particles of warp tile w form
-// one contiguous block of kmax rows of 32 (entry k of particle i at
-// nbr[((i / 32) * kmax + k) * 32 + i % 32]), so a warp reads row k as one
-// 128-byte line and its whole list as one contiguous range; the n_real[i]
-// real neighbours come first, then n_wall[i] wall dummies; rows[w] is the
-// longest list of tile w (rows worth prefetching).
+// step), in warp tiles of 4-entry chunks: the entries of the 32 particles of
+// warp tile w form one contiguous block; in it, chunk c (entries 4c..4c+3)
+// of lane l is the 16-byte word at (c * 32 + l), so a warp reads four
+// entries of all its particles with one 512-byte load and its whole list is
+// one contiguous range.  The n_real[i] real neighbours come first, then
+// n_wall[i] wall dummies; rows[w] is the longest list of tile w (the part
+// worth prefetching).
 struct NbrList {
   uint32_t *nbr;
   uint16_t *n_real, *n_wall;
   uint16_t *rows;
   int32_t stride;  // particle capacity
-  int32_t kmax;    // entries per particle
+  int32_t kmax;    // entries per particle, a multiple of 8
 };
 
 constexpr int kListTile = 32;
 
+// first entry of particle i; entry k is at list_at(p, k)
 __host__ __device__ __forceinline__ uint32_t *list_of(const NbrList &nl, int i) {
-  return nl.nbr + ((size_t)(i / kListTile) * (size_t)nl.kmax) * kListTile + (i % kListTile);
+  return nl.nbr + ((size_t)(i / kListTile) * (size_t)(nl.kmax / 4) * kListTile + (size_t)(i % kListTile)) * 4;
+}
+__host__ __device__ __forceinline__ size_t list_off(int k) { return (size_t)(k >> 2) * (4 * kListTile) + (k & 3); }
+__device__ __forceinline__ uint32_t list_at(const uint32_t *p, int k) { return p[list_off(k)]; }
+// chunk c (entries 4c..4c+3) of the particle whose first entry is p
+__device__ __forceinline__ uint4 list_chunk(const uint32_t *p, int c) {
+  return reinterpret_cast<const uint4 *>(p)[(size_t)c * kListTile];
 }
 
 // asynchronous L2 prefetch of the list tile that particle i belongs to
@@ -357,7 +365,7 @@ __device__ __forceinline__ void prefetch_list_tile(const NbrList &nl, int i) {
   const unsigned rows = nl.rows[w];
   if (rows == 0) return;
   const uint32_t *p = nl.nbr + (size_t)w * (size_t)nl.kmax * kListTile;
-  const unsigned bytes = rows * kListTile * 4u;
+  const unsigned bytes = ((rows + 3u) / 4u) * kListTile * 16u;
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 

@@ -48,7 +48,6 @@ __device__ __forceinline__ int list_one(const SweepArgs &a, const Packs<R> &pk, 
   decode_cell(I, a.keys[i], cx, cy, cz);
   const V4<R> Pi = pk.adv[RA * (size_t)i];
   uint32_t *__restrict__ out = list_of(a.nl, i);
-  const size_t LS = kListTile;
   const int K = a.nl.kmax;
   int nr = 0, nw = 0;
   // real neighbours, then wall dummies; 0 < |r|^2 < (2h)^2 excludes i itself
@@ -59,7 +58,7 @@ __device__ __forceinline__ int list_one(const SweepArgs &a, const Packs<R> &pk, 
     visit_cells<D, PER>(I, cx, cy, cz, 1, offs, [&](uint32_t jb, uint32_t je) {
       scan_range<R, D, PER>(g, Pi, recs, stride, jb, je, [&](uint32_t j) {
         const int k = nr + nw;
-        if (k < K) out[(size_t)k * LS] = j;
+        if (k < K) out[list_off(k)] = j;
         if (set == 0)
           ++nr;
         else
@@ -88,7 +87,6 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   const InstDev &I = a.inst[ii];
   const Geo<R> g = make_geo<R, D>(I);
   const uint32_t *__restrict__ Lst = list_of(a.nl, i);
-  const size_t LS = kListTile;
   const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
   const bool rans = I.rans != 0;
   // own record: 2D (x y V vx)(vy k eps nut), 3D (x y z V)(vx vy vz k)(eps nut - -)
@@ -123,47 +121,53 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   R dk = 0, de = 0;
 
   // real neighbours
-#pragma unroll 4
-  for (int kk = 0; kk < nr; ++kk) {
-    const uint32_t j = Lst[(size_t)kk * LS];
-    const V4<R> B0 = pk.adv[RA * (size_t)j], B1 = pk.adv[RA * (size_t)j + 1];
-    V4<R> B2 = B1;
-    if (D == 3 && rans) B2 = pk.adv[RA * (size_t)j + 2];
-    R d[3];
-    const R rr = pair_vec<R, D, PER>(g, A0, B0, d);
-    R r;
-    Ex<R>::len(rr, r);
-    const R F = kernel_F(g, r);  // dW/dr / r
-    const R V = vol<R, D>(B0);
-    if (!mirror || !(local0<R, D>(mo, mn, B0.x, B0.y, B0.z) < (R)0)) sym_add_outer<R, D>(A, d, -F * V);
-    const R vj[3] = {D == 2 ? B0.w : B1.x, D == 2 ? B1.x : B1.y, D == 2 ? (R)0 : B1.z};
-    const R vij[3] = {vi[0] - vj[0], vi[1] - vj[1], vi[2] - vj[2]};
-    const R f = Ex<R>::div(F * r, r + g.reg) * V;  // dW/dr / (r + 0.01h) V
-    R mu_ad = mu_i;                                // laminar: harmonic mean of equal values
-    if (rans) {
-      const R k_j = D == 2 ? B1.y : B1.w, e_j = D == 2 ? B1.z : B2.x, nut_j = D == 2 ? B1.w : B2.y;
-      const R mu_j = rho0 * (nu_l + nut_j);
-      const R mut = Ex<R>::div((R)2 * mu_i * mu_j, mu_i + mu_j);
-      R ve = -(vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2]) * Ex<R>::div((R)1, r);
-      R lim = eta * (ve > (R)0 ? ve : (R)0);
-      R muR = muRk * (lim < c0 ? lim : c0);
-      mu_ad = mut > muR ? mut : muR;
-      const R FV = F * V;
+  for (int k0 = 0; k0 < nr; k0 += 4) {
+    // four list entries per load, their four records gathered together
+    const uint4 q4 = list_chunk(Lst, k0 >> 2);
+    const uint32_t j4[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
-      for (int p = 0; p < D; ++p)
-#pragma unroll
-        for (int q = 0; q < D; ++q) G[p][q] += vij[p] * d[q] * FV;
-      const R Dk_j = nu_l + nut_j * (R)(1.0 / kSigK), De_j = nu_l + nut_j * (R)(1.0 / kSigE);
-      dk += rho0 * Ex<R>::div((R)2 * Dk_i * Dk_j, Dk_i + Dk_j) * (k_i - k_j) * f;
-      de += rho0 * Ex<R>::div((R)2 * De_i * De_j, De_i + De_j) * (e_i - e_j) * f;
+    for (int c = 0; c < 4; ++c) {
+      if (k0 + c >= nr) break;
+      const uint32_t j = j4[c];
+      const V4<R> B0 = pk.adv[RA * (size_t)j], B1 = pk.adv[RA * (size_t)j + 1];
+      V4<R> B2 = B1;
+      if (D == 3 && rans) B2 = pk.adv[RA * (size_t)j + 2];
+      R d[3];
+      const R rr = pair_vec<R, D, PER>(g, A0, B0, d);
+      R r;
+      Ex<R>::len(rr, r);
+      const R F = kernel_F(g, r);  // dW/dr / r
+      const R V = vol<R, D>(B0);
+      if (!mirror || !(local0<R, D>(mo, mn, B0.x, B0.y, B0.z) < (R)0)) sym_add_outer<R, D>(A, d, -F * V);
+      const R vj[3] = {D == 2 ? B0.w : B1.x, D == 2 ? B1.x : B1.y, D == 2 ? (R)0 : B1.z};
+      const R vij[3] = {vi[0] - vj[0], vi[1] - vj[1], vi[2] - vj[2]};
+      const R f = Ex<R>::div(F * r, r + g.reg) * V;  // dW/dr / (r + 0.01h) V
+      R mu_ad = mu_i;                                // laminar: harmonic mean of equal values
+      if (rans) {
+        const R k_j = D == 2 ? B1.y : B1.w, e_j = D == 2 ? B1.z : B2.x, nut_j = D == 2 ? B1.w : B2.y;
+        const R mu_j = rho0 * (nu_l + nut_j);
+        const R mut = Ex<R>::div((R)2 * mu_i * mu_j, mu_i + mu_j);
+        R ve = -(vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2]) * Ex<R>::div((R)1, r);
+        R lim = eta * (ve > (R)0 ? ve : (R)0);
+        R muR = muRk * (lim < c0 ? lim : c0);
+        mu_ad = mut > muR ? mut : muR;
+        const R FV = F * V;
+  #pragma unroll
+        for (int p = 0; p < D; ++p)
+  #pragma unroll
+          for (int q = 0; q < D; ++q) G[p][q] += vij[p] * d[q] * FV;
+        const R Dk_j = nu_l + nut_j * (R)(1.0 / kSigK), De_j = nu_l + nut_j * (R)(1.0 / kSigE);
+        dk += rho0 * Ex<R>::div((R)2 * Dk_i * Dk_j, Dk_i + Dk_j) * (k_i - k_j) * f;
+        de += rho0 * Ex<R>::div((R)2 * De_i * De_j, De_i + De_j) * (e_i - e_j) * f;
+      }
+  #pragma unroll
+      for (int c = 0; c < D; ++c) sv[c] += mu_ad * f * vij[c];
     }
-#pragma unroll
-    for (int c = 0; c < D; ++c) sv[c] += mu_ad * f * vij[c];
   }
 
   // wall dummies
   for (int kk = nr; kk < nr + nw; ++kk) {
-    const uint32_t w = Lst[(size_t)kk * LS];
+    const uint32_t w = list_at(Lst, kk);
     const V4<R> Wp = pk.WP[w];
     R d[3];
     const R rr = pair_vec<R, D, PER>(g, A0, Wp, d);
@@ -352,7 +356,6 @@ __device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, 
   if (a.sub >= I.n_ac) return;
   const Geo<R> g = make_geo<R, D>(I);
   const uint32_t *__restrict__ Lst = list_of(a.nl, i);
-  const size_t LS = kListTile;
   const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
   const bool rans = I.rans != 0;
   const R rho0 = sweep_const<R>(I).rho0, inv_c0sq = sweep_const<R>(I).inv_c0sq;
@@ -367,38 +370,44 @@ __device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, 
   const R pe_i = rans ? p_eff(p_i, kw_i, rho0, inv_c0sq) : p_i;
 
   R S1[3] = {0, 0, 0}, Cb[3] = {0, 0, 0}, S2[3] = {0, 0, 0}, Ct[3] = {0, 0, 0};
-#pragma unroll 4
-  for (int kk = 0; kk < nr; ++kk) {
-    const uint32_t j = Lst[(size_t)kk * LS];
-    const V4<R> N0 = pk.mom[RM * (size_t)j], N1 = pk.mom[RM * (size_t)j + 1];
-    V4<R> N2 = N1;
-    if (D == 3) N2 = pk.mom[RM * (size_t)j + 2];
-    R d[3];
-    const R rr = pair_vec<R, D, PER>(g, M0, N0, d);
-    R r;
-    Ex<R>::len(rr, r);
-    const R FV = kernel_F(g, r) * vol<R, D>(N0);       // V_j dW/dr / r
-    const R gw[3] = {FV * d[0], FV * d[1], FV * d[2]};  // V_j grad_i W_ij
-    R Bj[6], kw_j, p_j = N0.w;
-    const bool own = mom_B<R, D>(N1, N2, Bj, kw_j, p_j);
-    const R pe_j = rans ? p_eff(p_j, kw_j, rho0, inv_c0sq) : p_j;
-    if (own) {
-      R bg[3];
-      sym_matvec<R, D>(Bj, gw, bg);
+  for (int k0 = 0; k0 < nr; k0 += 4) {
+    // four list entries per load, their four records gathered together
+    const uint4 q4 = list_chunk(Lst, k0 >> 2);
+    const uint32_t j4[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
-      for (int c = 0; c < D; ++c) S1[c] += bg[c];
-    } else {
-#pragma unroll
-      for (int c = 0; c < D; ++c) Cb[c] += gw[c];  // pressure-buffer neighbour: B^_j = B_i
-    }
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      S2[c] += pe_j * gw[c];
-      Ct[c] += gw[c];
+    for (int c = 0; c < 4; ++c) {
+      if (k0 + c >= nr) break;
+      const uint32_t j = j4[c];
+      const V4<R> N0 = pk.mom[RM * (size_t)j], N1 = pk.mom[RM * (size_t)j + 1];
+      V4<R> N2 = N1;
+      if (D == 3) N2 = pk.mom[RM * (size_t)j + 2];
+      R d[3];
+      const R rr = pair_vec<R, D, PER>(g, M0, N0, d);
+      R r;
+      Ex<R>::len(rr, r);
+      const R FV = kernel_F(g, r) * vol<R, D>(N0);       // V_j dW/dr / r
+      const R gw[3] = {FV * d[0], FV * d[1], FV * d[2]};  // V_j grad_i W_ij
+      R Bj[6], kw_j, p_j = N0.w;
+      const bool own = mom_B<R, D>(N1, N2, Bj, kw_j, p_j);
+      const R pe_j = rans ? p_eff(p_j, kw_j, rho0, inv_c0sq) : p_j;
+      if (own) {
+        R bg[3];
+        sym_matvec<R, D>(Bj, gw, bg);
+  #pragma unroll
+        for (int c = 0; c < D; ++c) S1[c] += bg[c];
+      } else {
+  #pragma unroll
+        for (int c = 0; c < D; ++c) Cb[c] += gw[c];  // pressure-buffer neighbour: B^_j = B_i
+      }
+  #pragma unroll
+      for (int c = 0; c < D; ++c) {
+        S2[c] += pe_j * gw[c];
+        Ct[c] += gw[c];
+      }
     }
   }
   for (int kk = nr; kk < nr + nw; ++kk) {
-    const uint32_t w = Lst[(size_t)kk * LS];
+    const uint32_t w = list_at(Lst, kk);
     const V4<R> Wp = pk.WP[w];
     R d[3];
     const R rr = pair_vec<R, D, PER>(g, M0, Wp, d);
@@ -478,7 +487,6 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
   if (a.sub >= I.n_ac) return;
   const Geo<R> g = make_geo<R, D>(I);
   const uint32_t *__restrict__ Lst = list_of(a.nl, i);
-  const size_t LS = kListTile;
   const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
   const V4<R> C0 = pk.cont[2 * (size_t)i], C1 = pk.cont[2 * (size_t)i + 1];
   const R vi[3] = {D == 2 ? C1.x : C1.y, D == 2 ? C1.y : C1.z, D == 2 ? (R)0 : C1.w};
@@ -486,22 +494,28 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
   const R inv_rc = sweep_const<R>(I).inv_rc0;
   // drho_i / rho_i = sum_j [v_ij . r_ij / r + (p_i - p_j) / (rho0 c0)] dW/dr V_j
   R sum = 0;
-#pragma unroll 4
-  for (int kk = 0; kk < nr; ++kk) {
-    const uint32_t j = Lst[(size_t)kk * LS];
-    const V4<R> N0 = pk.cont[2 * (size_t)j], N1 = pk.cont[2 * (size_t)j + 1];
-    R d[3];
-    const R rr = pair_vec<R, D, PER>(g, C0, N0, d);
-    R r;
-    Ex<R>::len(rr, r);
-    const R FV = kernel_F(g, r) * vol<R, D>(N0);
-    const R vj[3] = {D == 2 ? N1.x : N1.y, D == 2 ? N1.y : N1.z, D == 2 ? (R)0 : N1.w};
-    const R p_j = D == 2 ? N0.w : N1.x;
-    const R vd = (vi[0] - vj[0]) * d[0] + (vi[1] - vj[1]) * d[1] + (vi[2] - vj[2]) * d[2];
-    sum += (vd + (p_i - p_j) * inv_rc * r) * FV;
+  for (int k0 = 0; k0 < nr; k0 += 4) {
+    // four list entries per load, their four records gathered together
+    const uint4 q4 = list_chunk(Lst, k0 >> 2);
+    const uint32_t j4[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (k0 + c >= nr) break;
+      const uint32_t j = j4[c];
+      const V4<R> N0 = pk.cont[2 * (size_t)j], N1 = pk.cont[2 * (size_t)j + 1];
+      R d[3];
+      const R rr = pair_vec<R, D, PER>(g, C0, N0, d);
+      R r;
+      Ex<R>::len(rr, r);
+      const R FV = kernel_F(g, r) * vol<R, D>(N0);
+      const R vj[3] = {D == 2 ? N1.x : N1.y, D == 2 ? N1.y : N1.z, D == 2 ? (R)0 : N1.w};
+      const R p_j = D == 2 ? N0.w : N1.x;
+      const R vd = (vi[0] - vj[0]) * d[0] + (vi[1] - vj[1]) * d[1] + (vi[2] - vj[2]) * d[2];
+      sum += (vd + (p_i - p_j) * inv_rc * r) * FV;
+    }
   }
   for (int kk = nr; kk < nr + nw; ++kk) {
-    const uint32_t w = Lst[(size_t)kk * LS];
+    const uint32_t w = list_at(Lst, kk);
     const V4<R> Wp = pk.WP[w];
     R d[3];
     const R rr = pair_vec<R, D, PER>(g, C0, Wp, d);
