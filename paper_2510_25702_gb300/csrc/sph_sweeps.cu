@@ -50,6 +50,9 @@ __device__ __forceinline__ int list_one(const SweepArgs &a, const Packs<R> &pk, 
   uint32_t *__restrict__ out = list_of(a.nl, i);
   const int K = a.nl.kmax;
   int nr = 0, nw = 0;
+  // entries are collected four at a time and stored as one 16-byte chunk
+  uint4 buf = make_uint4(0u, 0u, 0u, 0u);
+  uint4 *__restrict__ out4 = reinterpret_cast<uint4 *>(out);
   // real neighbours, then wall dummies; 0 < |r|^2 < (2h)^2 excludes i itself
   for (int set = 0; set < 2; ++set) {
     const uint32_t *offs = set == 0 ? a.off : a.woff;
@@ -58,13 +61,28 @@ __device__ __forceinline__ int list_one(const SweepArgs &a, const Packs<R> &pk, 
     visit_cells<D, PER>(I, cx, cy, cz, 1, offs, [&](uint32_t jb, uint32_t je) {
       scan_range<R, D, PER>(g, Pi, recs, stride, jb, je, [&](uint32_t j) {
         const int k = nr + nw;
-        if (k < K) out[list_off(k)] = j;
+        buf.x = buf.y;
+        buf.y = buf.z;
+        buf.z = buf.w;
+        buf.w = j;
+        if ((k & 3) == 3 && k < K) out4[(size_t)(k >> 2) * kListTile] = buf;
         if (set == 0)
           ++nr;
         else
           ++nw;
       });
     });
+  }
+  {
+    // the last, partly filled chunk: its r entries are the newest in buf
+    const int tot = nr + nw, r = tot & 3;
+    if (r && tot <= K) {
+      uint4 c = buf;
+      if (r == 1) c = make_uint4(buf.w, 0u, 0u, 0u);
+      if (r == 2) c = make_uint4(buf.z, buf.w, 0u, 0u);
+      if (r == 3) c = make_uint4(buf.y, buf.z, buf.w, 0u);
+      out4[(size_t)(tot >> 2) * kListTile] = c;
+    }
   }
   if (nr + nw > K) {  // more neighbours than the list holds
     set_status(a.status, SPH_ERR_CAPACITY);
@@ -309,12 +327,14 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
     const R Gk = nut_i * prod - (R)(2.0 / 3.0) * k_i * tr;
     const R dkdt = Gk - e_i + (R)2 * dk * inv_rho;
     const R dedt = (R)kC1 * e_i * inv_k * Gk - (R)kC2 * e_i * e_i * inv_k + (R)2 * de * inv_rho;
-    double k1 = m.k[i] + I.dt_ad * (double)dkdt, e1 = m.eps[i] + I.dt_ad * (double)dedt;
-    k1 = k1 > kFloor ? k1 : kFloor;
-    e1 = e1 > kFloor ? e1 : kFloor;
-    m.k[i] = k1;
-    m.eps[i] = e1;
-    const R k1r = (R)k1, e1r = (R)e1;
+    // explicit update over dt_ad in the sweep precision (k, eps are not
+    // among the FP64-integrated fields; in the FP64 form this is FP64)
+    const R dta = (R)I.dt_ad;
+    R k1r = k_i + dta * dkdt, e1r = e_i + dta * dedt;
+    k1r = k1r > (R)kFloor ? k1r : (R)kFloor;
+    e1r = e1r > (R)kFloor ? e1r : (R)kFloor;
+    m.k[i] = (double)k1r;
+    m.eps[i] = (double)e1r;
     m.nut[i] = (double)Ex<R>::div((R)kCmu * k1r * k1r, e1r);
     kw = (R)(2.0 / 3.0) * k1r;
   } else if (rans) {
