@@ -497,7 +497,8 @@ __global__ void k_adj_cont(AdjArgs a, int s) {
       const int j = (int)list_at(L, kk);
       const CRec cj = get_c<D>(a.rc, j);
       double d[3];
-      const double r = sqrt(pvec<D, PER>(g, ci.x, cj.x, d));
+      const double rr_ = pvec<D, PER>(g, ci.x, cj.x, d);
+      const double ir = rsqrt(rr_), r = rr_ * ir;
       double F, Fr;
       kernel_FF(g, r, F, Fr);
       const double vv[3] = {ci.v[0] - cj.v[0], ci.v[1] - cj.v[1], ci.v[2] - cj.v[2]};
@@ -510,8 +511,8 @@ __global__ void k_adj_cont(AdjArgs a, int s) {
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         lvi[c] += (lsi * cj.V + lsj * ci.V) * F * d[c];
-        lxi[c] += lsi * cj.V * (F * vv[c] + br * Fr * d[c] / r + dp * kap * F * d[c] / r) +
-                  lsj * ci.V * (F * vv[c] + br2 * Fr * d[c] / r - dp * kap * F * d[c] / r);
+        lxi[c] += lsi * cj.V * (F * vv[c] + br * Fr * d[c] * ir + dp * kap * F * d[c] * ir) +
+                  lsj * ci.V * (F * vv[c] + br2 * Fr * d[c] * ir - dp * kap * F * d[c] * ir);
       }
       lpi += (lsi * cj.V - lsj * ci.V) * kap * r * F;
       lVi += lsj * br2 * F;
@@ -520,7 +521,8 @@ __global__ void k_adj_cont(AdjArgs a, int s) {
       const int w = (int)list_at(L, kk);
       const double xw[3] = {a.wx[0][w], a.wx[1][w], a.wx[2][w]};
       double d[3];
-      const double r = sqrt(pvec<D, PER>(g, ci.x, xw, d));
+      const double rr_ = pvec<D, PER>(g, ci.x, xw, d);
+      const double ir = rsqrt(rr_), r = rr_ * ir;
       double F, Fr;
       kernel_FF(g, r, F, Fr);
       const V4<double> Wv = a.WV[w];
@@ -528,7 +530,7 @@ __global__ void k_adj_cont(AdjArgs a, int s) {
       const double vd = dot3(vv, d), Vw = I.Vw;
       for (int c = 0; c < D; ++c) {
         lvi[c] += lsi * 2.0 * F * Vw * d[c];
-        lxi[c] += lsi * 2.0 * Vw * (F * vv[c] + vd * Fr * d[c] / r);
+        lxi[c] += lsi * 2.0 * Vw * (F * vv[c] + vd * Fr * d[c] * ir);
       }
     }
     for (int c = 0; c < D; ++c) {
@@ -645,7 +647,8 @@ __global__ void k_adj_mom(AdjArgs a, int s) {
       const MRec mj = get_m<D>(a.rm, j);
       const SRec sj = get_s<D>(a.rs, j);
       double d[3];
-      const double r = sqrt(pvec<D, PER>(g, mi.x, mj.x, d));
+      const double rr_ = pvec<D, PER>(g, mi.x, mj.x, d);
+      const double ir = rsqrt(rr_), r = rr_ * ir;
       double F, Fr;
       kernel_FF(g, r, F, Fr);
       // own term: L = G . gw, gw = V_j F d
@@ -675,13 +678,14 @@ __global__ void k_adj_mom(AdjArgs a, int s) {
       lpe += a2g;
       lVi += -F * Gpd;
       for (int c = 0; c < D; ++c)
-        lxi[c] += mj.V * (F * Gv[c] + Gd * Fr * d[c] / r) - mi.V * (F * Gp[c] + Gpd * Fr * d[c] / r);
+        lxi[c] += mj.V * (F * Gv[c] + Gd * Fr * d[c] * ir) - mi.V * (F * Gp[c] + Gpd * Fr * d[c] * ir);
     }
     for (int kk = nr; kk < nr + nw; ++kk) {
       const int w = (int)list_at(L, kk);
       const double xw[3] = {a.wx[0][w], a.wx[1][w], a.wx[2][w]};
       double d[3];
-      const double r = sqrt(pvec<D, PER>(g, mi.x, xw, d));
+      const double rr_ = pvec<D, PER>(g, mi.x, xw, d);
+      const double ir = rsqrt(rr_), r = rr_ * ir;
       double F, Fr;
       kernel_FF(g, r, F, Fr);
       double Gv[3], Gd = 0.0, a2g = 0.0;
@@ -691,7 +695,7 @@ __global__ void k_adj_mom(AdjArgs a, int s) {
         a2g += si.a2[c] * I.Vw * F * d[c];
       }
       lpe += a2g;
-      for (int c = 0; c < D; ++c) lxi[c] += I.Vw * (F * Gv[c] + Gd * Fr * d[c] / r);
+      for (int c = 0; c < D; ++c) lxi[c] += I.Vw * (F * Gv[c] + Gd * Fr * d[c] * ir);
     }
     const double rsi = rho_s(a, s, i);
     const double kwi = I.rans ? (2.0 / 3.0) * a.m.k[i] : 0.0;
@@ -766,11 +770,11 @@ __global__ void k_adj_adv_seed(AdjArgs a) {
 
 // viscous coefficient of a pair and whether the ARD term is the active one
 __device__ __forceinline__ double visc_mu(const InstDev &I, double mu_a, double mu_b, bool harmonic,
-                                          const double vv[3], const double d[3], double r, bool &ard) {
+                                          const double vv[3], const double d[3], double ir, bool &ard) {
   ard = false;
   if (!I.rans) return mu_a;
   const double mut = harmonic ? 2.0 * mu_a * mu_b / (mu_a + mu_b) : mu_a;
-  const double ve = -dot3(vv, d) / r;
+  const double ve = -dot3(vv, d) * ir;
   const double lim = I.eta * (ve > 0.0 ? ve : 0.0);
   const double muR = I.muR_k * (lim < I.c0 ? lim : I.c0);
   if (mut > muR) return mut;
@@ -802,32 +806,34 @@ __global__ void k_adj_adv(AdjArgs a) {
       const int j = (int)list_at(L, kk);
       const ARec qj = get_a<D>(a.ra, j);
       double d[3];
-      const double r = sqrt(pvec<D, PER>(g, qi.x, qj.x, d));
+      const double rr_ = pvec<D, PER>(g, qi.x, qj.x, d);
+      const double ir = rsqrt(rr_), r = rr_ * ir;
       double F, Fr;
       kernel_FF(g, r, F, Fr);
       const double vv[3] = {qi.v[0] - qj.v[0], qi.v[1] - qj.v[1], qi.v[2] - qj.v[2]};
       bool ard;
-      const double mu = visc_mu(I, qi.mu, qj.mu, true, vv, d, r, ard);
-      const double rf = r / (r + reg), dfr = Fr * rf + F * reg / ((r + reg) * (r + reg));
+      const double mu = visc_mu(I, qi.mu, qj.mu, true, vv, d, ir, ard);
+      const double irg = 1.0 / (r + reg);
+      const double rf = r * irg, dfr = Fr * rf + F * reg * irg * irg;
       const double vd = dot3(vv, d);
       // ---- own terms (seeds of i) ----
       if (!mir_i || !(local_coord(a.buf[qi.mir], D, qj.x[0], qj.x[1], qj.x[2], 0) < 0.0)) {
         double u[3];
         sym_apply<D>(qi.L, d, u);
         const double q = dot3(d, u);
-        for (int c = 0; c < D; ++c) lxi[c] += -qj.V * (Fr * q * d[c] / r + 2.0 * F * u[c]);
+        for (int c = 0; c < D; ++c) lxi[c] += -qj.V * (Fr * q * d[c] * ir + 2.0 * F * u[c]);
       }
       {
         const double f = F * rf * qj.V, sv = dot3(qi.sg, vv);
         for (int c = 0; c < D; ++c) {
           lvi[c] += mu * f * qi.sg[c];
-          lxi[c] += mu * sv * qj.V * dfr * d[c] / r;
+          lxi[c] += mu * sv * qj.V * dfr * d[c] * ir;
         }
         if (ard) {
           const double Lm = f * sv * kR;
           for (int c = 0; c < D; ++c) {
-            lvi[c] += -Lm * d[c] / r;
-            lxi[c] += Lm * (-vv[c] / r + vd * d[c] / (r * r * r));
+            lvi[c] += -Lm * d[c] * ir;
+            lxi[c] += Lm * (-vv[c] * ir + vd * d[c] * (ir * ir * ir));
           }
         }
       }
@@ -837,20 +843,20 @@ __global__ void k_adj_adv(AdjArgs a) {
         sym_apply<D>(qj.L, d, u);
         const double q = dot3(d, u);
         lVi += -F * q;
-        for (int c = 0; c < D; ++c) lxi[c] += -qi.V * (Fr * q * d[c] / r + 2.0 * F * u[c]);
+        for (int c = 0; c < D; ++c) lxi[c] += -qi.V * (Fr * q * d[c] * ir + 2.0 * F * u[c]);
       }
       {
         const double fp = F * rf * qi.V, svp = -dot3(qj.sg, vv);  // v_ji = -v_ij
         for (int c = 0; c < D; ++c) {
           lvi[c] += -mu * fp * qj.sg[c];
-          lxi[c] += mu * svp * qi.V * dfr * d[c] / r;
+          lxi[c] += mu * svp * qi.V * dfr * d[c] * ir;
         }
         lVi += mu * F * rf * svp;
         if (ard) {
           const double Lm = fp * svp * kR;
           for (int c = 0; c < D; ++c) {
-            lvi[c] += -Lm * d[c] / r;
-            lxi[c] += Lm * (-vv[c] / r + vd * d[c] / (r * r * r));
+            lvi[c] += -Lm * d[c] * ir;
+            lxi[c] += Lm * (-vv[c] * ir + vd * d[c] * (ir * ir * ir));
           }
         }
       }
@@ -859,7 +865,8 @@ __global__ void k_adj_adv(AdjArgs a) {
       const int w = (int)list_at(L, kk);
       const double xw[3] = {a.wx[0][w], a.wx[1][w], a.wx[2][w]};
       double d[3];
-      const double r = sqrt(pvec<D, PER>(g, qi.x, xw, d));
+      const double rr_ = pvec<D, PER>(g, qi.x, xw, d);
+      const double ir = rsqrt(rr_), r = rr_ * ir;
       double F, Fr;
       kernel_FF(g, r, F, Fr);
       const double Vw = I.Vw;
@@ -867,23 +874,24 @@ __global__ void k_adj_adv(AdjArgs a) {
         double u[3];
         sym_apply<D>(qi.L, d, u);
         const double q = dot3(d, u);
-        for (int c = 0; c < D; ++c) lxi[c] += -Vw * (Fr * q * d[c] / r + 2.0 * F * u[c]);
+        for (int c = 0; c < D; ++c) lxi[c] += -Vw * (Fr * q * d[c] * ir + 2.0 * F * u[c]);
       }
       const V4<double> Wv = a.WV[w];
       const double vv[3] = {2.0 * (qi.v[0] - Wv.x), 2.0 * (qi.v[1] - Wv.y), 2.0 * (qi.v[2] - Wv.z)};
       bool ard;
-      const double mu = visc_mu(I, qi.mu, qi.mu, false, vv, d, r, ard);
-      const double rf = r / (r + reg), dfr = Fr * rf + F * reg / ((r + reg) * (r + reg));
+      const double mu = visc_mu(I, qi.mu, qi.mu, false, vv, d, ir, ard);
+      const double irg = 1.0 / (r + reg);
+      const double rf = r * irg, dfr = Fr * rf + F * reg * irg * irg;
       const double f = F * rf * Vw, sv = dot3(qi.sg, vv), vd = dot3(vv, d);
       for (int c = 0; c < D; ++c) {
         lvi[c] += 2.0 * mu * f * qi.sg[c];
-        lxi[c] += mu * sv * Vw * dfr * d[c] / r;
+        lxi[c] += mu * sv * Vw * dfr * d[c] * ir;
       }
       if (ard) {
         const double Lm = f * sv * kR;
         for (int c = 0; c < D; ++c) {
-          lvi[c] += -2.0 * Lm * d[c] / r;
-          lxi[c] += Lm * (-vv[c] / r + vd * d[c] / (r * r * r));
+          lvi[c] += -2.0 * Lm * d[c] * ir;
+          lxi[c] += Lm * (-vv[c] * ir + vd * d[c] * (ir * ir * ir));
         }
       }
     }
@@ -919,7 +927,7 @@ __global__ void k_adj_adv(AdjArgs a) {
               rr += dd[c] * dd[c];
             }
             if (!(rr > 0.0 && rr < g.cut2)) continue;
-            const double r = sqrt(rr);
+            const double ir = rsqrt(rr), r = rr * ir;
             double F, Fr;
             kernel_FF(g, r, F, Fr);
             double u[3];
@@ -927,7 +935,7 @@ __global__ void k_adj_adv(AdjArgs a) {
             const double q = dot3(dd, u);
             double gd[3] = {0, 0, 0};
             for (int c = 0; c < D; ++c) {
-              gd[c] = -Vk * (Fr * q * dd[c] / r + 2.0 * F * u[c]);
+              gd[c] = -Vk * (Fr * q * dd[c] * ir + 2.0 * F * u[c]);
               lxi[c] += gd[c];
             }
             if (set == 0) {
