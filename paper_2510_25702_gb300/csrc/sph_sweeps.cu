@@ -390,9 +390,12 @@ __device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, 
   const R pe_i = rans ? p_eff(p_i, kw_i, rho0, inv_c0sq) : p_i;
 
   R S1[3] = {0, 0, 0}, Cb[3] = {0, 0, 0}, S2[3] = {0, 0, 0}, Ct[3] = {0, 0, 0};
+  // four list entries per load, their four records gathered together; the
+  // next chunk is requested before this one is processed
+  uint4 nxt = nr > 0 ? list_chunk(Lst, 0) : make_uint4(0u, 0u, 0u, 0u);
   for (int k0 = 0; k0 < nr; k0 += 4) {
-    // four list entries per load, their four records gathered together
-    const uint4 q4 = list_chunk(Lst, k0 >> 2);
+    const uint4 q4 = nxt;
+    if (k0 + 4 < nr) nxt = list_chunk(Lst, (k0 >> 2) + 1);
     const uint32_t j4[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -514,9 +517,12 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
   const R inv_rc = sweep_const<R>(I).inv_rc0;
   // drho_i / rho_i = sum_j [v_ij . r_ij / r + (p_i - p_j) / (rho0 c0)] dW/dr V_j
   R sum = 0;
+  // four list entries per load, their four records gathered together; the
+  // next chunk is requested before this one is processed
+  uint4 nxt = nr > 0 ? list_chunk(Lst, 0) : make_uint4(0u, 0u, 0u, 0u);
   for (int k0 = 0; k0 < nr; k0 += 4) {
-    // four list entries per load, their four records gathered together
-    const uint4 q4 = list_chunk(Lst, k0 >> 2);
+    const uint4 q4 = nxt;
+    if (k0 + 4 < nr) nxt = list_chunk(Lst, (k0 >> 2) + 1);
     const uint32_t j4[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
