@@ -337,6 +337,8 @@ static int build_inst(const sph_config &c, InstDev &I, std::string &why) {
   I.c0sq = c.c0 * c.c0;
   fill_sweep_const(I, I.kf);
   fill_sweep_const(I, I.kd);
+  for (int a = 0; a < 3; ++a) I.lo_f[a] = (float)I.lo[a];
+  I.inv_cs_f = (float)I.inv_cs;
   I.n_ac = 1;
   return 0;
 }
@@ -863,6 +865,20 @@ int sph_add_buffer(sph_ctx *c, int32_t instance, const sph_buffer_desc *b, int32
   d.eps_in = b->eps_in;
   d.nut_in = (b->eps_in > 0) ? kCmu * b->k_in * b->k_in / b->eps_in : 0.0;
   d.gen_line = b->length + 0.5 * cfg.dp;
+  {
+    // FP32 bounding sphere: centre of the box and its half diagonal, widened
+    // by far more than the FP32 rounding of coordinates and of the test
+    double cen[3], hd2 = 0.25 * b->length * b->length + b->half[0] * b->half[0];
+    if (I.dim == 3) hd2 += b->half[1] * b->half[1];
+    double cabs = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      cen[a] = b->origin[a] + 0.5 * b->length * b->frame[a];
+      d.cen[a] = (float)cen[a];
+      cabs = std::max(cabs, std::fabs(cen[a]));
+    }
+    const double rad = std::sqrt(hd2) + 1e-5 * (cabs + std::sqrt(hd2)) + 1e-3 * cfg.dp;
+    d.rad2 = (float)(rad * rad * (1.0 + 1e-5));
+  }
   for (int q = 0; q < b->n_theta; ++q) d.theta[q] = b->theta[q];
   c->bufs[instance].push_back(d);
   if (out_id) *out_id = d.local_id;

@@ -62,6 +62,7 @@ struct InstDev {
   double c0sq;     // c0^2: p = c0^2 (rho - rho0), the stiff EOS of Sec. 2.1
   SweepConst<float> kf;
   SweepConst<double> kd;
+  float lo_f[3], inv_cs_f;  // FP32 copies for the cell-index prefilter
   // written every advection step by the time-step kernel
   double dt_ad, dt_ac, dt, t;
   int32_t n_ac;
@@ -87,6 +88,9 @@ struct BufDev {
   double length, half[2];
   double p_ob, rho_ob, noise, k_in, eps_in, nut_in;
   double gen_line;  // length + 0.5 dp (Sec. 3.1)
+  // FP32 bounding sphere of the box, widened for FP32 rounding (a point
+  // outside it is outside the box; inside it the exact test decides)
+  float cen[3], rad2;
   double theta[SPH_MAX_THETA];
 };
 
@@ -178,10 +182,24 @@ __device__ __forceinline__ int32_t cell_coord(const InstDev &I, double x, int a)
   return (int32_t)f;
 }
 
+// the same cell index from an FP32 estimate of (x - lo) / (2h) where that
+// estimate lies farther from a cell boundary than its rounding error can
+// reach (then both floors agree); the exact FP64 path otherwise.  The bound
+// adds the FP32 roundings of x, lo, their difference, 1/(2h) and the
+// product, with a factor 2 to spare.
+__device__ __forceinline__ int32_t cell_coord_fast(const InstDev &I, double x, int a) {
+  const float xf = (float)x, lof = I.lo_f[a], ics = I.inv_cs_f;
+  const float q = (xf - lof) * ics;
+  const float fq = floorf(q), fr = q - fq;
+  const float err = (fabsf(xf) + fabsf(lof)) * 1.2e-7f * ics + fabsf(q) * 4.8e-7f + 1e-6f;
+  if (q >= 0.0f && q < (float)I.nc[a] && fr > err && fr < 1.0f - err) return (int32_t)fq;
+  return cell_coord(I, x, a);
+}
+
 __device__ __forceinline__ uint32_t cell_key(const InstDev &I, double x, double y, double z) {
-  uint32_t cx = (uint32_t)cell_coord(I, x, 0);
-  uint32_t cy = (uint32_t)cell_coord(I, y, 1);
-  uint32_t cz = I.dim == 3 ? (uint32_t)cell_coord(I, z, 2) : 0u;
+  uint32_t cx = (uint32_t)cell_coord_fast(I, x, 0);
+  uint32_t cy = (uint32_t)cell_coord_fast(I, y, 1);
+  uint32_t cz = I.dim == 3 ? (uint32_t)cell_coord_fast(I, z, 2) : 0u;
   return I.cell_base + (cz * (uint32_t)I.nc[1] + cy) * (uint32_t)I.nc[0] + cx;
 }
 

@@ -75,8 +75,11 @@ __device__ __forceinline__ void permute_one(const TopoArgs &a, const Packs<R> &p
   D.uid[t] = S.uid[s];
   D.inst[t] = (uint16_t)ii;
   int32_t lab = S.label[s];
+  const float xf = (float)x, yf = (float)y, zf = (float)z;
   for (int b = 0; b < I.nbuf; ++b) {
     const BufDev &B = a.buf[I.buf0 + b];
+    const float ex = xf - B.cen[0], ey = yf - B.cen[1], ez = zf - B.cen[2];
+    if (ex * ex + ey * ey + ez * ez > B.rad2) continue;  // far from the box
     if (box_contains(B, I.dim, x, y, z)) lab = B.local_id + 1;
   }
   D.label[t] = lab;
@@ -90,10 +93,17 @@ __device__ __forceinline__ void permute_one(const TopoArgs &a, const Packs<R> &p
     pk.adv[3 * (size_t)t + 1] = V4<R>{(R)vx, (R)vy, (R)vz, (R)k};
     pk.adv[3 * (size_t)t + 2] = V4<R>{(R)eps, (R)nut, (R)0, (R)0};
   }
-  // |v|^2 with the plain left-to-right sum, nu_t
-  double v2 = dmul(vx, vx);
-  v2 = dadd(v2, dmul(vy, vy));
-  if (I.dim == 3) v2 = dadd(v2, dmul(vz, vz));
+  // |v|^2 with the plain left-to-right sum (in the sweep precision: the
+  // FP64 form keeps the exact FP64 maximum), nu_t
+  double v2;
+  if (sizeof(R) == 8) {
+    v2 = dmul(vx, vx);
+    v2 = dadd(v2, dmul(vy, vy));
+    if (I.dim == 3) v2 = dadd(v2, dmul(vz, vz));
+  } else {
+    const float fx = (float)vx, fy = (float)vy, fz = (float)vz;
+    v2 = (double)(fx * fx + fy * fy + (I.dim == 3 ? fz * fz : 0.0f));
+  }
   if (ii == s_ii) {
     atomicMax(s_v2, (unsigned long long)__double_as_longlong(v2));
     if (I.rans) atomicMax(s_nu, (unsigned long long)__double_as_longlong(nut));
