@@ -415,17 +415,16 @@ def main():
     eager = {"value": 0.5 * (e0["n"] + e1["n"]) * args.steps / (e_ms * 1e-3), "ms_per_step": e_ms / args.steps}
     log(f"profiled pass {e_ms:.1f} ms")
 
-    # dominant kernel and its roofline.  Momentum and continuity launch once
-    # per possible sub-step and exit at once beyond the step's count, so
-    # their work per step is n_ac passes over the particles; the time per
-    # processing launch is the stage's time per step over n_ac
+    # dominant kernel and its roofline.  The momentum and continuity stages
+    # time the first acoustic sub-step (one launch per step each); later
+    # sub-steps run in one cooperative launch of their own (stage
+    # later_sub_steps), so each stage is one pass over the particles per step
     dom = max(("advection_sweep", "momentum_sweep", "continuity_sweep"), key=lambda s: stages[s][0])
     dom_ms, dom_n = stages[dom]
     R = 4 if args.precision == "fp32" else 8
     per_particle = algorithmic_bytes(dom, wdim, R, wrans)
     nbar = 0.5 * (n0 + n1)
-    passes = max(1, int(e1["n_ac"])) if dom != "advection_sweep" else 1
-    launch_ms = dom_ms / args.steps / passes
+    launch_ms = dom_ms / args.steps
     achieved = per_particle * nbar / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
 
@@ -490,7 +489,7 @@ def main():
                          "traffic": NCU_TRAFFIC.get((dom, args.workload, csrc_hash())),
                          "csrc": csrc_hash(),
                          "bytes_per_particle": per_particle, "avg_launch_ms": launch_ms,
-                         "launch_time": "per processing launch: stage time per step / sub-steps"},
+                         "launch_time": "stage time per step (one launch per step)"},
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "stage_timing": "CUDA events around each stage in a second pass of the same K steps launched "
                             "kernel by kernel (value comes from graph replay)",

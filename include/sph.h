@@ -225,12 +225,15 @@ int sph_get_stats(sph_ctx *ctx, sph_stats *out);
 /* Stage timing (tracing aid, no counterpart in the paper).  While enabled,
    sph_step brackets every kernel stage with CUDA events on the context's
    stream and accumulates, per stage, the summed event time (ms) and the
-   number of launches.  Stages: 0 sort, 1 cells, 2 permute, 3 time step,
-   4 advection sweep, 5 momentum sweep, 6 continuity sweep, 7 buffer update,
+   number of launches.  Stages: 0 sort (with the live count), 1 cells (empty:
+   the permute writes the cell offsets), 2 permute, 3 time step (empty when
+   stepping: the neighbour-list launch takes it), 4 advection sweep,
+   5 momentum sweep, 6 continuity sweep (both: sub-step 1), 7 buffer update,
    8 neighbour list (built once per advection step, before the advection
-   sweep).  enable = 0 stops timing; enable = 2 also clears the totals.
+   sweep), 9 later sub-steps (momentum and continuity of sub-steps 2 ..
+   n_ac in one launch, which ends at once when no instance takes them).  enable = 0 stops timing; enable = 2 also clears the totals.
    sph_get_stage_times writes up to max_stages entries. */
-#define SPH_N_STAGES 9
+#define SPH_N_STAGES 10
 int sph_set_profiling(sph_ctx *ctx, int32_t enable);
 int sph_get_stage_times(sph_ctx *ctx, double *ms_total, int64_t *launches, int32_t max_stages,
                         int32_t *n_stages);

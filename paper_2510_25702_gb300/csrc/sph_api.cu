@@ -4,8 +4,9 @@
 //
 // Per advection step, all on the context's stream and without a host round
 // trip (counts stay in device memory and kernels read them):
-//   radix sort of pending (key, index) pairs -> cell offsets -> permute
-//   (+ labels, + time-step maxima) -> time step -> advection sweep ->
+//   cell sort of pending (key, index) pairs, one cooperative launch ->
+//   permute (+ cell offsets, + labels, + time-step maxima) -> neighbour
+//   list (+ time step) -> advection sweep ->
 //   n_ac_max x (momentum sweep, continuity sweep) -> buffer update (flags,
 //   scan, spawn + recycle + keys of the next step).
 // Instances whose own sub-step count is smaller skip the surplus sub-steps
@@ -79,7 +80,9 @@ struct sph_ctx {
   int32_t *inst_spawn = nullptr;
   uint8_t *flag = nullptr;
   int32_t *block_cnt = nullptr;
-  SortTemp sort_tmp{};
+  CellSortPlan cs_plan{};
+  uint32_t *cs_scratch = nullptr;  // cell_sort_words(cs_plan) words
+  GridBarrier *gbar = nullptr;     // barrier words of the sub-step launch
   uint32_t *sorted_keys = nullptr, *sorted_vals = nullptr;
   NbrList nl{};
   // stage timing (CUDA event pairs on the context's stream)
@@ -243,6 +246,7 @@ struct sph_ctx {
     a.cnt = cnt;
     a.status = &cnt->status;
     a.sub = sub;
+    a.gbar = gbar;
     a.any_periodic = 0;
     for (const InstDev &I : inst) a.any_periodic |= I.periodic[0] | I.periodic[1] | I.periodic[2];
     return a;
@@ -638,8 +642,13 @@ int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *
     ok &= (c->nl.n_real = alloc_arr<uint16_t>(c, cap)) != nullptr;
     ok &= (c->nl.n_wall = alloc_arr<uint16_t>(c, cap)) != nullptr;
   }
-  c->sort_tmp.max_blocks = (int)((cap + 2047) / 2048) + 1;
-  ok &= (c->sort_tmp.hist = alloc_arr<uint32_t>(c, (int64_t)radix_hist_words((int)cap, c->key_bits))) != nullptr;
+  if (cell_sort_plan(c->key_bits, &c->cs_plan) != 0) {
+    c->release();
+    delete c;
+    return fail(SPH_ERR_CUDA, "device without cooperative launch (cell sort)");
+  }
+  ok &= (c->cs_scratch = alloc_arr<uint32_t>(c, (int64_t)cell_sort_words(c->cs_plan))) != nullptr;
+  ok &= (c->gbar = alloc_arr<GridBarrier>(c, 1)) != nullptr;
   ok &= (c->d_inst = alloc_arr<InstDev>(c, n_instances)) != nullptr;
   ok &= (c->d_buf = alloc_arr<BufDev>(c, (int64_t)n_instances * SPH_MAX_BUFFERS)) != nullptr;
   if (ok) ok = (c->prec == SPH_PREC_FP32) ? alloc_packs(c, c->pkf, cap, nw_total) == 0
@@ -694,6 +703,13 @@ int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *
   Counters h{};
   h.m_pending = (int32_t)n_total;
   rc |= up(c->cnt, &h, sizeof(h));
+  {
+    // grid-barrier words start at zero (each launch leaves them so)
+    std::vector<uint32_t> zw(cell_sort_words(c->cs_plan), 0u);
+    rc |= up(c->cs_scratch, zw.data(), sizeof(uint32_t) * zw.size());
+    GridBarrier gz{};
+    rc |= up(c->gbar, &gz, sizeof(gz));
+  }
   std::vector<int32_t> zi(2 * n_instances, 0);
   rc |= up(c->inst_spawn, zi.data(), sizeof(int32_t) * 2 * n_instances);
   rc |= up(c->d_inst, c->inst.data(), sizeof(InstDev) * n_instances);
@@ -731,7 +747,7 @@ void sph_destroy(sph_ctx *c) {
 const char *sph_stage_name(int32_t stage) {
   static const char *names[SPH_N_STAGES] = {"sort", "cells", "permute", "time_step",
                                             "advection_sweep", "momentum_sweep", "continuity_sweep",
-                                            "buffer_update", "neighbour_list"};
+                                            "buffer_update", "neighbour_list", "later_sub_steps"};
   return (stage >= 0 && stage < SPH_N_STAGES) ? names[stage] : "unknown";
 }
 
@@ -925,52 +941,62 @@ int sph_set_profile(sph_ctx *c, int32_t instance, int32_t buffer_id, const doubl
 // sort + cell offsets + permute (+labels, +time-step maxima)
 static void enqueue_topology(sph_ctx *c) {
   uint32_t *ks = nullptr, *vs = nullptr;
+  // one cooperative launch: sort, live count, and the zeroing of the
+  // per-instance time-step maxima (v2max and nutmax, 2 x ninst doubles) and
+  // of the sub-step count that the time step folds with atomicMax
   int ev = c->prof_begin(0);
-  radix_sort(c->K[0], c->Vv[0], c->K[1], c->Vv[1], &c->cnt->m_pending, (int)c->cap, c->key_bits, c->sort_tmp,
-             c->stream, &ks, &vs);
+  uint32_t *keys[2] = {c->K[0], c->K[1]}, *vals[2] = {c->Vv[0], c->Vv[1]};
+  cell_sort(c->cs_plan, c->cs_scratch, keys, vals, &c->cnt->m_pending, (int)c->cap, c->ncell, &c->cnt->n_live,
+            &c->cnt->status, reinterpret_cast<uint32_t *>(c->v2max), 4 * c->ninst,
+            reinterpret_cast<uint32_t *>(&c->cnt->n_ac_all), 1, c->stream, &ks, &vs);
   c->prof_end(ev);
-  ev = c->prof_begin(1);
-  cell_offsets(ks, &c->cnt->m_pending, c->ncell, c->off, &c->cnt->n_live, c->stream);
-  cudaMemsetAsync(c->v2max, 0, sizeof(unsigned long long) * 2 * c->ninst, c->stream);
-  cudaMemsetAsync(&c->cnt->n_ac_all, 0, sizeof(int32_t), c->stream);
-  c->prof_end(ev);
+  // the permute writes the cell offsets (stage 1 stays empty)
   TopoArgs t = c->topo();
   t.sorted_vals = vs;
+  t.sorted_keys = ks;
+  t.off = c->off;
   ev = c->prof_begin(2);
   launch_permute(t, (int)c->cap, c->prec, c->stream, c->packs());
   c->prof_end(ev);
   c->cur = 1 - c->cur;
   c->sorted_keys = ks;
   c->sorted_vals = vs;
-  c->launches += kSortKernelsPerPass * radix_passes(c->key_bits) + 2;
+  c->launches += 2;
 }
 
 static void enqueue_step(sph_ctx *c) {
   enqueue_topology(c);
   const int maxn = (int)c->cap;
   if (!c->kinematic) {
-    int ev = c->prof_begin(3);
-    launch_time_step(c->topo(), c->stream);
-    c->prof_end(ev);
-    ev = c->prof_begin(8);
-    launch_neighbour_list(c->sweep(0, 0), c->packs(), c->prec, c->dim, maxn, c->stream);
+    // the list builder's block 0 also takes the time step (stage 3 stays
+    // empty): one launch fewer on the step's critical path
+    SweepArgs la = c->sweep(0, 0);
+    la.ts = step_args(c->topo());
+    la.with_time_step = 1;
+    int ev = c->prof_begin(8);
+    launch_neighbour_list(la, c->packs(), c->prec, c->dim, maxn, c->stream);
     c->prof_end(ev);
     ev = c->prof_begin(4);
     launch_advection_sweep(c->sweep(0, 1), c->packs(), c->prec, c->dim, maxn, c->stream);
     c->prof_end(ev);
-    for (int s = 0; s < c->n_ac_max; ++s) {
-      ev = c->prof_begin(5);
-      launch_momentum_sweep(c->sweep(s, 2), c->packs(), c->prec, c->dim, maxn, s, c->stream);
-      c->prof_end(ev);
-      ev = c->prof_begin(6);
-      launch_continuity_sweep(c->sweep(s, 3), c->packs(), c->prec, c->dim, maxn, s, c->stream);
+    ev = c->prof_begin(5);
+    launch_momentum_sweep(c->sweep(0, 2), c->packs(), c->prec, c->dim, maxn, 0, c->stream);
+    c->prof_end(ev);
+    ev = c->prof_begin(6);
+    launch_continuity_sweep(c->sweep(0, 3), c->packs(), c->prec, c->dim, maxn, 0, c->stream);
+    c->prof_end(ev);
+    if (c->n_ac_max > 1) {
+      // sub-steps 1 .. n_ac - 1: one cooperative launch, empty when every
+      // instance takes a single sub-step
+      ev = c->prof_begin(9);
+      launch_substeps(c->sweep(1, 2), c->packs(), c->prec, c->dim, maxn, c->stream);
       c->prof_end(ev);
     }
   }
   int ev = c->prof_begin(7);
   launch_buffer_update(c->topo(), maxn, c->stream);
   c->prof_end(ev);
-  c->launches += 3 + (c->kinematic ? 0 : 3 + 2 * c->n_ac_max);
+  c->launches += 3 + (c->kinematic ? 0 : 4 + (c->n_ac_max > 1 ? 1 : 0));
   c->step += 1;
 }
 

@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include "sph.h"
+#include "sph_grid.cuh"
 
 namespace sphk {
 
@@ -255,6 +256,51 @@ __device__ __forceinline__ void set_status(int32_t *status, int32_t code) {
   atomicCAS(status, 0, code);
 }
 
+// a4 dual-criteria time step of one instance (Sec. 2.3): advection step
+// from max |v| (or U_ref) and the viscous limit with nu_l + max nu_t,
+// acoustic step from c0 + max |v|, sub-step count ceil(dt_ad / dt_ac)
+// (fixed or single-step modes override); folds the count into n_ac_all
+struct StepArgs {
+  InstDev *inst;
+  const unsigned long long *v2max, *nutmax;  // per instance, from the permute
+  Counters *cnt;
+  int32_t ninst, n_ac_max;
+};
+
+__device__ __forceinline__ void time_step_instance(const StepArgs &a, int ii) {
+  InstDev &I = a.inst[ii];
+  double v2max = __longlong_as_double((long long)a.v2max[ii]);
+  double nutmax = __longlong_as_double((long long)a.nutmax[ii]);
+  double vmax = __dsqrt_rn(v2max);
+  double u = (vmax > I.U_ref) ? vmax : I.U_ref;
+  double dt_adv = ddiv(dmul(0.25, I.h), u);
+  double nu_eff = dadd(I.nu_l, nutmax);
+  double dt_visc = ddiv(dmul(dmul(0.125, I.h), I.h), nu_eff);
+  double dt_ad = (dt_adv < dt_visc) ? dt_adv : dt_visc;
+  double dt_ac = ddiv(dmul(0.6, I.h), dadd(I.c0, vmax));
+  int n;
+  if (I.dt_mode == SPH_DT_FIXED) {
+    dt_ad = I.dt_ad_fixed;
+    n = I.n_ac_fixed;
+  } else if (I.dt_mode == SPH_DT_SINGLE) {
+    if (dt_ac < dt_ad) dt_ad = dt_ac;
+    n = 1;
+  } else {
+    double f = ceil(ddiv(dt_ad, dt_ac));
+    n = (f >= 1.0) ? (int)fmin(f, 1.0e9) : 1;
+  }
+  if (n > a.n_ac_max) {
+    set_status(&a.cnt->status, SPH_ERR_STATE);
+    n = a.n_ac_max;
+  }
+  I.dt_ad = dt_ad;
+  I.dt_ac = dt_ac;
+  I.n_ac = n;
+  I.dt = ddiv(dt_ad, (double)n);
+  I.t = dadd(I.t, dt_ad);
+  atomicMax(&a.cnt->n_ac_all, n);
+}
+
 // velocity-profile value at transverse coordinate s1 (linear in theta)
 __device__ __forceinline__ double profile_U(const BufDev &b, double s1) {
   if (b.n_theta <= 1) return b.theta[0];
@@ -304,15 +350,10 @@ __device__ __forceinline__ void apply_bc(const InstDev &I, const BufDev &b, cons
 // host-side launch wrappers implemented in the .cu files
 // ------------------------------------------------------------------------
 struct SortTemp {
-  uint32_t *hist;  // radix_hist_words(max_count, bits) words
+  uint32_t *hist;  // digit histograms [1 << digit bits][tiles] + scan chunk totals
   int max_blocks;
 };
 
-// passes and histogram words (digit histogram + scan chunk totals) of a sort
-// of up to max_count keys of the given bit length
-int radix_passes(int bits);
-size_t radix_hist_words(int max_count, int bits);
-constexpr int kSortKernelsPerPass = 4;
 
 // radix sort of (keys, vals) over *d_count entries (device count); bits of
 // key to sort; results in keys_out / vals_out.  Uses keys_tmp/vals_tmp.
@@ -323,6 +364,22 @@ void radix_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *va
 void cell_offsets(const uint32_t *keys, const int32_t *d_count, uint32_t ncell, uint32_t *off,
                   int32_t *d_nlive, cudaStream_t st);
 
+// The cell sort of the stepping path: one cooperative launch that sorts
+// (key, index) pairs stably by key, writes the count of keys below the
+// sentinel and zeroes two optional word ranges.  The plan fixes the digit
+// width, the passes and the grid (co-resident blocks); scratch holds
+// cell_sort_words(plan) words, zeroed once when allocated.
+constexpr int kCellSortBlocksPerSm = 2;
+struct CellSortPlan {
+  int rb, passes, grid;
+};
+int cell_sort_plan(int bits, CellSortPlan *plan);
+size_t cell_sort_words(const CellSortPlan &plan);
+void cell_sort(const CellSortPlan &plan, uint32_t *scratch, uint32_t *keys[2], uint32_t *vals[2],
+               const int32_t *d_count, int max_count, uint32_t sentinel, int32_t *d_below, int32_t *status,
+               uint32_t *clear0, int nclear0, uint32_t *clear1, int nclear1, cudaStream_t st,
+               uint32_t **keys_result, uint32_t **vals_result);
+
 struct TopoArgs {
   const InstDev *inst;
   const BufDev *buf;
@@ -330,6 +387,8 @@ struct TopoArgs {
   Derived der;
   uint32_t *keys, *idx;
   const uint32_t *sorted_vals;
+  const uint32_t *sorted_keys;  // permute: keys in sorted order, for the cell offsets
+  uint32_t *off;                // permute: cell offsets out (NULL: not written)
   Counters *cnt;
   unsigned long long *v2max, *nutmax;  // per instance
   uint32_t *next_uid;                  // per instance
@@ -344,6 +403,7 @@ struct TopoArgs {
 
 void launch_permute(const TopoArgs &a, int max_n, int prec, cudaStream_t st, void *packs);
 void launch_time_step(const TopoArgs &a, cudaStream_t st);
+StepArgs step_args(const TopoArgs &a);  // the time-step fields of a
 void launch_buffer_update(const TopoArgs &a, int max_n, cudaStream_t st);
 void launch_keys(const TopoArgs &a, int max_n, int all_live, cudaStream_t st);
 void launch_iota(uint32_t *idx, int max_n, cudaStream_t st);
@@ -402,6 +462,9 @@ struct SweepArgs {
   int32_t any_periodic;  // some instance has a periodic axis
   int32_t block;         // threads per block of the launch
   double *tape_S;        // optional: momentum sums S1, Cb, S2, Ct per sub-step
+  StepArgs ts;           // list builder: time step of every instance by block 0
+  int32_t with_time_step;
+  GridBarrier *gbar;     // sub-step launch: grid barrier words (zeroed once)
 };
 
 // sweeps: prec 0 -> double packs, 1 -> float packs; dim 2 / 3
@@ -412,6 +475,9 @@ void launch_momentum_sweep(const SweepArgs &a, void *packs, int prec, int dim, i
                            cudaStream_t st);
 void launch_continuity_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n, int sub,
                              cudaStream_t st);
+// acoustic sub-steps 1 .. n_ac_all - 1 (momentum, continuity) in one
+// cooperative launch that ends at once when no instance takes them
+void launch_substeps(const SweepArgs &a, void *packs, int prec, int dim, int max_n, cudaStream_t st);
 // ------------------------------------------------------------------------
 // adjoint of the step (differentiated windows, FP64 contexts)
 // ------------------------------------------------------------------------

@@ -1,10 +1,11 @@
 // sph_noalloc.cu -- cell sort of a caller's point set that allocates no
 // device memory (declared in include/sph.h as sph_cell_sort_noalloc).
 //
-// It runs the same kernels as the cell sort inside sph_step (cell keys of
-// cell size 2h, stable LSD radix sort, cell offsets), but its scratch lives
-// in one file-scope static device array instead of memory the context
-// allocates.  Callers that must not allocate -- code running while a CUDA
+// It computes what the cell sort inside sph_step computes (cell keys of
+// cell size 2h, stable LSD radix sort, cell offsets) with the multi-launch
+// radix sort of sph_sort.cu, whose launches never wait on one another, and
+// its scratch lives in one file-scope static device array instead of memory
+// the context allocates.  Callers that must not allocate -- code running while a CUDA
 // stream is being captured into a graph, or a host application whose device
 // memory is reserved up front and may not grow during a run -- can call it
 // with their own input and output buffers only.

@@ -1,6 +1,8 @@
 // sph_sort.cu -- stable LSD radix sort of (cell key, index) pairs and the
-// cell offsets of the cell-linked list (Sec. 2.4.1: the list is rebuilt
-// after deletion every advection step, Sec. 2.4.3).
+// cell offsets of the cell-linked list (Sec. 2.4.1), in launches that never
+// wait on one another: the cell sort of a caller's point set
+// (sph_cell_sort_noalloc).  The stepping path sorts with the single
+// cooperative launch of sph_cellsort.cu instead.
 //
 // Digit width RB (8..10 bits) is chosen from the key length so that keys of
 // up to 20 bits sort in two passes.  Per pass:
@@ -170,22 +172,6 @@ static int digit_bits(int bits, int *passes) {
   if (rb < 8) rb = 8;
   *passes = p;
   return rb;
-}
-
-int radix_passes(int bits) {
-  int p;
-  digit_bits(bits, &p);
-  return p;
-}
-
-size_t radix_hist_words(int max_count, int bits) {
-  int p;
-  int rb = digit_bits(bits, &p);
-  size_t nblocks = (size_t)((max_count + RS_TILE - 1) / RS_TILE);
-  if (nblocks < 1) nblocks = 1;
-  size_t total = ((size_t)1 << rb) * nblocks;
-  size_t nchunks = (total + SC_CHUNK - 1) / SC_CHUNK;
-  return total + nchunks;
 }
 
 template <int RB>

@@ -32,6 +32,10 @@
 // small fraction of the FP32 rate, so with R = float the FP64 work per
 // particle is a few adds and conversions, and divisions are the fast
 // reciprocal form.  With R = double every operation is FP64 and IEEE.
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "sph_pair.cuh"
 
 namespace sphk {
@@ -614,6 +618,10 @@ __global__ void __launch_bounds__(kMaxBlock) k_list(SweepArgs a, Packs<R> pk) {
   // advanced further: non-finite positions would all fall into one edge
   // cell and make the candidate scan quadratic
   if (a.cnt->status) return;
+  // the time step of every instance (needs the permute's maxima, which are
+  // complete when this launch starts; read first by the advection sweep)
+  if (a.with_time_step && blockIdx.x == 0)
+    for (int ii = threadIdx.x; ii < a.ts.ninst; ii += blockDim.x) time_step_instance(a.ts, ii);
   const int n = a.cnt->n_live;
   // whole blocks iterate together so that every lane of a warp takes part
   // in the reduction of the tile's longest list
@@ -659,6 +667,39 @@ __global__ void __launch_bounds__(kMaxBlock) k_cont(SweepArgs a, Packs<R> pk) {
     if ((threadIdx.x & 31) == 0 && i + step < n) prefetch_list_tile(a.nl, i + step);
     cont_one<R, D, PER>(a, pk, i);
   }
+}
+
+// Sub-steps 1 .. n_ac_all - 1 in one cooperative launch: momentum over all
+// particles, grid barrier, continuity, grid barrier, and so on.  When no
+// instance takes a second acoustic sub-step -- the usual case -- every block
+// ends at once, so the bound on sub-steps costs one empty launch instead of
+// two per surplus sub-step.  Every block reads the same n_ac_all (written by
+// the time step before this launch), so all of them take the same barriers.
+// There is no early exit on the status word here: a block could see a word
+// that another block set during the launch and leave the barriers unmatched;
+// the work after an error is bounded (fixed lists) and its result unused.
+template <typename R, int D, bool PER>
+__global__ void __launch_bounds__(kMaxBlock) k_substeps(SweepArgs a, Packs<R> pk, GridBarrier *gb) {
+  __shared__ int s_ok;
+  const int nac = a.cnt->n_ac_all;
+  if (nac <= 1) return;
+  const int n = a.cnt->n_live;
+  const int step = gridDim.x * blockDim.x;
+  uint32_t k = 0;
+  for (int s = 1; s < nac; ++s) {
+    a.sub = s;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+      if ((threadIdx.x & 31) == 0 && i + step < n) prefetch_list_tile(a.nl, i + step);
+      mom_one<R, D, PER>(a, pk, i);
+    }
+    if (!grid_sync(gb, ++k, a.status, &s_ok)) break;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+      if ((threadIdx.x & 31) == 0 && i + step < n) prefetch_list_tile(a.nl, i + step);
+      cont_one<R, D, PER>(a, pk, i);
+    }
+    if (s + 1 < nac && !grid_sync(gb, ++k, a.status, &s_ok)) break;
+  }
+  grid_leave(gb);
 }
 
 // =========================================================================
@@ -725,28 +766,50 @@ __global__ void __launch_bounds__(kBlock) k_pairs(SweepArgs a, const double *__r
 // ------------------------------------------------------------------------
 // blocks to launch: all resident blocks of the GPU at the chosen block size,
 // or fewer when the particles need fewer.  The occupancy query runs once per
-// kernel and block size (64, 128 or 256 threads).
-template <typename K>
-static int resident_grid(K kernel, int block, int max_n) {
-  static int per_gpu[3] = {0, 0, 0};
-  const int slot = block <= 64 ? 0 : (block <= 128 ? 1 : 2);
-  if (per_gpu[slot] == 0) {
-    int dev = 0, sms = 1, per_sm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
-    per_gpu[slot] = sms * (per_sm > 0 ? per_sm : 1);
-  }
-  int need = (max_n + block - 1) / block;
-  if (need < 1) need = 1;
-  return need < per_gpu[slot] ? need : per_gpu[slot];
+// device, kernel and block size (64, 128 or 256 threads).
+static int resident_blocks(const void *kernel, int block) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void *, int>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_tuple(dev, kernel, block);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int sms = 1, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
+  const int r = sms * (per_sm > 0 ? per_sm : 1);
+  cache[key] = r;
+  return r;
 }
 
-// which: 0 advection, 1 momentum, 2 continuity, 3 neighbour list
+template <typename K>
+static int resident_grid(K kernel, int block, int max_n) {
+  const int per_gpu = resident_blocks((const void *)kernel, block);
+  int need = (max_n + block - 1) / block;
+  if (need < 1) need = 1;
+  return need < per_gpu ? need : per_gpu;
+}
+
+// which: 0 advection, 1 momentum, 2 continuity, 3 neighbour list,
+// 4 sub-steps after the first (cooperative)
 template <typename R, int D, bool PER>
 static void launch_sweeps_impl(int which, const SweepArgs &a, Packs<R> &pk, int max_n, cudaStream_t st) {
   const int b = (a.block == 64 || a.block == 256) ? a.block : 128;
-  if (which == 3) {
+  if (which == 4) {
+    auto k = k_substeps<R, D, PER>;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)resident_grid(k, b, max_n));
+    cfg.blockDim = dim3((unsigned)b);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, a, pk, a.gbar);
+  } else if (which == 3) {
     auto k = k_list<R, D, PER>;
     k<<<resident_grid(k, b, max_n), b, 0, st>>>(a, pk);
   } else if (which == 0) {
@@ -806,6 +869,14 @@ void launch_continuity_sweep(const SweepArgs &a, void *packs, int prec, int dim,
     launch_sweeps<float>(2, a, packs, dim, max_n, st);
   else
     launch_sweeps<double>(2, a, packs, dim, max_n, st);
+}
+
+// sub-steps 1 .. n_ac_all - 1 (momentum and continuity) in one launch
+void launch_substeps(const SweepArgs &a, void *packs, int prec, int dim, int max_n, cudaStream_t st) {
+  if (prec == SPH_PREC_FP32)
+    launch_sweeps<float>(4, a, packs, dim, max_n, st);
+  else
+    launch_sweeps<double>(4, a, packs, dim, max_n, st);
 }
 
 void launch_debug_pairs(const SweepArgs &a, const double *wx, const double *wy, const double *wz,

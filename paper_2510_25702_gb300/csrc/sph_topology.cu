@@ -24,10 +24,31 @@ template <typename R>
 __device__ __forceinline__ void permute_one(const TopoArgs &a, const Packs<R> &pk, int t, int s_ii,
                                             unsigned long long *s_v2, unsigned long long *s_nu);
 
+// cell offsets of the sorted keys: off[c] = first slot t whose key is >= c,
+// for c in [0, sentinel]; slot t writes the cells after its predecessor's key
+// up to its own, the last live slot also the cells up to the sentinel, so
+// off[sentinel] = n (the live count)
+__device__ __forceinline__ void cell_offsets_at(const TopoArgs &a, int t, int n) {
+  if (n == 0) {
+    for (uint32_t c = (uint32_t)t; c <= a.sentinel; c += gridDim.x * blockDim.x) a.off[c] = 0u;
+    return;
+  }
+  if (t >= n) return;
+  const uint32_t key = a.sorted_keys[t];
+  const uint32_t c0 = t > 0 ? a.sorted_keys[t - 1] + 1u : 0u;
+  for (uint32_t c = c0; c <= key; ++c) a.off[c] = (uint32_t)t;
+  if (t == n - 1)
+    for (uint32_t c = key + 1u; c <= a.sentinel; ++c) a.off[c] = (uint32_t)n;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kBlock) k_permute(TopoArgs a, Packs<R> pk) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  // an earlier error (the sort's bounded waits among them) leaves the sorted
+  // order undefined: nothing after it runs
+  if (a.cnt->status) return;
   const int n = a.cnt->n_live;
+  if (a.off) cell_offsets_at(a, t, n);
   // time-step maxima are reduced in shared memory for the instance of the
   // block's first particle (particles are instance-sorted, so almost every
   // block has one) and go straight to global memory otherwise
@@ -125,44 +146,24 @@ void launch_permute(const TopoArgs &a, int max_n, int prec, cudaStream_t st, voi
 // ------------------------------------------------------------------------
 // a4 dual-criteria time step, one thread per instance
 // ------------------------------------------------------------------------
-__global__ void k_time_step(TopoArgs a) {
+__global__ void k_time_step(StepArgs a) {
   const int ii = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ii >= a.ninst) return;
-  InstDev &I = const_cast<InstDev &>(a.inst[ii]);
-  double v2max = __longlong_as_double((long long)a.v2max[ii]);
-  double nutmax = __longlong_as_double((long long)a.nutmax[ii]);
-  double vmax = __dsqrt_rn(v2max);
-  double u = (vmax > I.U_ref) ? vmax : I.U_ref;
-  double dt_adv = ddiv(dmul(0.25, I.h), u);
-  double nu_eff = dadd(I.nu_l, nutmax);
-  double dt_visc = ddiv(dmul(dmul(0.125, I.h), I.h), nu_eff);
-  double dt_ad = (dt_adv < dt_visc) ? dt_adv : dt_visc;
-  double dt_ac = ddiv(dmul(0.6, I.h), dadd(I.c0, vmax));
-  int n;
-  if (I.dt_mode == SPH_DT_FIXED) {
-    dt_ad = I.dt_ad_fixed;
-    n = I.n_ac_fixed;
-  } else if (I.dt_mode == SPH_DT_SINGLE) {
-    if (dt_ac < dt_ad) dt_ad = dt_ac;
-    n = 1;
-  } else {
-    double f = ceil(ddiv(dt_ad, dt_ac));
-    n = (f >= 1.0) ? (int)fmin(f, 1.0e9) : 1;
-  }
-  if (n > a.n_ac_max) {
-    set_status(&a.cnt->status, SPH_ERR_STATE);
-    n = a.n_ac_max;
-  }
-  I.dt_ad = dt_ad;
-  I.dt_ac = dt_ac;
-  I.n_ac = n;
-  I.dt = ddiv(dt_ad, (double)n);
-  I.t = dadd(I.t, dt_ad);
-  atomicMax(&a.cnt->n_ac_all, n);
+  if (ii < a.ninst) time_step_instance(a, ii);
+}
+
+StepArgs step_args(const TopoArgs &a) {
+  StepArgs s{};
+  s.inst = const_cast<InstDev *>(a.inst);
+  s.v2max = a.v2max;
+  s.nutmax = a.nutmax;
+  s.cnt = a.cnt;
+  s.ninst = a.ninst;
+  s.n_ac_max = a.n_ac_max;
+  return s;
 }
 
 void launch_time_step(const TopoArgs &a, cudaStream_t st) {
-  k_time_step<<<(a.ninst + 63) / 64, 64, 0, st>>>(a);
+  k_time_step<<<(a.ninst + 63) / 64, 64, 0, st>>>(step_args(a));
 }
 
 // ------------------------------------------------------------------------

@@ -104,7 +104,7 @@ EXPORTS = ("sph_create", "sph_add_buffer", "sph_set_profile", "sph_step", "sph_r
            "sph_save_state", "sph_restore_state", "sph_drop_state", "sph_adjoint_forward",
            "sph_adjoint_backward", "sph_adjoint_release")
 NOALLOC_MAX_POINTS = 1 << 19
-N_STAGES = 9
+N_STAGES = 10
 
 
 def library_path() -> str:
