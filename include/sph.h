@@ -329,6 +329,16 @@ int sph_adjoint_release(sph_ctx *ctx);
    Test and debug aid; re-sorts the particles by cell. */
 int sph_debug_pairs(sph_ctx *ctx, int64_t *out, int64_t max, int64_t *count);
 
+/* Test aid (no counterpart in the paper): the binary64 -> binary32 and
+   binary32 -> binary64 conversions that the FP32 form performs with integer
+   operations instead of the conversion instructions (which issue on the
+   FP64 pipe), applied to n values in host memory: out32[k] = in64[k]
+   rounded to nearest, ties to even; out64[k] = in32[k] exactly.  Either
+   direction may be skipped with a NULL input.  Uses temporary device
+   buffers.  Errors: SPH_ERR_ARG (n outside 0..2^24, missing output),
+   SPH_ERR_ALLOC, SPH_ERR_CUDA. */
+int sph_debug_convert(const double *in64, float *out32, const float *in32, double *out64, int64_t n);
+
 /* Cell sort of a caller's point set that allocates no device memory.  The
    paper has no counterpart: this exists for callers that cannot allocate,
    such as code running while a CUDA stream is being captured into a graph,

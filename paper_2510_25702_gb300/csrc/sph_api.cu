@@ -1898,3 +1898,40 @@ int sph_debug_pairs(sph_ctx *c, int64_t *out, int64_t max, int64_t *count) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// test aid: the integer-pipe binary64 <-> binary32 conversions
+// ------------------------------------------------------------------------
+namespace {
+__global__ void k_debug_convert(const double *in64, float *out32, const float *in32, double *out64, int64_t n) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  if (in64) out32[k] = f64_to_f32(in64[k]);
+  if (in32) out64[k] = f32_to_f64(in32[k]);
+}
+}  // namespace
+
+extern "C" int sph_debug_convert(const double *in64, float *out32, const float *in32, double *out64, int64_t n) {
+  if (n < 0 || n > ((int64_t)1 << 24)) return fail(SPH_ERR_ARG, "n must be 0..2^24");
+  if ((in64 && !out32) || (in32 && !out64)) return fail(SPH_ERR_ARG, "output missing");
+  if (n == 0 || (!in64 && !in32)) return SPH_OK;
+  // test aid, not on the stepping path: temporary device buffers
+  char *d = nullptr;
+  const size_t b8 = 8 * (size_t)n, b4 = 4 * (size_t)n;
+  if (cudaMalloc(&d, 2 * (b8 + b4)) != cudaSuccess) return fail(SPH_ERR_ALLOC, "convert buffers");
+  double *d_in64 = (double *)d, *d_out64 = (double *)(d + b8);
+  float *d_in32 = (float *)(d + 2 * b8), *d_out32 = (float *)(d + 2 * b8 + b4);
+  cudaError_t e = cudaSuccess;
+  if (in64) e = cudaMemcpy(d_in64, in64, b8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && in32) e = cudaMemcpy(d_in32, in32, b4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_debug_convert<<<(unsigned)((n + 255) / 256), 256>>>(in64 ? d_in64 : nullptr, d_out32, in32 ? d_in32 : nullptr,
+                                                           d_out64, n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && in64) e = cudaMemcpy(out32, d_out32, b4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && in32) e = cudaMemcpy(out64, d_out64, b8, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(SPH_ERR_CUDA, cudaGetErrorString(e));
+  return SPH_OK;
+}

@@ -168,6 +168,65 @@ __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a,
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
 
+// ------------------------------------------------------------------------
+// binary64 <-> binary32 conversions with 32-bit integer operations.  On
+// GB300 the conversion instructions issue on the FP64 pipe (a small
+// fraction of the FP32 rate), and the FP32 form converts every field it
+// gathers or writes back; these run on the integer pipe instead.  Both
+// follow the IEEE 754 encodings (1 sign, 11 / 8 exponent bits with biases
+// 1023 / 127, 52 / 23 fraction bits) and give the same results as the
+// conversion instructions:
+//  * binary64 -> binary32, round to nearest, ties to even: for a value in
+//    the normal binary32 range the exponent is rebased by 1023 - 127 = 896
+//    and the 52-bit fraction keeps its top 23 bits, plus one unit when the
+//    29 dropped bits exceed half a unit or equal it with an odd result (a
+//    carry into the exponent is the correct next binade, at the top the
+//    correct overflow to infinity);
+//  * binary32 -> binary64 is exact: exponent rebased, fraction shifted.
+// Zeros take a direct path; subnormals, infinities and NaNs (rare here) use
+// the conversion instruction.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ float f64_to_f32(double d) {
+  const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+  const uint32_t mag = hi & 0x7FFFFFFFu;
+  const uint32_t e = mag >> 20;
+  if (e - 897u > 253u) {  // binary32 exponent field outside 1..254
+    if ((mag | lo) == 0u) return __uint_as_float(hi);  // +-0
+    return __double2float_rn(d);
+  }
+  uint32_t f = ((mag - (896u << 20)) << 3) | (lo >> 29);
+  const uint32_t rem = lo & 0x1FFFFFFFu;
+  f += (uint32_t)(rem > 0x10000000u) | ((uint32_t)(rem == 0x10000000u) & f);
+  return __uint_as_float(f | (hi & 0x80000000u));
+}
+
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t mag = u & 0x7FFFFFFFu;
+  const uint32_t e = mag >> 23;
+  if (e - 1u > 253u) {  // zero, subnormal, infinity, NaN
+    if (mag == 0u) return __hiloint2double((int)u, 0);  // +-0
+    return (double)x;
+  }
+  return __hiloint2double((int)((u & 0x80000000u) | ((mag >> 3) + (896u << 20))), (int)(u << 29));
+}
+
+// conversions into and out of the sweep precision R
+template <typename R>
+__device__ __forceinline__ R to_R(double d) {
+  if constexpr (sizeof(R) == 4)
+    return f64_to_f32(d);
+  else
+    return d;
+}
+template <typename R>
+__device__ __forceinline__ double from_R(R x) {
+  if constexpr (sizeof(R) == 4)
+    return f32_to_f64(x);
+  else
+    return x;
+}
+
 // floor((x - lo) / (2h)) with the correctly rounded quotient, clamped.  The
 // product with 1/(2h) is within 3.4e-10 cells of that quotient for grids of
 // up to 1e6 cells per axis, so when it lies more than 1e-9 away from an

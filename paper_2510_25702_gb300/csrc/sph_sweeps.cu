@@ -274,7 +274,7 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
     }
     double Bd[6];
     invert_guarded<D>(Ad, Bd);  // FP64 inversion (one reciprocal)
-    for (int c = 0; c < 6; ++c) BR[c] = (R)Bd[c];
+    for (int c = 0; c < 6; ++c) BR[c] = to_R<R>(Bd[c]);
     if (sizeof(R) == 8) {  // FP64 form: keep every bit of the FP64 inverse
       a.der.B[0][i] = Bd[0];
       a.der.B[1][i] = Bd[1];
@@ -287,22 +287,22 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
     }
   }
   if (sizeof(R) == 4) {
-    a.der.B[0][i] = (double)BR[0];
-    a.der.B[1][i] = (double)BR[1];
-    a.der.B[3][i] = (double)BR[3];
+    a.der.B[0][i] = from_R<R>(BR[0]);
+    a.der.B[1][i] = from_R<R>(BR[1]);
+    a.der.B[3][i] = from_R<R>(BR[3]);
     if (D == 3) {
-      a.der.B[2][i] = (double)BR[2];
-      a.der.B[4][i] = (double)BR[4];
-      a.der.B[5][i] = (double)BR[5];
+      a.der.B[2][i] = from_R<R>(BR[2]);
+      a.der.B[4][i] = from_R<R>(BR[4]);
+      a.der.B[5][i] = from_R<R>(BR[5]);
     }
   }
   const double rho_i = m.rho[i];
-  const R inv_rho = Ex<R>::div((R)1, (R)rho_i);
+  const R inv_rho = Ex<R>::div((R)1, to_R<R>(rho_i));
   R an[3] = {0, 0, 0};
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     an[c] = (R)2 * sv[c] * inv_rho;
-    a.der.an[c][i] = (double)an[c];
+    a.der.an[c][i] = from_R<R>(an[c]);
   }
   pk.Ap[i] = V4<R>{an[0] + kc.g[0], an[1] + kc.g[1], D == 3 ? an[2] + kc.g[2] : (R)0, (R)0};
 
@@ -333,13 +333,13 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
     const R dedt = (R)kC1 * e_i * inv_k * Gk - (R)kC2 * e_i * e_i * inv_k + (R)2 * de * inv_rho;
     // explicit update over dt_ad in the sweep precision (k, eps are not
     // among the FP64-integrated fields; in the FP64 form this is FP64)
-    const R dta = (R)I.dt_ad;
+    const R dta = to_R<R>(I.dt_ad);
     R k1r = k_i + dta * dkdt, e1r = e_i + dta * dedt;
     k1r = k1r > (R)kFloor ? k1r : (R)kFloor;
     e1r = e1r > (R)kFloor ? e1r : (R)kFloor;
-    m.k[i] = (double)k1r;
-    m.eps[i] = (double)e1r;
-    m.nut[i] = (double)Ex<R>::div((R)kCmu * k1r * k1r, e1r);
+    m.k[i] = from_R<R>(k1r);
+    m.eps[i] = from_R<R>(e1r);
+    m.nut[i] = from_R<R>(Ex<R>::div((R)kCmu * k1r * k1r, e1r));
     kw = (R)(2.0 / 3.0) * k1r;
   } else if (rans) {
     kw = (R)(2.0 / 3.0) * k_i;  // turbulence held over a differentiated window
@@ -349,14 +349,14 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   // first half, so only that one is stored.
   const double hdt = 0.5 * I.dt;
   const double rho = rho_i + hdt * m.drho[i];
-  const R p = (R)(rho - I.rho0) * sweep_const<R>(I).c0sq;
+  const R p = to_R<R>(rho - I.rho0) * sweep_const<R>(I).c0sq;
   m.rho[i] = rho;
-  if (I.n_ac == 1) m.p[i] = (double)p;
+  if (I.n_ac == 1) m.p[i] = from_R<R>(p);
 #pragma unroll
   for (int c = 0; c < D; ++c) m.x[c][i] = m.x[c][i] + hdt * m.v[c][i];
   // momentum record; pressure-buffer particles are marked so that their
   // neighbours use their own B (the condition B_k = B_i, Sec. 3.3)
-  const R V = Ex<R>::div((R)m.mass[i], (R)rho);
+  const R V = Ex<R>::div(to_R<R>(m.mass[i]), to_R<R>(rho));
   const R bxx = mirror ? (R)-1 : BR[0];
   if (D == 2) {
     pk.mom[2 * (size_t)i] = V4<R>{A0.x, A0.y, V, p};
@@ -451,7 +451,7 @@ __device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, 
   }
   // a = -(1/rho_i) (p_i (S1 + B_i Cb) + B_i S2) [+ (2 p_ob / rho_i) B_i Ct]
   const double rho_i = m.rho[i];
-  const R inv_rho = Ex<R>::div((R)1, (R)rho_i);
+  const R inv_rho = Ex<R>::div((R)1, to_R<R>(rho_i));
   R bcb[3], bs2[3];
   sym_matvec<R, D>(Bi, Cb, bcb);
   sym_matvec<R, D>(Bi, S2, bs2);
@@ -488,10 +488,10 @@ __device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, 
   R vo[3] = {(R)0, (R)0, (R)0};
 #pragma unroll
   for (int c = 0; c < D; ++c) {
-    const double v = m.v[c][i] + dt * (double)(acc[c] + apr[c]);
+    const double v = m.v[c][i] + dt * from_R<R>(acc[c] + apr[c]);
     m.v[c][i] = v;
     m.x[c][i] = m.x[c][i] + hdt * v;
-    vo[c] = (R)v;
+    vo[c] = to_R<R>(v);
   }
   // continuity record: 2D (x y V p)(vx vy - -), 3D (x y z V)(p vx vy vz)
   pk.cont[2 * (size_t)i] = M0;
@@ -558,7 +558,7 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
   }
   const double hdt = 0.5 * I.dt;
   const double rho_i = m.rho[i];
-  const double drho = rho_i * (double)sum;
+  const double drho = rho_i * from_R<R>(sum);
   m.drho[i] = drho;
   double rho = rho_i + hdt * drho;
   m.rho[i] = rho;
@@ -586,12 +586,12 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
     // (B and kw stay from the advection sweep unless a free-stream buffer
     // reset k)
     rho = rho + hdt * drho;
-    const R p = (R)(rho - I.rho0) * sweep_const<R>(I).c0sq;
+    const R p = to_R<R>(rho - I.rho0) * sweep_const<R>(I).c0sq;
     m.rho[i] = rho;
-    if (a.sub + 2 == I.n_ac) m.p[i] = (double)p;  // the step's last first half
+    if (a.sub + 2 == I.n_ac) m.p[i] = from_R<R>(p);  // the step's last first half
 #pragma unroll
     for (int c = 0; c < D; ++c) m.x[c][i] = m.x[c][i] + hdt * v[c];
-    const R Vn = Ex<R>::div((R)m.mass[i], (R)rho);
+    const R Vn = Ex<R>::div(to_R<R>(m.mass[i]), to_R<R>(rho));
     if (D == 2) {
       pk.mom[2 * (size_t)i] = V4<R>{C0.x, C0.y, Vn, p};
       if (kw_reset) {

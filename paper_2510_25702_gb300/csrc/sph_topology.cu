@@ -96,7 +96,7 @@ __device__ __forceinline__ void permute_one(const TopoArgs &a, const Packs<R> &p
   D.uid[t] = S.uid[s];
   D.inst[t] = (uint16_t)ii;
   int32_t lab = S.label[s];
-  const float xf = (float)x, yf = (float)y, zf = (float)z;
+  const float xf = f64_to_f32(x), yf = f64_to_f32(y), zf = f64_to_f32(z);
   for (int b = 0; b < I.nbuf; ++b) {
     const BufDev &B = a.buf[I.buf0 + b];
     const float ex = xf - B.cen[0], ey = yf - B.cen[1], ez = zf - B.cen[2];
@@ -105,14 +105,15 @@ __device__ __forceinline__ void permute_one(const TopoArgs &a, const Packs<R> &p
   }
   D.label[t] = lab;
   // advection-sweep record of this particle
-  const R V = (R)mass / (R)rho;
+  const R V = to_R<R>(mass) / to_R<R>(rho);
+  const R vxr = to_R<R>(vx), vyr = to_R<R>(vy);
   if (I.dim == 2) {
-    pk.adv[2 * (size_t)t] = V4<R>{(R)x, (R)y, V, (R)vx};
-    pk.adv[2 * (size_t)t + 1] = V4<R>{(R)vy, (R)k, (R)eps, (R)nut};
+    pk.adv[2 * (size_t)t] = V4<R>{to_R<R>(x), to_R<R>(y), V, vxr};
+    pk.adv[2 * (size_t)t + 1] = V4<R>{vyr, to_R<R>(k), to_R<R>(eps), to_R<R>(nut)};
   } else {
-    pk.adv[3 * (size_t)t] = V4<R>{(R)x, (R)y, (R)z, V};
-    pk.adv[3 * (size_t)t + 1] = V4<R>{(R)vx, (R)vy, (R)vz, (R)k};
-    pk.adv[3 * (size_t)t + 2] = V4<R>{(R)eps, (R)nut, (R)0, (R)0};
+    pk.adv[3 * (size_t)t] = V4<R>{to_R<R>(x), to_R<R>(y), to_R<R>(z), V};
+    pk.adv[3 * (size_t)t + 1] = V4<R>{vxr, vyr, to_R<R>(vz), to_R<R>(k)};
+    pk.adv[3 * (size_t)t + 2] = V4<R>{to_R<R>(eps), to_R<R>(nut), (R)0, (R)0};
   }
   // |v|^2 with the plain left-to-right sum (in the sweep precision: the
   // FP64 form keeps the exact FP64 maximum), nu_t
@@ -122,8 +123,8 @@ __device__ __forceinline__ void permute_one(const TopoArgs &a, const Packs<R> &p
     v2 = dadd(v2, dmul(vy, vy));
     if (I.dim == 3) v2 = dadd(v2, dmul(vz, vz));
   } else {
-    const float fx = (float)vx, fy = (float)vy, fz = (float)vz;
-    v2 = (double)(fx * fx + fy * fy + (I.dim == 3 ? fz * fz : 0.0f));
+    const float fx = f64_to_f32(vx), fy = f64_to_f32(vy), fz = f64_to_f32(vz);
+    v2 = f32_to_f64(fx * fx + fy * fy + (I.dim == 3 ? fz * fz : 0.0f));
   }
   if (ii == s_ii) {
     atomicMax(s_v2, (unsigned long long)__double_as_longlong(v2));

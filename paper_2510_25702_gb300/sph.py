@@ -102,7 +102,7 @@ EXPORTS = ("sph_create", "sph_add_buffer", "sph_set_profile", "sph_step", "sph_r
            "sph_last_error", "sph_abi_version", "sph_set_profiling", "sph_get_stage_times", "sph_stage_name",
            "sph_cell_sort_noalloc", "sph_set_graph", "sph_set_launch", "sph_get_launch", "sph_autotune",
            "sph_save_state", "sph_restore_state", "sph_drop_state", "sph_adjoint_forward",
-           "sph_adjoint_backward", "sph_adjoint_release")
+           "sph_adjoint_backward", "sph_adjoint_release", "sph_debug_convert")
 NOALLOC_MAX_POINTS = 1 << 19
 N_STAGES = 10
 
@@ -129,6 +129,7 @@ def lib():
         L.sph_write_fields.argtypes = [vp, C.c_uint32, C.POINTER(vp), C.c_int32, C.c_int64]
         L.sph_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.sph_debug_pairs.argtypes = [vp, C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_int64)]
+        L.sph_debug_convert.argtypes = [vp, vp, vp, vp, C.c_int64]
         L.sph_destroy.argtypes = [vp]
         L.sph_destroy.restype = None
         L.sph_set_profiling.argtypes = [vp, C.c_int32]
@@ -160,6 +161,20 @@ def _check(rc: int, what: str):
 
 def _dptr(a: np.ndarray) -> int:
     return a.ctypes.data
+
+
+def debug_convert(x64: np.ndarray, x32: np.ndarray):
+    """The FP32 form's integer-pipe conversions on the device (test aid):
+    returns (x64 rounded to binary32, x32 widened to binary64)."""
+    x64 = np.ascontiguousarray(x64, dtype=np.float64)
+    x32 = np.ascontiguousarray(x32, dtype=np.float32)
+    if x64.size != x32.size:
+        raise ValueError("x64 and x32 must have the same size")
+    o32 = np.empty(x64.size, dtype=np.float32)
+    o64 = np.empty(x32.size, dtype=np.float64)
+    _check(lib().sph_debug_convert(x64.ctypes.data, o32.ctypes.data, x32.ctypes.data, o64.ctypes.data, x64.size),
+           "sph_debug_convert")
+    return o32, o64
 
 
 def make_config(case, precision: str = "fp64", kinematic: bool = False) -> Config:
