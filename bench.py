@@ -430,7 +430,9 @@ def main():
     peak, peak_kind = peaks()
 
     # end to end through the C ABI: per step the inlet profile goes host ->
-    # device (sph_set_profile), the step runs, the statistics come back
+    # device (sph_set_profile, from pinned staging), the step is enqueued
+    # (sph_step_async), and the statistics with the device status word come
+    # back (sph_get_stats: the one wait of the step)
     e2e_steps = max(10, args.steps // 4)
     theta = np.array([1.0])
     sim.set_graph(True)
@@ -439,11 +441,14 @@ def main():
     ps = 0.0
     for s in range(e2e_steps):
         sim.set_profile(0, 0, theta)
-        sim.step(1)
-        ps += sim.stats()["n"]
+        sim.step_async(1)
+        st = sim.stats()
+        if st["status"] != 0:
+            raise RuntimeError(f"device status {st['status']} in the end-to-end loop")
+        ps += st["n"]
     t1 = time.perf_counter()
     e2e = {"value": ps / (t1 - t0) * (world if dist is not None else 1), "unit": UNIT,
-           "h2d_bytes_per_step": 4 + 8 * theta.size, "d2h_bytes_per_step": 4 + 40 + 40}
+           "h2d_bytes_per_step": 4 + 8 * theta.size, "d2h_bytes_per_step": 64 + 40}
 
     log("e2e done")
     fp64 = None

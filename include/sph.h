@@ -24,6 +24,7 @@
  *  - Work is ordered on the context's CUDA stream (sph_alloc.stream, or the
  *    legacy default stream when NULL).  sph_step does not synchronise with
  *    the host except for reading its 4-byte status word at the end;
+ *    sph_step_async and sph_set_profile do not wait at all;
  *    sph_read_fields, sph_write_fields and sph_get_stats synchronise.
  *  - Rows read or written by sph_read_fields / sph_write_fields are ordered
  *    by (instance, uid).
@@ -161,6 +162,9 @@ typedef struct sph_stats {
   int64_t capacity;
   int64_t device_bytes; /* device memory owned by the context */
   int64_t kernel_launches; /* cumulative kernels this context launched */
+  int32_t status;    /* device status word: 0 or the first SPH_ERR_* a kernel
+                        set (sticky; sph_step returns it too) */
+  int32_t reserved;
 } sph_stats;
 
 typedef struct sph_ctx sph_ctx;
@@ -179,7 +183,10 @@ int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *
    the first step, SPH_ERR_ARG on a bad frame or profile. */
 int sph_add_buffer(sph_ctx *ctx, int32_t instance, const sph_buffer_desc *b, int32_t *out_id);
 
-/* Replace the velocity profile theta of a velocity buffer (any time). */
+/* Replace the velocity profile theta of a velocity buffer (any time).  The
+   values are staged in pinned host memory and copied on the context's
+   stream, in order with the steps enqueued around the call; the call
+   returns without waiting (theta may be reused at once). */
 int sph_set_profile(sph_ctx *ctx, int32_t instance, int32_t buffer_id, const double *theta,
                     int32_t n_theta);
 
@@ -187,6 +194,12 @@ int sph_set_profile(sph_ctx *ctx, int32_t instance, int32_t buffer_id, const dou
    device error (SPH_ERR_CAPACITY, SPH_ERR_NONFINITE, SPH_ERR_TIMEOUT) seen
    in the status word; *t_out (may be NULL) receives instance 0's time. */
 int sph_step(sph_ctx *ctx, int32_t nsteps, double *t_out);
+
+/* Enqueue nsteps advection steps on the context's stream and return at once
+   (no wait for the GPU).  Device errors are not seen here: sph_get_stats
+   reports the status word (sph_stats.status), and sph_step returns it.
+   Errors: SPH_ERR_ARG (nsteps < 0), SPH_ERR_CUDA (launch or capture). */
+int sph_step_async(sph_ctx *ctx, int32_t nsteps);
 
 /* Field selectors for sph_read_fields / sph_write_fields.  dst[k] (src[k])
    is the array of the k-th set bit in increasing bit order. */

@@ -54,6 +54,17 @@ struct sph_ctx {
   std::vector<std::vector<BufDev>> bufs;  // per instance
   sph_alloc alloc{};
   cudaStream_t stream = nullptr;
+  // pinned host staging: the readback of counters, instance tail and
+  // status word, and one slot per buffer for profile uploads (each with an
+  // event, so that a slot is rewritten only after its last copy ran)
+  struct Pinned {
+    Counters cnt;
+    char inst_tail[sizeof(InstDev)];
+    int32_t status;
+  };
+  Pinned *pin = nullptr;
+  char *prof_stage = nullptr;  // ninst x SPH_MAX_BUFFERS slots of kProfSlot bytes
+  std::vector<cudaEvent_t> prof_ev;
   int64_t cap = 0, nw = 0;
   uint32_t ncell = 0;  // all instances; also the sentinel key of deleted entries
   int key_bits = 8;
@@ -659,6 +670,22 @@ int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *
     return fail(SPH_ERR_ALLOC, "device allocation failed");
   }
 
+  {
+    // pinned host staging for readback and profile uploads
+    const size_t nslots = (size_t)n_instances * SPH_MAX_BUFFERS;
+    void *pp = nullptr, *ps = nullptr;
+    if (cudaHostAlloc(&pp, sizeof(sph_ctx::Pinned), cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc(&ps, nslots * sizeof(BufDev), cudaHostAllocDefault) != cudaSuccess) {
+      if (pp) cudaFreeHost(pp);
+      c->release();
+      delete c;
+      return fail(SPH_ERR_ALLOC, "pinned host allocation failed");
+    }
+    c->pin = (sph_ctx::Pinned *)pp;
+    c->prof_stage = (char *)ps;
+    c->prof_ev.assign(nslots, nullptr);
+  }
+
   // ---- uploads ----
   auto up = [&](void *dst, const void *src, size_t n) -> int {
     if (n == 0) return 0;
@@ -734,6 +761,10 @@ int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *
 void sph_destroy(sph_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->pin) cudaFreeHost(c->pin);
+  if (c->prof_stage) cudaFreeHost(c->prof_stage);
+  for (cudaEvent_t e : c->prof_ev)
+    if (e) cudaEventDestroy(e);
   adj_free(c);
   for (size_t q = 0; q < c->snaps.size(); ++q)
     if (c->snaps[q].mem) sph_drop_state(c, (int32_t)q);
@@ -928,12 +959,24 @@ int sph_set_profile(sph_ctx *c, int32_t instance, int32_t buffer_id, const doubl
   b.n_theta = n_theta;
   for (int q = 0; q < n_theta; ++q) b.theta[q] = theta[q];
   if (c->started) {
-    // only the profile moves: n_theta and theta[0..n_theta)
-    int g = c->inst[instance].buf0 + buffer_id;
-    CUDA_TRY(cudaMemcpyAsync(&c->d_buf[g].n_theta, &b.n_theta, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(cudaMemcpyAsync(c->d_buf[g].theta, b.theta, sizeof(double) * n_theta, cudaMemcpyHostToDevice,
+    // only the profile moves: n_theta and theta[0..n_theta), from this
+    // buffer's pinned slot, without waiting for the stream; the slot is
+    // rewritten only after its previous copies have run
+    const int g = c->inst[instance].buf0 + buffer_id;
+    const int slot = instance * SPH_MAX_BUFFERS + buffer_id;
+    BufDev *stage = reinterpret_cast<BufDev *>(c->prof_stage) + slot;
+    cudaEvent_t &ev = c->prof_ev[slot];
+    if (ev)
+      CUDA_TRY(cudaEventSynchronize(ev));
+    else
+      CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    stage->n_theta = n_theta;
+    for (int q = 0; q < n_theta; ++q) stage->theta[q] = theta[q];
+    CUDA_TRY(cudaMemcpyAsync(&c->d_buf[g].n_theta, &stage->n_theta, sizeof(int32_t), cudaMemcpyHostToDevice,
                              c->stream));
-    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->d_buf[g].theta, stage->theta, sizeof(double) * n_theta, cudaMemcpyHostToDevice,
+                             c->stream));
+    CUDA_TRY(cudaEventRecord(ev, c->stream));
   }
   return SPH_OK;
 }
@@ -1001,8 +1044,9 @@ static void enqueue_step(sph_ctx *c) {
 }
 
 static int read_status(sph_ctx *c, int32_t *status) {
-  CUDA_TRY(cudaMemcpyAsync(status, &c->cnt->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(&c->pin->status, &c->cnt->status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
+  *status = c->pin->status;
   c->prof_collect();
   return 0;
 }
@@ -1040,7 +1084,7 @@ static int capture_graph(sph_ctx *c, int parity) {
   return 0;
 }
 
-int sph_step(sph_ctx *c, int32_t nsteps, double *t_out) {
+static int enqueue_steps(sph_ctx *c, int32_t nsteps) {
   if (!c) return fail(SPH_ERR_ARG, "ctx is NULL");
   if (nsteps < 0) return fail(SPH_ERR_ARG, "nsteps < 0");
   if (!c->started) {
@@ -1067,6 +1111,14 @@ int sph_step(sph_ctx *c, int32_t nsteps, double *t_out) {
     c->step += 1;
   }
   CUDA_TRY(cudaGetLastError());
+  return SPH_OK;
+}
+
+int sph_step_async(sph_ctx *c, int32_t nsteps) { return enqueue_steps(c, nsteps); }
+
+int sph_step(sph_ctx *c, int32_t nsteps, double *t_out) {
+  int rc0 = enqueue_steps(c, nsteps);
+  if (rc0) return rc0;
   int32_t status = 0;
   int rc = read_status(c, &status);
   if (rc) return rc;
@@ -1838,14 +1890,17 @@ int sph_write_fields(sph_ctx *c, uint32_t mask, const void *const *src, int32_t 
 
 int sph_get_stats(sph_ctx *c, sph_stats *out) {
   if (!c || !out) return fail(SPH_ERR_ARG, "NULL argument");
-  CUDA_TRY(cudaStreamSynchronize(c->stream));
-  Counters h;
-  CUDA_TRY(cudaMemcpy(&h, c->cnt, sizeof(h), cudaMemcpyDeviceToHost));
+  // two copies into pinned staging on the context's stream, one wait
+  CUDA_TRY(cudaMemcpyAsync(&c->pin->cnt, c->cnt, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
   // dt_ad, dt_ac, dt, t, n_ac are the trailing fields of the instance record
-  InstDev i0;
   const size_t tail = offsetof(InstDev, dt_ad);
-  CUDA_TRY(cudaMemcpy((char *)&i0 + tail, (const char *)c->d_inst + tail, sizeof(InstDev) - tail,
-                      cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpyAsync(c->pin->inst_tail + tail, (const char *)c->d_inst + tail, sizeof(InstDev) - tail,
+                           cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->prof_collect();
+  const Counters h = c->pin->cnt;
+  InstDev i0;
+  memcpy((char *)&i0 + tail, c->pin->inst_tail + tail, sizeof(InstDev) - tail);
   memset(out, 0, sizeof(*out));
   out->n = (int64_t)h.m_pending - (int64_t)h.n_del_step;
   out->step = c->step;
@@ -1859,6 +1914,7 @@ int sph_get_stats(sph_ctx *c, sph_stats *out) {
   out->capacity = c->cap;
   out->device_bytes = (int64_t)c->bytes;
   out->kernel_launches = c->launches;
+  out->status = h.status;
   return SPH_OK;
 }
 

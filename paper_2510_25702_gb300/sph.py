@@ -91,7 +91,8 @@ class Stats(C.Structure):
         ("n", C.c_int64), ("step", C.c_int64), ("t", C.c_double), ("dt_ad", C.c_double),
         ("dt_ac", C.c_double), ("n_ac", C.c_int32), ("n_instances", C.c_int32),
         ("spawned", C.c_int64), ("deleted", C.c_int64), ("capacity", C.c_int64),
-        ("device_bytes", C.c_int64), ("kernel_launches", C.c_int64),
+        ("device_bytes", C.c_int64), ("kernel_launches", C.c_int64), ("status", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
 
@@ -102,7 +103,7 @@ EXPORTS = ("sph_create", "sph_add_buffer", "sph_set_profile", "sph_step", "sph_r
            "sph_last_error", "sph_abi_version", "sph_set_profiling", "sph_get_stage_times", "sph_stage_name",
            "sph_cell_sort_noalloc", "sph_set_graph", "sph_set_launch", "sph_get_launch", "sph_autotune",
            "sph_save_state", "sph_restore_state", "sph_drop_state", "sph_adjoint_forward",
-           "sph_adjoint_backward", "sph_adjoint_release", "sph_debug_convert")
+           "sph_adjoint_backward", "sph_adjoint_release", "sph_debug_convert", "sph_step_async")
 NOALLOC_MAX_POINTS = 1 << 19
 N_STAGES = 10
 
@@ -125,6 +126,7 @@ def lib():
         L.sph_add_buffer.argtypes = [vp, C.c_int32, C.POINTER(BufferDesc), C.POINTER(C.c_int32)]
         L.sph_set_profile.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_int32]
         L.sph_step.argtypes = [vp, C.c_int32, C.POINTER(C.c_double)]
+        L.sph_step_async.argtypes = [vp, C.c_int32]
         L.sph_read_fields.argtypes = [vp, C.c_uint32, C.POINTER(vp), C.c_int32, C.POINTER(C.c_int64)]
         L.sph_write_fields.argtypes = [vp, C.c_uint32, C.POINTER(vp), C.c_int32, C.c_int64]
         L.sph_get_stats.argtypes = [vp, C.POINTER(Stats)]
@@ -294,6 +296,10 @@ class Simulation:
         t = C.c_double()
         _check(lib().sph_step(self.ctx, int(nsteps), C.byref(t)), "sph_step")
         return t.value
+
+    def step_async(self, nsteps: int = 1):
+        """Enqueue steps without waiting; stats()["status"] reports device errors."""
+        _check(lib().sph_step_async(self.ctx, int(nsteps)), "sph_step_async")
 
     def step_rc(self, nsteps: int = 1) -> int:
         """sph_step's return code (no exception)."""

@@ -71,7 +71,7 @@ def test_conversions_match_ieee_round_to_nearest(sph):
     x32 = np.resize(x32, n)
     with np.errstate(over="ignore", invalid="ignore"):
         want32 = x64.astype(np.float32)
-    want64 = x32.astype(np.float64)
+        want64 = x32.astype(np.float64)
     got32, got64 = sph.debug_convert(x64, x32)
     nan32 = np.isnan(want32)
     assert np.array_equal(np.isnan(got32), nan32)

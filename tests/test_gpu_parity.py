@@ -229,6 +229,33 @@ def test_nonfinite_state_is_reported(sph):
     assert sim.step_rc(1) == -4
 
 
+def test_async_stepping_matches_and_reports_status(sph):
+    """sph_step_async + sph_get_stats (one wait per step, profiles staged
+    in pinned memory) give the same state as sph_step, bit for bit, and the
+    stats carry the device status word."""
+    case = cases.turbulent_channel(length=0.3, height=0.1, dp=0.005, jitter_frac=0.05)
+    a = sph.Simulation(case, precision="fp32")
+    b = sph.Simulation(case, precision="fp32")
+    for s in range(6):
+        theta = np.array([1.0 + 0.05 * s])
+        a.set_profile(0, 0, theta)
+        a.step(1)
+        b.set_profile(0, 0, theta)
+        theta[0] = -7.0  # the staged copy is independent of the caller's array
+        b.step_async(1)
+        assert b.stats()["status"] == 0
+    fa, fb = a.read(["pos", "vel", "rho", "uid"]), b.read(["pos", "vel", "rho", "uid"])
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    box = cases.periodic_box(n_per_axis=10, dim=2)
+    sim = sph.Simulation(box)
+    v = sim.read(["vel"])["vel"]
+    v[3, 0] = np.nan
+    sim.write({"vel": v})
+    sim.step_async(1)
+    assert sim.stats()["status"] == -4
+
+
 # --------------------------------------------------------------------------
 # FP32 sweeps (precision pattern): error against the FP64 oracle
 # --------------------------------------------------------------------------
