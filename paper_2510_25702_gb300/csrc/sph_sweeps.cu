@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_adv(SweepArgs a, Packs<R> pk) {
 }
 
 template <typename R, int D, bool PER>
-__global__ void __launch_bounds__(kMaxBlock) k_mom(SweepArgs a, Packs<R> pk) {
+__global__ void __launch_bounds__(kMaxBlock, 5) k_mom(SweepArgs a, Packs<R> pk) {
   if (a.sub >= a.cnt->n_ac_all || a.cnt->status) return;  // no instance takes this sub-step
   const int n = a.cnt->n_live;
   const int step = gridDim.x * blockDim.x;
@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_mom(SweepArgs a, Packs<R> pk) {
 }
 
 template <typename R, int D, bool PER>
-__global__ void __launch_bounds__(kMaxBlock) k_cont(SweepArgs a, Packs<R> pk) {
+__global__ void __launch_bounds__(kMaxBlock, 5) k_cont(SweepArgs a, Packs<R> pk) {
   if (a.sub >= a.cnt->n_ac_all || a.cnt->status) return;
   const int n = a.cnt->n_live;
   const int step = gridDim.x * blockDim.x;
