@@ -28,8 +28,8 @@ namespace sphk {
 
 constexpr int CS_THREADS = 256;
 constexpr int CS_WARPS = CS_THREADS / 32;
-constexpr int CS_ROUNDS = 8;
-constexpr int CS_CHUNK = CS_THREADS * CS_ROUNDS;  // 2048 keys ranked at once
+constexpr int CS_ROUNDS = 16;
+constexpr int CS_CHUNK = CS_THREADS * CS_ROUNDS;  // 4096 keys ranked at once
 constexpr int CS_MAX_RADIX = 1 << 10;
 
 struct CellSortArgs {
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(CS_THREADS) k_cell_sort(CellSortArgs a) {
   if (n > a.max_count) n = a.max_count;
   const int per = (n + G - 1) / G;
   const int s0 = min(n, b * per), s1 = min(n, s0 + per);
-  // a slice of at most one chunk (the usual case: up to grid x 2048 keys)
+  // a slice of at most one chunk (the usual case: up to grid x 4096 keys)
   // is loaded and ranked once per pass and kept in registers
   const bool one = s1 - s0 <= CS_CHUNK;
 

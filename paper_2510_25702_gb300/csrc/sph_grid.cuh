@@ -37,14 +37,16 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
 }
 
 // barrier number k of this launch; false when the launch was aborted.
-// s_ok is a __shared__ int of the calling block.
+// s_ok is a __shared__ int of the calling block.  The arrival is a
+// release add and the wait an acquire load at GPU scope; with the block
+// barriers on both sides, every write made before the barrier by any thread
+// of any block is visible to every thread after it.
 __device__ __forceinline__ bool grid_sync(GridBarrier *g, uint32_t k, int32_t *status, int *s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
     const uint32_t target = k * gridDim.x;
-    __threadfence();
-    atomicAdd(&g->arrive, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&g->arrive), "r"(1u) : "memory");
     uint32_t it = 0;
     while (ld_acquire_u32(&g->arrive) < target) {
       if (ld_relaxed_u32(&g->abort)) {
@@ -59,7 +61,6 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *g, uint32_t k, int32_t *s
       }
       if (it > 64) __nanosleep(64);
     }
-    __threadfence();
     *s_ok = ok;
   }
   __syncthreads();

@@ -428,7 +428,7 @@ void cell_offsets(const uint32_t *keys, const int32_t *d_count, uint32_t ncell, 
 // sentinel and zeroes two optional word ranges.  The plan fixes the digit
 // width, the passes and the grid (co-resident blocks); scratch holds
 // cell_sort_words(plan) words, zeroed once when allocated.
-constexpr int kCellSortBlocksPerSm = 2;
+constexpr int kCellSortBlocksPerSm = 1;
 struct CellSortPlan {
   int rb, passes, grid;
 };
