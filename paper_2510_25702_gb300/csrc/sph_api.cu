@@ -243,6 +243,13 @@ struct sph_ctx {
     return a;
   }
 
+  SweepArgs with_flags(SweepArgs a) {
+    a.flag = flag;
+    a.inst_spawn = inst_spawn;
+    a.block_cnt = block_cnt;
+    return a;
+  }
+
   SweepArgs sweep(int sub, int which) {
     SweepArgs a{};
     a.block = blk[which];
@@ -985,13 +992,20 @@ int sph_set_profile(sph_ctx *c, int32_t instance, int32_t buffer_id, const doubl
 static void enqueue_topology(sph_ctx *c) {
   uint32_t *ks = nullptr, *vs = nullptr;
   // one cooperative launch: sort, live count, and the zeroing of the
-  // per-instance time-step maxima (v2max and nutmax, 2 x ninst doubles) and
-  // of the sub-step count that the time step folds with atomicMax
+  // per-instance time-step maxima (v2max and nutmax, 2 x ninst doubles), of
+  // the sub-step count that the time step folds with atomicMax and of the
+  // per-block inject counts that the continuity sweep adds to
   int ev = c->prof_begin(0);
   uint32_t *keys[2] = {c->K[0], c->K[1]}, *vals[2] = {c->Vv[0], c->Vv[1]};
+  ClearSpans clear{};
+  clear.p[0] = reinterpret_cast<uint32_t *>(c->v2max);
+  clear.n[0] = 4 * c->ninst;
+  clear.p[1] = reinterpret_cast<uint32_t *>(&c->cnt->n_ac_all);
+  clear.n[1] = 1;
+  clear.p[2] = reinterpret_cast<uint32_t *>(c->block_cnt);
+  clear.n[2] = (int)((c->cap + kBlock - 1) / kBlock);
   cell_sort(c->cs_plan, c->cs_scratch, keys, vals, &c->cnt->m_pending, (int)c->cap, c->ncell, &c->cnt->n_live,
-            &c->cnt->status, reinterpret_cast<uint32_t *>(c->v2max), 4 * c->ninst,
-            reinterpret_cast<uint32_t *>(&c->cnt->n_ac_all), 1, c->stream, &ks, &vs);
+            &c->cnt->status, clear, c->stream, &ks, &vs);
   c->prof_end(ev);
   // the permute writes the cell offsets (stage 1 stays empty)
   TopoArgs t = c->topo();
@@ -1025,21 +1039,23 @@ static void enqueue_step(sph_ctx *c) {
     ev = c->prof_begin(5);
     launch_momentum_sweep(c->sweep(0, 2), c->packs(), c->prec, c->dim, maxn, 0, c->stream);
     c->prof_end(ev);
+    // the continuity sweep of each instance's last sub-step also takes the
+    // buffer-update flags
     ev = c->prof_begin(6);
-    launch_continuity_sweep(c->sweep(0, 3), c->packs(), c->prec, c->dim, maxn, 0, c->stream);
+    launch_continuity_sweep(c->with_flags(c->sweep(0, 3)), c->packs(), c->prec, c->dim, maxn, 0, c->stream);
     c->prof_end(ev);
     if (c->n_ac_max > 1) {
       // sub-steps 1 .. n_ac - 1: one cooperative launch, empty when every
       // instance takes a single sub-step
       ev = c->prof_begin(9);
-      launch_substeps(c->sweep(1, 2), c->packs(), c->prec, c->dim, maxn, c->stream);
+      launch_substeps(c->with_flags(c->sweep(1, 2)), c->packs(), c->prec, c->dim, maxn, c->stream);
       c->prof_end(ev);
     }
   }
   int ev = c->prof_begin(7);
-  launch_buffer_update(c->topo(), maxn, c->stream);
+  launch_buffer_update(c->topo(), maxn, c->kinematic ? 0 : 1, c->stream);
   c->prof_end(ev);
-  c->launches += 3 + (c->kinematic ? 0 : 4 + (c->n_ac_max > 1 ? 1 : 0));
+  c->launches += c->kinematic ? 3 : 2 + 4 + (c->n_ac_max > 1 ? 1 : 0);
   c->step += 1;
 }
 
@@ -1450,7 +1466,7 @@ static void enqueue_step_taped(sph_ctx *c, sph_ctx::Adj::Slot &sl) {
   }
   TopoArgs t = c->topo();
   t.spawn_dst = sl.T.spawn_dst;
-  launch_buffer_update(t, maxn, st);
+  launch_buffer_update(t, maxn, 0, st);
   // the state the reverse kernels index
   auto cp = [&](void *dst, const void *src, size_t n) { cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, st); };
   const size_t tiles = (cap + kListTile - 1) / kListTile;

@@ -43,8 +43,7 @@ struct CellSortArgs {
   uint32_t *hist;               // [radix][grid]
   uint32_t *total;              // [radix]
   GridBarrier *sync;            // word: keys at or above the sentinel
-  uint32_t *clear[2];           // words zeroed by the launch (may be NULL)
-  int nclear[2];
+  ClearSpans clear;             // words zeroed by the launch
 };
 
 template <int RB>
@@ -69,9 +68,9 @@ __global__ void __launch_bounds__(CS_THREADS) k_cell_sort(CellSortArgs a) {
   const bool one = s1 - s0 <= CS_CHUNK;
 
 #pragma unroll
-  for (int q = 0; q < 2; ++q)
-    if (a.clear[q])
-      for (int i = b * CS_THREADS + threadIdx.x; i < a.nclear[q]; i += G * CS_THREADS) a.clear[q][i] = 0u;
+  for (int q = 0; q < 3; ++q)
+    if (a.clear.p[q])
+      for (int i = b * CS_THREADS + threadIdx.x; i < a.clear.n[q]; i += G * CS_THREADS) a.clear.p[q][i] = 0u;
 
   uint32_t key[CS_ROUNDS], val[CS_ROUNDS], rank[CS_ROUNDS], tot[DPT];
   // load chunk c0 of the slice, rank every key among the equal digits of
@@ -301,8 +300,7 @@ size_t cell_sort_words(const CellSortPlan &plan) {
 
 void cell_sort(const CellSortPlan &plan, uint32_t *scratch, uint32_t *keys[2], uint32_t *vals[2],
                const int32_t *d_count, int max_count, uint32_t sentinel, int32_t *d_below, int32_t *status,
-               uint32_t *clear0, int nclear0, uint32_t *clear1, int nclear1, cudaStream_t st,
-               uint32_t **keys_result, uint32_t **vals_result) {
+               const ClearSpans &clear, cudaStream_t st, uint32_t **keys_result, uint32_t **vals_result) {
   CellSortArgs a{};
   for (int q = 0; q < 2; ++q) {
     a.keys[q] = keys[q];
@@ -317,10 +315,7 @@ void cell_sort(const CellSortPlan &plan, uint32_t *scratch, uint32_t *keys[2], u
   a.hist = scratch;
   a.total = scratch + (size_t)CS_MAX_RADIX * plan.grid;
   a.sync = reinterpret_cast<GridBarrier *>(a.total + CS_MAX_RADIX);
-  a.clear[0] = clear0;
-  a.nclear[0] = nclear0;
-  a.clear[1] = clear1;
-  a.nclear[1] = nclear1;
+  a.clear = clear;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)plan.grid);
   cfg.blockDim = dim3(CS_THREADS);

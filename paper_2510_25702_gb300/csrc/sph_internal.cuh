@@ -434,10 +434,13 @@ struct CellSortPlan {
 };
 int cell_sort_plan(int bits, CellSortPlan *plan);
 size_t cell_sort_words(const CellSortPlan &plan);
+struct ClearSpans {
+  uint32_t *p[3];  // word ranges the sort launch zeroes (NULL: unused)
+  int n[3];
+};
 void cell_sort(const CellSortPlan &plan, uint32_t *scratch, uint32_t *keys[2], uint32_t *vals[2],
                const int32_t *d_count, int max_count, uint32_t sentinel, int32_t *d_below, int32_t *status,
-               uint32_t *clear0, int nclear0, uint32_t *clear1, int nclear1, cudaStream_t st,
-               uint32_t **keys_result, uint32_t **vals_result);
+               const ClearSpans &clear, cudaStream_t st, uint32_t **keys_result, uint32_t **vals_result);
 
 struct TopoArgs {
   const InstDev *inst;
@@ -463,7 +466,18 @@ struct TopoArgs {
 void launch_permute(const TopoArgs &a, int max_n, int prec, cudaStream_t st, void *packs);
 void launch_time_step(const TopoArgs &a, cudaStream_t st);
 StepArgs step_args(const TopoArgs &a);  // the time-step fields of a
-void launch_buffer_update(const TopoArgs &a, int max_n, cudaStream_t st);
+// flags_done: the continuity sweep already wrote the flags, the per-instance
+// inject counts and the per-128-block inject counts (zeroed by the sort)
+void launch_buffer_update(const TopoArgs &a, int max_n, int flags_done, cudaStream_t st);
+
+// buffer-update flag of a particle (inject / delete / keep), Sec. 2.4.2,
+// 2.4.3, 3.1: inject when its local x'_0 has crossed the generation line
+// L_b + 0.5 dp, delete when x'_0 < 0 (behind the buffer)
+enum : uint8_t { kKeep = 0, kInject = 1, kDelete = 2 };
+__device__ __forceinline__ uint8_t buffer_flag(const BufDev &B, int dim, double x, double y, double z) {
+  const double x0 = local_coord(B, dim, x, y, z, 0);
+  return x0 >= B.gen_line ? kInject : (x0 < 0.0 ? kDelete : kKeep);
+}
 void launch_keys(const TopoArgs &a, int max_n, int all_live, cudaStream_t st);
 void launch_iota(uint32_t *idx, int max_n, cudaStream_t st);
 
@@ -523,6 +537,10 @@ struct SweepArgs {
   double *tape_S;        // optional: momentum sums S1, Cb, S2, Ct per sub-step
   StepArgs ts;           // list builder: time step of every instance by block 0
   int32_t with_time_step;
+  // continuity sweep, last sub-step of an instance: the buffer-update flags
+  // of its particles (NULL flag: the buffer update computes them)
+  uint8_t *flag;
+  int32_t *inst_spawn, *block_cnt;
   GridBarrier *gbar;     // sub-step launch: grid barrier words (zeroed once)
 };
 

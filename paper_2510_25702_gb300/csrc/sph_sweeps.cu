@@ -563,6 +563,19 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
   double rho = rho_i + hdt * drho;
   m.rho[i] = rho;
   const int lab = m.label[i];
+  if (a.flag && a.sub + 1 == I.n_ac) {
+    // the step's last sub-step of this instance: positions are final, so
+    // the buffer-update flag is taken here (as the flags kernel would)
+    uint8_t f = kKeep;
+    if (lab > 0 && lab <= I.nbuf) {
+      f = buffer_flag(a.buf[I.buf0 + lab - 1], I.dim, m.x[0][i], m.x[1][i], m.x[2][i]);
+      if (f == kInject) {
+        atomicAdd(&a.inst_spawn[ii], 1);
+        atomicAdd(&a.block_cnt[i / kBlock], 1);
+      }
+    }
+    a.flag[i] = f;
+  }
   bool kw_reset = false;
   R kw_bc = (R)0;
   if (lab > 0 && lab <= I.nbuf) {

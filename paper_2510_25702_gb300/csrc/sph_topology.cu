@@ -170,8 +170,6 @@ void launch_time_step(const TopoArgs &a, cudaStream_t st) {
 // ------------------------------------------------------------------------
 // buffer update
 // ------------------------------------------------------------------------
-enum : uint8_t { kKeep = 0, kInject = 1, kDelete = 2 };
-
 __global__ void __launch_bounds__(kBlock) k_flags(TopoArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = a.cnt->n_live;
@@ -181,14 +179,8 @@ __global__ void __launch_bounds__(kBlock) k_flags(TopoArgs a) {
     const int ii = a.src.inst[i];
     const InstDev &I = a.inst[ii];
     if (lab > 0 && lab <= I.nbuf) {
-      const BufDev &B = a.buf[I.buf0 + lab - 1];
-      double s0 = local_coord(B, I.dim, a.src.x[0][i], a.src.x[1][i], a.src.x[2][i], 0);
-      if (s0 >= B.gen_line) {
-        f = kInject;
-        atomicAdd(&a.inst_spawn[ii], 1);
-      } else if (s0 < 0.0) {
-        f = kDelete;
-      }
+      f = buffer_flag(a.buf[I.buf0 + lab - 1], I.dim, a.src.x[0][i], a.src.x[1][i], a.src.x[2][i]);
+      if (f == kInject) atomicAdd(&a.inst_spawn[ii], 1);
     }
     a.flag[i] = f;
   }
@@ -335,10 +327,10 @@ __global__ void __launch_bounds__(kBlock) k_spawn(TopoArgs a, const uint32_t *ui
   wrap_and_key(I, m, i, a.keys);
 }
 
-void launch_buffer_update(const TopoArgs &a, int max_n, cudaStream_t st) {
+void launch_buffer_update(const TopoArgs &a, int max_n, int flags_done, cudaStream_t st) {
   int g = (max_n + kBlock - 1) / kBlock;
   if (g < 1) g = 1;
-  k_flags<<<g, kBlock, 0, st>>>(a);
+  if (!flags_done) k_flags<<<g, kBlock, 0, st>>>(a);
   // uid bases live after the per-instance spawn counters
   uint32_t *uid_base = reinterpret_cast<uint32_t *>(a.inst_spawn + a.ninst);
   k_spawn_scan<<<1, 1024, 0, st>>>(a, g, uid_base);
