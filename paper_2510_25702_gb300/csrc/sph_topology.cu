@@ -203,10 +203,18 @@ __global__ void __launch_bounds__(1024) k_spawn_scan(TopoArgs a, int nblocks, ui
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int base = 0; base < nblocks; base += 1024) {
-    int i = base + threadIdx.x;
-    int32_t v = i < nblocks ? a.block_cnt[i] : 0;
-    int32_t x = v;
+  // four consecutive counts per thread: up to 4096 blocks in one pass, their
+  // loads in flight together
+  constexpr int V = 4;
+  for (int base = 0; base < nblocks; base += 1024 * V) {
+    const int i0 = base + threadIdx.x * V;
+    int32_t v[V], sum = 0;
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      v[q] = i0 + q < nblocks ? a.block_cnt[i0 + q] : 0;
+      sum += v[q];
+    }
+    int32_t x = sum;
     for (int o = 1; o < 32; o <<= 1) {
       int32_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
@@ -222,35 +230,64 @@ __global__ void __launch_bounds__(1024) k_spawn_scan(TopoArgs a, int nblocks, ui
       ws[lane] = s;
     }
     __syncthreads();
-    int32_t excl = carry + (warp > 0 ? ws[warp - 1] : 0) + x - v;
-    if (i < nblocks) a.block_cnt[i] = excl;
+    int32_t excl = carry + (warp > 0 ? ws[warp - 1] : 0) + x - sum;
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      if (i0 + q < nblocks) a.block_cnt[i0 + q] = excl;
+      excl += v[q];
+    }
     __syncthreads();
-    if (threadIdx.x == 1023) carry = excl + v;
+    if (threadIdx.x == 1023) carry = excl;
+    __syncthreads();
+  }
+  const int32_t total = carry;
+  const int32_t n = a.cnt->n_live;
+  const int over = (int64_t)n + total > a.capacity;
+  // per-instance uid bases: copy number r (global rank) of instance ii gets
+  // uid next_uid[ii] + (r - first global rank of ii); an exclusive scan of
+  // the per-instance copy counts, by the whole block
+  __syncthreads();
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < a.ninst; base += 1024) {
+    const int ii = base + threadIdx.x;
+    const int32_t c = ii < a.ninst ? a.inst_spawn[ii] : 0;
+    int32_t x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int32_t t = ws[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      ws[lane] = t;
+    }
+    __syncthreads();
+    const int32_t run = carry + (warp > 0 ? ws[warp - 1] : 0) + x - c;
+    if (ii < a.ninst) {
+      uid_base[ii] = a.next_uid[ii] - (uint32_t)run;
+      if (!over) a.next_uid[ii] += (uint32_t)c;
+      a.inst_spawn[ii] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = run + c;
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    int32_t total = carry;
-    int32_t n = a.cnt->n_live;
-    int over = (int64_t)n + total > a.capacity;
     a.cnt->overflow = over;
     if (over) set_status(&a.cnt->status, SPH_ERR_CAPACITY);
-    int32_t S = over ? 0 : total;
+    const int32_t S = over ? 0 : total;
     a.cnt->n_spawn = S;
     a.cnt->m_pending = n + S;
     a.cnt->n_del_step = 0;
     a.cnt->spawned += (unsigned long long)S;
     a.cnt->spawn_step = a.cnt->step;
     a.cnt->step += 1;
-    // per-instance uid bases: copy number r (global rank) of instance ii gets
-    // uid next_uid[ii] + (r - first global rank of ii)
-    int32_t run = 0;
-    for (int ii = 0; ii < a.ninst; ++ii) {
-      int32_t c = a.inst_spawn[ii];
-      uid_base[ii] = a.next_uid[ii] - (uint32_t)run;
-      if (!over) a.next_uid[ii] += (uint32_t)c;
-      run += c;
-      a.inst_spawn[ii] = 0;
-    }
   }
 }
 
