@@ -700,6 +700,12 @@ int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *
     return 0;
   };
   int rc = 0;
+  // z components of both master copies over the whole capacity: 0 in 2D,
+  // where nothing moves them (the permute skips them)
+  for (int q = 0; q < 2; ++q) {
+    rc |= cudaMemset(c->M[q].x[2], 0, sizeof(double) * (size_t)cap) != cudaSuccess;
+    rc |= cudaMemset(c->M[q].v[2], 0, sizeof(double) * (size_t)cap) != cudaSuccess;
+  }
   Masters &M = c->M[0];
   for (int a = 0; a < 3 && !rc; ++a) {
     rc |= up(M.x[a], X[a].data(), sizeof(double) * n_total);
@@ -1012,6 +1018,7 @@ static void enqueue_topology(sph_ctx *c) {
   t.sorted_vals = vs;
   t.sorted_keys = ks;
   t.off = c->off;
+  t.carry_p = c->kinematic;
   ev = c->prof_begin(2);
   launch_permute(t, (int)c->cap, c->prec, c->stream, c->packs());
   c->prof_end(ev);

@@ -451,6 +451,7 @@ struct TopoArgs {
   const uint32_t *sorted_vals;
   const uint32_t *sorted_keys;  // permute: keys in sorted order, for the cell offsets
   uint32_t *off;                // permute: cell offsets out (NULL: not written)
+  int32_t carry_p;              // permute: move the pressure master (kinematic stepping)
   Counters *cnt;
   unsigned long long *v2max, *nutmax;  // per instance
   uint32_t *next_uid;                  // per instance

@@ -15,14 +15,78 @@ namespace sphk {
 // ------------------------------------------------------------------------
 // permute + label + time-step maxima
 // ------------------------------------------------------------------------
-__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *slot, double v) {
-  // non-negative doubles order like their bit patterns
-  atomicMax(slot, (unsigned long long)__double_as_longlong(v));
-}
 
+// gather of particle t (source slot sorted_vals[t]) into cell order, its
+// label, its advection record; returns |v|^2 and nu_t (as the bit patterns
+// of non-negative doubles, which order like the values) and its instance
 template <typename R>
-__device__ __forceinline__ void permute_one(const TopoArgs &a, const Packs<R> &pk, int t, int s_ii,
-                                            unsigned long long *s_v2, unsigned long long *s_nu);
+__device__ __forceinline__ int permute_one(const TopoArgs &a, const Packs<R> &pk, int t, unsigned long long *v2_out,
+                                           unsigned long long *nu_out) {
+  const int s = (int)a.sorted_vals[t];
+  const Masters S = a.src, D = a.dst;
+  const int ii = S.inst[s];
+  const InstDev &I = a.inst[ii];
+  const bool d3 = I.dim == 3;
+  // in 2D the z components of both master copies stay 0 (set at creation,
+  // written as 0 by sph_write_fields) and are not moved
+  double x = S.x[0][s], y = S.x[1][s], z = d3 ? S.x[2][s] : 0.0;
+  double vx = S.v[0][s], vy = S.v[1][s], vz = d3 ? S.v[2][s] : 0.0;
+  double rho = S.rho[s], mass = S.mass[s];
+  D.x[0][t] = x;
+  D.x[1][t] = y;
+  D.v[0][t] = vx;
+  D.v[1][t] = vy;
+  if (d3) {
+    D.x[2][t] = z;
+    D.v[2][t] = vz;
+  }
+  D.rho[t] = rho;
+  D.mass[t] = mass;
+  D.drho[t] = S.drho[s];
+  // the pressure master is rewritten by the advection or continuity sweep
+  // of every step before anything reads it; only kinematic stepping keeps it
+  if (a.carry_p) D.p[t] = S.p[s];
+  double k = S.k[s], eps = S.eps[s], nut = S.nut[s];
+  D.k[t] = k;
+  D.eps[t] = eps;
+  D.nut[t] = nut;
+  D.uid[t] = S.uid[s];
+  D.inst[t] = (uint16_t)ii;
+  int32_t lab = S.label[s];
+  const float xf = f64_to_f32(x), yf = f64_to_f32(y), zf = f64_to_f32(z);
+  for (int b = 0; b < I.nbuf; ++b) {
+    const BufDev &B = a.buf[I.buf0 + b];
+    const float ex = xf - B.cen[0], ey = yf - B.cen[1], ez = zf - B.cen[2];
+    if (ex * ex + ey * ey + ez * ez > B.rad2) continue;  // far from the box
+    if (box_contains(B, I.dim, x, y, z)) lab = B.local_id + 1;
+  }
+  D.label[t] = lab;
+  // advection-sweep record of this particle
+  const R V = to_R<R>(mass) / to_R<R>(rho);
+  const R vxr = to_R<R>(vx), vyr = to_R<R>(vy);
+  if (!d3) {
+    pk.adv[2 * (size_t)t] = V4<R>{to_R<R>(x), to_R<R>(y), V, vxr};
+    pk.adv[2 * (size_t)t + 1] = V4<R>{vyr, to_R<R>(k), to_R<R>(eps), to_R<R>(nut)};
+  } else {
+    pk.adv[3 * (size_t)t] = V4<R>{to_R<R>(x), to_R<R>(y), to_R<R>(z), V};
+    pk.adv[3 * (size_t)t + 1] = V4<R>{vxr, vyr, to_R<R>(vz), to_R<R>(k)};
+    pk.adv[3 * (size_t)t + 2] = V4<R>{to_R<R>(eps), to_R<R>(nut), (R)0, (R)0};
+  }
+  // |v|^2 with the plain left-to-right sum (in the sweep precision: the
+  // FP64 form keeps the exact FP64 maximum), nu_t
+  double v2;
+  if (sizeof(R) == 8) {
+    v2 = dmul(vx, vx);
+    v2 = dadd(v2, dmul(vy, vy));
+    if (d3) v2 = dadd(v2, dmul(vz, vz));
+  } else {
+    const float fx = f64_to_f32(vx), fy = f64_to_f32(vy), fz = f64_to_f32(vz);
+    v2 = f32_to_f64(fx * fx + fy * fy + (d3 ? fz * fz : 0.0f));
+  }
+  *v2_out = (unsigned long long)__double_as_longlong(v2);
+  *nu_out = I.rans ? (unsigned long long)__double_as_longlong(nut) : 0ull;
+  return ii;
+}
 
 // cell offsets of the sorted keys: off[c] = first slot t whose key is >= c,
 // for c in [0, sentinel]; slot t writes the cells after its predecessor's key
@@ -49,9 +113,10 @@ __global__ void __launch_bounds__(kBlock) k_permute(TopoArgs a, Packs<R> pk) {
   if (a.cnt->status) return;
   const int n = a.cnt->n_live;
   if (a.off) cell_offsets_at(a, t, n);
-  // time-step maxima are reduced in shared memory for the instance of the
-  // block's first particle (particles are instance-sorted, so almost every
-  // block has one) and go straight to global memory otherwise
+  // time-step maxima: reduced over the warp, then the block, for the
+  // instance of the block's first particle (particles are instance-sorted,
+  // so almost every block has one); other instances go straight to global
+  // memory
   __shared__ int s_ii;
   __shared__ unsigned long long s_v2, s_nu;
   const int base = blockIdx.x * blockDim.x;
@@ -61,77 +126,30 @@ __global__ void __launch_bounds__(kBlock) k_permute(TopoArgs a, Packs<R> pk) {
     s_nu = 0ull;
   }
   __syncthreads();
-  if (t < n) permute_one<R>(a, pk, t, s_ii, &s_v2, &s_nu);
+  unsigned long long v2 = 0ull, nu = 0ull;
+  int ii = -1;
+  if (t < n) ii = permute_one<R>(a, pk, t, &v2, &nu);
+  const bool mine = ii == s_ii;
+  unsigned long long w2 = mine ? v2 : 0ull, wn = mine ? nu : 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y2 = __shfl_xor_sync(0xffffffffu, w2, o);
+    const unsigned long long yn = __shfl_xor_sync(0xffffffffu, wn, o);
+    w2 = y2 > w2 ? y2 : w2;
+    wn = yn > wn ? yn : wn;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&s_v2, w2);
+    atomicMax(&s_nu, wn);
+  }
+  if (ii >= 0 && !mine) {
+    atomicMax(&a.v2max[ii], v2);
+    atomicMax(&a.nutmax[ii], nu);
+  }
   __syncthreads();
   if (threadIdx.x == 0 && s_ii >= 0) {
     atomicMax(&a.v2max[s_ii], s_v2);
     atomicMax(&a.nutmax[s_ii], s_nu);
-  }
-}
-
-template <typename R>
-__device__ __forceinline__ void permute_one(const TopoArgs &a, const Packs<R> &pk, int t, int s_ii,
-                                            unsigned long long *s_v2, unsigned long long *s_nu) {
-  const int s = (int)a.sorted_vals[t];
-  const Masters S = a.src, D = a.dst;
-  const int ii = S.inst[s];
-  const InstDev &I = a.inst[ii];
-  double x = S.x[0][s], y = S.x[1][s], z = S.x[2][s];
-  double vx = S.v[0][s], vy = S.v[1][s], vz = S.v[2][s];
-  double rho = S.rho[s], mass = S.mass[s];
-  D.x[0][t] = x;
-  D.x[1][t] = y;
-  D.x[2][t] = z;
-  D.v[0][t] = vx;
-  D.v[1][t] = vy;
-  D.v[2][t] = vz;
-  D.rho[t] = rho;
-  D.mass[t] = mass;
-  D.drho[t] = S.drho[s];
-  D.p[t] = S.p[s];
-  double k = S.k[s], eps = S.eps[s], nut = S.nut[s];
-  D.k[t] = k;
-  D.eps[t] = eps;
-  D.nut[t] = nut;
-  D.uid[t] = S.uid[s];
-  D.inst[t] = (uint16_t)ii;
-  int32_t lab = S.label[s];
-  const float xf = f64_to_f32(x), yf = f64_to_f32(y), zf = f64_to_f32(z);
-  for (int b = 0; b < I.nbuf; ++b) {
-    const BufDev &B = a.buf[I.buf0 + b];
-    const float ex = xf - B.cen[0], ey = yf - B.cen[1], ez = zf - B.cen[2];
-    if (ex * ex + ey * ey + ez * ez > B.rad2) continue;  // far from the box
-    if (box_contains(B, I.dim, x, y, z)) lab = B.local_id + 1;
-  }
-  D.label[t] = lab;
-  // advection-sweep record of this particle
-  const R V = to_R<R>(mass) / to_R<R>(rho);
-  const R vxr = to_R<R>(vx), vyr = to_R<R>(vy);
-  if (I.dim == 2) {
-    pk.adv[2 * (size_t)t] = V4<R>{to_R<R>(x), to_R<R>(y), V, vxr};
-    pk.adv[2 * (size_t)t + 1] = V4<R>{vyr, to_R<R>(k), to_R<R>(eps), to_R<R>(nut)};
-  } else {
-    pk.adv[3 * (size_t)t] = V4<R>{to_R<R>(x), to_R<R>(y), to_R<R>(z), V};
-    pk.adv[3 * (size_t)t + 1] = V4<R>{vxr, vyr, to_R<R>(vz), to_R<R>(k)};
-    pk.adv[3 * (size_t)t + 2] = V4<R>{to_R<R>(eps), to_R<R>(nut), (R)0, (R)0};
-  }
-  // |v|^2 with the plain left-to-right sum (in the sweep precision: the
-  // FP64 form keeps the exact FP64 maximum), nu_t
-  double v2;
-  if (sizeof(R) == 8) {
-    v2 = dmul(vx, vx);
-    v2 = dadd(v2, dmul(vy, vy));
-    if (I.dim == 3) v2 = dadd(v2, dmul(vz, vz));
-  } else {
-    const float fx = f64_to_f32(vx), fy = f64_to_f32(vy), fz = f64_to_f32(vz);
-    v2 = f32_to_f64(fx * fx + fy * fy + (I.dim == 3 ? fz * fz : 0.0f));
-  }
-  if (ii == s_ii) {
-    atomicMax(s_v2, (unsigned long long)__double_as_longlong(v2));
-    if (I.rans) atomicMax(s_nu, (unsigned long long)__double_as_longlong(nut));
-  } else {
-    atomic_max_nonneg(&a.v2max[ii], v2);
-    if (I.rans) atomic_max_nonneg(&a.nutmax[ii], nut);
   }
 }
 
