@@ -342,6 +342,18 @@ int sph_adjoint_release(sph_ctx *ctx);
    Test and debug aid; re-sorts the particles by cell. */
 int sph_debug_pairs(sph_ctx *ctx, int64_t *out, int64_t max, int64_t *count);
 
+/* Total mass and momentum of every instance, summed in FP64 on the GPU
+   over the live particles (deleted rows excluded, copies of the last buffer
+   update included) in an order that does not depend on timing, so two
+   calls on the same state agree bit for bit.  mass: host [n_instances],
+   momentum: host [n_instances][3] (z = 0 in 2D); either may be NULL.  The
+   mass budget of the buffers (Sec. 2.4.2, 2.4.3: copies enter with their
+   parent's mass, deleted particles leave with theirs) can be checked with
+   it.  The first call allocates the reduction buffers (a few KB per
+   instance).  Synchronises.  Errors: SPH_ERR_ARG, SPH_ERR_ALLOC,
+   SPH_ERR_CUDA. */
+int sph_reduce_mass_momentum(sph_ctx *ctx, double *mass, double *momentum);
+
 /* Test aid (no counterpart in the paper): the binary64 -> binary32 and
    binary32 -> binary64 conversions that the FP32 form performs with integer
    operations instead of the conversion instructions (which issue on the

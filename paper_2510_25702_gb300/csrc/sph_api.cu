@@ -94,6 +94,7 @@ struct sph_ctx {
   CellSortPlan cs_plan{};
   uint32_t *cs_scratch = nullptr;  // cell_sort_words(cs_plan) words
   GridBarrier *gbar = nullptr;     // barrier words of the sub-step launch
+  double *red = nullptr;           // mass / momentum reduction buffers (first use)
   uint32_t *sorted_keys = nullptr, *sorted_vals = nullptr;
   NbrList nl{};
   // stage timing (CUDA event pairs on the context's stream)
@@ -2012,5 +2013,98 @@ extern "C" int sph_debug_convert(const double *in64, float *out32, const float *
   if (e == cudaSuccess && in32) e = cudaMemcpy(out64, d_out64, b8, cudaMemcpyDeviceToHost);
   cudaFree(d);
   if (e != cudaSuccess) return fail(SPH_ERR_CUDA, cudaGetErrorString(e));
+  return SPH_OK;
+}
+
+// ------------------------------------------------------------------------
+// FP64 mass and momentum of every instance (deterministic order)
+// ------------------------------------------------------------------------
+namespace {
+constexpr int kRedSlices = 32;   // blocks per instance
+constexpr int kRedThreads = 256;
+
+// first index in [lo, hi) whose instance is >= q (instances non-decreasing
+// there)
+__device__ int inst_lower_bound(const uint16_t *inst, int lo, int hi, int q) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((int)inst[mid] < q)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// block (q, s): slice s of instance q's rows, which are one run in
+// [0, n_live) (the sorted particles) and one in [n_live, m_pending) (the
+// copies appended by the last buffer update); deleted rows carry the
+// sentinel key.  Each thread sums a fixed strided subset, the block sums
+// the threads in a fixed tree: the result does not depend on timing.
+__global__ void __launch_bounds__(kRedThreads) k_reduce_partial(Masters m, const uint32_t *keys, uint32_t sentinel,
+                                                                 const Counters *cnt, int dim, double *partial) {
+  const int q = blockIdx.x / kRedSlices, sl = blockIdx.x % kRedSlices;
+  const int n1 = cnt->n_live, n2 = cnt->m_pending;
+  __shared__ int s_r[4];
+  if (threadIdx.x == 0) {
+    s_r[0] = inst_lower_bound(m.inst, 0, n1, q);
+    s_r[1] = inst_lower_bound(m.inst, s_r[0], n1, q + 1);
+    s_r[2] = inst_lower_bound(m.inst, n1, n2, q);
+    s_r[3] = inst_lower_bound(m.inst, s_r[2], n2, q + 1);
+  }
+  __syncthreads();
+  const int a0 = s_r[0], la = s_r[1] - s_r[0], b0 = s_r[2], L = la + (s_r[3] - s_r[2]);
+  const int64_t k0 = (int64_t)L * sl / kRedSlices, k1 = (int64_t)L * (sl + 1) / kRedSlices;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += kRedThreads) {
+    const int i = k < la ? a0 + (int)k : b0 + (int)(k - la);
+    if (keys[i] == sentinel) continue;
+    const double mi = m.mass[i];
+    acc[0] = sphk::dadd(acc[0], mi);
+    for (int d = 0; d < dim; ++d) acc[1 + d] = sphk::dadd(acc[1 + d], sphk::dmul(mi, m.v[d][i]));
+  }
+  __shared__ double red[4][kRedThreads];
+  for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = sphk::dadd(red[c][threadIdx.x], red[c][threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 4; ++c) partial[(size_t)blockIdx.x * 4 + c] = red[c][0];
+}
+
+__global__ void k_reduce_final(const double *partial, int ninst, double *out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ninst) return;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int sl = 0; sl < kRedSlices; ++sl)
+    for (int c = 0; c < 4; ++c) acc[c] = sphk::dadd(acc[c], partial[((size_t)q * kRedSlices + sl) * 4 + c]);
+  for (int c = 0; c < 4; ++c) out[(size_t)q * 4 + c] = acc[c];
+}
+}  // namespace
+
+extern "C" int sph_reduce_mass_momentum(sph_ctx *c, double *mass, double *momentum) {
+  if (!c || (!mass && !momentum)) return fail(SPH_ERR_ARG, "NULL argument");
+  if (!c->red) {
+    // partial sums [ninst * slices][4] and results [ninst][4], owned by the
+    // context from the first call on
+    c->red = (double *)c->dalloc(sizeof(double) * 4 * ((size_t)c->ninst * kRedSlices + c->ninst));
+    if (!c->red) return fail(SPH_ERR_ALLOC, "reduction buffers");
+  }
+  double *partial = c->red, *res = c->red + 4 * (size_t)c->ninst * kRedSlices;
+  k_reduce_partial<<<c->ninst * kRedSlices, kRedThreads, 0, c->stream>>>(c->M[c->cur], c->K[0], c->ncell, c->cnt,
+                                                                         c->dim, partial);
+  k_reduce_final<<<(c->ninst + 127) / 128, 128, 0, c->stream>>>(partial, c->ninst, res);
+  CUDA_TRY(cudaGetLastError());
+  std::vector<double> h(4 * (size_t)c->ninst);
+  CUDA_TRY(cudaMemcpyAsync(h.data(), res, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  for (int q = 0; q < c->ninst; ++q) {
+    if (mass) mass[q] = h[4 * (size_t)q];
+    if (momentum)
+      for (int d = 0; d < 3; ++d) momentum[3 * (size_t)q + d] = h[4 * (size_t)q + 1 + d];
+  }
   return SPH_OK;
 }

@@ -103,7 +103,8 @@ EXPORTS = ("sph_create", "sph_add_buffer", "sph_set_profile", "sph_step", "sph_r
            "sph_last_error", "sph_abi_version", "sph_set_profiling", "sph_get_stage_times", "sph_stage_name",
            "sph_cell_sort_noalloc", "sph_set_graph", "sph_set_launch", "sph_get_launch", "sph_autotune",
            "sph_save_state", "sph_restore_state", "sph_drop_state", "sph_adjoint_forward",
-           "sph_adjoint_backward", "sph_adjoint_release", "sph_debug_convert", "sph_step_async")
+           "sph_adjoint_backward", "sph_adjoint_release", "sph_debug_convert", "sph_step_async",
+           "sph_reduce_mass_momentum")
 NOALLOC_MAX_POINTS = 1 << 19
 N_STAGES = 10
 
@@ -127,6 +128,7 @@ def lib():
         L.sph_set_profile.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_int32]
         L.sph_step.argtypes = [vp, C.c_int32, C.POINTER(C.c_double)]
         L.sph_step_async.argtypes = [vp, C.c_int32]
+        L.sph_reduce_mass_momentum.argtypes = [vp, vp, vp]
         L.sph_read_fields.argtypes = [vp, C.c_uint32, C.POINTER(vp), C.c_int32, C.POINTER(C.c_int64)]
         L.sph_write_fields.argtypes = [vp, C.c_uint32, C.POINTER(vp), C.c_int32, C.c_int64]
         L.sph_get_stats.argtypes = [vp, C.POINTER(Stats)]
@@ -300,6 +302,13 @@ class Simulation:
     def step_async(self, nsteps: int = 1):
         """Enqueue steps without waiting; stats()["status"] reports device errors."""
         _check(lib().sph_step_async(self.ctx, int(nsteps)), "sph_step_async")
+
+    def mass_momentum(self):
+        """FP64 total mass [n_instances] and momentum [n_instances][3]."""
+        m = np.zeros(len(self.cases), np.float64)
+        p = np.zeros((len(self.cases), 3), np.float64)
+        _check(lib().sph_reduce_mass_momentum(self.ctx, m.ctypes.data, p.ctypes.data), "sph_reduce_mass_momentum")
+        return m, p
 
     def step_rc(self, nsteps: int = 1) -> int:
         """sph_step's return code (no exception)."""

@@ -229,6 +229,39 @@ def test_nonfinite_state_is_reported(sph):
     assert sim.step_rc(1) == -4
 
 
+def test_fp64_mass_momentum_reduction(sph, orc):
+    """sph_reduce_mass_momentum (FP64, fixed summation order): equal to the
+    oracle's totals after a step within the field tolerance, the same bits on
+    a repeated call, and a mass budget that closes exactly over steps with
+    injection and deletion (Sec. 2.4.2, 2.4.3: copies carry their parent's
+    mass, deleted particles take theirs away; all masses are equal here)."""
+    case = cases.poiseuille_channel(length=1.0, height=0.5)
+    case.vel[:, 0] = 0.2
+    sim = sph.Simulation(case, precision="fp64")
+    m0, p0 = sim.mass_momentum()
+    assert m0[0] == pytest.approx(case.mass.sum(), rel=1e-13)
+    sim.step(1)
+    o = orc.OracleSim(case)
+    o.step(1)
+    f = o.fields()
+    m1, p1 = sim.mass_momentum()
+    m1b, p1b = sim.mass_momentum()
+    assert np.array_equal(m1, m1b) and np.array_equal(p1, p1b)
+    assert rel_l2(m1, [f["mass"].sum()]) < 1e-13
+    mom = (f["mass"][:, None] * f["vel"]).sum(0)
+    assert rel_l2(p1[0], mom) < TOL64
+    st0 = sim.stats()
+    sim.step(12)
+    st1 = sim.stats()
+    m2, _ = sim.mass_momentum()
+    net = (st1["spawned"] - st0["spawned"]) - (st1["deleted"] - st0["deleted"])
+    assert st1["spawned"] > st0["spawned"] and st1["deleted"] > st0["deleted"]
+    mp = float(case.mass[0])
+    assert np.all(case.mass == mp)
+    assert m2[0] - m1[0] == pytest.approx(net * mp, abs=1e-12 * m1[0])
+    assert m2[0] == pytest.approx(sim.count() * mp, rel=1e-13)
+
+
 def test_async_stepping_matches_and_reports_status(sph):
     """sph_step_async + sph_get_stats (one wait per step, profiles staged
     in pinned memory) give the same state as sph_step, bit for bit, and the
