@@ -96,7 +96,25 @@ typedef struct sph_config {
   double dt_ad_fixed;
   double gravity[3];
   double domain_lo[3], domain_hi[3];
+  int32_t obc;        /* SPH_OBC_*: open-boundary treatment (0 = the paper's) */
+  int32_t reserved;
 } sph_config;
+
+/* sph_config.obc: the open-boundary treatments compared in Sec. 4.1 (Table
+   of the four cases), for ablation.  IMPROVED (case 4, default): B_i with
+   the mirror support at pressure-buffer particles, B^_j = B_i at buffer
+   neighbours, compensation (2 p_ob / rho_i) B_i sum_j V_j grad W (final Eq.
+   of Sec. 3.3).  VIPO (case 1): no kernel correction (B = I).  VIPO_RKGC
+   (case 2): B from the truncated support, own B_j at buffer neighbours,
+   compensation without B_i.  VIPO_RKGC_MIRROR (case 3): as IMPROVED but the
+   compensation without B_i.  MINIMAL_MIRROR: as IMPROVED but B_i from the
+   truncated support (the literal reading of B_k = B_i alone).  Adjoint
+   windows take IMPROVED only. */
+#define SPH_OBC_IMPROVED 0
+#define SPH_OBC_VIPO 1
+#define SPH_OBC_VIPO_RKGC 2
+#define SPH_OBC_VIPO_RKGC_MIRROR 3
+#define SPH_OBC_MINIMAL_MIRROR 4
 
 /* Initial particles of one instance.  Pointers are host memory when
    on_device == 0, device memory of the context's GPU when 1.  k, eps, uid

@@ -47,7 +47,7 @@ class OrcConfig(C.Structure):
         ("hi", C.c_double * 3), ("periodic", C.c_int * 3), ("seed", C.c_uint32),
         ("gen_offset", C.c_double), ("id_check", C.c_int), ("contain_check", C.c_int),
         ("mirror_B", C.c_int), ("compensation", C.c_int), ("neighbor_mode", C.c_int),
-        ("rkgc", C.c_int), ("freeze_turb", C.c_int),
+        ("rkgc", C.c_int), ("freeze_turb", C.c_int), ("comp_B", C.c_int), ("bhat_buffer", C.c_int),
     ]
 
 
@@ -133,6 +133,17 @@ def _check(rc: int, what: str):
         raise OracleError(f"{what} returned {rc}")
 
 
+# (rkgc, mirror_B, comp_B, bhat_buffer) of the open-boundary treatments
+# compared in Sec. 4.1 (Table of the four cases): 1 the original VIPO (no
+# kernel correction), 2 VIPO with the correction applied directly (truncated
+# support, own B_j at buffer neighbours), 3 VIPO with the corrected RKGC
+# (mirror support and B_k = B_i, compensation without B_i), 4 the improved
+# VIPO (the default); "minimal_mirror" is case 4 with B_i from the truncated
+# support (B_k = B_i and the corrected compensation only).
+OBC_SWITCHES = {"improved": None, "vipo": (0, 0, 0, 0), "vipo_rkgc": (1, 0, 0, 0),
+                "vipo_rkgc_mirror": (1, 1, 0, 1), "minimal_mirror": (1, 0, 1, 1)}
+
+
 class OracleSim:
     """State of the FP64 oracle for one case.
 
@@ -143,7 +154,8 @@ class OracleSim:
 
     def __init__(self, case, capacity: Optional[int] = None, neighbor_mode: int = 1,
                  gen_offset: float = 0.5, id_check: int = 1, contain_check: int = 1,
-                 mirror_B: int = 1, compensation: int = 1, rkgc: int = 1, freeze_turb: int = 0):
+                 mirror_B: int = 1, compensation: int = 1, rkgc: int = 1, freeze_turb: int = 0,
+                 comp_B: int = 1, bhat_buffer: int = 1):
         self.case = case
         cap = int(capacity or case.capacity or case.n + 16)
         n, nw = case.n, case.nw
@@ -168,6 +180,12 @@ class OracleSim:
         c.neighbor_mode = neighbor_mode
         c.rkgc = rkgc
         c.freeze_turb = freeze_turb
+        c.comp_B, c.bhat_buffer = comp_B, bhat_buffer
+        # the open-boundary treatment of the case (Table of Sec. 4.1) sets
+        # the switches it names; the improved scheme keeps the arguments
+        obc = OBC_SWITCHES[getattr(case, "obc", "improved")]
+        if obc is not None:
+            c.rkgc, c.mirror_B, c.comp_B, c.bhat_buffer = obc
 
         z3 = lambda m: np.zeros((m, 3))
         self.a: Dict[str, np.ndarray] = dict(

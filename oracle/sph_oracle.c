@@ -925,6 +925,8 @@ int orc_half1(const orc_config *c, orc_state *s, double dt) {
 /* Pressure-buffer particle (compensated term, final Eq. of Sec. 3.3,   */
 /* survey reading 4):  a_i += (2 p_ob / rho_i) B_i sum_j V_j grad_i W_ij */
 /* over all real and wall neighbours, with p_ob + 2/3 rho_i k_i in RANS. */
+/* The ablation cases of Sec. 4.1 drop B_i there (comp_B = 0) or take   */
+/* B^_j = B_j at buffer neighbours (bhat_buffer = 0).                   */
 /* ------------------------------------------------------------------ */
 static double p_eff(const orc_config *c, const orc_state *s, int64_t i) {
   return c->rans ? s->p[i] + (2.0 / 3.0) * s->rho[i] * s->k[i] : s->p[i];
@@ -955,7 +957,7 @@ static int orc_momentum_impl(const orc_config *c, orc_state *s, const nblist *Lp
       } else {
         V = vol_of(s, j);
         pj = p_eff(c, s, j);
-        Bj = is_pressure_buffer(s, s->label[j]) ? Bi : &s->B[9 * j];
+        Bj = (c->bhat_buffer && is_pressure_buffer(s, s->label[j])) ? Bi : &s->B[9 * j];
       }
       double bj[3], bi[3];
       matvec(dim, Bj, G.gw, bj);
@@ -968,8 +970,8 @@ static int orc_momentum_impl(const orc_config *c, orc_state *s, const nblist *Lp
     if (c->compensation && is_pressure_buffer(s, s->label[i])) {
       double pob = s->buf[s->label[i] - 1].p_ob;
       if (c->rans) pob += (2.0 / 3.0) * s->rho[i] * s->k[i];
-      double bc[3];
-      matvec(dim, Bi, C, bc);
+      double bc[3] = {C[0], C[1], C[2]};
+      if (c->comp_B) matvec(dim, Bi, C, bc);
       for (int a = 0; a < dim; ++a) acc[a] += 2.0 * pob / s->rho[i] * bc[a];
     }
   }

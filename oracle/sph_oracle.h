@@ -69,6 +69,10 @@ typedef struct orc_config {
   int neighbor_mode; /* 0 brute force, 1 cell grid */
   int rkgc;          /* 1: kernel correction B (Sec. 2.2); 0: B = I (Case 1) */
   int freeze_turb;   /* 1: k, eps, nu_t held (frozen-turbulence gradient windows) */
+  int comp_B;        /* compensation multiplied by B_i (final Eq. of Sec. 3.3); */
+                     /* 0: the uncorrected form of the original VIPO (Cases 1-3) */
+  int bhat_buffer;   /* B^_j = B_i for pressure-buffer neighbours (B_k = B_i,   */
+                     /* Sec. 3.3); 0: their own B_j (Case 2)                     */
 } orc_config;
 
 typedef struct orc_buffer {

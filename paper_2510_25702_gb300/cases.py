@@ -78,6 +78,10 @@ class Case:
     n_ac_fixed: int = 1
     seed: int = 0
     capacity: int = 0
+    # open-boundary treatment (Sec. 4.1, Table of the four cases): "improved"
+    # (case 4, the default), "vipo" (1), "vipo_rkgc" (2), "vipo_rkgc_mirror"
+    # (3), or "minimal_mirror" (case 4 with B_i from the truncated support)
+    obc: str = "improved"
 
     @property
     def n(self) -> int:

@@ -312,11 +312,13 @@ static int build_inst(const sph_config &c, InstDev &I, std::string &why) {
     return why = "fixed dt needs dt_ad_fixed > 0 and n_ac_fixed >= 1", -1;
   if (c.dt_mode != SPH_DT_FIXED && !(c.U_ref > 0)) return why = "U_ref must be > 0", -1;
   if (c.dt_mode != SPH_DT_FIXED && !c.rans && !(c.nu_l > 0)) return why = "nu_l must be > 0", -1;
+  if (c.obc < SPH_OBC_IMPROVED || c.obc > SPH_OBC_MINIMAL_MIRROR) return why = "bad obc", -1;
   I.dim = c.dim;
   I.rans = c.rans ? 1 : 0;
   I.dt_mode = c.dt_mode;
   I.n_ac_fixed = c.n_ac_fixed;
   I.kinematic = c.kinematic ? 1 : 0;
+  I.obc = c.obc;
   I.seed = c.seed;
   I.dp = c.dp;
   I.h = c.h;
@@ -1533,8 +1535,10 @@ int sph_adjoint_forward(sph_ctx *c, const sph_adjoint_desc *d, double *J_out) {
   if (d->steps < 1 || d->checkpoint_every < 1) return fail(SPH_ERR_ARG, "steps and checkpoint_every must be >= 1");
   if (d->n_theta < 1 || d->n_theta > SPH_MAX_THETA) return fail(SPH_ERR_ARG, "n_theta must be 1..64");
   if (!(d->slab > 0)) return fail(SPH_ERR_ARG, "slab must be > 0");
-  for (int i = 0; i < c->ninst; ++i)
+  for (int i = 0; i < c->ninst; ++i) {
     if (c->cfg[i].dt_mode != SPH_DT_FIXED) return fail(SPH_ERR_ARG, "differentiated windows need SPH_DT_FIXED");
+    if (c->cfg[i].obc != SPH_OBC_IMPROVED) return fail(SPH_ERR_ARG, "differentiated windows need SPH_OBC_IMPROVED");
+  }
   const auto &bufs = c->bufs[d->instance];
   if (d->profile_buffer < 0 || d->profile_buffer >= (int32_t)bufs.size() ||
       bufs[d->profile_buffer].type != SPH_BUF_VELOCITY)

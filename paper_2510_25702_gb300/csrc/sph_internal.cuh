@@ -47,6 +47,7 @@ struct InstDev {
   uint32_t seed;
   uint32_t cell_base;  // first global cell key of this instance
   uint32_t ncell;
+  int32_t obc;  // SPH_OBC_*: open-boundary treatment (Sec. 4.1 ablation cases)
   double dp, h, rho0, c0, nu_l, eta, U_ref, dt_ad_fixed;
   double g[3], lo[3], hi[3], L[3];
   double cs;       // cell size 2h

@@ -129,7 +129,12 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
 
   const int lab = m.label[i];
   const BufDev *mb = (lab > 0 && lab <= I.nbuf) ? &a.buf[I.buf0 + lab - 1] : nullptr;
-  const bool mirror = mb && mb->type == SPH_BUF_PRESSURE;
+  // pressure-buffer particle: the mirror support completes its A (cases 3
+  // and 4 of the open-boundary ablation), and its neighbours take B^ = B_i
+  // (every case with the condition B_k = B_i)
+  const bool pbuf = mb && mb->type == SPH_BUF_PRESSURE;
+  const bool mirror = pbuf && (I.obc == SPH_OBC_IMPROVED || I.obc == SPH_OBC_VIPO_RKGC_MIRROR);
+  const bool own_B = pbuf && I.obc != SPH_OBC_VIPO && I.obc != SPH_OBC_VIPO_RKGC;
   R mo[3] = {0, 0, 0}, mn[3] = {0, 0, 0};
   if (mirror)
     for (int c = 0; c < 3; ++c) {
@@ -263,7 +268,19 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   // particles of the FP32 form, whose A is close to the full-support
   // lattice value (about 0.97 I), invert in the sweep precision.
   R BR[6] = {(R)0, (R)0, (R)0, (R)0, (R)0, (R)0};
-  if (sizeof(R) == 4 && nw == 0 && lab == 0) {
+  if (I.obc == SPH_OBC_VIPO) {
+    // case 1 of the ablation: no kernel correction
+    BR[0] = BR[1] = (R)1;
+    if (D == 3) BR[2] = (R)1;
+    a.der.B[0][i] = 1.0;
+    a.der.B[1][i] = 1.0;
+    a.der.B[3][i] = 0.0;
+    if (D == 3) {
+      a.der.B[2][i] = 1.0;
+      a.der.B[4][i] = 0.0;
+      a.der.B[5][i] = 0.0;
+    }
+  } else if (sizeof(R) == 4 && nw == 0 && lab == 0) {
     invert_guarded_fast<R, D>(A, BR);
   } else {
     double Ad[6] = {(double)A[0], (double)A[1], 0.0, (double)A[3], 0.0, 0.0};
@@ -286,7 +303,7 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
       }
     }
   }
-  if (sizeof(R) == 4) {
+  if (sizeof(R) == 4 && I.obc != SPH_OBC_VIPO) {
     a.der.B[0][i] = from_R<R>(BR[0]);
     a.der.B[1][i] = from_R<R>(BR[1]);
     a.der.B[3][i] = from_R<R>(BR[3]);
@@ -357,7 +374,7 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   // momentum record; pressure-buffer particles are marked so that their
   // neighbours use their own B (the condition B_k = B_i, Sec. 3.3)
   const R V = Ex<R>::div(to_R<R>(m.mass[i]), to_R<R>(rho));
-  const R bxx = mirror ? (R)-1 : BR[0];
+  const R bxx = own_B ? (R)-1 : BR[0];
   if (D == 2) {
     pk.mom[2 * (size_t)i] = V4<R>{A0.x, A0.y, V, p};
     pk.mom[2 * (size_t)i + 1] = V4<R>{bxx, BR[3], BR[1], kw};
@@ -464,8 +481,10 @@ __device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, 
     if (b.type == SPH_BUF_PRESSURE) {
       R pob = (R)b.p_ob;
       if (rans) pob += (R)(2.0 / 3.0) * (R)rho_i * (R)m.k[i];
-      R bct[3];
-      sym_matvec<R, D>(Bi, Ct, bct);
+      // compensation with B_i (final Eq. of Sec. 3.3), or without it as in
+      // the original VIPO (ablation cases 1-3)
+      R bct[3] = {Ct[0], Ct[1], Ct[2]};
+      if (I.obc == SPH_OBC_IMPROVED || I.obc == SPH_OBC_MINIMAL_MIRROR) sym_matvec<R, D>(Bi, Ct, bct);
 #pragma unroll
       for (int c = 0; c < D; ++c) acc[c] += (R)2 * pob * inv_rho * bct[c];
     }

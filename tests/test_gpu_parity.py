@@ -122,6 +122,23 @@ def test_one_step_fp64(sph, orc, name):
     assert st["dt_ad"] == o.stats["dt_ad"]  # identical state -> identical step
 
 
+@pytest.mark.parametrize("obc", ["vipo", "vipo_rkgc", "vipo_rkgc_mirror", "minimal_mirror"])
+def test_obc_ablation_cases_fp64(sph, orc, obc):
+    """The open-boundary treatments of the Sec. 4.1 ablation (sph_config.obc)
+    against the oracle with the same switches: three steps of the pressure
+    buffer channel, every float field within the FP64 tolerance."""
+    case = cases.poiseuille_channel(length=1.0, height=0.5).replace(obc=obc)
+    case.vel[:, 0] = 0.2
+    sim = sph.Simulation(case, precision="fp64")
+    sim.step(3)
+    o = orc.OracleSim(case)
+    o.step(3)
+    g = sim.read(["uid", "label", "pos", "vel", "rho", "p", "B"])
+    f = o.fields()
+    f["B"] = f["B"].reshape(-1, 9)
+    compare_state(g, f, ["pos", "vel", "rho", "p", "B"], skip_new=g["uid"] >= case.n)
+
+
 def test_trajectory_fp64_channel(sph, orc):
     """Ten steps of the pressure-buffer channel: injection, recycling and
     deletion happen, uids of the copies agree, fields stay within 1e-9."""

@@ -566,3 +566,43 @@ def test_profile_replacement_moves_inlet_velocity(orc):
     y = f["pos"][inlet, 1]
     # linear profile across the width: U = 0.5 at the bottom, 1.5 at the top
     assert np.allclose(f["vel"][inlet, 0], 0.5 + (y - 0.0) / 0.1, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# open-boundary ablation (Sec. 4.1, Table of the four cases)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("obc,consistent", [("improved", True), ("vipo", True), ("minimal_mirror", True),
+                                            ("vipo_rkgc_mirror", False), ("vipo_rkgc", False)])
+def test_obc_cases_uniform_pressure_at_open_face(orc, obc, consistent):
+    """A uniform pressure equal to p_ob has no gradient.  At a pressure buffer
+    whose particles' whole support lies in the buffer, the schemes that treat
+    the internal sum and the open-boundary compensation alike (case 1
+    without correction, case 4 with B_i in both; the minimal-mirror reading
+    too) give zero pressure acceleration; case 3 keeps B_i inside and drops
+    it from the compensation, and case 2 also mixes the neighbours' own B_j,
+    so both leave a residual: the inconsistency Sec. 4.1 reports for them."""
+    n, dp = 25, 0.1
+    c = cases.lattice_block(n, 2, dp=dp)
+    keep = c.pos[:, 0] < 12.0 * dp
+    cut = c.replace(pos=c.pos[keep].copy(), vel=c.vel[keep].copy(), rho=c.rho[keep].copy(),
+                    mass=c.mass[keep].copy(), k=c.k[keep].copy(), eps=c.eps[keep].copy(), obc=obc)
+    p_ob = 0.05
+    cut.buffers = [cases.BufferSpec("pressure", (12.0 * dp, 12.5 * dp, 0.0), cases.frame_2d((-1, 0)),
+                                    length=8 * dp, half=(20 * dp, 0.0), p_ob=p_ob)]
+    o = orc.OracleSim(cut, neighbor_mode=0)
+    o.label()
+    o.bmatrix()
+    o.a["p"][: o.n] = p_ob
+    o.momentum()
+    pos = o.a["pos"][: o.n]
+    lab = o.a["label"][: o.n]
+    x_face = 12.0 * dp - pos[:, 0]  # distance from the open face into the block
+    sel = (lab == 1) & (x_face < 8 * dp - 2 * c.h) & (pos[:, 1] > 3 * c.h) & (pos[:, 1] < n * dp - 3 * c.h)
+    assert sel.sum() >= 20
+    acc = np.abs(o.a["acc_p"][: o.n][sel]).max()
+    scale = 2 * p_ob / c.rho0 * np.abs(o.kernel_gradient_sum()[sel]).max()
+    assert scale > 0
+    if consistent:
+        assert acc < 1e-12 * scale
+    else:
+        assert acc > 1e-3 * scale
