@@ -644,6 +644,18 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
 // ------------------------------------------------------------------------
 // kernels: grid-stride over the live particles
 // ------------------------------------------------------------------------
+// resident 256-thread blocks per SM asked of the FP32 sweeps (registers =
+// 65536 / (256 x blocks)): more warps for their latency-bound gathers where
+// that costs few spills (measured): momentum 2D and continuity at 48, the
+// fused later sub-steps at 48 (2D) or 64 (3D); the FP64 forms and the 3D
+// momentum sweep keep the compiler's count
+template <typename R, int D>
+constexpr int kMomMinBlocks = (sizeof(R) == 4 && D == 2) ? 5 : 1;
+template <typename R, int D>
+constexpr int kContMinBlocks = sizeof(R) == 4 ? 5 : 1;
+template <typename R, int D>
+constexpr int kSubMinBlocks = sizeof(R) == 4 ? (D == 2 ? 5 : 4) : 1;
+
 template <typename R, int D, bool PER>
 __global__ void __launch_bounds__(kMaxBlock) k_list(SweepArgs a, Packs<R> pk) {
   // after a device error (non-finite state, capacity) the state is not
@@ -678,7 +690,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_adv(SweepArgs a, Packs<R> pk) {
 }
 
 template <typename R, int D, bool PER>
-__global__ void __launch_bounds__(kMaxBlock, 5) k_mom(SweepArgs a, Packs<R> pk) {
+__global__ void __launch_bounds__(kMaxBlock, kMomMinBlocks<R, D>) k_mom(SweepArgs a, Packs<R> pk) {
   if (a.sub >= a.cnt->n_ac_all || a.cnt->status) return;  // no instance takes this sub-step
   const int n = a.cnt->n_live;
   const int step = gridDim.x * blockDim.x;
@@ -690,7 +702,7 @@ __global__ void __launch_bounds__(kMaxBlock, 5) k_mom(SweepArgs a, Packs<R> pk) 
 }
 
 template <typename R, int D, bool PER>
-__global__ void __launch_bounds__(kMaxBlock, 5) k_cont(SweepArgs a, Packs<R> pk) {
+__global__ void __launch_bounds__(kMaxBlock, kContMinBlocks<R, D>) k_cont(SweepArgs a, Packs<R> pk) {
   if (a.sub >= a.cnt->n_ac_all || a.cnt->status) return;
   const int n = a.cnt->n_live;
   const int step = gridDim.x * blockDim.x;
@@ -711,7 +723,7 @@ __global__ void __launch_bounds__(kMaxBlock, 5) k_cont(SweepArgs a, Packs<R> pk)
 // that another block set during the launch and leave the barriers unmatched;
 // the work after an error is bounded (fixed lists) and its result unused.
 template <typename R, int D, bool PER>
-__global__ void __launch_bounds__(kMaxBlock) k_substeps(SweepArgs a, Packs<R> pk, GridBarrier *gb) {
+__global__ void __launch_bounds__(kMaxBlock, kSubMinBlocks<R, D>) k_substeps(SweepArgs a, Packs<R> pk, GridBarrier *gb) {
   __shared__ int s_ok;
   const int nac = a.cnt->n_ac_all;
   if (nac <= 1) return;
