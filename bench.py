@@ -376,7 +376,9 @@ def main():
     log(f"autotune {tuned}")
     # timed region: K steps replayed from the two captured CUDA graphs
     sim.set_graph(True)
-    sim.step(3)  # one uncaptured step, then both graphs are captured
+    # one uncaptured step, both graphs captured, then a few replays of each
+    # before the clock starts
+    sim.step(max(10, args.warmup))
     s0 = sim.stats()
     n0 = s0["n"]
     barrier()

@@ -101,6 +101,40 @@ __device__ __forceinline__ R local0(const R o[3], const R n[3], R x, R y, R z) {
   return s;
 }
 
+// The cells of visit_cells (span 1, no periodic axes) without those that
+// cannot hold a point within the cut-off of a particle at offset o (o in
+// [0, cs)^d from its cell's low corner): a row (dy, dz) is left out when
+// its distance from the particle in y and z alone reaches the cut-off, and
+// the row's first or last cell when the distance to that cell's box does.
+// Only the ends of a row's index range move, so the candidates that remain
+// come in the same order.  The test keeps a margin of 1e-3 cs for the FP32
+// offsets: a cell it drops has no point closer than 1.001 cut-offs.
+template <int D, typename F>
+__device__ __forceinline__ void visit_cells_trimmed(const InstDev &I, int cx, int cy, int cz, const float o[3],
+                                                    float cs, const uint32_t *__restrict__ off, F &&f) {
+  const int nx = I.nc[0], ny = I.nc[1];
+  const int nz = (D == 3) ? I.nc[2] : 1;
+  const float far2 = (1.001f * cs) * (1.001f * cs);  // cut-off = cs = 2h
+  const float lx = o[0], rx = cs - o[0];              // distances to the x faces
+  const int a0 = max(cx - 1, 0), a1 = min(cx + 1, nx - 1);
+  for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); ++dz) {
+    const int zz = cz + dz;
+    if (zz < 0 || zz >= nz) continue;
+    const float pz = dz == 0 ? 0.0f : (dz < 0 ? o[2] : cs - o[2]);
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int yy = cy + dy;
+      if (yy < 0 || yy >= ny) continue;
+      const float py = dy == 0 ? 0.0f : (dy < 0 ? o[1] : cs - o[1]);
+      const float b2 = py * py + pz * pz;
+      if (b2 > far2) continue;
+      const int c0 = (a0 < cx && lx * lx + b2 > far2) ? cx : a0;
+      const int c1 = (a1 > cx && rx * rx + b2 > far2) ? cx : a1;
+      const uint32_t row = I.cell_base + ((uint32_t)zz * (uint32_t)ny + (uint32_t)yy) * (uint32_t)nx;
+      f(off[row + c0], off[row + c1 + 1]);
+    }
+  }
+}
+
 // visit the index ranges of the cells within +-span of (cx, cy, cz): the
 // clamped part of each x row is one contiguous range; periodic axes hold at
 // least 2 span + 1 cells (checked at creation), so wrapped coordinates are

@@ -54,6 +54,16 @@ __device__ __forceinline__ int list_one(const SweepArgs &a, const Packs<R> &pk, 
   uint32_t *__restrict__ out = list_of(a.nl, i);
   const int K = a.nl.kmax;
   int nr = 0, nw = 0;
+  // offset of the particle from its cell's low corner (FP32, clamped to the
+  // cell), for dropping cells out of reach
+  const float cs = (float)I.cs;
+  float o[3] = {0.0f, 0.0f, 0.0f};
+  {
+    const float p[3] = {(float)Pi.x, (float)Pi.y, (float)Pi.z};
+    const int cc[3] = {cx, cy, cz};
+#pragma unroll
+    for (int q = 0; q < D; ++q) o[q] = fminf(fmaxf(p[q] - (I.lo_f[q] + (float)cc[q] * cs), 0.0f), cs);
+  }
   // entries are collected four at a time and stored as one 16-byte chunk
   uint4 buf = make_uint4(0u, 0u, 0u, 0u);
   uint4 *__restrict__ out4 = reinterpret_cast<uint4 *>(out);
@@ -62,7 +72,7 @@ __device__ __forceinline__ int list_one(const SweepArgs &a, const Packs<R> &pk, 
     const uint32_t *offs = set == 0 ? a.off : a.woff;
     const V4<R> *recs = set == 0 ? pk.adv : pk.WP;
     const int stride = set == 0 ? RA : 1;
-    visit_cells<D, PER>(I, cx, cy, cz, 1, offs, [&](uint32_t jb, uint32_t je) {
+    auto scan = [&](uint32_t jb, uint32_t je) {
       scan_range<R, D, PER>(g, Pi, recs, stride, jb, je, [&](uint32_t j) {
         const int k = nr + nw;
         buf.x = buf.y;
@@ -75,7 +85,11 @@ __device__ __forceinline__ int list_one(const SweepArgs &a, const Packs<R> &pk, 
         else
           ++nw;
       });
-    });
+    };
+    if (PER)
+      visit_cells<D, PER>(I, cx, cy, cz, 1, offs, scan);
+    else
+      visit_cells_trimmed<D>(I, cx, cy, cz, o, cs, offs, scan);
   }
   {
     // the last, partly filled chunk: its r entries are the newest in buf
