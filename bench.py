@@ -371,7 +371,7 @@ def main():
     tuned = None
     if not args.no_tune:
         # sweep block sizes, cached per (GPU, workload shape) next to the build
-        tuned, hit = sim.autotune(steps=3, cache_path=os.path.join(os.path.dirname(_b.LIB), "autotune.txt"))
+        tuned, hit = sim.autotune(steps=8, cache_path=os.path.join(os.path.dirname(_b.LIB), "autotune.txt"))
         tuned = {"blocks": dict(zip(("list", "adv", "mom", "cont"), tuned)), "from_cache": hit}
     log(f"autotune {tuned}")
     # timed region: K steps replayed from the two captured CUDA graphs

@@ -669,9 +669,12 @@ template <typename R, int D>
 constexpr int kContMinBlocks = sizeof(R) == 4 ? 5 : 1;
 template <typename R, int D>
 constexpr int kSubMinBlocks = sizeof(R) == 4 ? (D == 2 ? 5 : 4) : 1;
+// the FP32 list builder at 48 registers as well (few spills)
+template <typename R, int D>
+constexpr int kListMinBlocks = (sizeof(R) == 4 && D == 3) ? 5 : 0;
 
 template <typename R, int D, bool PER>
-__global__ void __launch_bounds__(kMaxBlock) k_list(SweepArgs a, Packs<R> pk) {
+__global__ void __launch_bounds__(kMaxBlock, kListMinBlocks<R, D>) k_list(SweepArgs a, Packs<R> pk) {
   // after a device error (non-finite state, capacity) the state is not
   // advanced further: non-finite positions would all fall into one edge
   // cell and make the candidate scan quadratic
