@@ -294,10 +294,12 @@ int sph_get_launch(sph_ctx *ctx, int32_t block[4]);
 /* Autotuner of the sweep block sizes (no counterpart in the paper).  Looks
    up the key (GPU name and SM count, dimension, precision, instances, live
    particles, walls, RANS, sub-step bound) in the text file cache_path (may
-   be NULL: no cache); on a miss it saves the state, times each sweep kernel
-   at 64, 128 and 256 threads per block over `steps` advection steps per
-   trial (one more untimed), restores the state, applies the fastest choice
-   and appends "key b_list b_adv b_mom b_cont" to the file.  The state after
+   be NULL: no cache); on a miss it saves the state and, for each sweep in
+   turn (coordinate descent), times `steps` whole advection steps replayed
+   from the step's CUDA graphs with that sweep at 64, 128 and 256 threads per
+   block (three untimed steps before each trial, the state restored before
+   each), applies the fastest choice and appends
+   "key b_list b_adv b_mom b_cont" to the file.  The state after
    the call equals the state before it.  block_out (may be NULL) receives
    the four block sizes; *from_cache (may be NULL) 1 on a cache hit. */
 int sph_autotune(sph_ctx *ctx, int32_t steps, const char *cache_path, int32_t block_out[4],

@@ -1682,16 +1682,17 @@ int sph_autotune(sph_ctx *c, int32_t steps, const char *cache_path, int32_t bloc
   int rc = sph_save_state(c, &slot);
   if (rc) return rc;
   const bool prof = c->prof, graph = c->use_graph;
-  double keep_ms[SPH_N_STAGES];
-  int64_t keep_n[SPH_N_STAGES];
-  memcpy(keep_ms, c->stage_ms, sizeof(keep_ms));
-  memcpy(keep_n, c->stage_n, sizeof(keep_n));
-  const int stage_of[4] = {8, 4, 5, 6};  // profiling stage of each sweep
+  // each trial times whole advection steps as they are normally run, replayed
+  // from the step's CUDA graphs, so that the choice includes how the sweeps
+  // share the GPU with the kernels around them; the sweeps are tuned in turn
+  // (coordinate descent)
   const int cand[3] = {64, 128, 256};
   int32_t best[4];
   for (int q = 0; q < 4; ++q) best[q] = c->blk[q];
-  c->use_graph = false;
-  c->prof = true;
+  c->prof = false;
+  c->use_graph = true;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = fail(SPH_ERR_CUDA, "events");
   for (int q = 0; q < 4 && !rc; ++q) {
     double best_ms = 1e300;
     for (int t = 0; t < 3 && !rc; ++t) {
@@ -1699,24 +1700,29 @@ int sph_autotune(sph_ctx *c, int32_t steps, const char *cache_path, int32_t bloc
       for (int u = 0; u < 4; ++u) trial[u] = best[u];
       trial[q] = cand[t];
       if ((rc = sph_set_launch(c, trial)) || (rc = sph_restore_state(c, slot))) break;
-      enqueue_step(c);  // untimed
+      // untimed: one uncaptured step, then both graphs captured and replayed
+      if ((rc = enqueue_steps(c, 3))) break;
       int32_t st = 0;
       if ((rc = read_status(c, &st))) break;
-      for (int k = 0; k < SPH_N_STAGES; ++k) c->stage_ms[k] = 0, c->stage_n[k] = 0;
-      for (int k = 0; k < steps; ++k) enqueue_step(c);
+      cudaEventRecord(e0, c->stream);
+      if ((rc = enqueue_steps(c, steps))) break;
+      cudaEventRecord(e1, c->stream);
       if ((rc = read_status(c, &st))) break;
-      const int sg = stage_of[q];
-      const double ms = c->stage_n[sg] ? c->stage_ms[sg] / (double)c->stage_n[sg] : 1e300;
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = fail(SPH_ERR_CUDA, "event timing");
+        break;
+      }
       if (ms < best_ms) {
         best_ms = ms;
         best[q] = cand[t];
       }
     }
   }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   c->prof = prof;
   c->use_graph = graph;
-  memcpy(c->stage_ms, keep_ms, sizeof(keep_ms));
-  memcpy(c->stage_n, keep_n, sizeof(keep_n));
   int rc2 = sph_restore_state(c, slot);
   if (!rc) rc = rc2;
   rc2 = sph_drop_state(c, slot);
