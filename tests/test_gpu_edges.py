@@ -1,0 +1,98 @@
+"""Degenerate inputs of the GPU step, through the C ABI: a lone particle (no
+neighbours: B falls back to I, nothing acts on it), an empty instance in a
+batch (zero keys to sort, no cells occupied), and a context whose particles
+are all deleted by an outlet (the live count drops to zero and stepping
+goes on with nothing to do)."""
+import numpy as np
+import pytest
+
+from paper_2510_25702_gb300 import cases
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+def rel_l2(a, b):
+    den = np.linalg.norm(b)
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / (den if den > 0 else 1.0))
+
+
+@pytest.fixture(scope="module")
+def sph():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2510_25702_gb300 import build
+    from paper_2510_25702_gb300 import sph as S
+
+    build.build()
+    return S
+
+
+def test_lone_particle_matches_oracle(sph, orc):
+    case = cases.lattice_block(1, 2)
+    case.vel[0, :2] = (0.3, -0.2)
+    sim = sph.Simulation(case, precision="fp64")
+    sim.step(2)
+    g = sim.read(["uid", "pos", "vel", "rho", "B"])
+    o = orc.OracleSim(case)
+    o.step(2)
+    f = o.fields()
+    assert g["uid"].tolist() == [0]
+    for k in ("pos", "vel", "rho"):
+        assert rel_l2(g[k], f[k]) < TOL64, k
+    assert np.array_equal(g["B"].reshape(-1, 9)[0], np.array([1.0, 0, 0, 0, 1.0, 0, 0, 0, 0]))
+    assert np.allclose(g["vel"][0, :2], (0.3, -0.2), rtol=0, atol=1e-14)
+
+
+def test_empty_instance_in_a_batch(sph):
+    box = cases.periodic_box(n_per_axis=10, dim=2, vel_amp=0.3)
+    empty = cases.lattice_block(0, 2)
+    assert empty.n == 0
+    alone = sph.Simulation(box, precision="fp64")
+    alone.step(3)
+    ref = alone.read(["uid", "pos", "vel", "rho"])
+    for order in ([box, empty], [empty, box]):
+        sim = sph.Simulation(order, precision="fp64")
+        sim.set_graph(True)
+        assert sim.step_rc(3) == 0
+        g = sim.read(["inst", "uid", "pos", "vel", "rho"])
+        q = 0 if order[0] is box else 1
+        assert np.all(g["inst"] == q)
+        for k in ("uid", "pos", "vel", "rho"):
+            assert np.array_equal(g[k], ref[k]), k
+
+
+def test_every_particle_deleted(sph):
+    """Kinematic stepping: the particles are put in the outlet buffer (they
+    take its label), then behind its open face (x'_0 < 0: deleted), after
+    which further steps run on an empty context."""
+    dp = 0.05
+    pos = cases.lattice((12, 20), dp)
+    arr = cases._fluid_arrays(pos, 2, dp, 1.0)
+    outlet = cases.BufferSpec("pressure", (0.6, 0.5, 0.0), cases.frame_2d((-1, 0)), 4 * dp, (0.5, 0.0),
+                              p_ob=0.01)
+    case = cases.Case(name="drain", dim=2, dp=dp, h=1.3 * dp, rho0=1.0, c0=10.0, nu_l=0.01, rans=False,
+                      U_ref=1.0, lo=np.array([-0.5, -0.5, 0]), hi=np.array([1.5, 1.5, 0]), periodic=(0, 0, 0),
+                      wpos=np.zeros((0, 3)), wvel=np.zeros((0, 3)), buffers=[outlet], capacity=400, seed=3,
+                      **arr)
+    sim = sph.Simulation(case, kinematic=True)
+    n = case.n
+    p = sim.read(["pos"])["pos"]
+    p[:, 0] = 0.5 + 0.0005 * (np.arange(n) % 10)  # inside the box: 0.4 < x <= 0.6
+    p[:, 1] = 0.02 + 0.96 * np.arange(n) / n
+    sim.write({"pos": p})
+    assert sim.step_rc(1) == 0
+    assert (sim.read(["label"])["label"] == 1).all()
+    p = sim.read(["pos"])["pos"]
+    p[:, 0] = 0.7  # behind the open face
+    sim.write({"pos": p})
+    assert sim.step_rc(1) == 0
+    assert sim.count() == 0
+    assert sim.stats()["deleted"] == n
+    assert sim.step_rc(3) == 0
+    assert sim.count() == 0
+    assert sim.read(["pos"])["pos"].shape == (0, 3)
+    m, _ = sim.mass_momentum()
+    assert m[0] == 0.0
