@@ -55,6 +55,10 @@ def workload(name: str, seed: int = 2):
         return cases.plane_jet(dp=0.002, seed=seed + 2)
     if name == "mixer_3d":
         return cases.mixer_3d(dp=0.01, seed=seed + 4)
+    if name == "mixer_3d_small":
+        # 951k fluid + 243k wall particles: the 3D sweeps at a size that a
+        # profiler captures quickly, inputs still larger than L2
+        return cases.mixer_3d(dp=0.015, seed=seed + 4)
     raise ValueError(name)
 
 

@@ -159,7 +159,11 @@ typedef struct sph_buffer_desc {
 } sph_buffer_desc;
 
 /* Optional device allocator (e.g. a caching allocator); NULL functions mean
-   cudaMalloc / cudaFree.  stream is a cudaStream_t (NULL = legacy stream). */
+   cudaMalloc / cudaFree.  stream is a cudaStream_t (NULL = legacy stream).
+   Every block returned must start on a 256-byte boundary (as cudaMalloc's
+   do): the sweeps read 32-byte records with single 256-bit loads.  A block
+   that does not is handed back to free and the call fails with
+   SPH_ERR_ALLOC. */
 typedef struct sph_alloc {
   void *(*alloc)(void *user, size_t bytes, void *stream);
   void (*free)(void *user, void *ptr, void *stream);

@@ -8,6 +8,24 @@
 
 namespace sphk {
 
+// A neighbour's two consecutive record 4-vectors.  FP32: one 256-bit load
+// (the 32 bytes start on a 32-byte boundary: record arrays are 256-byte
+// aligned and the record stride is 32 bytes), so that a scattered gather
+// costs one L1 wavefront per lane instead of two.  Not volatile: the
+// address depends on a list entry loaded after any barrier that orders the
+// record's writes.  FP64 records (64 bytes) keep plain vector loads.
+template <typename R>
+__device__ __forceinline__ void ld_rec2(const V4<R> *p, V4<R> &a, V4<R> &b) {
+  a = p[0];
+  b = p[1];
+}
+template <>
+__device__ __forceinline__ void ld_rec2<float>(const V4<float> *p, V4<float> &a, V4<float> &b) {
+  asm("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(p));
+}
+
 template <typename R>
 struct Ex;
 template <>
