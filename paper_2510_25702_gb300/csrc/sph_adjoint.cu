@@ -49,10 +49,6 @@ __device__ __forceinline__ void sym_full(const double s[6], double M[3][3]) {
   M[1][2] = M[2][1] = s[5];
 }
 
-__device__ __forceinline__ void matvec3(const double M[3][3], const double x[3], double y[3]) {
-  for (int a = 0; a < 3; ++a) y[a] = M[a][0] * x[0] + M[a][1] * x[1] + M[a][2] * x[2];
-}
-
 // add the symmetric part of u (x) w to the stored symmetric adjoint
 __device__ __forceinline__ void sym_acc(double s[6], const double u[3], const double w[3], double c) {
   s[0] += c * u[0] * w[0];

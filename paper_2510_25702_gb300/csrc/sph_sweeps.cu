@@ -573,21 +573,22 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
     const uint4 q4 = nxt;
     if (k0 + 4 < nr) nxt = list_chunk(Lst, (k0 >> 2) + 1);
     const uint32_t j4[4] = {q4.x, q4.y, q4.z, q4.w};
+    // all four gathers issued before any is used; entries past the list's
+    // end re-read entry 0 and add nothing
+    V4<R> N0[4], N1[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) ld_rec2<R>(pk.cont + 2 * (size_t)(k0 + c < nr ? j4[c] : j4[0]), N0[c], N1[c]);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      if (k0 + c >= nr) break;
-      const uint32_t j = j4[c];
-      V4<R> N0, N1;
-      ld_rec2<R>(pk.cont + 2 * (size_t)j, N0, N1);
       R d[3];
-      const R rr = pair_vec<R, D, PER>(g, C0, N0, d);
+      const R rr = pair_vec<R, D, PER>(g, C0, N0[c], d);
       R r;
       Ex<R>::len(rr, r);
-      const R FV = kernel_F(g, r) * vol<R, D>(N0);
-      const R vj[3] = {D == 2 ? N1.x : N1.y, D == 2 ? N1.y : N1.z, D == 2 ? (R)0 : N1.w};
-      const R p_j = D == 2 ? N0.w : N1.x;
+      const R FV = kernel_F(g, r) * vol<R, D>(N0[c]);
+      const R vj[3] = {D == 2 ? N1[c].x : N1[c].y, D == 2 ? N1[c].y : N1[c].z, D == 2 ? (R)0 : N1[c].w};
+      const R p_j = D == 2 ? N0[c].w : N1[c].x;
       const R vd = (vi[0] - vj[0]) * d[0] + (vi[1] - vj[1]) * d[1] + (vi[2] - vj[2]) * d[2];
-      sum += (vd + (p_i - p_j) * inv_rc * r) * FV;
+      if (k0 + c < nr) sum += (vd + (p_i - p_j) * inv_rc * r) * FV;
     }
   }
   for (int kk = nr; kk < nr + nw; ++kk) {
