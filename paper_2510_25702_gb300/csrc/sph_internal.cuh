@@ -124,7 +124,10 @@ struct alignas(4 * sizeof(R)) V4 {
 //                                       3D (x y z V)(vx vy vz k)(eps nut - -)
 //   mom  (advection / continuity -> momentum)
 //                                       2D (x y V p)(Bxx Bxy Byy kw)
-//                                       3D (x y z V)(p kw Bxx Byy)(Bzz Bxy Bxz Byz)
+//                                       3D (x y z V)(p kw Bxx Byy), with
+//                                          (Bzz Bxy Bxz Byz) in mom_b: the
+//                                          first 32 bytes stay one aligned
+//                                          256-bit load and one sector
 //   cont (momentum -> continuity)       2D (x y V p)(vx vy - -)
 //                                       3D (x y z V)(p vx vy vz)
 // kw = 2/3 k (effective pressure); Bxx < 0 marks a pressure-buffer
@@ -132,6 +135,7 @@ struct alignas(4 * sizeof(R)) V4 {
 template <typename R>
 struct Packs {
   V4<R> *adv, *mom, *cont;  // records, RV 4-vectors per particle
+  V4<R> *mom_b;             // 3D: the momentum record's B tail (Bzz Bxy Bxz Byz)
   V4<R> *Ap;                // a_nu + g of the advection step
   V4<R> *WP, *WV;           // walls: (x, y, z, V) and (vx, vy, vz, 0)
 };
@@ -139,7 +143,7 @@ struct Packs {
 template <int D>
 struct RecLayout {
   static constexpr int adv = (D == 2) ? 2 : 3;
-  static constexpr int mom = (D == 2) ? 2 : 3;
+  static constexpr int mom = 2;
   static constexpr int cont = 2;
 };
 

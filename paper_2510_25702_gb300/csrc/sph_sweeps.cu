@@ -399,9 +399,9 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
     pk.mom[2 * (size_t)i] = V4<R>{A0.x, A0.y, V, p};
     pk.mom[2 * (size_t)i + 1] = V4<R>{bxx, BR[3], BR[1], kw};
   } else {
-    pk.mom[3 * (size_t)i] = V4<R>{A0.x, A0.y, A0.z, V};
-    pk.mom[3 * (size_t)i + 1] = V4<R>{p, kw, bxx, BR[1]};
-    pk.mom[3 * (size_t)i + 2] = V4<R>{BR[2], BR[3], BR[4], BR[5]};
+    pk.mom[2 * (size_t)i] = V4<R>{A0.x, A0.y, A0.z, V};
+    pk.mom[2 * (size_t)i + 1] = V4<R>{p, kw, bxx, BR[1]};
+    pk.mom_b[i] = V4<R>{BR[2], BR[3], BR[4], BR[5]};
   }
 }
 
@@ -422,7 +422,7 @@ __device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, 
   const R rho0 = sweep_const<R>(I).rho0, inv_c0sq = sweep_const<R>(I).inv_c0sq;
   const V4<R> M0 = pk.mom[RM * (size_t)i], M1 = pk.mom[RM * (size_t)i + 1];
   V4<R> M2 = M1;
-  if (D == 3) M2 = pk.mom[RM * (size_t)i + 2];
+  if (D == 3) M2 = pk.mom_b[i];
   R Bi[6], kw_i, p_i = M0.w;
   if (!mom_B<R, D>(M1, M2, Bi, kw_i, p_i)) {  // pressure-buffer particle: FP64 master B
     for (int c = 0; c < 6; ++c) Bi[c] = (R)a.der.B[c][i];
@@ -443,14 +443,8 @@ __device__ __forceinline__ void mom_one(const SweepArgs &a, const Packs<R> &pk, 
       if (k0 + c >= nr) break;
       const uint32_t j = j4[c];
       V4<R> N0, N1, N2;
-      if (D == 2) {
-        ld_rec2<R>(pk.mom + RM * (size_t)j, N0, N1);
-        N2 = N1;
-      } else {
-        N0 = pk.mom[RM * (size_t)j];
-        N1 = pk.mom[RM * (size_t)j + 1];
-        N2 = pk.mom[RM * (size_t)j + 2];
-      }
+      ld_rec2<R>(pk.mom + RM * (size_t)j, N0, N1);
+      N2 = D == 3 ? pk.mom_b[j] : N1;
       R d[3];
       const R rr = pair_vec<R, D, PER>(g, M0, N0, d);
       R r;
