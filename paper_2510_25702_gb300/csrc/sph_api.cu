@@ -434,10 +434,11 @@ static int alloc_packs(sph_ctx *c, Packs<R> &pk, int64_t cap, int64_t nw) {
   pk.mom = alloc_arr<V4<R>>(c, cap * (d3 ? RecLayout<3>::mom : RecLayout<2>::mom));
   pk.cont = alloc_arr<V4<R>>(c, cap * (d3 ? RecLayout<3>::cont : RecLayout<2>::cont));
   pk.mom_b = alloc_arr<V4<R>>(c, d3 ? cap : 1);
+  pk.adv_b = alloc_arr<V4<R>>(c, d3 ? cap : 1);
   pk.Ap = alloc_arr<V4<R>>(c, cap);
   pk.WP = alloc_arr<V4<R>>(c, nw);
   pk.WV = alloc_arr<V4<R>>(c, nw);
-  if (!pk.adv || !pk.mom || !pk.mom_b || !pk.cont || !pk.Ap || !pk.WP || !pk.WV) return -1;
+  if (!pk.adv || !pk.adv_b || !pk.mom || !pk.mom_b || !pk.cont || !pk.Ap || !pk.WP || !pk.WV) return -1;
   return 0;
 }
 

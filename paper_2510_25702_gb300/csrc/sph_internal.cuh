@@ -121,7 +121,8 @@ struct alignas(4 * sizeof(R)) V4 {
 // that a neighbour costs one gather.  Written by the kernel before the
 // sweep that reads them:
 //   adv  (permute -> advection sweep)   2D (x y V vx)(vy k eps nut)
-//                                       3D (x y z V)(vx vy vz k)(eps nut - -)
+//                                       3D (x y z V)(vx vy vz k), with
+//                                          (eps nut - -) in adv_b
 //   mom  (advection / continuity -> momentum)
 //                                       2D (x y V p)(Bxx Bxy Byy kw)
 //                                       3D (x y z V)(p kw Bxx Byy), with
@@ -136,13 +137,14 @@ template <typename R>
 struct Packs {
   V4<R> *adv, *mom, *cont;  // records, RV 4-vectors per particle
   V4<R> *mom_b;             // 3D: the momentum record's B tail (Bzz Bxy Bxz Byz)
+  V4<R> *adv_b;             // 3D: the advection record's k-epsilon tail (eps nut - -)
   V4<R> *Ap;                // a_nu + g of the advection step
   V4<R> *WP, *WV;           // walls: (x, y, z, V) and (vx, vy, vz, 0)
 };
 
 template <int D>
 struct RecLayout {
-  static constexpr int adv = (D == 2) ? 2 : 3;
+  static constexpr int adv = 2;
   static constexpr int mom = 2;
   static constexpr int cont = 2;
 };

@@ -128,7 +128,7 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   // own record: 2D (x y V vx)(vy k eps nut), 3D (x y z V)(vx vy vz k)(eps nut - -)
   const V4<R> A0 = pk.adv[RA * (size_t)i], A1 = pk.adv[RA * (size_t)i + 1];
   V4<R> A2 = A1;
-  if (D == 3 && rans) A2 = pk.adv[RA * (size_t)i + 2];
+  if (D == 3 && rans) A2 = pk.adv_b[i];
   const R vi[3] = {D == 2 ? A0.w : A1.x, D == 2 ? A1.x : A1.y, D == 2 ? (R)0 : A1.z};
   const SweepConst<R> &kc = sweep_const<R>(I);
   const R rho0 = kc.rho0, nu_l = kc.nu_l, c0 = kc.c0, eta = kc.eta, muRk = kc.muR_k;
@@ -171,14 +171,9 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
       if (k0 + c >= nr) break;
       const uint32_t j = j4[c];
       V4<R> B0, B1;
-      if (D == 2) {
-        ld_rec2<R>(pk.adv + RA * (size_t)j, B0, B1);
-      } else {
-        B0 = pk.adv[RA * (size_t)j];
-        B1 = pk.adv[RA * (size_t)j + 1];
-      }
+      ld_rec2<R>(pk.adv + RA * (size_t)j, B0, B1);
       V4<R> B2 = B1;
-      if (D == 3 && rans) B2 = pk.adv[RA * (size_t)j + 2];
+      if (D == 3 && rans) B2 = pk.adv_b[j];
       R d[3];
       const R rr = pair_vec<R, D, PER>(g, A0, B0, d);
       R r;

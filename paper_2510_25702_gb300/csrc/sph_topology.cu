@@ -68,9 +68,9 @@ __device__ __forceinline__ int permute_one(const TopoArgs &a, const Packs<R> &pk
     pk.adv[2 * (size_t)t] = V4<R>{to_R<R>(x), to_R<R>(y), V, vxr};
     pk.adv[2 * (size_t)t + 1] = V4<R>{vyr, to_R<R>(k), to_R<R>(eps), to_R<R>(nut)};
   } else {
-    pk.adv[3 * (size_t)t] = V4<R>{to_R<R>(x), to_R<R>(y), to_R<R>(z), V};
-    pk.adv[3 * (size_t)t + 1] = V4<R>{vxr, vyr, to_R<R>(vz), to_R<R>(k)};
-    pk.adv[3 * (size_t)t + 2] = V4<R>{to_R<R>(eps), to_R<R>(nut), (R)0, (R)0};
+    pk.adv[2 * (size_t)t] = V4<R>{to_R<R>(x), to_R<R>(y), to_R<R>(z), V};
+    pk.adv[2 * (size_t)t + 1] = V4<R>{vxr, vyr, to_R<R>(vz), to_R<R>(k)};
+    if (I.rans) pk.adv_b[t] = V4<R>{to_R<R>(eps), to_R<R>(nut), (R)0, (R)0};
   }
   // |v|^2 with the plain left-to-right sum (in the sweep precision: the
   // FP64 form keeps the exact FP64 maximum), nu_t
