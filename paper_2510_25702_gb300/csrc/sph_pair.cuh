@@ -35,6 +35,8 @@ struct Ex<double> {
   static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
   static __device__ __forceinline__ double div(double a, double b) { return a / b; }
   static __device__ __forceinline__ void len(double rr, double &r) { r = sqrt(rr); }
+  // 1 / |r| given |r|^2 and |r|
+  static __device__ __forceinline__ double inv_len(double rr, double r) { return 1.0 / r; }
 };
 template <>
 struct Ex<float> {
@@ -43,6 +45,8 @@ struct Ex<float> {
   static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
   static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
   static __device__ __forceinline__ void len(float rr, float &r) { r = rr * rsqrtf(rr); }
+  // 1 / |r| given |r|^2 and |r|: the reciprocal square root len already took
+  static __device__ __forceinline__ float inv_len(float rr, float r) { return rsqrtf(rr); }
 };
 
 // per-thread copy of the instance geometry in sweep precision

@@ -140,6 +140,11 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   }
   const R mu_i = rho0 * (nu_l + nut_i);
   const R Dk_i = nu_l + nut_i * (R)(1.0 / kSigK), De_i = nu_l + nut_i * (R)(1.0 / kSigE);
+  // pair-invariant factors: the harmonic mean of mu_i, mu_j is
+  // 2 rho0 nu_i nu_j / (nu_i + nu_j); mu_R = min(muRk eta max(v_e, 0), muRk c0);
+  // the k and eps diffusion sums carry 2 rho0 D_i outside
+  const R nu_i = nu_l + nut_i, mu2_i = (R)2 * mu_i;
+  const R muR_eta = muRk * eta, muR_c0 = muRk * c0;
 
   const int lab = m.label[i];
   const BufDev *mb = (lab > 0 && lab <= I.nbuf) ? &a.buf[I.buf0 + lab - 1] : nullptr;
@@ -187,11 +192,11 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
       R mu_ad = mu_i;                                // laminar: harmonic mean of equal values
       if (rans) {
         const R k_j = D == 2 ? B1.y : B1.w, e_j = D == 2 ? B1.z : B2.x, nut_j = D == 2 ? B1.w : B2.y;
-        const R mu_j = rho0 * (nu_l + nut_j);
-        const R mut = Ex<R>::div((R)2 * mu_i * mu_j, mu_i + mu_j);
-        R ve = -(vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2]) * Ex<R>::div((R)1, r);
-        R lim = eta * (ve > (R)0 ? ve : (R)0);
-        R muR = muRk * (lim < c0 ? lim : c0);
+        const R nu_j = nu_l + nut_j;
+        const R mut = Ex<R>::div(mu2_i * nu_j, nu_i + nu_j);
+        R muR = -(vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2]) * Ex<R>::inv_len(rr, r) * muR_eta;
+        muR = muR > (R)0 ? muR : (R)0;
+        muR = muR < muR_c0 ? muR : muR_c0;
         mu_ad = mut > muR ? mut : muR;
         const R FV = F * V;
   #pragma unroll
@@ -199,8 +204,8 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   #pragma unroll
           for (int q = 0; q < D; ++q) G[p][q] += vij[p] * d[q] * FV;
         const R Dk_j = nu_l + nut_j * (R)(1.0 / kSigK), De_j = nu_l + nut_j * (R)(1.0 / kSigE);
-        dk += rho0 * Ex<R>::div((R)2 * Dk_i * Dk_j, Dk_i + Dk_j) * (k_i - k_j) * f;
-        de += rho0 * Ex<R>::div((R)2 * De_i * De_j, De_i + De_j) * (e_i - e_j) * f;
+        dk += Ex<R>::div(Dk_j, Dk_i + Dk_j) * (k_i - k_j) * f;
+        de += Ex<R>::div(De_j, De_i + De_j) * (e_i - e_j) * f;
       }
   #pragma unroll
       for (int c = 0; c < D; ++c) sv[c] += mu_ad * f * vij[c];
@@ -223,9 +228,9 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
     const R vij[3] = {(R)2 * (vi[0] - Wv.x), (R)2 * (vi[1] - Wv.y), (R)2 * (vi[2] - Wv.z)};
     R mu_ad = mu_i;
     if (rans) {
-      R ve = -(vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2]) * Ex<R>::div((R)1, r);
-      R lim = eta * (ve > (R)0 ? ve : (R)0);
-      R muR = muRk * (lim < c0 ? lim : c0);
+      R muR = -(vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2]) * Ex<R>::inv_len(rr, r) * muR_eta;
+      muR = muR > (R)0 ? muR : (R)0;
+      muR = muR < muR_c0 ? muR : muR_c0;
       mu_ad = mu_i > muR ? mu_i : muR;
       const R FV = F * V;
 #pragma unroll
@@ -361,8 +366,9 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
     }
     const R inv_k = Ex<R>::div((R)1, k_i);
     const R Gk = nut_i * prod - (R)(2.0 / 3.0) * k_i * tr;
-    const R dkdt = Gk - e_i + (R)2 * dk * inv_rho;
-    const R dedt = (R)kC1 * e_i * inv_k * Gk - (R)kC2 * e_i * e_i * inv_k + (R)2 * de * inv_rho;
+    const R dk_all = (R)2 * rho0 * Dk_i * dk, de_all = (R)2 * rho0 * De_i * de;
+    const R dkdt = Gk - e_i + (R)2 * dk_all * inv_rho;
+    const R dedt = (R)kC1 * e_i * inv_k * Gk - (R)kC2 * e_i * e_i * inv_k + (R)2 * de_all * inv_rho;
     // explicit update over dt_ad in the sweep precision (k, eps are not
     // among the FP64-integrated fields; in the FP64 form this is FP64)
     const R dta = to_R<R>(I.dt_ad);
@@ -675,10 +681,11 @@ constexpr int kSubMinBlocks = sizeof(R) == 4 ? (D == 2 ? 5 : 4) : 1;
 // the FP32 list builder at 48 registers as well (few spills)
 template <typename R, int D>
 constexpr int kListMinBlocks = (sizeof(R) == 4 && D == 3) ? 5 : 0;
-// the 3D FP32 advection sweep at 85 registers instead of 97 (5 resident
-// 128-thread blocks instead of 4: 1.79 against 2.27 ms on the 3D mixer)
+// the FP32 advection sweep at 85 registers in 3D instead of 97 (5 resident
+// 128-thread blocks instead of 4: 1.79 against 2.27 ms on the 3D mixer) and
+// at 64 in 2D instead of 76 (87.4 against 90.7 us on the 2D channel)
 template <typename R, int D>
-constexpr int kAdvMinBlocks = (sizeof(R) == 4 && D == 3) ? 3 : 0;
+constexpr int kAdvMinBlocks = sizeof(R) == 4 ? (D == 3 ? 3 : 4) : 0;
 
 template <typename R, int D, bool PER>
 __global__ void __launch_bounds__(kMaxBlock, kListMinBlocks<R, D>) k_list(SweepArgs a, Packs<R> pk) {
