@@ -194,9 +194,11 @@ struct sph_ctx {
 
   void *packs() { return prec == SPH_PREC_FP32 ? (void *)&pkf : (void *)&pkd; }
 
-  void *dalloc(size_t n) {
-    if (n == 0) n = 16;
-    n = (n + 255) & ~(size_t)255;
+  // one block from the caller's allocator (or cudaMalloc), NULL on failure;
+  // a block off a 256-byte boundary is handed back and counts as a failure
+  // (the sweeps' 256-bit record loads need 32-byte alignment, and 256 is
+  // what cudaMalloc gives and what the ABI asks of an allocator)
+  void *raw_alloc(size_t n) {
     void *p = nullptr;
     if (alloc.alloc) {
       p = alloc.alloc(alloc.user, n, alloc.stream);
@@ -204,14 +206,19 @@ struct sph_ctx {
       p = nullptr;
     }
     if (p && ((uintptr_t)p & 255u) != 0) {
-      // the sweeps' 256-bit record loads need 32-byte alignment; 256 is
-      // what cudaMalloc gives and what the ABI asks of an allocator
       if (alloc.free)
         alloc.free(alloc.user, p, alloc.stream);
       else
         cudaFree(p);
       p = nullptr;
     }
+    return p;
+  }
+
+  void *dalloc(size_t n) {
+    if (n == 0) n = 16;
+    n = (n + 255) & ~(size_t)255;
+    void *p = raw_alloc(n);
     if (p) {
       blocks.push_back(p);
       bytes += n;
@@ -1240,11 +1247,7 @@ int sph_save_state(sph_ctx *c, int32_t *slot_out) {
   snap_parts(c, parts);
   size_t total = 0;
   for (auto &p : parts) total += align256(p.second);
-  void *mem = nullptr;
-  if (c->alloc.alloc)
-    mem = c->alloc.alloc(c->alloc.user, total, c->alloc.stream);
-  else if (cudaMalloc(&mem, total) != cudaSuccess)
-    mem = nullptr;
+  void *mem = c->raw_alloc(total);
   if (!mem) return fail(SPH_ERR_ALLOC, "snapshot allocation failed");
   size_t off = 0;
   for (auto &p : parts) {
@@ -1337,11 +1340,7 @@ static int adj_alloc(sph_ctx *c) {
   const size_t bytes = nd * (cap * 8 + 256) + 2 * (cap * 4 + 256) + 2 * 256 + (size_t)A.d.n_theta * 8 + 8 +
                        (3 + 3 + 3 + 5) * (cap * 32 + 256) +
                        (size_t)A.n_region + 4096;
-  void *mem = nullptr;
-  if (c->alloc.alloc)
-    mem = c->alloc.alloc(c->alloc.user, bytes, c->alloc.stream);
-  else if (cudaMalloc(&mem, bytes) != cudaSuccess)
-    mem = nullptr;
+  void *mem = c->raw_alloc(bytes);
   if (!mem) return fail(SPH_ERR_ALLOC, "adjoint work arrays");
   A.mem = mem;
   A.bytes = bytes;
@@ -1381,11 +1380,7 @@ static int slot_alloc(sph_ctx *c, sph_ctx::Adj::Slot &sl) {
   const size_t nd = 8 + ns * 20 + 9 + 6;
   const size_t bytes = nd * (cap * 8 + 256) + (nbr * 4 + 256) + 2 * (cap * 2 + 256) + 5 * (cap * 4 + 256) +
                        (cap * 2 + 256) + (cap + 256) + (ncell1 * 4 + 256) + 512 + 4096;
-  void *mem = nullptr;
-  if (c->alloc.alloc)
-    mem = c->alloc.alloc(c->alloc.user, bytes, c->alloc.stream);
-  else if (cudaMalloc(&mem, bytes) != cudaSuccess)
-    mem = nullptr;
+  void *mem = c->raw_alloc(bytes);
   if (!mem) return fail(SPH_ERR_ALLOC, "adjoint step records");
   sl.mem = mem;
   char *p = (char *)mem;

@@ -96,3 +96,36 @@ def test_every_particle_deleted(sph):
     assert sim.read(["pos"])["pos"].shape == (0, 3)
     m, _ = sim.mass_momentum()
     assert m[0] == 0.0
+
+
+def test_misaligned_allocator_is_refused(sph, monkeypatch):
+    """The sweeps gather 32-byte records with 256-bit loads, so the ABI asks
+    a caller's allocator for 256-byte aligned blocks: a context given blocks
+    16 bytes off fails with SPH_ERR_ALLOC, runs nothing, and hands every
+    block back."""
+    made = []
+
+    class Shifted(sph._TorchAlloc):
+        def __init__(self):
+            self.live = {}
+            self.calls = 0
+            super().__init__()
+            made.append(self)
+
+        def _do_alloc(self, user, nbytes, stream):
+            base = int(self.torch.cuda.caching_allocator_alloc(int(nbytes) + 256, self.device, self.stream))
+            self.calls += 1
+            self.live[base + 16] = base
+            return base + 16
+
+        def _do_free(self, user, ptr, stream):
+            self.torch.cuda.caching_allocator_delete(self.live.pop(int(ptr)))
+
+    monkeypatch.setattr(sph, "_TorchAlloc", Shifted)
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation(cases.periodic_box(n_per_axis=10, dim=2), precision="fp32")
+    assert e.value.code == -8
+    assert made and made[0].calls > 0 and made[0].live == {}
+    monkeypatch.undo()
+    sim = sph.Simulation(cases.periodic_box(n_per_axis=10, dim=2), precision="fp32")
+    assert sim.step_rc(2) == 0
