@@ -339,8 +339,8 @@ static int all_candidates(const orc_state *s, nblist *cand) {
 }
 
 /* Neighbours of the frozen configuration: real j != i and wall w with
-   0 < |r_ij|^2 < (2h)^2 (survey reading 7: the cut-off tie is out, coincident
-   pairs are skipped), in ascending (wall, j) order whichever mode finds them. */
+   0 < |r_ij|^2 < (2h)^2 (the tie at the cut-off is out, coincident pairs
+   are skipped), in ascending (wall, j) order whichever mode finds them. */
 static int build_pairs(const orc_config *c, const orc_state *s, nblist *L) {
   memset(L, 0, sizeof(*L));
   L->start = (int64_t *)calloc((size_t)s->n + 1, sizeof(int64_t));
@@ -559,8 +559,8 @@ int orc_label(const orc_config *c, orc_state *s) {
 }
 
 /* ------------------------------------------------------------------ */
-/* a4: dual-criteria time step (Sec. 2.3; the constants are those of   */
-/* the cited scheme, survey reading 9):                                 */
+/* a4: dual-criteria time step (Sec. 2.3 names the two criteria; the   */
+/* constants are the usual ones of the dual-criteria scheme):           */
 /*   dt_ad = min(0.25 h / max(|v|max, U_ref), 0.125 h^2 / nu_eff,max)   */
 /*   dt_ac = 0.6 h / (c0 + |v|max)                                      */
 /* DUAL: n = ceil(dt_ad / dt_ac) equal sub-steps dt_ad / n, so the      */
@@ -603,12 +603,12 @@ int orc_time_step(const orc_config *c, orc_state *s) {
 /* ------------------------------------------------------------------ */
 /* a5: correction matrix B_i = (-sum_j r_ij (x) grad_i W_ij V_j)^-1     */
 /* (Sec. 2.2) over real neighbours and wall dummies.                   */
-/* Mirror condition (Sec. 3.3, survey reading 5): for a particle        */
+/* Mirror condition (Sec. 3.3): for a particle                          */
 /* labelled in a pressure buffer, neighbours beyond the open face       */
 /* (x'_0 < 0 in that buffer's frame) are left out and the mirror        */
 /* images across the face x'_0 = 0 of every particle with x'_0 >= 0     */
 /* are summed instead, so the truncated support is completed.           */
-/* Guard (paper silent, survey reading 6): det A <= 1e-3 (tr A / d)^d   */
+/* Guard (the paper is silent): det A <= 1e-3 (tr A / d)^d             */
 /* gives B = I.                                                         */
 /* ------------------------------------------------------------------ */
 static void accum_A(int dim, double *A, const double *r, const double *gw, double V) {
@@ -739,11 +739,11 @@ int orc_bmatrix(const orc_config *c, orc_state *s, double *Aout) {
 /*   a_i = (2/rho_i) sum_j mu_ad v_ij dW/(r_ij + 0.01h) V_j,            */
 /*   mu_ad = max(harmonic(mu_i, mu_j), mu_R), mu = rho0 nu_eff,         */
 /*   mu_R = 0.5 rho0 h min(eta max(v_ij . e_ij, 0), c0), e_ij the unit  */
-/*   vector from i to j (survey readings 1-3); mu_R = 0 when laminar.   */
+/*   vector from i to j; mu_R = 0 when laminar.                         */
 /* Wall dummy (no-slip, Sec. 2.3): the dummy carries v_j = 2 v_wall - v_i */
 /* so that the no-slip plane lies on the wall surface, and the harmonic  */
-/* mean is replaced by mu_i.  (The survey's reading v_j = v_wall puts    */
-/* the no-slip plane inside the wall and fails the Poiseuille pin.)      */
+/* mean is replaced by mu_i.  (Taking v_j = v_wall instead puts the    */
+/* no-slip plane inside the wall and fails the Poiseuille pin.)         */
 /* ------------------------------------------------------------------ */
 static double mu_of(const orc_config *c, const orc_state *s, int64_t i) {
   double nu = c->nu_l + (c->rans ? s->nut[i] : 0.0);
@@ -805,7 +805,7 @@ int orc_viscous(const orc_config *c, orc_state *s) {
 /* a7: k-epsilon sweep (Sec. 2.1, 2.2; App. A), explicit Euler over the */
 /* advection step with floors 1e-12, then nu_t = C_mu k^2 / eps.        */
 /*   grad v_i = -sum_j v_ij (x) (B_i grad_i W_ij) V_j, (a,b) = dv_a/dx_b */
-/*     (sign fixed so a linear field is reproduced; survey reading 1)   */
+/*     (sign fixed so that a linear field is reproduced)                */
 /*   G_k = tau_t : grad v, tau_t = nu_t (grad v + grad v^T) - 2k I / 3   */
 /*   dk/dt = G_k - eps + (2/rho_i) sum_j rho0 harm(D_k) k_ij f_ij V_j    */
 /*   deps/dt = C1 eps/k G_k - C2 eps^2/k + same with D_eps              */
@@ -919,11 +919,11 @@ int orc_half1(const orc_config *c, orc_state *s, double dt) {
 /* (Sec. 2.2):  a_i = -(1/rho_i) sum_j V_j (p_i B^_j + p_j B_i) grad_i W */
 /* with p the effective pressure p + 2/3 rho k in RANS (Table 1).        */
 /* B^_j = B_i for wall dummies and pressure-buffer particles (the       */
-/* condition B_k = B_i of Sec. 3.3, survey reading 5), else B_j.        */
+/* condition B_k = B_i of Sec. 3.3), else B_j.                         */
 /* Wall dummy: p_j = p_i (Riemann wall condition without gravity,       */
 /* Sec. 2.3).                                                           */
-/* Pressure-buffer particle (compensated term, final Eq. of Sec. 3.3,   */
-/* survey reading 4):  a_i += (2 p_ob / rho_i) B_i sum_j V_j grad_i W_ij */
+/* Pressure-buffer particle (compensated term, final Eq. of Sec. 3.3):  */
+/*   a_i += (2 p_ob / rho_i) B_i sum_j V_j grad_i W_ij                  */
 /* over all real and wall neighbours, with p_ob + 2/3 rho_i k_i in RANS. */
 /* The ablation cases of Sec. 4.1 drop B_i there (comp_B = 0) or take   */
 /* B^_j = B_j at buffer neighbours (bhat_buffer = 0).                   */
@@ -1004,7 +1004,7 @@ int orc_kick(const orc_config *c, orc_state *s, double dt) {
 /*   drho_i/dt = 2 rho_i sum_j (v_i - v*) . grad_i W_ij V_j,             */
 /*   v* = U* e_ij + (vbar_ij - Ubar_ij e_ij), Ubar = vbar . e_ij,        */
 /*   U* = Ubar + (p_i - p_j) / (2 rho0 c0),                             */
-/* e_ij the unit vector from i to j (survey reading 1), p the EOS        */
+/* e_ij the unit vector from i to j, p the EOS                          */
 /* pressure.  Wall dummy: v_j = 2 v_wall - v_i (so vbar = v_wall) and    */
 /* p_j = p_i.                                                           */
 /* ------------------------------------------------------------------ */
@@ -1075,8 +1075,7 @@ int orc_density(const orc_config *c, orc_state *s, double dt) {
 /* Velocity buffer: v = U(s) n_b + a U(s) xi, s = x'_1, U interpolated  */
 /* linearly in theta over [-half0, half0], a the noise amplitude and xi */
 /* in [-1,1)^d from Philox4x32-10 keyed by (seed, uid) with counter      */
-/* (step, sub, 0|1, 0).  Pressure and density are extrapolated (kept;   */
-/* survey reading 11).                                                  */
+/* (step, sub, 0|1, 0).  Pressure and density are extrapolated (kept). */
 /* Pressure buffer: p = p_ob, rho = rho0 (1 + p_ob / (rho0 c0^2));       */
 /* velocity extrapolated (kept).                                         */
 /* Turbulence: freestream sets (k_in, eps_in) and nu_t; zero gradient    */
@@ -1212,7 +1211,7 @@ int orc_buffer_update(const orc_config *c, orc_state *s, int64_t step) {
 }
 
 /* ------------------------------------------------------------------ */
-/* One advection step, in the order of the survey's step definition:    */
+/* One advection step, in this order:                                   */
 /* commit + sort, label, dt, frozen configuration, B, viscous, RANS,     */
 /* acoustic sub-steps (half1, momentum, kick, continuity, density, BC),  */
 /* buffer update.                                                       */

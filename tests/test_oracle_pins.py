@@ -59,9 +59,9 @@ def _centre(n, dim):
 
 @pytest.mark.parametrize("dim,n,ksum,aval", [(2, 15, 1.010473, 0.973921), (3, 9, 1.009501, 0.978896)])
 def test_lattice_kernel_sum_and_A(orc, dim, n, ksum, aval):
-    """Full-support lattice at h = 1.3 dp: sum W V and A are the lattice sums
-    the survey's independent brute-force probe measured (6 digits), A is
-    isotropic (off-diagonal terms vanish by symmetry)."""
+    """Full-support lattice at h = 1.3 dp: sum W V and A equal the lattice
+    sums of an independent brute-force summation over the lattice (6 digits),
+    A is isotropic (off-diagonal terms vanish by symmetry)."""
     o = orc.OracleSim(cases.lattice_block(n, dim), neighbor_mode=0)
     A = o.bmatrix(want_A=True)[_centre(n, dim)]
     ks = o.kernel_sum()[_centre(n, dim)]
