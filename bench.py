@@ -328,6 +328,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiated-window timing")
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--adjoint-dp", type=float, default=0.002)
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="time only the differentiated window and print its record (for profiling)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -352,6 +354,11 @@ def main():
 
     if not os.path.exists(_b.LIB):
         _b.build()
+    if args.adjoint_only:
+        rec = adjoint_bench(steps=args.adjoint_steps, every=max(1, args.adjoint_steps // 10), dp=args.adjoint_dp)
+        if rank == 0:
+            print(json.dumps(rec))
+        return
     case = workload(args.workload, seed=2 + rank)
     if args.workload == "batched_channels" and world > 1:
         # instances of one batch partitioned across ranks by particle count
