@@ -294,6 +294,41 @@ def adjoint_bench(steps: int = 200, every: int = 20, dp: float = 0.002):
             "fd_rel_err": abs(float(g @ u) - fd) / max(abs(fd), 1e-300), "dtype": "f64"}
 
 
+def fp32_error(case, sim64, steps: int):
+    """The FP32-sweep form against the plain FP64 form after the same number
+    of advection steps from the same initial state (`sim64` has taken
+    `steps`): relative L2 difference per field over the particles of the
+    initial state that both runs still hold, matched by (instance, uid).
+    Copies are left out: uids are given in injection order, so one injection
+    decision taken differently (a particle within rounding of a buffer line)
+    would shift the uids of every later copy."""
+    from paper_2510_25702_gb300 import sph
+
+    sim32 = sph.Simulation(case, precision="fp32")
+    sim32.step(steps)
+    names = ["inst", "uid", "pos", "vel", "rho", "k", "eps"]
+    f32, f64 = sim32.read(names), sim64.read(names)
+    t32, t64 = sim32.stats()["t"], sim64.stats()["t"]
+    sim32.close()
+    n0 = np.array([c.n for c in as_list(case)], np.int64)
+    keep32 = f32["uid"].astype(np.int64) < n0[f32["inst"]]
+    keep64 = f64["uid"].astype(np.int64) < n0[f64["inst"]]
+    f32 = {k: v[keep32] for k, v in f32.items()}
+    f64 = {k: v[keep64] for k, v in f64.items()}
+    k32 = f32["inst"].astype(np.int64) << 32 | f32["uid"].astype(np.int64)
+    k64 = f64["inst"].astype(np.int64) << 32 | f64["uid"].astype(np.int64)
+    common, i32, i64 = np.intersect1d(k32, k64, assume_unique=True, return_indices=True)
+    out = {"steps": steps, "particles_compared": int(common.size),
+           "particles_in_one_run_only": int(k32.size + k64.size - 2 * common.size),
+           "t_rel_diff": abs(t32 - t64) / max(abs(t64), 1e-300), "rel_l2": {}}
+    for name in ("pos", "vel", "rho", "k", "eps"):
+        a, b = f32[name][i32], f64[name][i64]
+        den = float(np.linalg.norm(b))
+        if den > 0:
+            out["rel_l2"][name] = float(np.linalg.norm(a - b)) / den
+    return out
+
+
 def run_reference(args, rank: int):
     """--impl reference: the oracle on the host cores, each step one oracle
     advection step of the bounded sample; rank 0 only."""
@@ -465,6 +500,7 @@ def main():
 
     log("e2e done")
     fp64 = None
+    fp32_err = None
     if not args.no_fp64 and args.precision == "fp32" and rank == 0:
         sim64 = sph.Simulation(case, precision="fp64")
         if tuned:
@@ -478,6 +514,7 @@ def main():
         b.record(stream)
         torch.cuda.synchronize()
         fp64 = sim64.stats()["n"] * k64 / (a.elapsed_time(b) * 1e-3)
+        fp32_err = fp32_error(case, sim64, args.warmup + k64)
         sim64.close()
 
     log("fp64 done")
@@ -512,7 +549,7 @@ def main():
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "stage_timing": "CUDA events around each stage in a second pass of the same K steps launched "
                             "kernel by kernel (value comes from graph replay)",
-            "fp64_value": fp64, "fp32_over_fp64": (value / fp64) if fp64 else None,
+            "fp64_value": fp64, "fp32_over_fp64": (value / fp64) if fp64 else None, "fp32_error": fp32_err,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "eager": eager, "autotune": tuned, "adjoint": adj,
             "clocks": clk.summary(),
         }
