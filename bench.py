@@ -133,21 +133,37 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device: int):
+    def __init__(self, device: int, interval_ms: int = 20):
         self.device = device
+        self.interval_ms = interval_ms
         self.proc = None
         self.lines = []
+        self.span = (0, None)
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.interval_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the first sample arrives once nvidia-smi is up; only then does
+            # the timed region start
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except (OSError, ValueError):
             self.proc = None
         return self
+
+    def begin(self):
+        """Mark the start of the timed region: samples before it are left out."""
+        self.span = (len(self.lines), None)
+
+    def end(self):
+        """Mark the end of the timed region (at least the first sample after
+        its start is kept)."""
+        self.span = (self.span[0], max(len(self.lines), self.span[0] + 1))
 
     def _read(self):
         for line in self.proc.stdout:
@@ -164,7 +180,8 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lo, hi = self.span
+        for ln in self.lines[lo:hi]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -430,10 +447,12 @@ def main():
     barrier()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        clk.begin()
         start.record(stream)
         sim.step(args.steps)
         end.record(stream)
         torch.cuda.synchronize()
+        clk.end()
     barrier()
     ms = start.elapsed_time(end)
     s1 = sim.stats()
