@@ -266,7 +266,10 @@ int sph_get_stats(sph_ctx *ctx, sph_stats *out);
    5 momentum sweep, 6 continuity sweep (both: sub-step 1), 7 buffer update,
    8 neighbour list (built once per advection step, before the advection
    sweep), 9 later sub-steps (momentum and continuity of sub-steps 2 ..
-   n_ac in one launch, which ends at once when no instance takes them).  enable = 0 stops timing; enable = 2 also clears the totals.
+   n_ac: in 2D one launch, which ends at once when no instance takes them;
+   in 3D one momentum and one continuity launch per sub-step up to the
+   context's bound on the sub-step count, each returning at once past every
+   instance's count).  enable = 0 stops timing; enable = 2 also clears the totals.
    sph_get_stage_times writes up to max_stages entries. */
 #define SPH_N_STAGES 10
 int sph_set_profiling(sph_ctx *ctx, int32_t enable);

@@ -561,7 +561,8 @@ void launch_momentum_sweep(const SweepArgs &a, void *packs, int prec, int dim, i
 void launch_continuity_sweep(const SweepArgs &a, void *packs, int prec, int dim, int max_n, int sub,
                              cudaStream_t st);
 // acoustic sub-steps 1 .. n_ac_all - 1 (momentum, continuity) in one
-// cooperative launch that ends at once when no instance takes them
+// cooperative launch that ends at once when no instance takes them (2D
+// contexts; 3D contexts launch the two sweeps per sub-step)
 void launch_substeps(const SweepArgs &a, void *packs, int prec, int dim, int max_n, cudaStream_t st);
 // ------------------------------------------------------------------------
 // adjoint of the step (differentiated windows, FP64 contexts)

@@ -670,8 +670,8 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
 // resident 256-thread blocks per SM asked of the FP32 sweeps (registers =
 // 65536 / (256 x blocks)): more warps for their latency-bound gathers where
 // that costs few spills (measured): momentum 2D and continuity at 48, the
-// fused later sub-steps at 48 (2D) or 64 (3D); the FP64 forms and the 3D
-// momentum sweep keep the compiler's count
+// fused later sub-steps of 2D at 48 (3D takes them as separate launches);
+// the FP64 forms and the 3D momentum sweep keep the compiler's count
 template <typename R, int D>
 constexpr int kMomMinBlocks = (sizeof(R) == 4 && D == 2) ? 5 : 1;
 template <typename R, int D>
@@ -744,7 +744,8 @@ __global__ void __launch_bounds__(kMaxBlock, kContMinBlocks<R, D>) k_cont(SweepA
   }
 }
 
-// Sub-steps 1 .. n_ac_all - 1 in one cooperative launch: momentum over all
+// Sub-steps 1 .. n_ac_all - 1 in one cooperative launch (2D; 3D contexts
+// launch the momentum and continuity sweeps per sub-step): momentum over all
 // particles, grid barrier, continuity, grid barrier, and so on.  When no
 // instance takes a second acoustic sub-step -- the usual case -- every block
 // ends at once, so the bound on sub-steps costs one empty launch instead of
@@ -946,7 +947,7 @@ void launch_continuity_sweep(const SweepArgs &a, void *packs, int prec, int dim,
     launch_sweeps<double>(2, a, packs, dim, max_n, st);
 }
 
-// sub-steps 1 .. n_ac_all - 1 (momentum and continuity) in one launch
+// sub-steps 1 .. n_ac_all - 1 (momentum and continuity) in one launch (2D)
 void launch_substeps(const SweepArgs &a, void *packs, int prec, int dim, int max_n, cudaStream_t st) {
   if (prec == SPH_PREC_FP32)
     launch_sweeps<float>(4, a, packs, dim, max_n, st);
