@@ -346,6 +346,57 @@ def fp32_error(case, sim64, steps: int):
     return out
 
 
+def probe_error(steps: int, nx: int = 120, ny: int = 40):
+    """The FP32-sweep form against the plain FP64 form after `steps`
+    advection steps of the 2D turbulent channel, compared on a fixed nx x ny
+    grid of probes over the channel by Shepard-normalised SPH interpolation
+    (Wendland C2 weights, support 2h): after thousands of steps the two runs
+    hold different particles, so the fields are compared at fixed points."""
+    from scipy.spatial import cKDTree
+
+    from paper_2510_25702_gb300 import sph
+
+    case = workload("turbulent_channel")
+    lo, hi = case.pos[:, :2].min(0), case.pos[:, :2].max(0)
+    xs = lo[0] + (np.arange(nx) + 0.5) * (hi[0] - lo[0]) / nx
+    ys = lo[1] + (np.arange(ny) + 0.5) * (hi[1] - lo[1]) / ny
+    probes = np.stack(np.meshgrid(xs, ys, indexing="ij"), -1).reshape(-1, 2)
+    names = ("u", "v", "rho", "k", "eps")
+    res = {}
+    for prec in ("fp32", "fp64"):
+        sim = sph.Simulation(case, precision=prec)
+        sim.set_graph(True)
+        done = 0
+        while done < steps:
+            k = min(500, steps - done)
+            rc = sim.step_rc(k)
+            if rc:
+                sim.close()
+                return {"workload": case.name, "error": f"{prec}: status {rc} within steps {done}..{done + k}"}
+            done += k
+        f = sim.read(["pos", "vel", "rho", "mass", "k", "eps"])
+        t = sim.stats()["t"]
+        sim.close()
+        x = f["pos"][:, :2]
+        vol = f["mass"] / f["rho"]
+        vals = {"u": f["vel"][:, 0], "v": f["vel"][:, 1], "rho": f["rho"], "k": f["k"], "eps": f["eps"]}
+        out = {nm: np.zeros(len(probes)) for nm in names}
+        for p_i, js in enumerate(cKDTree(x).query_ball_point(probes, 2.0 * case.h)):
+            js = np.asarray(js, dtype=np.int64)
+            if js.size == 0:
+                continue
+            q = np.linalg.norm(x[js] - probes[p_i], axis=1) / case.h
+            w = (1.0 - 0.5 * q) ** 4 * (1.0 + 2.0 * q) * vol[js]
+            for nm in names:
+                out[nm][p_i] = (w @ vals[nm][js]) / w.sum()
+        res[prec] = (out, t, int(f["pos"].shape[0]))
+    (a, ta, na), (b, tb, nb) = res["fp32"], res["fp64"]
+    rel = {nm: float(np.linalg.norm(a[nm] - b[nm]) / max(np.linalg.norm(b[nm]), 1e-300)) for nm in names}
+    vel = float(np.sqrt(np.sum((a["u"] - b["u"]) ** 2 + (a["v"] - b["v"]) ** 2) / np.sum(b["u"] ** 2 + b["v"] ** 2)))
+    return {"workload": case.name, "steps": steps, "probes": [nx, ny], "t_fp32": ta, "t_fp64": tb,
+            "particles_fp32": na, "particles_fp64": nb, "rel_l2_velocity": vel, "rel_l2": rel}
+
+
 def run_reference(args, rank: int):
     """--impl reference: the oracle on the host cores, each step one oracle
     advection step of the bounded sample; rank 0 only."""
@@ -382,6 +433,8 @@ def main():
     ap.add_argument("--adjoint-dp", type=float, default=0.002)
     ap.add_argument("--adjoint-only", action="store_true",
                     help="time only the differentiated window and print its record (for profiling)")
+    ap.add_argument("--probe-error", type=int, default=0, metavar="STEPS",
+                    help="only compare the FP32 and FP64 forms of the 2D channel after STEPS steps on a probe grid")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -406,6 +459,11 @@ def main():
 
     if not os.path.exists(_b.LIB):
         _b.build()
+    if args.probe_error > 0:
+        rec = probe_error(args.probe_error)
+        if rank == 0:
+            print(json.dumps(rec))
+        return
     if args.adjoint_only:
         rec = adjoint_bench(steps=args.adjoint_steps, every=max(1, args.adjoint_steps // 10), dp=args.adjoint_dp)
         if rank == 0:
