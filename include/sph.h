@@ -369,6 +369,20 @@ int sph_adjoint_release(sph_ctx *ctx);
    Test and debug aid; re-sorts the particles by cell. */
 int sph_debug_pairs(sph_ctx *ctx, int64_t *out, int64_t max, int64_t *count);
 
+/* The neighbour list that the pair sweeps of a step walk, built from the
+   configuration at the current positions by the same kernel, precision and
+   launch shape as in sph_step (the frozen configuration of the dual-criteria
+   advection step, Sec. 2.3; pairs 0 < |r_ij|^2 < (2h)^2 from the cell-linked
+   list, Sec. 2.4.1): rows (uid_i, uid_j or wall index, is_wall, instance),
+   one per list entry, in no particular order.  In the FP32 form candidates
+   near the cut-off are decided by the FP64 test, so both forms hold the
+   pairs of sph_debug_pairs.  Writes up to max rows into out (host memory,
+   [max][4] int64) and the total into *count.  Test aid; re-sorts the
+   particles by cell.  Errors: SPH_ERR_ARG, SPH_ERR_STATE (kinematic
+   context), SPH_ERR_ALLOC, SPH_ERR_CUDA, SPH_ERR_CAPACITY (a particle has
+   more neighbours than its list holds; its surplus is missing). */
+int sph_debug_list(sph_ctx *ctx, int64_t *out, int64_t max, int64_t *count);
+
 /* Total mass and momentum of every instance, summed in FP64 on the GPU
    over the live particles (deleted rows excluded, copies of the last buffer
    update included) in an order that does not depend on timing, so two
@@ -411,7 +425,10 @@ int sph_debug_convert(const double *in64, float *out32, const float *in32, doubl
    SPH_ERR_CUDA.  All calls on a device share the array and leave their
    contents in it; calls that overlap on the GPU race.  The first call on a
    device looks up the array's address (cudaGetSymbolAddress) with that
-   device current: make it before any stream capture. */
+   device current: make it before any stream capture.  That address is kept
+   for the process, so the call is not valid after cudaDeviceReset.  Errors
+   set the sph_last_error() message; a CUDA error already pending on the
+   thread at entry is returned as SPH_ERR_CUDA before anything is launched. */
 #define SPH_NOALLOC_MAX_POINTS (1 << 19)
 int sph_cell_sort_noalloc(const sph_config *cfg, const double *pos, int32_t n, uint32_t *order,
                           uint32_t *cell_start, int64_t cell_start_len, int64_t *ncell_out, void *stream);

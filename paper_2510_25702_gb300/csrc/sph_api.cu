@@ -46,6 +46,11 @@ const double kPi = 3.14159265358979323846;
 
 }  // namespace
 
+namespace sphk {
+// the message sph_last_error returns, for the entry points of other files
+int set_error(int code, const char *msg) { return fail(code, msg); }
+}  // namespace sphk
+
 struct sph_ctx {
   int dim = 2, prec = SPH_PREC_FP64, ninst = 0;
   bool kinematic = false;
@@ -290,6 +295,7 @@ struct sph_ctx {
     a.status = &cnt->status;
     a.sub = sub;
     a.gbar = gbar;
+    for (int q = 0; q < 3; ++q) a.wx[q] = wx[q];
     a.any_periodic = 0;
     for (const InstDev &I : inst) a.any_periodic |= I.periodic[0] | I.periodic[1] | I.periodic[2];
     return a;
@@ -1978,15 +1984,15 @@ int sph_get_stats(sph_ctx *c, sph_stats *out) {
   return SPH_OK;
 }
 
-int sph_debug_pairs(sph_ctx *c, int64_t *out, int64_t max, int64_t *count) {
-  if (!c || !count) return fail(SPH_ERR_ARG, "NULL argument");
+// bring the live particles into cell order, then restore a pending state
+// equal to that order (keys sorted, identity indices), so that the next
+// step sorts nothing new
+static int debug_topology(sph_ctx *c) {
   if (!c->started) {
     int rc = upload_buffers(c);
     if (rc) return rc;
     c->started = true;
   }
-  // bring the live particles into cell order, then restore a pending state
-  // equal to that order (keys sorted, identity indices)
   enqueue_topology(c);
   if (c->sorted_keys != c->K[0])
     CUDA_TRY(cudaMemcpyAsync(c->K[0], c->sorted_keys, 4 * (size_t)c->cap, cudaMemcpyDeviceToDevice, c->stream));
@@ -1994,12 +2000,19 @@ int sph_debug_pairs(sph_ctx *c, int64_t *out, int64_t max, int64_t *count) {
   CUDA_TRY(cudaMemcpyAsync(&c->cnt->m_pending, &c->cnt->n_live, 4, cudaMemcpyDeviceToDevice, c->stream));
   launch_iota(c->Vv[0], (int)c->cap, c->stream);
   CUDA_TRY(cudaMemsetAsync(c->pair_counter, 0, 8, c->stream));
-  // test aid, not on the stepping path: a temporary device buffer
+  return 0;
+}
+
+}  // extern "C"
+
+// rows of a debug read: run `emit` into a temporary device buffer (test aid,
+// not on the stepping path) and copy the first max rows out
+template <typename F>
+static int debug_rows(sph_ctx *c, int64_t *out, int64_t max, int64_t *count, const char *what, F &&emit) {
   int64_t *dout = nullptr;
   if (max > 0 && cudaMalloc(&dout, sizeof(int64_t) * 4 * (size_t)max) != cudaSuccess)
-    return fail(SPH_ERR_ALLOC, "pair buffer");
-  launch_debug_pairs(c->sweep(0, 0), c->wx[0], c->wx[1], c->wx[2], c->wall_index, dout, max, c->pair_counter, (int)c->cap,
-                     c->stream);
+    return fail(SPH_ERR_ALLOC, std::string(what) + " buffer");
+  emit(dout);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   unsigned long long n = 0;
@@ -2008,9 +2021,40 @@ int sph_debug_pairs(sph_ctx *c, int64_t *out, int64_t max, int64_t *count) {
   if (e == cudaSuccess && dout && out && k > 0)
     e = cudaMemcpy(out, dout, sizeof(int64_t) * 4 * k, cudaMemcpyDeviceToHost);
   if (dout) cudaFree(dout);
-  if (e != cudaSuccess) return fail(SPH_ERR_CUDA, std::string("debug pairs: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(SPH_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   *count = (int64_t)n;
   return SPH_OK;
+}
+
+extern "C" {
+
+int sph_debug_pairs(sph_ctx *c, int64_t *out, int64_t max, int64_t *count) {
+  if (!c || !count) return fail(SPH_ERR_ARG, "NULL argument");
+  int rc = debug_topology(c);
+  if (rc) return rc;
+  return debug_rows(c, out, max, count, "debug pairs", [&](int64_t *dout) {
+    launch_debug_pairs(c->sweep(0, 0), c->wx[0], c->wx[1], c->wx[2], c->wall_index, dout, max, c->pair_counter,
+                       (int)c->cap, c->stream);
+  });
+}
+
+int sph_debug_list(sph_ctx *c, int64_t *out, int64_t max, int64_t *count) {
+  if (!c || !count) return fail(SPH_ERR_ARG, "NULL argument");
+  if (c->kinematic) return fail(SPH_ERR_STATE, "a kinematic context builds no neighbour list");
+  int rc = debug_topology(c);
+  if (rc) return rc;
+  // the list builder of the stepping path, in the context's precision and
+  // launch shape, without the time step its first block takes when stepping
+  SweepArgs la = c->sweep(0, 0);
+  la.with_time_step = 0;
+  launch_neighbour_list(la, c->packs(), c->prec, c->dim, (int)c->cap, c->stream);
+  rc = debug_rows(c, out, max, count, "debug list", [&](int64_t *dout) {
+    launch_debug_list(c->sweep(0, 0), c->wall_index, dout, max, c->pair_counter, (int)c->cap, c->stream);
+  });
+  if (rc) return rc;
+  int32_t status = 0;
+  rc = read_status(c, &status);
+  return rc ? rc : status;
 }
 
 }  // extern "C"

@@ -412,6 +412,9 @@ __device__ __forceinline__ void apply_bc(const InstDev &I, const BufDev &b, cons
   }
 }
 
+// record msg as this thread's sph_last_error() message and return code
+int set_error(int code, const char *msg);
+
 // ------------------------------------------------------------------------
 // host-side launch wrappers implemented in the .cu files
 // ------------------------------------------------------------------------
@@ -550,6 +553,8 @@ struct SweepArgs {
   uint8_t *flag;
   int32_t *inst_spawn, *block_cnt;
   GridBarrier *gbar;     // sub-step launch: grid barrier words (zeroed once)
+  const double *wx[3];   // FP64 wall positions in wall cell order (FP32 list: the
+                         // exact test of candidates near the cut-off)
 };
 
 // sweeps: prec 0 -> double packs, 1 -> float packs; dim 2 / 3
@@ -621,6 +626,8 @@ void launch_adj_substep_rev(const AdjArgs &a, int dim, int any_periodic, int sub
 void launch_adj_adv_rev(const AdjArgs &a, int dim, int any_periodic, int max_n, cudaStream_t st);
 void launch_adj_perm_rev(const AdjArgs &a, int max_n, cudaStream_t st);
 
+void launch_debug_list(const SweepArgs &a, const uint32_t *wall_index, int64_t *out, int64_t max,
+                       unsigned long long *counter, int max_n, cudaStream_t st);
 void launch_debug_pairs(const SweepArgs &a, const double *wx, const double *wy, const double *wz,
                         const uint32_t *wall_index, int64_t *out, int64_t max, unsigned long long *counter,
                         int max_n, cudaStream_t st);

@@ -21,7 +21,13 @@
 //    streams without ordering) race on it;
 //  * the first call on a device looks up the array's device address with
 //    cudaGetSymbolAddress (host code must not use the array's name as a
-//    device pointer); make that first call before any stream capture.
+//    device pointer); make that first call before any stream capture.  The
+//    address is kept for the life of the process: after cudaDeviceReset the
+//    module holding the array is loaded anew and the kept address is stale,
+//    so the call is not valid across a device reset;
+//  * errors set the message of sph_last_error(); a CUDA error already
+//    pending on the thread when the call starts is reported as such (the
+//    call then launches nothing) instead of being taken for its own.
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -56,12 +62,15 @@ Scratch *g_scratch_ptr[kMaxDevices] = {nullptr};
 // device (the symbol's name in host code is not a device address)
 int scratch_for_current_device(Scratch **out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SPH_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return sphk::set_error(SPH_ERR_CUDA, "sph_cell_sort_noalloc: no usable current device");
   std::lock_guard<std::mutex> lock(g_mutex);
   if (!g_scratch_ptr[dev]) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || !p) return SPH_ERR_CUDA;
+    if (e != cudaSuccess || !p)
+      return sphk::set_error(SPH_ERR_CUDA, (std::string("sph_cell_sort_noalloc: cudaGetSymbolAddress: ") +
+                                            cudaGetErrorString(e)).c_str());
     g_scratch_ptr[dev] = (Scratch *)p;
   }
   *out = g_scratch_ptr[dev];
@@ -102,9 +111,11 @@ __global__ void k_noalloc_copy(const uint32_t *__restrict__ src, uint32_t *__res
 extern "C" int sph_cell_sort_noalloc(const sph_config *cfg, const double *pos, int32_t n, uint32_t *order,
                                      uint32_t *cell_start, int64_t cell_start_len, int64_t *ncell_out,
                                      void *stream) {
-  if (!cfg || n < 0 || (n > 0 && (!pos || !order)) || !cell_start) return SPH_ERR_ARG;
-  if (n > kMaxPoints) return SPH_ERR_ARG;  // beyond SPH_NOALLOC_MAX_POINTS
-  if ((cfg->dim != 2 && cfg->dim != 3) || !(cfg->h > 0)) return SPH_ERR_ARG;
+  auto arg = [](const char *why) { return sphk::set_error(SPH_ERR_ARG, why); };
+  if (!cfg || n < 0 || (n > 0 && (!pos || !order)) || !cell_start)
+    return arg("sph_cell_sort_noalloc: NULL pointer or negative n");
+  if (n > kMaxPoints) return arg("sph_cell_sort_noalloc: n above SPH_NOALLOC_MAX_POINTS");
+  if ((cfg->dim != 2 && cfg->dim != 3) || !(cfg->h > 0)) return arg("sph_cell_sort_noalloc: bad dim or h");
   Grid g{};
   g.dim = cfg->dim;
   g.cs = 2.0 * cfg->h;
@@ -114,15 +125,22 @@ extern "C" int sph_cell_sort_noalloc(const sph_config *cfg, const double *pos, i
     g.lo[a] = cfg->domain_lo[a];
     if (a < cfg->dim) {
       double L = cfg->domain_hi[a] - cfg->domain_lo[a];
-      if (!(L > 0)) return SPH_ERR_ARG;
+      if (!(L > 0)) return arg("sph_cell_sort_noalloc: domain_hi must exceed domain_lo");
       double f = std::floor(L / g.cs);
-      if (f > 1.0e6) return SPH_ERR_ARG;
+      if (f > 1.0e6) return arg("sph_cell_sort_noalloc: cell grid too large");
       g.nc[a] = (f >= 1.0) ? (int)f : 1;
     }
     ncell *= g.nc[a];
   }
   if (ncell_out) *ncell_out = ncell;
-  if (ncell >= (1ll << 31) || cell_start_len < ncell + 1) return SPH_ERR_ARG;
+  if (ncell >= (1ll << 31)) return arg("sph_cell_sort_noalloc: cell grid too large");
+  if (cell_start_len < ncell + 1) return arg("sph_cell_sort_noalloc: cell_start shorter than ncell + 1");
+  {
+    const cudaError_t pre = cudaPeekAtLastError();
+    if (pre != cudaSuccess)
+      return sphk::set_error(SPH_ERR_CUDA, (std::string("sph_cell_sort_noalloc: CUDA error pending before the call: ") +
+                                            cudaGetErrorString(pre)).c_str());
+  }
   Scratch *s = nullptr;
   int rc = scratch_for_current_device(&s);
   if (rc) return rc;
@@ -137,6 +155,9 @@ extern "C" int sph_cell_sort_noalloc(const sph_config *cfg, const double *pos, i
                    &vr);
   sphk::cell_offsets(kr, &s->count, (uint32_t)ncell, cell_start, &s->nlive, st);
   if (n > 0) k_noalloc_copy<<<blocks, 256, 0, st>>>(vr, order, n);
+  // nothing was pending at entry, so an error here is one of this call's launches
   cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+  if (e != cudaSuccess)
+    return sphk::set_error(SPH_ERR_CUDA, (std::string("sph_cell_sort_noalloc: ") + cudaGetErrorString(e)).c_str());
+  return SPH_OK;
 }

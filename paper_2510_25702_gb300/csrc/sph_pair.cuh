@@ -201,32 +201,58 @@ __device__ __forceinline__ void visit_cells(const InstDev &I, int cx, int cy, in
 }
 
 // candidates j in [jb, je) whose position leads the 4-vector P[j * stride],
-// four loads in flight; hit(j) is called for every j with
-// 0 < |r_ij|^2 < (2h)^2
-template <typename R, int D, bool PER, typename H>
+// four loads in flight; hit(j) is called, in increasing j, for every j with
+// 0 < |r_ij|^2 < (2h)^2.  In FP64 (lo = hi = (2h)^2) that test is the
+// definition itself.  In FP32 a candidate is a pair outright when its FP32
+// |r|^2 lies in (0, lo), is not one at or beyond hi, and in between (or at
+// zero) exact(j) decides with the FP64 test of the definition on the FP64
+// positions; [lo, hi) brackets the cut-off by more than the rounding of the
+// FP32 positions and sum can move |r|^2, so the FP32 list holds exactly the
+// pairs of the FP64 test.
+template <typename R, int D, bool PER, typename H, typename X>
 __device__ __forceinline__ void scan_range(const Geo<R> &g, const V4<R> &Pi, const V4<R> *__restrict__ P,
-                                           int stride, uint32_t jb, uint32_t je, H &&hit) {
+                                           int stride, uint32_t jb, uint32_t je, R lo, R hi, H &&hit,
+                                           X &&exact) {
   for (uint32_t j = jb; j < je; j += 4) {
     const V4<R> q0 = P[(size_t)j * stride];
     const V4<R> q1 = (j + 1 < je) ? P[(size_t)(j + 1) * stride] : q0;
     const V4<R> q2 = (j + 2 < je) ? P[(size_t)(j + 2) * stride] : q0;
     const V4<R> q3 = (j + 3 < je) ? P[(size_t)(j + 3) * stride] : q0;
     R d[3];
-    unsigned mask = 0;
+    unsigned sure = 0, maybe = 0;
     R rr = pair_vec<R, D, PER>(g, Pi, q0, d);
-    mask |= (rr > (R)0 && rr < g.cut2) ? 1u : 0u;
+    sure |= (rr > (R)0 && rr < lo) ? 1u : 0u;
+    if (sizeof(R) == 4) maybe |= (rr < hi) ? 1u : 0u;
     rr = pair_vec<R, D, PER>(g, Pi, q1, d);
-    mask |= (j + 1 < je && rr > (R)0 && rr < g.cut2) ? 2u : 0u;
+    sure |= (j + 1 < je && rr > (R)0 && rr < lo) ? 2u : 0u;
+    if (sizeof(R) == 4) maybe |= (j + 1 < je && rr < hi) ? 2u : 0u;
     rr = pair_vec<R, D, PER>(g, Pi, q2, d);
-    mask |= (j + 2 < je && rr > (R)0 && rr < g.cut2) ? 4u : 0u;
+    sure |= (j + 2 < je && rr > (R)0 && rr < lo) ? 4u : 0u;
+    if (sizeof(R) == 4) maybe |= (j + 2 < je && rr < hi) ? 4u : 0u;
     rr = pair_vec<R, D, PER>(g, Pi, q3, d);
-    mask |= (j + 3 < je && rr > (R)0 && rr < g.cut2) ? 8u : 0u;
-    while (mask) {
-      const int k = __ffs(mask) - 1;
-      mask &= mask - 1;
-      hit(j + (uint32_t)k);
+    sure |= (j + 3 < je && rr > (R)0 && rr < lo) ? 8u : 0u;
+    if (sizeof(R) == 4) maybe |= (j + 3 < je && rr < hi) ? 8u : 0u;
+    if (sizeof(R) == 8) maybe = sure;
+    while (maybe) {
+      const int k = __ffs(maybe) - 1;
+      maybe &= maybe - 1;
+      if (((sure >> k) & 1u) || exact(j + (uint32_t)k)) hit(j + (uint32_t)k);
     }
   }
+}
+
+// Half-width of the FP32 band around the cut-off within which the FP32
+// |r|^2 cannot decide the pair (see scan_range).  With u = 2^-24, each FP32
+// coordinate is within u |x| of the FP64 one and the FP32 difference adds
+// u |x_i - x_j| (and u L when it is wrapped across a periodic length L, the
+// shift itself being exact); near the cut-off |x_j| <= |x_i| + 2h, so each
+// component of r is within u (2 M + 2 cs + L) of the FP64 one (M the
+// largest |coordinate| of i, cs = 2h the cut-off), which moves |r|^2 by at
+// most 2 sqrt(D) cs u (2 M + 2 cs + L) plus the rounding of the contracted
+// sum (3 u cs^2) and of the FP32 cut-off itself (u cs^2).  The band is four
+// times that bound: cs 2^-20 (D (M + cs + L) + cs).
+__device__ __forceinline__ float cutoff_band(int D, float cs, float M, float L) {
+  return cs * 9.5367431640625e-07f * ((float)D * (M + cs + L) + cs);
 }
 
 __device__ __forceinline__ void decode_cell(const InstDev &I, uint32_t key, int &cx, int &cy, int &cz) {

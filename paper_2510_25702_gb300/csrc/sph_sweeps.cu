@@ -64,6 +64,18 @@ __device__ __forceinline__ int list_one(const SweepArgs &a, const Packs<R> &pk, 
 #pragma unroll
     for (int q = 0; q < D; ++q) o[q] = fminf(fmaxf(p[q] - (I.lo_f[q] + (float)cc[q] * cs), 0.0f), cs);
   }
+  // FP32: the band around the cut-off that the FP64 test decides
+  R lo = g.cut2, hi = g.cut2;
+  if (sizeof(R) == 4) {
+    float M = fmaxf(fabsf((float)Pi.x), fabsf((float)Pi.y)), Lp = 0.0f;
+    if (D == 3) M = fmaxf(M, fabsf((float)Pi.z));
+    if (PER)
+      for (int q = 0; q < D; ++q)
+        if (g.per[q]) Lp = fmaxf(Lp, (float)g.L[q]);
+    const float band = cutoff_band(D, cs, M, Lp);
+    lo = (R)((float)g.cut2 - band);
+    hi = (R)((float)g.cut2 + band);
+  }
   // entries are collected four at a time and stored as one 16-byte chunk
   uint4 buf = make_uint4(0u, 0u, 0u, 0u);
   uint4 *__restrict__ out4 = reinterpret_cast<uint4 *>(out);
@@ -72,8 +84,26 @@ __device__ __forceinline__ int list_one(const SweepArgs &a, const Packs<R> &pk, 
     const uint32_t *offs = set == 0 ? a.off : a.woff;
     const V4<R> *recs = set == 0 ? pk.adv : pk.WP;
     const int stride = set == 0 ? RA : 1;
+    // the definition in FP64 on the masters (rare: candidates in the band)
+    auto exact = [&](uint32_t j) -> bool {
+      if (set == 0 && j == (uint32_t)i) return false;
+      double rr = 0.0;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        double v = dsub(a.m.x[c][i], set == 0 ? a.m.x[c][j] : a.wx[c][j]);
+        if (PER && I.periodic[c]) {
+          const double hl = 0.5 * I.L[c];
+          if (v > hl)
+            v = dsub(v, I.L[c]);
+          else if (v < -hl)
+            v = dadd(v, I.L[c]);
+        }
+        rr = (c == 0) ? dmul(v, v) : dadd(rr, dmul(v, v));
+      }
+      return rr > 0.0 && rr < I.cut2;
+    };
     auto scan = [&](uint32_t jb, uint32_t je) {
-      scan_range<R, D, PER>(g, Pi, recs, stride, jb, je, [&](uint32_t j) {
+      scan_range<R, D, PER>(g, Pi, recs, stride, jb, je, lo, hi, [&](uint32_t j) {
         const int k = nr + nw;
         buf.x = buf.y;
         buf.y = buf.z;
@@ -84,7 +114,7 @@ __device__ __forceinline__ int list_one(const SweepArgs &a, const Packs<R> &pk, 
           ++nr;
         else
           ++nw;
-      });
+      }, exact);
     };
     if (PER)
       visit_cells<D, PER>(I, cx, cy, cz, 1, offs, scan);
@@ -680,7 +710,7 @@ template <typename R, int D>
 constexpr int kSubMinBlocks = sizeof(R) == 4 ? (D == 2 ? 5 : 4) : 1;
 // the FP32 list builder at 48 registers as well (few spills)
 template <typename R, int D>
-constexpr int kListMinBlocks = (sizeof(R) == 4 && D == 3) ? 5 : 0;
+constexpr int kListMinBlocks = sizeof(R) == 4 ? 5 : 0;
 // the FP32 advection sweep at 85 registers in 3D instead of 97 (5 resident
 // 128-thread blocks instead of 4: 1.79 against 2.27 ms on the 3D mixer) and
 // at 64 in 2D instead of 76 (87.4 against 90.7 us on the 2D channel)
@@ -837,6 +867,29 @@ __global__ void __launch_bounds__(kBlock) k_pairs(SweepArgs a, const double *__r
   }
 }
 
+// =========================================================================
+// the neighbour list the sweeps walk, as rows (uid_i, uid_j or wall index,
+// is_wall, instance), test aid
+// =========================================================================
+__global__ void __launch_bounds__(kBlock) k_list_rows(SweepArgs a, const uint32_t *__restrict__ wall_index,
+                                                      int64_t *out, int64_t max, unsigned long long *counter) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.cnt->n_live) return;
+  const uint32_t *L = list_of(a.nl, i);
+  const int nr = a.nl.n_real[i], nw = a.nl.n_wall[i];
+  for (int k = 0; k < nr + nw; ++k) {
+    const uint32_t j = list_at(L, k);
+    const bool wall = k >= nr;
+    const unsigned long long t = atomicAdd(counter, 1ull);
+    if ((int64_t)t < max) {
+      out[4 * t + 0] = a.m.uid[i];
+      out[4 * t + 1] = wall ? wall_index[j] : a.m.uid[j];
+      out[4 * t + 2] = wall ? 1 : 0;
+      out[4 * t + 3] = a.m.inst[i];
+    }
+  }
+}
+
 // ------------------------------------------------------------------------
 // launch wrappers
 // ------------------------------------------------------------------------
@@ -953,6 +1006,12 @@ void launch_substeps(const SweepArgs &a, void *packs, int prec, int dim, int max
     launch_sweeps<float>(4, a, packs, dim, max_n, st);
   else
     launch_sweeps<double>(4, a, packs, dim, max_n, st);
+}
+
+void launch_debug_list(const SweepArgs &a, const uint32_t *wall_index, int64_t *out, int64_t max,
+                       unsigned long long *counter, int max_n, cudaStream_t st) {
+  int g = (max_n + kBlock - 1) / kBlock;
+  k_list_rows<<<g < 1 ? 1 : g, kBlock, 0, st>>>(a, wall_index, out, max, counter);
 }
 
 void launch_debug_pairs(const SweepArgs &a, const double *wx, const double *wy, const double *wz,

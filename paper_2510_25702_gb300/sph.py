@@ -102,7 +102,7 @@ class Stats(C.Structure):
 _lib = None
 
 EXPORTS = ("sph_create", "sph_add_buffer", "sph_set_profile", "sph_step", "sph_read_fields",
-           "sph_write_fields", "sph_get_stats", "sph_debug_pairs", "sph_destroy", "sph_error_string",
+           "sph_write_fields", "sph_get_stats", "sph_debug_pairs", "sph_debug_list", "sph_destroy", "sph_error_string",
            "sph_last_error", "sph_abi_version", "sph_set_profiling", "sph_get_stage_times", "sph_stage_name",
            "sph_cell_sort_noalloc", "sph_set_graph", "sph_set_launch", "sph_get_launch", "sph_autotune",
            "sph_save_state", "sph_restore_state", "sph_drop_state", "sph_adjoint_forward",
@@ -136,6 +136,7 @@ def lib():
         L.sph_write_fields.argtypes = [vp, C.c_uint32, C.POINTER(vp), C.c_int32, C.c_int64]
         L.sph_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.sph_debug_pairs.argtypes = [vp, C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_int64)]
+        L.sph_debug_list.argtypes = [vp, C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_int64)]
         L.sph_debug_convert.argtypes = [vp, vp, vp, vp, C.c_int64]
         L.sph_destroy.argtypes = [vp]
         L.sph_destroy.restype = None
@@ -451,15 +452,22 @@ class Simulation:
     def adjoint_release(self):
         _check(lib().sph_adjoint_release(self.ctx), "sph_adjoint_release")
 
-    def debug_pairs(self, max_pairs: Optional[int] = None) -> np.ndarray:
+    def _debug_rows(self, fn, name: str, max_rows: Optional[int]) -> np.ndarray:
         cnt = C.c_int64()
-        if max_pairs is None:
-            _check(lib().sph_debug_pairs(self.ctx, None, 0, C.byref(cnt)), "sph_debug_pairs")
-            max_pairs = cnt.value
-        out = np.zeros((max(max_pairs, 1), 4), np.int64)
-        _check(lib().sph_debug_pairs(self.ctx, out.ctypes.data_as(C.POINTER(C.c_int64)), max_pairs,
-                                     C.byref(cnt)), "sph_debug_pairs")
-        return out[: min(cnt.value, max_pairs)]
+        if max_rows is None:
+            _check(fn(self.ctx, None, 0, C.byref(cnt)), name)
+            max_rows = cnt.value
+        out = np.zeros((max(max_rows, 1), 4), np.int64)
+        _check(fn(self.ctx, out.ctypes.data_as(C.POINTER(C.c_int64)), max_rows, C.byref(cnt)), name)
+        return out[: min(cnt.value, max_rows)]
+
+    def debug_pairs(self, max_pairs: Optional[int] = None) -> np.ndarray:
+        """(uid_i, uid_j | wall index, is_wall, instance) of the FP64 pair test."""
+        return self._debug_rows(lib().sph_debug_pairs, "sph_debug_pairs", max_pairs)
+
+    def debug_list(self, max_rows: Optional[int] = None) -> np.ndarray:
+        """The same rows read from the neighbour list the sweeps walk."""
+        return self._debug_rows(lib().sph_debug_list, "sph_debug_list", max_rows)
 
     def close(self):
         if getattr(self, "ctx", None) is not None and self.ctx.value:

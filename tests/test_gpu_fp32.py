@@ -1,0 +1,117 @@
+"""The FP32 form (FP32 pair sweeps with FP32 accumulation; FP64 positions,
+velocities, densities, time integration, B inversion and reductions)
+against the FP64 oracle, per field, in 2D, in 3D and in the batch.
+
+Bounds: the sweeps carry the FP32 unit roundoff (6e-8) amplified by the
+cancellation of their pair sums (|sum of |terms|| / |sum| up to ~1e2 for
+the pressure force; more at a large background pressure, below), so the
+increments of v, k and eps are good to ~1e-5 relative; B sums positive-definite outer products
+(little cancellation: ~1e-6); FP64 state plus those increments gives
+velocities to ~1e-6 of |v| and positions to ~1e-8.  Positions in the FP32
+records are absolute coordinates: at |x| ~ X their spacing is X 1.2e-7,
+i.e. X / dp 1.2e-7 of a particle spacing, which enters every pair vector.
+
+Where a large background pressure p is summed against a weak gradient, the
+terms of the pressure force are ~p / h while their sum is |grad p|: the
+cancellation is p / (h |grad p|).  The U-channels run at p ~ 2.3 (outlet
+0.01 rho0 c0^2 with c0 = 15) under gradients 12 nu U / W^2 = 12 / Re: at
+dp = 0.05 and Re 50 (the U-channel case here) that is ~4e2, and in the batch
+(dp down to 0.0125, Re up to 200) ~2e3, so their velocity increments carry
+~2e-5 and ~1.5e-4 relative error (bounds 1e-4 and 5e-4).
+"""
+import numpy as np
+import pytest
+
+from paper_2510_25702_gb300 import cases
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    den = np.linalg.norm(b)
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / (den if den > 0 else 1.0))
+
+
+@pytest.fixture(scope="module")
+def sph():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2510_25702_gb300 import build
+    from paper_2510_25702_gb300 import sph as S
+
+    build.build()
+    return S
+
+
+def _lat3_buf():
+    c = cases.lattice_block(9, 3)
+    c.buffers = [cases.BufferSpec("pressure", (0.0, 0.45, 0.45), cases.frame_3d((1, 0, 0), (0, 1, 0)),
+                                  0.4, (0.5, 0.5), p_ob=0.05)]
+    c.vel[:, 0] = 0.1
+    return c
+
+
+# name -> (case factory, steps, bounds per field)
+B2 = {"pos": 1e-8, "vel": 1e-5, "rho": 1e-7, "B": 1e-5}
+B3 = {"pos": 1e-8, "vel": 1e-5, "rho": 1e-7, "B": 1e-5}
+CASES = {
+    "box3": (lambda: cases.periodic_box(n_per_axis=8, dim=3, vel_amp=0.3, jitter_frac=0.1), 2, B3),
+    "lattice3_buf": (_lat3_buf, 2, B3),
+    "mixer3d": (lambda: cases.mixer_3d(dp=0.05), 2, B3),
+    "u_channel": (lambda: cases.u_channel(dp=0.05, nu=0.02), 2, dict(B2, vel=1e-4)),
+    "plane_jet": (lambda: cases.plane_jet(dp=0.02, jitter_frac=0.05), 2,
+                  dict(B2, k=1e-5, eps=1e-5)),
+    "channel": (lambda: cases.poiseuille_channel(length=1.0, height=0.5), 2, B2),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp32_form_against_oracle(sph, orc, name):
+    make, steps, bounds = CASES[name]
+    case = make()
+    sim = sph.Simulation(case, precision="fp32")
+    sim.step(steps)
+    g = sim.read(["uid", "label", "pos", "vel", "rho", "k", "eps", "B"])
+    o = orc.OracleSim(case)
+    o.step(steps)
+    f = o.fields()
+    f["B"] = f["B"].reshape(-1, 9)
+    assert np.array_equal(g["uid"], f["uid"]), "particle sets differ"
+    assert np.array_equal(g["label"], f["label"]), "labels differ"
+    old = g["uid"] < case.n  # B of the copies appended at the last step is not theirs
+    errs = {k: rel_l2(g[k], f[k]) for k in bounds if k != "B"}
+    errs["B"] = rel_l2(g["B"][old], f["B"][old])
+    print(name, {k: f"{v:.2e}" for k, v in errs.items()})
+    assert all(errs[k] < bounds[k] for k in bounds), errs
+
+
+def _split(g, ninst):
+    return [{k: v[g["inst"] == q] for k, v in g.items()} for q in range(ninst)]
+
+
+def test_fp32_batch_against_oracle_sampled_instances(sph, orc):
+    """All 64 channels and U-channels of the batch in one FP32 context with
+    graph replay (the bench's batched form), two steps; the smallest, the
+    largest, the median instance and instance 1 against the oracle run on
+    that instance alone."""
+    bat = cases.batched_channels()
+    sim = sph.Simulation(bat, precision="fp32")
+    sim.set_graph(True)
+    sim.step(2)
+    per = _split(sim.read(["inst", "uid", "label", "pos", "vel", "rho", "p"]), len(bat))
+    n = np.array([c.n for c in bat])
+    sample = sorted({int(np.argmin(n)), int(np.argmax(n)), int(np.argsort(n)[len(n) // 2]), 1})
+    bounds = {"pos": 1e-8, "vel": 5e-4, "rho": 1e-7}
+    worst = {}
+    for q in sample:
+        o = orc.OracleSim(bat[q])
+        o.step(2)
+        f = o.fields()
+        gq = per[q]
+        assert np.array_equal(gq["uid"], f["uid"]), f"instance {q}: uid sets differ"
+        assert np.array_equal(gq["label"], f["label"]), f"instance {q}: labels differ"
+        for k in bounds:
+            worst[k] = max(worst.get(k, 0.0), rel_l2(gq[k], f[k]))
+    print("batch", {k: f"{v:.2e}" for k, v in worst.items()})
+    assert all(worst[k] < bounds[k] for k in bounds), worst

@@ -73,6 +73,33 @@ def test_channel_480k_bench_configuration(sph, channel_oracle, tmp_path):
     assert all(errs[k] < bounds[k] for k in bounds), errs
 
 
+def test_channel_480k_fp32_sweep_list_bit_exact(sph, orc, tmp_path):
+    """The FP32 form's neighbour list in the bench configuration (autotuned
+    block sizes, graph replay), read after a step, holds exactly the oracle's
+    pairs at the same FP64 positions: about 10 M entries."""
+    case = cases.turbulent_channel()
+    sim = sph.Simulation(case, precision="fp32")
+    sim.autotune(steps=2, cache_path=str(tmp_path / "tune.txt"))
+    sim.set_graph(True)
+    sim.step(2)
+    rows = sim.debug_list()
+    g = sim.read(["uid", "pos"])
+    sim.close()
+    r = rows.astype(np.int64)
+    got = np.sort(r[:, 0] * (1 << 32) + r[:, 2] * (1 << 31) + r[:, 1])
+    n = len(g["uid"])
+    c = case.replace(pos=g["pos"].copy(), vel=np.zeros((n, 3)), rho=np.ones(n), mass=np.full(n, case.dp ** 2),
+                     k=np.full(n, 1e-3), eps=np.full(n, 1e-3), capacity=n + 16)
+    op = orc.OracleSim(c, neighbor_mode=1).pairs()
+    uid = g["uid"].astype(np.int64)
+    j = op[:, 1].copy()
+    real = op[:, 2] == 0
+    j[real] = uid[j[real]]
+    want = np.sort(uid[op[:, 0]] * (1 << 32) + op[:, 2] * (1 << 31) + j)
+    assert len(want) > 9_000_000
+    assert np.array_equal(got, want)
+
+
 def test_plane_jet_1m_fp64_one_step(sph, orc):
     case = cases.plane_jet(dp=0.002, jitter_frac=0.02)
     assert case.n == 1_000_000
