@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define SPH_ABI_VERSION 1
+#define SPH_ABI_VERSION 2
 
 /* return codes */
 #define SPH_OK 0
@@ -97,8 +97,25 @@ typedef struct sph_config {
   double gravity[3];
   double domain_lo[3], domain_hi[3];
   int32_t obc;        /* SPH_OBC_*: open-boundary treatment (0 = the paper's) */
-  int32_t reserved;
+  int32_t density_sum; /* 1: density of fluid particles re-evaluated once per
+                          advection step by kernel summation (below) */
+  double tvf_alpha;   /* transport-velocity correction (below); 0 = off */
 } sph_config;
+
+/* The two stages of the advection step that Sec. 2.3 names through the
+   schemes it cites (without formulas), both switched per instance and both
+   taken over the frozen configuration of the step, for fluid particles
+   (label 0) only, after the correction matrix, viscous and k-epsilon terms
+   (which use the volumes m / rho from before them):
+   - transport-velocity correction: x_i += -2 tvf_alpha h^2 sum_j V_j grad_i W_ij
+     over real and wall neighbours (the background-pressure term of the
+     transport-velocity formulation, with the background pressure tied to
+     the step so that the shift is a fixed fraction of h^2);
+   - density reinitialisation: rho_i = rho0 sigma_i / sigma_0 with
+     sigma_i = W(0) + sum_j W_ij over real and wall neighbours and sigma_0
+     the same sum on the perfect lattice of spacing dp.
+   The acoustic sub-steps start from the reinitialised density.
+   Differentiated windows need both off. */
 
 /* sph_config.obc: the open-boundary treatments compared in Sec. 4.1 (Table
    of the four cases), for ablation.  IMPROVED (case 4, default): B_i with

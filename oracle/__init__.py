@@ -48,6 +48,7 @@ class OrcConfig(C.Structure):
         ("gen_offset", C.c_double), ("id_check", C.c_int), ("contain_check", C.c_int),
         ("mirror_B", C.c_int), ("compensation", C.c_int), ("neighbor_mode", C.c_int),
         ("rkgc", C.c_int), ("freeze_turb", C.c_int), ("comp_B", C.c_int), ("bhat_buffer", C.c_int),
+        ("density_sum", C.c_int), ("tvf_alpha", C.c_double),
     ]
 
 
@@ -98,7 +99,7 @@ def lib():
         L.orc_pairs.restype = C.c_int64
         L.orc_pairs.argtypes = [cfgp, stp, C.POINTER(C.c_int64), C.c_int64]
         for name in ("orc_compact_sort", "orc_configure", "orc_label", "orc_time_step",
-                     "orc_viscous", "orc_momentum", "orc_continuity"):
+                     "orc_viscous", "orc_momentum", "orc_continuity", "orc_transport", "orc_density_sum"):
             getattr(L, name).argtypes = [cfgp, stp]
         L.orc_bmatrix.argtypes = [cfgp, stp, _PD]
         for name in ("orc_rans", "orc_half1", "orc_kick", "orc_density"):
@@ -181,6 +182,8 @@ class OracleSim:
         c.rkgc = rkgc
         c.freeze_turb = freeze_turb
         c.comp_B, c.bhat_buffer = comp_B, bhat_buffer
+        c.tvf_alpha = float(getattr(case, "tvf", 0.0))
+        c.density_sum = int(bool(getattr(case, "density_sum", False)))
         # the open-boundary treatment of the case (Table of Sec. 4.1) sets
         # the switches it names; the improved scheme keeps the arguments
         obc = OBC_SWITCHES[getattr(case, "obc", "improved")]
@@ -283,6 +286,18 @@ class OracleSim:
 
     def viscous(self):
         _check(lib().orc_viscous(self._cp, self._sp), "orc_viscous")
+
+    def density_sum(self):
+        _check(lib().orc_density_sum(self._cp, self._sp), "orc_density_sum")
+
+    def lattice_kernel_sum(self) -> float:
+        L = lib()
+        L.orc_lattice_kernel_sum.restype = C.c_double
+        L.orc_lattice_kernel_sum.argtypes = [C.POINTER(OrcConfig)]
+        return float(L.orc_lattice_kernel_sum(self._cp))
+
+    def transport(self):
+        _check(lib().orc_transport(self._cp, self._sp), "orc_transport")
 
     def rans(self, dt: float):
         _check(lib().orc_rans(self._cp, self._sp, float(dt)), "orc_rans")

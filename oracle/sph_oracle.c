@@ -802,6 +802,109 @@ int orc_viscous(const orc_config *c, orc_state *s) {
 }
 
 /* ------------------------------------------------------------------ */
+/* Transport-velocity formulation (Sec. 2.3 names it and cites the       */
+/* generalized TVF of Zhang, Hu & Adams (2017) without a formula).       */
+/* Reading: particles are carried by the transport velocity v + dv,      */
+/* dv = -(2 p_b / rho) dt sum_j V_j grad_i W_ij (the background-pressure */
+/* term of the transport-velocity SPH of Adami, Hu & Adams 2013), and    */
+/* with the background pressure tied to the step so that p_b dt^2 / rho  */
+/* = alpha h^2, the displacement it adds over one advection step is      */
+/*   dr_i = -2 alpha h^2 sum_j V_j grad_i W_ij                          */
+/* over all real and wall neighbours of the frozen configuration, taken  */
+/* once per advection step (before the sub-steps), for fluid particles   */
+/* (label 0) only: buffer particles keep the motion their boundary       */
+/* condition gives them.  grad_i W points from i towards j, so a         */
+/* particle is moved away from where its neighbours crowd.  The pair     */
+/* geometry of the step stays that of the frozen configuration; the      */
+/* shift takes effect at the next rebuild and in the buffer update.      */
+/* ------------------------------------------------------------------ */
+static int orc_transport_impl(const orc_config *c, orc_state *s, const nblist *Lp) {
+  const nblist L = *Lp;
+  if (!(c->tvf_alpha > 0.0)) return ORC_OK;
+  double Vw = wall_volume(c);
+  double f = -2.0 * c->tvf_alpha * c->h * c->h;
+  for (int64_t i = 0; i < s->n; ++i) {
+    if (s->dead[i] || s->label[i] != 0) continue;
+    double S[3] = {0, 0, 0};
+    for (int64_t t = L.start[i]; t < L.start[i + 1]; ++t) {
+      int64_t j = L.nb[t].j;
+      int wall = L.nb[t].wall;
+      geom_t G;
+      pair_geom(c, &s->pos0[3 * i], xj_of(s, j, wall), &G);
+      double V = wall ? Vw : vol_of(s, j);
+      for (int a = 0; a < 3; ++a) S[a] += V * G.gw[a];
+    }
+    for (int a = 0; a < c->dim; ++a) s->pos[3 * i + a] += f * S[a];
+  }
+  return ORC_OK;
+}
+
+int orc_transport(const orc_config *c, orc_state *s) {
+  nblist L;
+  if (build_pairs(c, s, &L)) return ORC_ERR_NOMEM;
+  int rc = orc_transport_impl(c, s, &L);
+  nblist_free(&L);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Density reinitialisation (dual-criteria time stepping, Sec. 2.3: the  */
+/* scheme it cites re-evaluates the density from the particle            */
+/* configuration once per advection step; the acoustic sub-steps then    */
+/* integrate the Riemann continuity equation of Sec. 2.2).  Reading: for  */
+/* fluid particles (label 0) the density becomes                        */
+/*   rho_i = rho0 sigma_i / sigma_0,  sigma_i = W(0) + sum_j W_ij        */
+/* over all real and wall neighbours of the frozen configuration, with   */
+/* sigma_0 the same sum on the perfect lattice of spacing dp, so that an */
+/* undisturbed lattice has rho0 exactly.  Buffer particles keep their   */
+/* values (their boundary condition sets or extrapolates them).  It is  */
+/* taken after the correction matrix, viscous, k-epsilon and transport   */
+/* terms of the step, which use the volumes m / rho from before it.      */
+/* ------------------------------------------------------------------ */
+double orc_lattice_kernel_sum(const orc_config *c) {
+  int R = (int)ceil(2.0 * c->h / c->dp) + 1;
+  int Rz = c->dim == 3 ? R : 0;
+  double S = 0.0;
+  for (int a = -R; a <= R; ++a)
+    for (int b = -R; b <= R; ++b)
+      for (int k = -Rz; k <= Rz; ++k) {
+        double r = c->dp * sqrt((double)(a * a + b * b + k * k));
+        S += orc_W(c->dim, c->h, r);
+      }
+  return S;
+}
+
+static int orc_density_sum_impl(const orc_config *c, orc_state *s, const nblist *Lp) {
+  const nblist L = *Lp;
+  if (!c->density_sum) return ORC_OK;
+  double sigma0 = orc_lattice_kernel_sum(c);
+  double *rs = (double *)malloc((size_t)(s->n > 0 ? s->n : 1) * sizeof(double));
+  if (!rs) return ORC_ERR_NOMEM;
+  for (int64_t i = 0; i < s->n; ++i) {
+    rs[i] = s->rho[i];
+    if (s->dead[i] || s->label[i] != 0) continue;
+    double sigma = orc_W(c->dim, c->h, 0.0);
+    for (int64_t t = L.start[i]; t < L.start[i + 1]; ++t) {
+      geom_t G;
+      pair_geom(c, &s->pos0[3 * i], xj_of(s, L.nb[t].j, L.nb[t].wall), &G);
+      sigma += orc_W(c->dim, c->h, G.rl);
+    }
+    rs[i] = c->rho0 * sigma / sigma0;
+  }
+  for (int64_t i = 0; i < s->n; ++i) s->rho[i] = rs[i];
+  free(rs);
+  return ORC_OK;
+}
+
+int orc_density_sum(const orc_config *c, orc_state *s) {
+  nblist L;
+  if (build_pairs(c, s, &L)) return ORC_ERR_NOMEM;
+  int rc = orc_density_sum_impl(c, s, &L);
+  nblist_free(&L);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
 /* a7: k-epsilon sweep (Sec. 2.1, 2.2; App. A), explicit Euler over the */
 /* advection step with floors 1e-12, then nu_t = C_mu k^2 / eps.        */
 /*   grad v_i = -sum_j v_ij (x) (B_i grad_i W_ij) V_j, (a,b) = dv_a/dx_b */
@@ -1228,6 +1331,8 @@ int orc_step(const orc_config *c, orc_state *s, int nsteps) {
     rc = orc_bmatrix_impl(c, s, NULL, &L);
     if (!rc) rc = orc_viscous_impl(c, s, &L);
     if (!rc && c->rans && !c->freeze_turb) rc = orc_rans_impl(c, s, s->dt_ad, &L);
+    if (!rc) rc = orc_transport_impl(c, s, &L);
+    if (!rc) rc = orc_density_sum_impl(c, s, &L);
     for (int sub = 0; sub < s->n_ac && !rc; ++sub) {
       double dt = s->dt;
       rc = orc_half1(c, s, dt);

@@ -73,6 +73,11 @@ typedef struct orc_config {
                      /* 0: the uncorrected form of the original VIPO (Cases 1-3) */
   int bhat_buffer;   /* B^_j = B_i for pressure-buffer neighbours (B_k = B_i,   */
                      /* Sec. 3.3); 0: their own B_j (Case 2)                     */
+  int density_sum;   /* 1: fluid density reinitialised by kernel summation   */
+                     /* once per advection step (dual-criteria scheme, Sec. 2.3) */
+  double tvf_alpha;  /* transport-velocity correction (Sec. 2.3): fluid       */
+                     /* particles move by -2 alpha h^2 sum_j V_j grad_i W_ij    */
+                     /* once per advection step; 0 = off                       */
 } orc_config;
 
 typedef struct orc_buffer {
@@ -149,6 +154,11 @@ int orc_label(const orc_config *c, orc_state *s);               /* a3 */
 int orc_time_step(const orc_config *c, orc_state *s);           /* a4 */
 int orc_bmatrix(const orc_config *c, orc_state *s, double *A);  /* a5, A optional [cap][9] */
 int orc_viscous(const orc_config *c, orc_state *s);             /* a6 */
+int orc_transport(const orc_config *c, orc_state *s);           /* transport-velocity shift */
+int orc_density_sum(const orc_config *c, orc_state *s);         /* density reinitialisation */
+/* reference number density: sum of W over the lattice of spacing dp around
+   a site, the site included (the value a perfect lattice sums to) */
+double orc_lattice_kernel_sum(const orc_config *c);
 int orc_rans(const orc_config *c, orc_state *s, double dt);     /* a7 */
 int orc_half1(const orc_config *c, orc_state *s, double dt);    /* a8 */
 int orc_momentum(const orc_config *c, orc_state *s);            /* a9 force only -> acc_p */

@@ -82,6 +82,8 @@ class Case:
     # (case 4, the default), "vipo" (1), "vipo_rkgc" (2), "vipo_rkgc_mirror"
     # (3), or "minimal_mirror" (case 4 with B_i from the truncated support)
     obc: str = "improved"
+    tvf: float = 0.0  # transport-velocity shift coefficient alpha (0 = off)
+    density_sum: bool = False  # density reinitialised by summation every advection step
 
     @property
     def n(self) -> int:
@@ -203,6 +205,50 @@ def poiseuille_channel(length=2.0, height=1.0, dp=0.05, p_in=0.2, p_out=0.1, nu=
                 lo=np.array([-margin, -margin, 0.0]), hi=np.array([length + margin, height + margin, 0.0]),
                 periodic=(0, 0, 0), wpos=wpos, wvel=np.zeros_like(wpos), buffers=bufs,
                 seed=seed, capacity=int(capacity_factor * pos.shape[0]) + 64, **arr)
+
+
+def laminar_channel(length=2.0, height=1.0, dp=0.05, U_max=0.3125, nu=0.02, p_out=0.1, rho0=1.0,
+                    jitter_frac=0.01, seed=1, buffer_cells=4, n_theta=41, tvf=0.2, density_sum=True,
+                    developed=True, capacity_factor=1.5) -> Case:
+    """The laminar straight channel of Sec. 4.1 as the paper sets it up: a
+    velocity inlet buffer with the parabolic profile U(y) = 4 U_max y (H - y)
+    / H^2 (sampled at n_theta points across the width), a pressure outlet
+    buffer at p_out (0.1 in the paper), 4 wall layers, 20 particles across.
+    The plane Poiseuille flow of this inflow has the pressure gradient
+    G = 8 rho0 nu U_max / H^2 (0.05 here, so the inlet pressure is
+    p_out + G L = 0.2, the theoretical value the paper quotes).  developed:
+    start from that flow (parabolic velocity, linear pressure) instead of
+    rest.  The transport-velocity shift and the density reinitialisation
+    (Sec. 2.3) are on."""
+    nx, ny = int(round(length / dp)), int(round(height / dp))
+    pos = jitter(lattice((nx, ny), dp), 2, jitter_frac * dp, seed)
+    G = 8.0 * rho0 * nu * U_max / height**2
+    c0 = 10.0 * U_max
+    h = H_FAC * dp
+    wpos = _channel_walls(-WALL_LAYERS * dp, length + WALL_LAYERS * dp, height, dp)
+    Lb = buffer_cells * dp
+    s = np.linspace(0.0, 1.0, n_theta)
+    theta = tuple(U_max * 4.0 * s * (1.0 - s))
+    bufs = [
+        BufferSpec("velocity", (0.0, 0.5 * height, 0.0), frame_2d((1, 0)), Lb, (0.5 * height, 0.0),
+                   theta=theta),
+        BufferSpec("pressure", (length, 0.5 * height, 0.0), frame_2d((-1, 0)), Lb,
+                   (0.5 * height, 0.0), p_ob=p_out),
+    ]
+    margin = WALL_LAYERS * dp + 2 * h
+    arr = _fluid_arrays(pos, 2, dp, rho0)
+    if developed:
+        y, x = pos[:, 1], pos[:, 0]
+        arr["vel"][:, 0] = U_max * 4.0 * (y / height) * (1.0 - y / height)
+        p0 = p_out + G * (length - x)
+    else:
+        p0 = np.full(pos.shape[0], p_out)
+    arr["rho"][:] = rho0 * (1.0 + p0 / (rho0 * c0 * c0))
+    return Case(name=f"laminar_channel_2d_dp{dp:g}", dim=2, dp=dp, h=h, rho0=rho0, c0=c0, nu_l=nu,
+                rans=False, U_ref=U_max,
+                lo=np.array([-margin, -margin, 0.0]), hi=np.array([length + margin, height + margin, 0.0]),
+                periodic=(0, 0, 0), wpos=wpos, wvel=np.zeros_like(wpos), buffers=bufs, seed=seed,
+                capacity=int(capacity_factor * pos.shape[0]) + 64, tvf=tvf, density_sum=density_sum, **arr)
 
 
 def turbulent_channel(length=6.0, height=2.0, dp=0.005, U=1.0, Re=1.0e4, c0=10.0, rho0=1.0,

@@ -343,12 +343,17 @@ static int build_inst(const sph_config &c, InstDev &I, std::string &why) {
   if (c.dt_mode != SPH_DT_FIXED && !(c.U_ref > 0)) return why = "U_ref must be > 0", -1;
   if (c.dt_mode != SPH_DT_FIXED && !c.rans && !(c.nu_l > 0)) return why = "nu_l must be > 0", -1;
   if (c.obc < SPH_OBC_IMPROVED || c.obc > SPH_OBC_MINIMAL_MIRROR) return why = "bad obc", -1;
+  if (c.density_sum != 0 && c.density_sum != 1) return why = "density_sum must be 0 or 1", -1;
+  if (!(c.tvf_alpha >= 0.0 && c.tvf_alpha < 1.0)) return why = "tvf_alpha must be in [0, 1)", -1;
   I.dim = c.dim;
   I.rans = c.rans ? 1 : 0;
   I.dt_mode = c.dt_mode;
   I.n_ac_fixed = c.n_ac_fixed;
   I.kinematic = c.kinematic ? 1 : 0;
   I.obc = c.obc;
+  I.density_sum = c.density_sum;
+  I.tvf = c.tvf_alpha > 0.0 ? 1 : 0;
+  I.tvf_k = -2.0 * c.tvf_alpha * c.h * c.h;
   I.seed = c.seed;
   I.dp = c.dp;
   I.h = c.h;
@@ -381,6 +386,22 @@ static int build_inst(const sph_config &c, InstDev &I, std::string &why) {
   I.ncell = (uint32_t)ncell;
   double alpha = (c.dim == 2) ? 7.0 / (4.0 * kPi * c.h * c.h) : 21.0 / (16.0 * kPi * c.h * c.h * c.h);
   I.alpha_h = alpha / c.h;
+  {
+    // sigma_0 / alpha_d: the lattice sum of W(r) / alpha_d = (1 - q/2)^4 (1 + 2q)
+    // over the sites of spacing dp within the support, the centre included
+    const int R = (int)std::ceil(2.0 * c.h / c.dp) + 1, Rz = c.dim == 3 ? R : 0;
+    double s0 = 0.0;
+    for (int a = -R; a <= R; ++a)
+      for (int b = -R; b <= R; ++b)
+        for (int k = -Rz; k <= Rz; ++k) {
+          const double q = c.dp * std::sqrt((double)(a * a + b * b + k * k)) / c.h;
+          if (q < 2.0) {
+            const double w = 1.0 - 0.5 * q;
+            s0 += w * w * w * w * (1.0 + 2.0 * q);
+          }
+        }
+    I.dsum_k = c.rho0 / s0;
+  }
   I.Vw = (c.dim == 2) ? c.dp * c.dp : c.dp * c.dp * c.dp;
   I.rc0 = c.rho0 * c.c0;
   I.eos_k = c.rho0 * c.c0 * c.c0;
@@ -1570,6 +1591,8 @@ int sph_adjoint_forward(sph_ctx *c, const sph_adjoint_desc *d, double *J_out) {
   for (int i = 0; i < c->ninst; ++i) {
     if (c->cfg[i].dt_mode != SPH_DT_FIXED) return fail(SPH_ERR_ARG, "differentiated windows need SPH_DT_FIXED");
     if (c->cfg[i].obc != SPH_OBC_IMPROVED) return fail(SPH_ERR_ARG, "differentiated windows need SPH_OBC_IMPROVED");
+    if (c->cfg[i].density_sum || c->cfg[i].tvf_alpha != 0.0)
+      return fail(SPH_ERR_ARG, "differentiated windows need density_sum = 0 and tvf_alpha = 0");
   }
   const auto &bufs = c->bufs[d->instance];
   if (d->profile_buffer < 0 || d->profile_buffer >= (int32_t)bufs.size() ||

@@ -48,6 +48,10 @@ struct InstDev {
   uint32_t cell_base;  // first global cell key of this instance
   uint32_t ncell;
   int32_t obc;  // SPH_OBC_*: open-boundary treatment (Sec. 4.1 ablation cases)
+  int32_t density_sum;  // density reinitialised by kernel summation each advection step
+  int32_t tvf;          // transport-velocity shift on
+  double tvf_k;         // -2 alpha h^2: shift = tvf_k sum_j V_j grad_i W_ij
+  double dsum_k;        // rho0 alpha_d / sigma_0: rho = dsum_k (1 + sum_j w^4 (5 - 4 w))
   double dp, h, rho0, c0, nu_l, eta, U_ref, dt_ad_fixed;
   double g[3], lo[3], hi[3], L[3];
   double cs;       // cell size 2h

@@ -114,6 +114,15 @@ __device__ __forceinline__ R kernel_F(const Geo<R> &g, R r) {
   return g.c5 * w * w * w;
 }
 
+// Wendland C2 divided by its normalisation, W / alpha_d = w^4 (1 + 2q) with
+// w = 1 - q/2, i.e. w^4 (5 - 4w) (1 at r = 0)
+template <typename R>
+__device__ __forceinline__ R kernel_u(const Geo<R> &g, R r) {
+  const R w = (R)1 - (R)0.5 * (r * g.inv_h);
+  const R w2 = w * w;
+  return w2 * w2 * ((R)5 - (R)4 * w);
+}
+
 // buffer-frame coordinate 0 of a point, in sweep precision, plain order
 template <typename R, int D>
 __device__ __forceinline__ R local0(const R o[3], const R n[3], R x, R y, R z) {

@@ -195,6 +195,11 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   R sv[3] = {0, 0, 0};
   R G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   R dk = 0, de = 0;
+  // transport-velocity shift: sum_j V_j grad_i W_ij; density reinitialisation:
+  // sum_j W_ij / alpha_d = sum_j w^4 (5 - 4 w), w = 1 - q/2 (fluid particles)
+  const bool tvf = I.tvf && lab == 0, dsum = I.density_sum && lab == 0;
+  R gsum[3] = {0, 0, 0};
+  R sig = 0;
 
   // real neighbours
   for (int k0 = 0; k0 < nr; k0 += 4) {
@@ -216,6 +221,12 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
       const R F = kernel_F(g, r);  // dW/dr / r
       const R V = vol<R, D>(B0);
       if (!mirror || !(local0<R, D>(mo, mn, B0.x, B0.y, B0.z) < (R)0)) sym_add_outer<R, D>(A, d, -F * V);
+      if (tvf) {
+        const R FV = F * V;
+#pragma unroll
+        for (int c = 0; c < D; ++c) gsum[c] += FV * d[c];
+      }
+      if (dsum) sig += kernel_u(g, r);
       const R vj[3] = {D == 2 ? B0.w : B1.x, D == 2 ? B1.x : B1.y, D == 2 ? (R)0 : B1.z};
       const R vij[3] = {vi[0] - vj[0], vi[1] - vj[1], vi[2] - vj[2]};
       const R f = Ex<R>::div(F * r, r + g.reg) * V;  // dW/dr / (r + 0.01h) V
@@ -253,6 +264,12 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
     const R F = kernel_F(g, r);
     const R V = Wp.w;
     if (!mirror || !(local0<R, D>(mo, mn, Wp.x, Wp.y, Wp.z) < (R)0)) sym_add_outer<R, D>(A, d, -F * V);
+    if (tvf) {
+      const R FV = F * V;
+#pragma unroll
+      for (int c = 0; c < D; ++c) gsum[c] += FV * d[c];
+    }
+    if (dsum) sig += kernel_u(g, r);
     const V4<R> Wv = pk.WV[w];
     // no-slip: the dummy carries 2 v_wall - v_i
     const R vij[3] = {(R)2 * (vi[0] - Wv.x), (R)2 * (vi[1] - Wv.y), (R)2 * (vi[2] - Wv.z)};
@@ -415,13 +432,20 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   // first half of sub-step 0 (a8): rho += dt/2 drho; p = c0^2 (rho - rho0);
   // x += dt/2 v.  The pressure master keeps the value of the step's last
   // first half, so only that one is stored.
+  // The density reinitialisation and the transport-velocity shift of a fluid
+  // particle come before it (the terms above used the volumes from before).
   const double hdt = 0.5 * I.dt;
-  const double rho = rho_i + hdt * m.drho[i];
+  const double rho_s = dsum ? I.dsum_k * ((double)1 + from_R<R>(sig)) : rho_i;
+  const double rho = rho_s + hdt * m.drho[i];
   const R p = to_R<R>(rho - I.rho0) * sweep_const<R>(I).c0sq;
   m.rho[i] = rho;
   if (I.n_ac == 1) m.p[i] = from_R<R>(p);
 #pragma unroll
-  for (int c = 0; c < D; ++c) m.x[c][i] = m.x[c][i] + hdt * m.v[c][i];
+  for (int c = 0; c < D; ++c) {
+    double xc = m.x[c][i];
+    if (tvf) xc = xc + I.tvf_k * from_R<R>(gsum[c]);
+    m.x[c][i] = xc + hdt * m.v[c][i];
+  }
   // momentum record; pressure-buffer particles are marked so that their
   // neighbours use their own B (the condition B_k = B_i, Sec. 3.3)
   const R V = Ex<R>::div(to_R<R>(m.mass[i]), to_R<R>(rho));

@@ -50,7 +50,8 @@ class Config(C.Structure):
         ("seed", C.c_uint32), ("dp", C.c_double), ("h", C.c_double), ("rho0", C.c_double),
         ("c0", C.c_double), ("nu_l", C.c_double), ("eta", C.c_double), ("U_ref", C.c_double),
         ("dt_ad_fixed", C.c_double), ("gravity", C.c_double * 3), ("domain_lo", C.c_double * 3),
-        ("domain_hi", C.c_double * 3), ("obc", C.c_int32), ("reserved", C.c_int32),
+        ("domain_hi", C.c_double * 3), ("obc", C.c_int32), ("density_sum", C.c_int32),
+        ("tvf_alpha", C.c_double),
     ]
 
 
@@ -201,6 +202,8 @@ def make_config(case, precision: str = "fp64", kinematic: bool = False) -> Confi
     c.dp, c.h, c.rho0, c.c0, c.nu_l = case.dp, case.h, case.rho0, case.c0, case.nu_l
     c.eta, c.U_ref, c.dt_ad_fixed = case.eta, case.U_ref, case.dt_ad_fixed
     c.obc = OBC[getattr(case, "obc", "improved")]
+    c.density_sum = int(bool(getattr(case, "density_sum", False)))
+    c.tvf_alpha = float(getattr(case, "tvf", 0.0))
     return c
 
 
