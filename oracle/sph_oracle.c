@@ -23,6 +23,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define PI_D 3.14159265358979323846
 
@@ -349,38 +352,69 @@ static int build_pairs(const orc_config *c, const orc_state *s, nblist *L) {
   grid_t g;
   int use_grid = (c->neighbor_mode == 1);
   if (use_grid && grid_build(c, s, &g)) return ORC_ERR_NOMEM;
-  nblist cand;
-  memset(&cand, 0, sizeof(cand));
   int rc = ORC_OK;
-  for (int64_t i = 0; i < s->n && rc == ORC_OK; ++i) {
-    L->start[i] = L->count;
-    if (s->dead[i]) continue;
-    const double *xi = &s->pos0[3 * i];
-    cand.count = 0;
-    if (use_grid) {
-      rc = grid_candidates(c, &g, xi, 1, &cand);
-      if (rc) break;
-      qsort(cand.nb, (size_t)cand.count, sizeof(nb_t), nb_cmp);
-    } else {
-      rc = all_candidates(s, &cand);
-      if (rc) break;
-    }
-    for (int64_t t = 0; t < cand.count; ++t) {
-      int64_t j = cand.nb[t].j;
-      int wall = cand.nb[t].wall;
-      if (!wall && j == i) continue;
-      const double *xj = wall ? &s->wpos[3 * j] : &s->pos0[3 * j];
-      double r[3];
-      pair_vector(c, xi, xj, r);
-      double rr = dotd(c->dim, r, r);
-      if (rr > 0.0 && rr < cut2) {
-        rc = nblist_push(L, j, wall);
-        if (rc) break;
+  /* two passes over the particles (threads take particles independently):
+     count each list, place the lists by a prefix sum, then fill them */
+  for (int pass = 0; pass < 2 && rc == ORC_OK; ++pass) {
+    if (pass == 1) {
+      int64_t tot = 0;
+      for (int64_t i = 0; i < s->n; ++i) {
+        int64_t k = L->start[i];
+        L->start[i] = tot;
+        tot += k;
+      }
+      L->start[s->n] = tot;
+      L->count = L->cap = tot;
+      L->nb = (nb_t *)malloc((size_t)(tot > 0 ? tot : 1) * sizeof(nb_t));
+      if (!L->nb) {
+        rc = ORC_ERR_NOMEM;
+        break;
       }
     }
+#pragma omp parallel
+    {
+      nblist cand;
+      memset(&cand, 0, sizeof(cand));
+#pragma omp for schedule(dynamic, 256)
+      for (int64_t i = 0; i < s->n; ++i) {
+        int64_t k = 0;
+        if (!s->dead[i]) {
+          const double *xi = &s->pos0[3 * i];
+          cand.count = 0;
+          int r;
+          if (use_grid) {
+            r = grid_candidates(c, &g, xi, 1, &cand);
+            if (!r) qsort(cand.nb, (size_t)cand.count, sizeof(nb_t), nb_cmp);
+          } else {
+            r = all_candidates(s, &cand);
+          }
+          if (r) {
+#pragma omp atomic write
+            rc = r;
+          } else {
+            for (int64_t t = 0; t < cand.count; ++t) {
+              int64_t j = cand.nb[t].j;
+              int wall = cand.nb[t].wall;
+              if (!wall && j == i) continue;
+              const double *xj = wall ? &s->wpos[3 * j] : &s->pos0[3 * j];
+              double rv[3];
+              pair_vector(c, xi, xj, rv);
+              double rr = dotd(c->dim, rv, rv);
+              if (rr > 0.0 && rr < cut2) {
+                if (pass == 1) {
+                  L->nb[L->start[i] + k].j = j;
+                  L->nb[L->start[i] + k].wall = wall;
+                }
+                ++k;
+              }
+            }
+          }
+        }
+        if (pass == 0) L->start[i] = k;
+      }
+      free(cand.nb);
+    }
   }
-  L->start[s->n] = L->count;
-  free(cand.nb);
   if (use_grid) grid_free(&g);
   return rc;
 }
@@ -550,6 +584,7 @@ static int box_contains(const orc_config *c, const orc_buffer *b, const double *
 }
 
 int orc_label(const orc_config *c, orc_state *s) {
+  #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < s->n; ++i) {
     if (s->dead[i]) continue;
     for (int b = 0; b < s->nbuf; ++b)
@@ -661,11 +696,14 @@ static int orc_bmatrix_impl(const orc_config *c, orc_state *s, double *Aout, con
   grid_t g;
   int use_grid = (c->neighbor_mode == 1);
   if (use_grid && grid_build(c, s, &g)) return ORC_ERR_NOMEM;
-  nblist cand;
-  memset(&cand, 0, sizeof(cand));
   double cut2 = cutoff2(c);
   double Vw = wall_volume(c);
   int rc = ORC_OK;
+#pragma omp parallel
+  {
+  nblist cand;
+  memset(&cand, 0, sizeof(cand));
+#pragma omp for schedule(dynamic, 256)
   for (int64_t i = 0; i < s->n; ++i) {
     if (s->dead[i]) continue;
     const double *xi = &s->pos0[3 * i];
@@ -690,12 +728,20 @@ static int orc_bmatrix_impl(const orc_config *c, orc_state *s, double *Aout, con
         double si = local_coord(c, b, xi, 0);
         double q[3];
         for (int a = 0; a < 3; ++a) q[a] = xi[a] - 2.0 * si * b->frame[a];
-        rc = grid_candidates(c, &g, q, 2, &cand);
-        if (rc) break;
+        int r = grid_candidates(c, &g, q, 2, &cand);
+        if (r) {
+#pragma omp atomic write
+          rc = r;
+          continue;
+        }
         qsort(cand.nb, (size_t)cand.count, sizeof(nb_t), nb_cmp);
       } else {
-        rc = all_candidates(s, &cand);
-        if (rc) break;
+        int r = all_candidates(s, &cand);
+        if (r) {
+#pragma omp atomic write
+          rc = r;
+          continue;
+        }
       }
       for (int64_t t = 0; t < cand.count; ++t) {
         int64_t j = cand.nb[t].j;
@@ -722,6 +768,7 @@ static int orc_bmatrix_impl(const orc_config *c, orc_state *s, double *Aout, con
     }
   }
   free(cand.nb);
+  }
   if (use_grid) grid_free(&g);
   return rc;
 }
@@ -753,6 +800,7 @@ static double mu_of(const orc_config *c, const orc_state *s, int64_t i) {
 static int orc_viscous_impl(const orc_config *c, orc_state *s, const nblist *Lp) {
   const nblist L = *Lp;
   double Vw = wall_volume(c);
+  #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < s->n; ++i) {
     if (s->dead[i]) continue;
     const double *xi = &s->pos0[3 * i];
@@ -823,6 +871,7 @@ static int orc_transport_impl(const orc_config *c, orc_state *s, const nblist *L
   if (!(c->tvf_alpha > 0.0)) return ORC_OK;
   double Vw = wall_volume(c);
   double f = -2.0 * c->tvf_alpha * c->h * c->h;
+  #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < s->n; ++i) {
     if (s->dead[i] || s->label[i] != 0) continue;
     double S[3] = {0, 0, 0};
@@ -861,6 +910,22 @@ int orc_transport(const orc_config *c, orc_state *s) {
 /* taken after the correction matrix, viscous, k-epsilon and transport   */
 /* terms of the step, which use the volumes m / rho from before it.      */
 /* ------------------------------------------------------------------ */
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 double orc_lattice_kernel_sum(const orc_config *c) {
   int R = (int)ceil(2.0 * c->h / c->dp) + 1;
   int Rz = c->dim == 3 ? R : 0;
@@ -880,6 +945,7 @@ static int orc_density_sum_impl(const orc_config *c, orc_state *s, const nblist 
   double sigma0 = orc_lattice_kernel_sum(c);
   double *rs = (double *)malloc((size_t)(s->n > 0 ? s->n : 1) * sizeof(double));
   if (!rs) return ORC_ERR_NOMEM;
+  #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < s->n; ++i) {
     rs[i] = s->rho[i];
     if (s->dead[i] || s->label[i] != 0) continue;
@@ -931,6 +997,7 @@ static int orc_rans_impl(const orc_config *c, orc_state *s, double dt, const nbl
     return ORC_ERR_NOMEM;
   }
   int dim = c->dim;
+  #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     kn[i] = s->k[i];
     en[i] = s->eps[i];
@@ -982,6 +1049,7 @@ static int orc_rans_impl(const orc_config *c, orc_state *s, double dt, const nbl
     kn[i] = k1 > KE_FLOOR ? k1 : KE_FLOOR;
     en[i] = e1 > KE_FLOOR ? e1 : KE_FLOOR;
   }
+  #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     if (s->dead[i]) continue;
     s->k[i] = kn[i];
@@ -1008,6 +1076,7 @@ int orc_rans(const orc_config *c, orc_state *s, double dt) {
 /* x += dt/2 v.                                                         */
 /* ------------------------------------------------------------------ */
 int orc_half1(const orc_config *c, orc_state *s, double dt) {
+  #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < s->n; ++i) {
     if (s->dead[i]) continue;
     s->rho[i] += 0.5 * dt * s->drho[i];
@@ -1039,6 +1108,7 @@ static int orc_momentum_impl(const orc_config *c, orc_state *s, const nblist *Lp
   const nblist L = *Lp;
   double Vw = wall_volume(c);
   int dim = c->dim;
+  #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < s->n; ++i) {
     if (s->dead[i]) continue;
     const double *xi = &s->pos0[3 * i];
@@ -1092,6 +1162,7 @@ int orc_momentum(const orc_config *c, orc_state *s) {
 /* v += dt (a_p + a_nu + g); x += dt/2 v  (Eq. of the general momentum
    discretisation, Sec. 2.2; Verlet half, Sec. 2.3) */
 int orc_kick(const orc_config *c, orc_state *s, double dt) {
+  #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < s->n; ++i) {
     if (s->dead[i]) continue;
     for (int a = 0; a < c->dim; ++a) {
@@ -1115,6 +1186,7 @@ static int orc_continuity_impl(const orc_config *c, orc_state *s, const nblist *
   const nblist L = *Lp;
   double Vw = wall_volume(c);
   int dim = c->dim;
+  #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < s->n; ++i) {
     if (s->dead[i]) continue;
     const double *xi = &s->pos0[3 * i];
@@ -1165,6 +1237,7 @@ int orc_continuity(const orc_config *c, orc_state *s) {
 
 int orc_density(const orc_config *c, orc_state *s, double dt) {
   (void)c;
+  #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < s->n; ++i) {
     if (s->dead[i]) continue;
     s->rho[i] += 0.5 * dt * s->drho[i];
@@ -1227,6 +1300,7 @@ static void apply_bc_one(const orc_config *c, orc_state *s, int64_t i, int64_t s
 }
 
 int orc_apply_bc(const orc_config *c, orc_state *s, int64_t step, uint32_t sub) {
+  #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < s->n; ++i) {
     if (s->dead[i]) continue;
     if (s->label[i] > 0 && s->label[i] <= s->nbuf) apply_bc_one(c, s, i, step, sub);

@@ -159,6 +159,9 @@ int orc_density_sum(const orc_config *c, orc_state *s);         /* density reini
 /* reference number density: sum of W over the lattice of spacing dp around
    a site, the site included (the value a perfect lattice sums to) */
 double orc_lattice_kernel_sum(const orc_config *c);
+/* threads the per-particle loops use (1 without OpenMP; OMP_NUM_THREADS) */
+int orc_num_threads(void);
+void orc_set_threads(int n);
 int orc_rans(const orc_config *c, orc_state *s, double dt);     /* a7 */
 int orc_half1(const orc_config *c, orc_state *s, double dt);    /* a8 */
 int orc_momentum(const orc_config *c, orc_state *s);            /* a9 force only -> acc_p */

@@ -316,6 +316,22 @@ def test_periodic_pairs_use_minimum_image(orc):
     assert counts.min() == counts.max()  # every particle sees a full support
 
 
+def test_thread_count_changes_nothing(orc):
+    """Per-particle sums run in each particle's own neighbour order, so the
+    oracle on one thread and on all of them gives the same bits."""
+    out = []
+    nt = orc.num_threads()
+    for n in (1, max(nt, 2)):
+        orc.set_threads(n)
+        c = cases.turbulent_channel(length=0.3, height=0.1, dp=0.005, jitter_frac=0.05)
+        o = orc.OracleSim(c)
+        o.step(3)
+        out.append(o.fields())
+    orc.set_threads(nt)
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
+
+
 def test_full_step_cell_mode_bit_identical_to_brute_force(orc):
     c = cases.poiseuille_channel(length=1.0, height=0.5)
     a = orc.OracleSim(c, neighbor_mode=0)
