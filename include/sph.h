@@ -422,6 +422,15 @@ int sph_reduce_mass_momentum(sph_ctx *ctx, double *mass, double *momentum);
    SPH_ERR_ALLOC, SPH_ERR_CUDA. */
 int sph_debug_convert(const double *in64, float *out32, const float *in32, double *out64, int64_t n);
 
+/* Measurement aid (no counterpart in the paper): the fused multiply-add
+   throughput of the current GPU in FP32 or FP64 (SPH_PREC_*), in FLOP/s
+   (one FMA = 2 FLOP), from eight independent FMA chains per thread on
+   eight 256-thread blocks per SM, best of three timed launches after one
+   warm-up.  The denominator of the ALU roofline of the pair sweeps.
+   Allocates a small output buffer; synchronises.  Errors: SPH_ERR_ARG,
+   SPH_ERR_ALLOC, SPH_ERR_CUDA. */
+int sph_measure_fma_peak(int32_t precision, double *flops_per_s);
+
 /* Cell sort of a caller's point set that allocates no device memory.  The
    paper has no counterpart: this exists for callers that cannot allocate,
    such as code running while a CUDA stream is being captured into a graph,

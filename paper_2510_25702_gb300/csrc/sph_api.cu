@@ -2123,7 +2123,7 @@ extern "C" int sph_debug_convert(const double *in64, float *out32, const float *
 // FP64 mass and momentum of every instance (deterministic order)
 // ------------------------------------------------------------------------
 namespace {
-constexpr int kRedSlices = 32;   // blocks per instance
+constexpr int kRedSlices = 128;  // blocks per instance
 constexpr int kRedThreads = 256;
 
 // first index in [lo, hi) whose instance is >= q (instances non-decreasing

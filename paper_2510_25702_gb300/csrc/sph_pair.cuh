@@ -241,13 +241,46 @@ __device__ __forceinline__ void scan_range(const Geo<R> &g, const V4<R> &Pi, con
     rr = pair_vec<R, D, PER>(g, Pi, q3, d);
     sure |= (j + 3 < je && rr > (R)0 && rr < lo) ? 8u : 0u;
     if (sizeof(R) == 4) maybe |= (j + 3 < je && rr < hi) ? 8u : 0u;
-    if (sizeof(R) == 8) maybe = sure;
-    while (maybe) {
-      const int k = __ffs(maybe) - 1;
-      maybe &= maybe - 1;
-      if (((sure >> k) & 1u) || exact(j + (uint32_t)k)) hit(j + (uint32_t)k);
+    if (sizeof(R) == 4) {
+      // candidates the FP32 test cannot decide (rare): the FP64 test, out of
+      // the common path
+      unsigned amb = maybe & ~sure;
+      if (__builtin_expect(amb != 0u, 0)) {
+        while (amb) {
+          const int k = __ffs(amb) - 1;
+          amb &= amb - 1;
+          if (exact(j + (uint32_t)k)) sure |= 1u << k;
+        }
+      }
+    }
+    while (sure) {
+      const int k = __ffs(sure) - 1;
+      sure &= sure - 1;
+      hit(j + (uint32_t)k);
     }
   }
+}
+
+// The FP64 test of the definition, 0 < |x_i - x_j|^2 < (2h)^2 summed left to
+// right without contraction (minimum image on periodic axes), on the FP64
+// positions of i (xi) and j (xj[c][j]): the decision for the rare FP32
+// candidates within the band of the cut-off.  Not inlined, so that the
+// FP64 work stays off the candidate loop.
+static __device__ __noinline__ bool exact_pair_test(const InstDev &I, int dim, const double xi[3],
+                                             const double *const xj[3], uint32_t j) {
+  double rr = 0.0;
+  for (int c = 0; c < dim; ++c) {
+    double v = dsub(xi[c], xj[c][j]);
+    if (I.periodic[c]) {
+      const double hl = 0.5 * I.L[c];
+      if (v > hl)
+        v = dsub(v, I.L[c]);
+      else if (v < -hl)
+        v = dadd(v, I.L[c]);
+    }
+    rr = (c == 0) ? dmul(v, v) : dadd(rr, dmul(v, v));
+  }
+  return rr > 0.0 && rr < I.cut2;
 }
 
 // Half-width of the FP32 band around the cut-off within which the FP32

@@ -87,20 +87,8 @@ __device__ __forceinline__ int list_one(const SweepArgs &a, const Packs<R> &pk, 
     // the definition in FP64 on the masters (rare: candidates in the band)
     auto exact = [&](uint32_t j) -> bool {
       if (set == 0 && j == (uint32_t)i) return false;
-      double rr = 0.0;
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        double v = dsub(a.m.x[c][i], set == 0 ? a.m.x[c][j] : a.wx[c][j]);
-        if (PER && I.periodic[c]) {
-          const double hl = 0.5 * I.L[c];
-          if (v > hl)
-            v = dsub(v, I.L[c]);
-          else if (v < -hl)
-            v = dadd(v, I.L[c]);
-        }
-        rr = (c == 0) ? dmul(v, v) : dadd(rr, dmul(v, v));
-      }
-      return rr > 0.0 && rr < I.cut2;
+      const double xi[3] = {a.m.x[0][i], a.m.x[1][i], D == 3 ? a.m.x[2][i] : 0.0};
+      return exact_pair_test(I, D, xi, set == 0 ? a.m.x : a.wx, j);
     };
     auto scan = [&](uint32_t jb, uint32_t je) {
       scan_range<R, D, PER>(g, Pi, recs, stride, jb, je, lo, hi, [&](uint32_t j) {

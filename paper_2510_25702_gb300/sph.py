@@ -108,7 +108,7 @@ EXPORTS = ("sph_create", "sph_add_buffer", "sph_set_profile", "sph_step", "sph_r
            "sph_cell_sort_noalloc", "sph_set_graph", "sph_set_launch", "sph_get_launch", "sph_autotune",
            "sph_save_state", "sph_restore_state", "sph_drop_state", "sph_adjoint_forward",
            "sph_adjoint_backward", "sph_adjoint_release", "sph_debug_convert", "sph_step_async",
-           "sph_reduce_mass_momentum")
+           "sph_reduce_mass_momentum", "sph_measure_fma_peak")
 NOALLOC_MAX_POINTS = 1 << 19
 N_STAGES = 10
 
@@ -157,6 +157,7 @@ def lib():
         L.sph_adjoint_forward.argtypes = [vp, C.POINTER(AdjointDesc), C.POINTER(C.c_double)]
         L.sph_adjoint_backward.argtypes = [vp, C.POINTER(C.c_double), C.c_int32]
         L.sph_adjoint_release.argtypes = [vp]
+        L.sph_measure_fma_peak.argtypes = [C.c_int32, C.POINTER(C.c_double)]
         L.sph_error_string.restype = C.c_char_p
         L.sph_last_error.restype = C.c_char_p
         _lib = L
@@ -170,6 +171,13 @@ def _check(rc: int, what: str):
 
 def _dptr(a: np.ndarray) -> int:
     return a.ctypes.data
+
+
+def measure_fma_peak(precision: str = "fp32") -> float:
+    """FMA throughput of the current GPU in FLOP/s (sph_measure_fma_peak)."""
+    out = C.c_double()
+    _check(lib().sph_measure_fma_peak(PREC[precision], C.byref(out)), "sph_measure_fma_peak")
+    return out.value
 
 
 def debug_convert(x64: np.ndarray, x32: np.ndarray):
