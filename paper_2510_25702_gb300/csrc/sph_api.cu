@@ -2127,16 +2127,25 @@ constexpr int kRedSlices = 128;  // blocks per instance
 constexpr int kRedThreads = 256;
 
 // first index in [lo, hi) whose instance is >= q (instances non-decreasing
-// there)
-__device__ int inst_lower_bound(const uint16_t *inst, int lo, int hi, int q) {
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if ((int)inst[mid] < q)
-      lo = mid + 1;
-    else
-      hi = mid;
+// there), found by the 32 lanes of a warp together: each round probes 32
+// evenly spaced rows and keeps the interval between the last probe below q
+// and the first at or above it, so a search over n rows takes about
+// log32(n) dependent loads
+__device__ int inst_lower_bound_warp(const uint16_t *inst, int lo, int hi, int q) {
+  const int lane = threadIdx.x & 31;
+  while (hi - lo > 32) {
+    const int step = (hi - lo + 31) / 32;
+    const int probe = lo + lane * step;
+    const unsigned below = __ballot_sync(0xffffffffu, probe < hi && (int)inst[probe] < q);
+    const int t = __popc(below);  // lanes 0 .. t-1 probe rows below q
+    const int nlo = t == 0 ? lo : lo + (t - 1) * step + 1;
+    const int nhi = t == 32 ? hi : min(hi, lo + t * step);
+    lo = nlo;
+    hi = nhi;
   }
-  return lo;
+  const int probe = lo + lane;
+  const unsigned below = __ballot_sync(0xffffffffu, probe < hi && (int)inst[probe] < q);
+  return lo + __popc(below);
 }
 
 // block (q, s): slice s of instance q's rows, which are one run in
@@ -2149,11 +2158,12 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(Masters m, const
   const int q = blockIdx.x / kRedSlices, sl = blockIdx.x % kRedSlices;
   const int n1 = cnt->n_live, n2 = cnt->m_pending;
   __shared__ int s_r[4];
-  if (threadIdx.x == 0) {
-    s_r[0] = inst_lower_bound(m.inst, 0, n1, q);
-    s_r[1] = inst_lower_bound(m.inst, s_r[0], n1, q + 1);
-    s_r[2] = inst_lower_bound(m.inst, n1, n2, q);
-    s_r[3] = inst_lower_bound(m.inst, s_r[2], n2, q + 1);
+  // the four run bounds, one warp each
+  const int wq = threadIdx.x >> 5;
+  if (wq < 4) {
+    const int lo = wq < 2 ? 0 : n1, hi = wq < 2 ? n1 : n2;
+    const int r = inst_lower_bound_warp(m.inst, lo, hi, q + (wq & 1));
+    if ((threadIdx.x & 31) == 0) s_r[wq] = r;
   }
   __syncthreads();
   const int a0 = s_r[0], la = s_r[1] - s_r[0], b0 = s_r[2], L = la + (s_r[3] - s_r[2]);
@@ -2178,13 +2188,18 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(Masters m, const
     for (int c = 0; c < 4; ++c) partial[(size_t)blockIdx.x * 4 + c] = red[c][0];
 }
 
-__global__ void k_reduce_final(const double *partial, int ninst, double *out) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= ninst) return;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int sl = 0; sl < kRedSlices; ++sl)
-    for (int c = 0; c < 4; ++c) acc[c] = sphk::dadd(acc[c], partial[((size_t)q * kRedSlices + sl) * 4 + c]);
-  for (int c = 0; c < 4; ++c) out[(size_t)q * 4 + c] = acc[c];
+// one block per instance: the slices' partial sums in a fixed tree
+__global__ void __launch_bounds__(kRedSlices) k_reduce_final(const double *partial, int ninst, double *out) {
+  const int q = blockIdx.x;
+  __shared__ double red[4][kRedSlices];
+  for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = partial[((size_t)q * kRedSlices + threadIdx.x) * 4 + c];
+  __syncthreads();
+  for (int w = kRedSlices / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = sphk::dadd(red[c][threadIdx.x], red[c][threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) out[(size_t)q * 4 + threadIdx.x] = red[threadIdx.x][0];
 }
 }  // namespace
 
@@ -2199,7 +2214,7 @@ extern "C" int sph_reduce_mass_momentum(sph_ctx *c, double *mass, double *moment
   double *partial = c->red, *res = c->red + 4 * (size_t)c->ninst * kRedSlices;
   k_reduce_partial<<<c->ninst * kRedSlices, kRedThreads, 0, c->stream>>>(c->M[c->cur], c->K[0], c->ncell, c->cnt,
                                                                          c->dim, partial);
-  k_reduce_final<<<(c->ninst + 127) / 128, 128, 0, c->stream>>>(partial, c->ninst, res);
+  k_reduce_final<<<c->ninst, kRedSlices, 0, c->stream>>>(partial, c->ninst, res);
   CUDA_TRY(cudaGetLastError());
   std::vector<double> h(4 * (size_t)c->ninst);
   CUDA_TRY(cudaMemcpyAsync(h.data(), res, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
