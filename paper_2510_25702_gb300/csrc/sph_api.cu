@@ -297,7 +297,11 @@ struct sph_ctx {
     a.gbar = gbar;
     for (int q = 0; q < 3; ++q) a.wx[q] = wx[q];
     a.any_periodic = 0;
-    for (const InstDev &I : inst) a.any_periodic |= I.periodic[0] | I.periodic[1] | I.periodic[2];
+    a.any_extra = 0;
+    for (const InstDev &I : inst) {
+      a.any_periodic |= I.periodic[0] | I.periodic[1] | I.periodic[2];
+      a.any_extra |= I.tvf | I.density_sum;
+    }
     return a;
   }
 };

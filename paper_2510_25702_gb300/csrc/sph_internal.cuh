@@ -548,6 +548,7 @@ struct SweepArgs {
   int32_t *status;
   int32_t sub;
   int32_t any_periodic;  // some instance has a periodic axis
+  int32_t any_extra;     // some instance takes the transport shift or the density reinitialisation
   int32_t block;         // threads per block of the launch
   double *tape_S;        // optional: momentum sums S1, Cb, S2, Ct per sub-step
   StepArgs ts;           // list builder: time step of every instance by block 0

@@ -133,7 +133,10 @@ __device__ __forceinline__ int list_one(const SweepArgs &a, const Packs<R> &pk, 
 // =========================================================================
 // advection sweep: B (+ mirror), viscous acceleration, k-epsilon, half 1
 // =========================================================================
-template <typename R, int D, bool PER>
+// X: some instance of the context takes the transport-velocity shift or the
+// density reinitialisation (their sums cost the pair loop a few percent, so
+// contexts without them run a form that leaves them out)
+template <typename R, int D, bool PER, bool X>
 __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, const int i) {
   constexpr int RA = RecLayout<D>::adv;
   const Masters &m = a.m;
@@ -185,7 +188,7 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   R dk = 0, de = 0;
   // transport-velocity shift: sum_j V_j grad_i W_ij; density reinitialisation:
   // sum_j W_ij / alpha_d = sum_j w^4 (5 - 4 w), w = 1 - q/2 (fluid particles)
-  const bool tvf = I.tvf && lab == 0, dsum = I.density_sum && lab == 0;
+  const bool tvf = X && I.tvf && lab == 0, dsum = X && I.density_sum && lab == 0;
   R gsum[3] = {0, 0, 0};
   R sig = 0;
 
@@ -750,7 +753,7 @@ __global__ void __launch_bounds__(kMaxBlock, kListMinBlocks<R, D>) k_list(SweepA
   }
 }
 
-template <typename R, int D, bool PER>
+template <typename R, int D, bool PER, bool X>
 __global__ void __launch_bounds__(kMaxBlock, kAdvMinBlocks<R, D>) k_adv(SweepArgs a, Packs<R> pk) {
   if (a.cnt->status) return;
   const int n = a.cnt->n_live;
@@ -758,7 +761,7 @@ __global__ void __launch_bounds__(kMaxBlock, kAdvMinBlocks<R, D>) k_adv(SweepArg
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
     // the next tile's neighbour list on its way to L2 while this one runs
     if ((threadIdx.x & 31) == 0 && i + step < n) prefetch_list_tile(a.nl, i + step);
-    adv_one<R, D, PER>(a, pk, i);
+    adv_one<R, D, PER, X>(a, pk, i);
   }
 }
 
@@ -954,7 +957,7 @@ static void launch_sweeps_impl(int which, const SweepArgs &a, Packs<R> &pk, int 
     auto k = k_list<R, D, PER>;
     k<<<resident_grid(k, b, max_n), b, 0, st>>>(a, pk);
   } else if (which == 0) {
-    auto k = k_adv<R, D, PER>;
+    auto k = a.any_extra ? k_adv<R, D, PER, true> : k_adv<R, D, PER, false>;
     k<<<resident_grid(k, b, max_n), b, 0, st>>>(a, pk);
   } else if (which == 1) {
     auto k = k_mom<R, D, PER>;
