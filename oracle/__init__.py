@@ -51,7 +51,7 @@ class OrcConfig(C.Structure):
         ("gen_offset", C.c_double), ("id_check", C.c_int), ("contain_check", C.c_int),
         ("mirror_B", C.c_int), ("compensation", C.c_int), ("neighbor_mode", C.c_int),
         ("rkgc", C.c_int), ("freeze_turb", C.c_int), ("comp_B", C.c_int), ("bhat_buffer", C.c_int),
-        ("density_sum", C.c_int), ("tvf_alpha", C.c_double),
+        ("density_sum", C.c_int), ("wall_fn", C.c_int), ("pad_wf", C.c_int), ("tvf_alpha", C.c_double),
     ]
 
 
@@ -114,6 +114,8 @@ def lib():
         L.orc_kernel_sum.argtypes = [cfgp, stp, _PD]
         L.orc_num_threads.restype = C.c_int
         L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_wall_utau.restype = C.c_double
+        L.orc_wall_utau.argtypes = [C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int)]
         _lib = L
     return _lib
 
@@ -121,6 +123,13 @@ def lib():
 def num_threads() -> int:
     """Threads the oracle's per-particle loops run on (OMP_NUM_THREADS)."""
     return int(lib().orc_num_threads())
+
+
+def wall_utau(ut: float, y: float, nu: float):
+    """(u_tau, log_layer) of the step-wise wall law."""
+    lg = C.c_int()
+    u = lib().orc_wall_utau(float(ut), float(y), float(nu), C.byref(lg))
+    return float(u), bool(lg.value)
 
 
 def set_threads(n: int):
@@ -198,6 +207,7 @@ class OracleSim:
         c.comp_B, c.bhat_buffer = comp_B, bhat_buffer
         c.tvf_alpha = float(getattr(case, "tvf", 0.0))
         c.density_sum = int(bool(getattr(case, "density_sum", False)))
+        c.wall_fn = int(bool(getattr(case, "wall_function", False)))
         # the open-boundary treatment of the case (Table of Sec. 4.1) sets
         # the switches it names; the improved scheme keeps the arguments
         obc = OBC_SWITCHES[getattr(case, "obc", "improved")]

@@ -782,6 +782,96 @@ int orc_bmatrix(const orc_config *c, orc_state *s, double *Aout) {
 }
 
 /* ------------------------------------------------------------------ */
+/* Step-wise wall function (Sec. 2.3 uses the one of its reference for   */
+/* turbulent walls and gives no formula; this is the standard two-layer  */
+/* wall law).  A near-wall particle is a fluid particle (label 0) of a   */
+/* RANS run with the wall function on that has wall neighbours and lies  */
+/* less than dp from the wall surface: y_i = min_w |r_iw| - dp/2 (the    */
+/* first dummy layer sits dp/2 inside the wall).  Its wall normal is     */
+/* n = -sum_w V_w grad_i W_iw normalised (pointing away from the wall),  */
+/* its tangential speed u_t = |v_r - (v_r . n) n| with v_r = v_i - v_w of */
+/* the nearest dummy.  The friction velocity u_tau solves the viscous    */
+/* sublayer law u_t = u_tau^2 y / nu_l while y+ = u_tau y / nu_l <=      */
+/* 11.225 (where the two laws meet), else the log law                    */
+/* u_t = (u_tau / kappa) ln(E y u_tau / nu_l), kappa = 0.4187, E = 9.793 */
+/* (the two laws meet at y+ = 11.225), by 8 Newton steps from the        */
+/* sublayer value (the log-law residual is                               */
+/* convex and increasing in u_tau and that value lies below the root).   */
+/* Effects: the viscous term of its wall pairs uses nu_w = u_tau^2 y /   */
+/* u_t, so that the wall shear stress is rho0 u_tau^2; in the k-eps      */
+/* sweep its production is the log-law value G_k = u_tau^3 / (kappa y)    */
+/* (0 in the sublayer) and after the update eps is set to the wall value */
+/* C_mu^(3/4) k^(3/2) / (kappa y) (2 nu_l k / y^2 in the sublayer).      */
+/* ------------------------------------------------------------------ */
+#define WF_KAPPA 0.4187
+#define WF_E 9.793
+#define WF_YPLUS 11.225
+
+double orc_wall_utau(double ut, double y, double nu, int *log_layer) {
+  if (!(ut > 0.0) || !(y > 0.0)) {
+    if (log_layer) *log_layer = 0;
+    return 0.0;
+  }
+  double u = sqrt(nu * ut / y);
+  if (u * y / nu <= WF_YPLUS) {
+    if (log_layer) *log_layer = 0;
+    return u;
+  }
+  for (int it = 0; it < 8; ++it) {
+    double L = log(WF_E * y * u / nu);
+    double f = u * L / WF_KAPPA - ut;
+    double fp = (L + 1.0) / WF_KAPPA;
+    u = u - f / fp;
+  }
+  if (log_layer) *log_layer = 1;
+  return u;
+}
+
+typedef struct {
+  int on;        /* near-wall particle */
+  int log_layer; /* u_tau from the log law */
+  double y, ut, utau;
+} nearwall_t;
+
+static void near_wall(const orc_config *c, const orc_state *s, const nblist *L, int64_t i, nearwall_t *w) {
+  memset(w, 0, sizeof(*w));
+  if (!c->rans || !c->wall_fn || s->label[i] != 0) return;
+  double Vw = wall_volume(c);
+  double rmin = 0.0, nsum[3] = {0, 0, 0};
+  int64_t wmin = -1;
+  for (int64_t t = L->start[i]; t < L->start[i + 1]; ++t) {
+    if (!L->nb[t].wall) continue;
+    int64_t j = L->nb[t].j;
+    geom_t G;
+    pair_geom(c, &s->pos0[3 * i], &s->wpos[3 * j], &G);
+    if (wmin < 0 || G.rl < rmin) {
+      rmin = G.rl;
+      wmin = j;
+    }
+    for (int a = 0; a < 3; ++a) nsum[a] -= Vw * G.gw[a];
+  }
+  if (wmin < 0) return;
+  double y = rmin - 0.5 * c->dp;
+  if (!(y > 0.0 && y < c->dp)) return;
+  double nn = sqrt(dotd(c->dim, nsum, nsum));
+  if (!(nn > 0.0)) return;
+  double vr[3] = {0, 0, 0}, vn = 0.0;
+  for (int a = 0; a < c->dim; ++a) {
+    vr[a] = s->vel[3 * i + a] - s->wvel[3 * wmin + a];
+    vn += vr[a] * (nsum[a] / nn);
+  }
+  double ut2 = 0.0;
+  for (int a = 0; a < c->dim; ++a) {
+    double t = vr[a] - vn * (nsum[a] / nn);
+    ut2 += t * t;
+  }
+  w->on = 1;
+  w->y = y;
+  w->ut = sqrt(ut2);
+  w->utau = orc_wall_utau(w->ut, y, c->nu_l, &w->log_layer);
+}
+
+/* ------------------------------------------------------------------ */
 /* a6: ARD viscous acceleration (Sec. 2.2), once per advection step:    */
 /*   a_i = (2/rho_i) sum_j mu_ad v_ij dW/(r_ij + 0.01h) V_j,            */
 /*   mu_ad = max(harmonic(mu_i, mu_j), mu_R), mu = rho0 nu_eff,         */
@@ -806,6 +896,11 @@ static int orc_viscous_impl(const orc_config *c, orc_state *s, const nblist *Lp)
     const double *xi = &s->pos0[3 * i];
     const double *vi = &s->vel[3 * i];
     double mui = mu_of(c, s, i);
+    /* wall pairs of a near-wall particle: the wall-function viscosity */
+    double muw = mui;
+    nearwall_t nw;
+    near_wall(c, s, &L, i, &nw);
+    if (nw.on && nw.ut > 0.0) muw = c->rho0 * (nw.utau * nw.utau * nw.y / nw.ut);
     double S[3] = {0, 0, 0};
     for (int64_t t = L.start[i]; t < L.start[i + 1]; ++t) {
       int64_t j = L.nb[t].j;
@@ -819,7 +914,7 @@ static int orc_viscous_impl(const orc_config *c, orc_state *s, const nblist *Lp)
       }
       double mut;
       if (wall) {
-        mut = mui;
+        mut = muw;
       } else {
         double muj = mu_of(c, s, j);
         mut = 2.0 * mui * muj / (mui + muj);
@@ -1042,12 +1137,22 @@ static int orc_rans_impl(const orc_config *c, orc_state *s, double dt, const nbl
       for (int b = 0; b < dim; ++b) prod += (gv[3 * a + b] + gv[3 * b + a]) * gv[3 * a + b];
     }
     double Gk = s->nut[i] * prod - (2.0 / 3.0) * ki * tr;
+    nearwall_t nw;
+    near_wall(c, s, &L, i, &nw);
+    if (nw.on) Gk = nw.log_layer ? nw.utau * nw.utau * nw.utau / (WF_KAPPA * nw.y) : 0.0;
     double dkdt = Gk - ei + 2.0 * dk / s->rho[i];
     double dedt = KE_C1 * (ei / ki) * Gk - KE_C2 * ei * ei / ki + 2.0 * de / s->rho[i];
     double k1 = ki + dt * dkdt;
     double e1 = ei + dt * dedt;
     kn[i] = k1 > KE_FLOOR ? k1 : KE_FLOOR;
     en[i] = e1 > KE_FLOOR ? e1 : KE_FLOOR;
+    if (nw.on) {
+      /* the wall value of eps from the updated k */
+      double kk = kn[i];
+      double ew = nw.log_layer ? pow(KE_CMU, 0.75) * (kk * sqrt(kk)) / (WF_KAPPA * nw.y)
+                               : 2.0 * c->nu_l * kk / (nw.y * nw.y);
+      en[i] = ew > KE_FLOOR ? ew : KE_FLOOR;
+    }
   }
   #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {

@@ -75,6 +75,8 @@ typedef struct orc_config {
                      /* Sec. 3.3); 0: their own B_j (Case 2)                     */
   int density_sum;   /* 1: fluid density reinitialised by kernel summation   */
                      /* once per advection step (dual-criteria scheme, Sec. 2.3) */
+  int wall_fn;       /* 1: step-wise wall function at the walls (RANS, Sec. 2.3) */
+  int pad_wf;
   double tvf_alpha;  /* transport-velocity correction (Sec. 2.3): fluid       */
                      /* particles move by -2 alpha h^2 sum_j V_j grad_i W_ij    */
                      /* once per advection step; 0 = off                       */
@@ -162,6 +164,11 @@ double orc_lattice_kernel_sum(const orc_config *c);
 /* threads the per-particle loops use (1 without OpenMP; OMP_NUM_THREADS) */
 int orc_num_threads(void);
 void orc_set_threads(int n);
+/* friction velocity of the step-wise wall law for the tangential speed ut
+   at wall distance y: viscous sublayer ut = utau^2 y / nu when
+   y+ = utau y / nu <= 11.225, else ut = (utau / 0.4187) ln(9.793 y utau / nu);
+   *log_layer (may be NULL) tells which */
+double orc_wall_utau(double ut, double y, double nu, int *log_layer);
 int orc_rans(const orc_config *c, orc_state *s, double dt);     /* a7 */
 int orc_half1(const orc_config *c, orc_state *s, double dt);    /* a8 */
 int orc_momentum(const orc_config *c, orc_state *s);            /* a9 force only -> acc_p */

@@ -84,6 +84,7 @@ class Case:
     obc: str = "improved"
     tvf: float = 0.0  # transport-velocity shift coefficient alpha (0 = off)
     density_sum: bool = False  # density reinitialised by summation every advection step
+    wall_function: bool = False  # step-wise wall function at the walls (RANS)
 
     @property
     def n(self) -> int:
