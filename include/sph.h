@@ -100,6 +100,9 @@ typedef struct sph_config {
   int32_t density_sum; /* 1: density of fluid particles re-evaluated once per
                           advection step by kernel summation (below) */
   double tvf_alpha;   /* transport-velocity correction (below); 0 = off */
+  int32_t wall_function; /* 1: step-wise wall function at the walls (RANS
+                            instances; below) */
+  int32_t reserved;
 } sph_config;
 
 /* The two stages of the advection step that Sec. 2.3 names through the
@@ -115,7 +118,18 @@ typedef struct sph_config {
      sigma_i = W(0) + sum_j W_ij over real and wall neighbours and sigma_0
      the same sum on the perfect lattice of spacing dp.
    The acoustic sub-steps start from the reinitialised density.
-   Differentiated windows need both off. */
+   Step-wise wall function (Sec. 2.3 uses the one of its reference at
+   turbulent walls; the standard two-layer wall law): a fluid particle of a
+   RANS instance lying y < dp from the wall surface (y = distance to its
+   nearest wall dummy - dp/2) takes the friction velocity u_tau of the law
+   u_t = u_tau^2 y / nu_l (y+ <= 11.225) or u_t = (u_tau / 0.4187)
+   ln(9.793 y u_tau / nu_l), u_t its speed along the wall relative to that
+   dummy (the wall normal from its wall kernel-gradient sum); its wall pairs
+   carry the viscosity u_tau^2 y / u_t (wall stress rho0 u_tau^2), its k
+   production is u_tau^3 / (0.4187 y) (0 in the sublayer) and after the
+   k-eps update eps takes the wall value C_mu^(3/4) k^(3/2) / (0.4187 y)
+   (2 nu_l k / y^2 in the sublayer).
+   Differentiated windows need all three off. */
 
 /* sph_config.obc: the open-boundary treatments compared in Sec. 4.1 (Table
    of the four cases), for ablation.  IMPROVED (case 4, default): B_i with

@@ -300,7 +300,7 @@ struct sph_ctx {
     a.any_extra = 0;
     for (const InstDev &I : inst) {
       a.any_periodic |= I.periodic[0] | I.periodic[1] | I.periodic[2];
-      a.any_extra |= I.tvf | I.density_sum;
+      a.any_extra |= I.tvf | I.density_sum | I.wall_fn;
     }
     return a;
   }
@@ -349,6 +349,7 @@ static int build_inst(const sph_config &c, InstDev &I, std::string &why) {
   if (c.obc < SPH_OBC_IMPROVED || c.obc > SPH_OBC_MINIMAL_MIRROR) return why = "bad obc", -1;
   if (c.density_sum != 0 && c.density_sum != 1) return why = "density_sum must be 0 or 1", -1;
   if (!(c.tvf_alpha >= 0.0 && c.tvf_alpha < 1.0)) return why = "tvf_alpha must be in [0, 1)", -1;
+  if (c.wall_function != 0 && c.wall_function != 1) return why = "wall_function must be 0 or 1", -1;
   I.dim = c.dim;
   I.rans = c.rans ? 1 : 0;
   I.dt_mode = c.dt_mode;
@@ -358,6 +359,8 @@ static int build_inst(const sph_config &c, InstDev &I, std::string &why) {
   I.density_sum = c.density_sum;
   I.tvf = c.tvf_alpha > 0.0 ? 1 : 0;
   I.tvf_k = -2.0 * c.tvf_alpha * c.h * c.h;
+  I.wall_fn = c.wall_function ? 1 : 0;
+  I.wf_cmu34 = std::pow(kCmu, 0.75);
   I.seed = c.seed;
   I.dp = c.dp;
   I.h = c.h;
@@ -1595,8 +1598,8 @@ int sph_adjoint_forward(sph_ctx *c, const sph_adjoint_desc *d, double *J_out) {
   for (int i = 0; i < c->ninst; ++i) {
     if (c->cfg[i].dt_mode != SPH_DT_FIXED) return fail(SPH_ERR_ARG, "differentiated windows need SPH_DT_FIXED");
     if (c->cfg[i].obc != SPH_OBC_IMPROVED) return fail(SPH_ERR_ARG, "differentiated windows need SPH_OBC_IMPROVED");
-    if (c->cfg[i].density_sum || c->cfg[i].tvf_alpha != 0.0)
-      return fail(SPH_ERR_ARG, "differentiated windows need density_sum = 0 and tvf_alpha = 0");
+    if (c->cfg[i].density_sum || c->cfg[i].tvf_alpha != 0.0 || c->cfg[i].wall_function)
+      return fail(SPH_ERR_ARG, "differentiated windows need density_sum = 0, tvf_alpha = 0 and wall_function = 0");
   }
   const auto &bufs = c->bufs[d->instance];
   if (d->profile_buffer < 0 || d->profile_buffer >= (int32_t)bufs.size() ||

@@ -123,6 +123,29 @@ __device__ __forceinline__ R kernel_u(const Geo<R> &g, R r) {
   return w2 * w2 * ((R)5 - (R)4 * w);
 }
 
+// Friction velocity of the step-wise (two-layer) wall law for the
+// tangential speed ut at wall distance y (FP64): the viscous sublayer
+// ut = u_tau^2 y / nu while y+ = u_tau y / nu <= 11.225, else the log law
+// ut = (u_tau / kappa) ln(E y u_tau / nu) by 8 Newton steps from the
+// sublayer value (the residual is convex and increasing in u_tau and that
+// value lies below its root); kappa = 0.4187 and E = 9.793 make the two
+// laws meet at y+ = 11.225
+constexpr double kWfKappa = 0.4187, kWfE = 9.793, kWfYplus = 11.225;
+__device__ __forceinline__ double wall_utau(double ut, double y, double nu, bool &log_layer) {
+  log_layer = false;
+  if (!(ut > 0.0) || !(y > 0.0)) return 0.0;
+  double u = sqrt(nu * ut / y);
+  if (u * y / nu <= kWfYplus) return u;
+  for (int it = 0; it < 8; ++it) {
+    const double L = log(kWfE * y * u / nu);
+    const double f = u * L / kWfKappa - ut;
+    const double fp = (L + 1.0) / kWfKappa;
+    u = u - f / fp;
+  }
+  log_layer = true;
+  return u;
+}
+
 // buffer-frame coordinate 0 of a point, in sweep precision, plain order
 template <typename R, int D>
 __device__ __forceinline__ R local0(const R o[3], const R n[3], R x, R y, R z) {

@@ -192,6 +192,58 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   R gsum[3] = {0, 0, 0};
   R sig = 0;
 
+  // step-wise wall function (RANS, a fluid particle less than dp from the
+  // wall surface): wall distance, normal and nearest dummy from a first pass
+  // over the wall neighbours, then the friction velocity of the two-layer
+  // wall law in FP64; its wall pairs then carry nu_w = u_tau^2 y / u_t
+  bool wf = false, wf_log = false;
+  double wf_y = 0.0, wf_utau = 0.0;
+  R mu_wall = mu_i;
+  if (X && rans && I.wall_fn && lab == 0 && nw > 0) {
+    R rmin = (R)0, ns[3] = {0, 0, 0};
+    uint32_t wmin = 0;
+    for (int kk = nr; kk < nr + nw; ++kk) {
+      const uint32_t w = list_at(Lst, kk);
+      const V4<R> Wp = pk.WP[w];
+      R d[3];
+      const R rr = pair_vec<R, D, PER>(g, A0, Wp, d);
+      R r;
+      Ex<R>::len(rr, r);
+      if (kk == nr || r < rmin) {
+        rmin = r;
+        wmin = w;
+      }
+      const R FV = kernel_F(g, r) * Wp.w;
+#pragma unroll
+      for (int c = 0; c < D; ++c) ns[c] -= FV * d[c];
+    }
+    const double y = from_R<R>(rmin) - 0.5 * I.dp;
+    double nn = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) nn += from_R<R>(ns[c]) * from_R<R>(ns[c]);
+    nn = sqrt(nn);
+    if (y > 0.0 && y < I.dp && nn > 0.0) {
+      const V4<R> Wv = pk.WV[wmin];
+      const double wv[3] = {from_R<R>(Wv.x), from_R<R>(Wv.y), from_R<R>(Wv.z)};
+      double vr[3] = {0.0, 0.0, 0.0}, vn = 0.0, ut2 = 0.0;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        vr[c] = from_R<R>(vi[c]) - wv[c];
+        vn += vr[c] * (from_R<R>(ns[c]) / nn);
+      }
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const double t = vr[c] - vn * (from_R<R>(ns[c]) / nn);
+        ut2 += t * t;
+      }
+      const double ut = sqrt(ut2);
+      wf = true;
+      wf_y = y;
+      wf_utau = wall_utau(ut, y, I.nu_l, wf_log);
+      if (ut > 0.0) mu_wall = to_R<R>(I.rho0 * (wf_utau * wf_utau * y / ut));
+    }
+  }
+
   // real neighbours
   for (int k0 = 0; k0 < nr; k0 += 4) {
     // four list entries per load, their four records gathered together
@@ -264,12 +316,12 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
     const V4<R> Wv = pk.WV[w];
     // no-slip: the dummy carries 2 v_wall - v_i
     const R vij[3] = {(R)2 * (vi[0] - Wv.x), (R)2 * (vi[1] - Wv.y), (R)2 * (vi[2] - Wv.z)};
-    R mu_ad = mu_i;
+    R mu_ad = mu_wall;
     if (rans) {
       R muR = -(vij[0] * d[0] + vij[1] * d[1] + vij[2] * d[2]) * Ex<R>::inv_len(rr, r) * muR_eta;
       muR = muR > (R)0 ? muR : (R)0;
       muR = muR < muR_c0 ? muR : muR_c0;
-      mu_ad = mu_i > muR ? mu_i : muR;
+      mu_ad = mu_wall > muR ? mu_wall : muR;
       const R FV = F * V;
 #pragma unroll
       for (int p = 0; p < D; ++p)
@@ -403,7 +455,10 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
       for (int q = 0; q < D; ++q) prod += (gv[p][q] + gv[q][p]) * gv[p][q];
     }
     const R inv_k = Ex<R>::div((R)1, k_i);
-    const R Gk = nut_i * prod - (R)(2.0 / 3.0) * k_i * tr;
+    R Gk = nut_i * prod - (R)(2.0 / 3.0) * k_i * tr;
+    // wall function: the log-law production tau_w du/dy = u_tau^3 / (kappa y)
+    // (none in the viscous sublayer)
+    if (wf) Gk = wf_log ? to_R<R>(wf_utau * wf_utau * wf_utau / (kWfKappa * wf_y)) : (R)0;
     const R dk_all = (R)2 * rho0 * Dk_i * dk, de_all = (R)2 * rho0 * De_i * de;
     const R dkdt = Gk - e_i + (R)2 * dk_all * inv_rho;
     const R dedt = (R)kC1 * e_i * inv_k * Gk - (R)kC2 * e_i * e_i * inv_k + (R)2 * de_all * inv_rho;
@@ -413,6 +468,12 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
     R k1r = k_i + dta * dkdt, e1r = e_i + dta * dedt;
     k1r = k1r > (R)kFloor ? k1r : (R)kFloor;
     e1r = e1r > (R)kFloor ? e1r : (R)kFloor;
+    if (wf) {
+      // the wall value of eps from the updated k
+      const double kk = from_R<R>(k1r);
+      const double ew = wf_log ? I.wf_cmu34 * (kk * sqrt(kk)) / (kWfKappa * wf_y) : 2.0 * I.nu_l * kk / (wf_y * wf_y);
+      e1r = to_R<R>(ew > kFloor ? ew : kFloor);
+    }
     m.k[i] = from_R<R>(k1r);
     m.eps[i] = from_R<R>(e1r);
     m.nut[i] = from_R<R>(Ex<R>::div((R)kCmu * k1r * k1r, e1r));

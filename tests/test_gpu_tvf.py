@@ -1,5 +1,6 @@
-"""The transport-velocity shift and the density reinitialisation (Sec. 2.3;
-sph_config.tvf_alpha, sph_config.density_sum) on the GPU against the
+"""The transport-velocity shift, the density reinitialisation and the
+step-wise wall function (Sec. 2.3; sph_config.tvf_alpha, density_sum,
+wall_function) on the GPU against the
 oracle: one step of every input kind in FP64 (relative L2 1e-10, the
 particle sets and labels equal), the FP32 form within the bounds of the
 other FP32 tests, and the laminar channel of Sec. 4.1 followed for 200
@@ -50,6 +51,11 @@ CASES = {
     "lattice3_buf": lambda: _on(_lat3_buf()),
     "u_channel": lambda: _on(cases.u_channel(dp=0.05, nu=0.02)),
     "mixer3d": lambda: _on(cases.mixer_3d(dp=0.05)),
+    # the step-wise wall function alone and with the other two stages
+    "rans_channel_wallfn": lambda: cases.turbulent_channel(length=0.3, height=0.1, dp=0.005,
+                                                           jitter_frac=0.05).replace(wall_function=True),
+    "rans_channel_all": lambda: _on(cases.turbulent_channel(length=0.3, height=0.1, dp=0.005,
+                                                            jitter_frac=0.05)).replace(wall_function=True),
 }
 FIELDS = ["pos", "vel", "rho", "p", "B", "acc_nu"]
 
@@ -70,11 +76,12 @@ def test_one_step_fp64_with_tvf_and_density_sum(sph, orc, name):
             for k in FIELDS + (["k", "eps"] if case.rans else [])}
     assert all(e < 1e-10 for e in errs.values()), errs
     # the stages did something: positions differ from a run without them
-    off = sph.Simulation(case.replace(tvf=0.0, density_sum=False), precision="fp64")
+    off = sph.Simulation(case.replace(tvf=0.0, density_sum=False, wall_function=False), precision="fp64")
     off.step(1)
     g0 = off.read(["uid", "pos", "rho"])
     if np.array_equal(g0["uid"], g["uid"]):
-        assert rel_l2(g0["rho"], g["rho"]) > 1e-12 or rel_l2(g0["pos"], g["pos"]) > 1e-12
+        assert rel_l2(g0["rho"], g["rho"]) > 1e-12 or rel_l2(g0["pos"], g["pos"]) > 1e-12 or \
+            (case.rans and rel_l2(off.read(["eps"])["eps"], g["eps"]) > 1e-12)
 
 
 def test_laminar_channel_200_steps_fp64(sph, orc):
@@ -93,7 +100,23 @@ def test_laminar_channel_200_steps_fp64(sph, orc):
     assert all(e < 1e-9 for e in errs.values()), errs
 
 
-@pytest.mark.parametrize("name", ["laminar_channel", "rans_channel", "box3", "mixer3d"])
+def test_rans_channel_wall_function_trajectory_fp64(sph, orc):
+    """Eight steps of the turbulent channel with the wall function: inlet
+    injection, the near-wall particles' k, eps and wall shear, at 1e-9."""
+    case = CASES["rans_channel_wallfn"]()
+    sim = sph.Simulation(case, precision="fp64")
+    o = orc.OracleSim(case)
+    sim.step(8)
+    o.step(8)
+    g = sim.read(["uid", "label", "pos", "vel", "rho", "k", "eps", "nut"])
+    f = o.fields()
+    assert o.stats["n_spawned"] > 0
+    assert np.array_equal(g["uid"], f["uid"]) and np.array_equal(g["label"], f["label"])
+    errs = {k: rel_l2(g[k], f[k]) for k in ("pos", "vel", "rho", "k", "eps", "nut")}
+    assert all(e < 1e-9 for e in errs.values()), errs
+
+
+@pytest.mark.parametrize("name", ["laminar_channel", "rans_channel", "box3", "mixer3d", "rans_channel_all"])
 def test_one_step_fp32_with_tvf_and_density_sum(sph, orc, name):
     case = CASES[name]()
     sim = sph.Simulation(case, precision="fp32")
