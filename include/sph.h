@@ -436,6 +436,18 @@ int sph_reduce_mass_momentum(sph_ctx *ctx, double *mass, double *momentum);
    SPH_ERR_ALLOC, SPH_ERR_CUDA. */
 int sph_debug_convert(const double *in64, float *out32, const float *in32, double *out64, int64_t n);
 
+/* Test aid (no counterpart in the paper): the bounded wait of the grid
+   barrier that the cooperative launches use.  Launches a two-block
+   cooperative kernel on the context's barrier words in which every block
+   waits for arrivals that never come, with a short poll limit (about 2^14
+   polls), and synchronises.  *status_out receives the status word of that
+   launch (a private word, not the context's): SPH_ERR_TIMEOUT when the
+   waits ran out as they must; words_after (may be NULL, 4 uint32 in host
+   memory) the barrier words after the launch, which the last block to
+   leave resets to zero for the next cooperative launch.  Errors:
+   SPH_ERR_ARG, SPH_ERR_ALLOC, SPH_ERR_CUDA. */
+int sph_debug_barrier_timeout(sph_ctx *ctx, int32_t *status_out, uint32_t *words_after);
+
 /* Measurement aid (no counterpart in the paper): the fused multiply-add
    throughput of the current GPU in FP32 or FP64 (SPH_PREC_*), in FLOP/s
    (one FMA = 2 FLOP), from eight independent FMA chains per thread on

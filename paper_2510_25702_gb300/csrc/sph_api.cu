@@ -2090,6 +2090,49 @@ int sph_debug_list(sph_ctx *c, int64_t *out, int64_t max, int64_t *count) {
 }  // extern "C"
 
 // ------------------------------------------------------------------------
+// test aid: a grid barrier whose wait runs out
+// ------------------------------------------------------------------------
+namespace {
+// every block waits at barrier 2 first, whose target (2 x gridDim.x
+// arrivals) the launch never reaches: each wait ends at its poll limit or
+// at the abort flag the first block to run out sets, then every block
+// leaves, and the last one resets the barrier words
+__global__ void k_barrier_timeout(sphk::GridBarrier *gb, int32_t *status, uint32_t spin_limit) {
+  __shared__ int s_ok;
+  sphk::grid_sync(gb, 2u, status, &s_ok, spin_limit);
+  sphk::grid_leave(gb);
+}
+}  // namespace
+
+extern "C" int sph_debug_barrier_timeout(sph_ctx *c, int32_t *status_out, uint32_t *words_after) {
+  if (!c || !status_out) return fail(SPH_ERR_ARG, "NULL argument");
+  int32_t *d_status = nullptr;
+  if (cudaMalloc(&d_status, sizeof(int32_t)) != cudaSuccess) return fail(SPH_ERR_ALLOC, "status word");
+  cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int32_t), c->stream);
+  if (e == cudaSuccess) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(32);
+    cfg.stream = c->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // a short limit: about 2^14 polls per wait
+    e = cudaLaunchKernelEx(&cfg, k_barrier_timeout, c->gbar, d_status, 1u << 14);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  int32_t st = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&st, d_status, sizeof(st), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && words_after) e = cudaMemcpy(words_after, c->gbar, sizeof(sphk::GridBarrier), cudaMemcpyDeviceToHost);
+  cudaFree(d_status);
+  if (e != cudaSuccess) return fail(SPH_ERR_CUDA, std::string("debug barrier: ") + cudaGetErrorString(e));
+  *status_out = st;
+  return SPH_OK;
+}
+
+// ------------------------------------------------------------------------
 // test aid: the integer-pipe binary64 <-> binary32 conversions
 // ------------------------------------------------------------------------
 namespace {

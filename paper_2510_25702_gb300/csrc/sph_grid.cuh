@@ -41,7 +41,8 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
 // release add and the wait an acquire load at GPU scope; with the block
 // barriers on both sides, every write made before the barrier by any thread
 // of any block is visible to every thread after it.
-__device__ __forceinline__ bool grid_sync(GridBarrier *g, uint32_t k, int32_t *status, int *s_ok) {
+__device__ __forceinline__ bool grid_sync(GridBarrier *g, uint32_t k, int32_t *status, int *s_ok,
+                                          uint32_t spin_limit = kGridSpinLimit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
@@ -53,7 +54,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *g, uint32_t k, int32_t *s
         ok = 0;
         break;
       }
-      if (++it > kGridSpinLimit) {
+      if (++it > spin_limit) {
         atomicExch(&g->abort, 1u);
         atomicCAS(status, 0, SPH_ERR_TIMEOUT);
         ok = 0;

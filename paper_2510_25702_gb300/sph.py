@@ -108,7 +108,7 @@ EXPORTS = ("sph_create", "sph_add_buffer", "sph_set_profile", "sph_step", "sph_r
            "sph_cell_sort_noalloc", "sph_set_graph", "sph_set_launch", "sph_get_launch", "sph_autotune",
            "sph_save_state", "sph_restore_state", "sph_drop_state", "sph_adjoint_forward",
            "sph_adjoint_backward", "sph_adjoint_release", "sph_debug_convert", "sph_step_async",
-           "sph_reduce_mass_momentum", "sph_measure_fma_peak")
+           "sph_reduce_mass_momentum", "sph_measure_fma_peak", "sph_debug_barrier_timeout")
 NOALLOC_MAX_POINTS = 1 << 19
 N_STAGES = 10
 
@@ -158,6 +158,7 @@ def lib():
         L.sph_adjoint_backward.argtypes = [vp, C.POINTER(C.c_double), C.c_int32]
         L.sph_adjoint_release.argtypes = [vp]
         L.sph_measure_fma_peak.argtypes = [C.c_int32, C.POINTER(C.c_double)]
+        L.sph_debug_barrier_timeout.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_uint32)]
         L.sph_error_string.restype = C.c_char_p
         L.sph_last_error.restype = C.c_char_p
         _lib = L
@@ -472,6 +473,14 @@ class Simulation:
         out = np.zeros((max(max_rows, 1), 4), np.int64)
         _check(fn(self.ctx, out.ctypes.data_as(C.POINTER(C.c_int64)), max_rows, C.byref(cnt)), name)
         return out[: min(cnt.value, max_rows)]
+
+    def debug_barrier_timeout(self):
+        """(status, barrier words after) of a cooperative launch whose grid
+        barrier can never complete (sph_debug_barrier_timeout)."""
+        st = C.c_int32()
+        words = (C.c_uint32 * 4)()
+        _check(lib().sph_debug_barrier_timeout(self.ctx, C.byref(st), words), "sph_debug_barrier_timeout")
+        return int(st.value), [int(w) for w in words]
 
     def debug_pairs(self, max_pairs: Optional[int] = None) -> np.ndarray:
         """(uid_i, uid_j | wall index, is_wall, instance) of the FP64 pair test."""

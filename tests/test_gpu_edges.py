@@ -129,3 +129,26 @@ def test_misaligned_allocator_is_refused(sph, monkeypatch):
     monkeypatch.undo()
     sim = sph.Simulation(cases.periodic_box(n_per_axis=10, dim=2), precision="fp32")
     assert sim.step_rc(2) == 0
+
+
+def test_grid_barrier_wait_runs_out_and_recovers(sph):
+    """The bounded wait of the grid barrier: a cooperative launch whose
+    barrier can never complete ends with SPH_ERR_TIMEOUT in its status word
+    (every block leaves at its poll limit or at the abort flag), resets the
+    barrier words, and the context's following steps -- whose later
+    sub-steps wait on the same words -- are bit-identical to a context that
+    never saw it."""
+    case = cases.poiseuille_channel(length=1.0, height=0.5)
+    a = sph.Simulation(case, precision="fp64")
+    for _ in range(2):
+        st, words = a.debug_barrier_timeout()
+        assert st == -5
+        assert words == [0, 0, 0, 0]
+    a.step(3)
+    assert a.stats()["n_ac"] > 1  # the cooperative later-sub-steps launch ran
+    b = sph.Simulation(case, precision="fp64")
+    b.step(3)
+    ga, gb = a.read(["uid", "pos", "vel", "rho"]), b.read(["uid", "pos", "vel", "rho"])
+    for k in ga:
+        assert np.array_equal(ga[k], gb[k]), k
+    assert a.stats()["status"] == 0
