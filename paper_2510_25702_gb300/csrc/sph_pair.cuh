@@ -232,6 +232,31 @@ __device__ __forceinline__ void visit_cells(const InstDev &I, int cx, int cy, in
   }
 }
 
+// |r|^2 of i with two candidates at once on paired FP32 operations: the
+// same roundings as pair_vec's FP32 path (difference, square, contracted
+// sum), two lanes per instruction
+template <int D>
+__device__ __forceinline__ void rr_pairs_f32x2(const V4<float> &pi, const V4<float> &a, const V4<float> &b,
+                                               float &ra, float &rb) {
+  unsigned long long xi, xj, dx, yi, yj, dy, r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(xi) : "f"(pi.x));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(xj) : "f"(a.x), "f"(b.x));
+  asm("mov.b64 %0, {%1, %1};" : "=l"(yi) : "f"(pi.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(yj) : "f"(a.y), "f"(b.y));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(xi), "l"(xj));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(yi), "l"(yj));
+  asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(r) : "l"(dx));
+  asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(dy), "l"(r));
+  if (D == 3) {
+    unsigned long long zi, zj, dz;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(zi) : "f"(pi.z));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(zj) : "f"(a.z), "f"(b.z));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(zi), "l"(zj));
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(dz), "l"(r));
+  }
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(ra), "=f"(rb) : "l"(r));
+}
+
 // candidates j in [jb, je) whose position leads the 4-vector P[j * stride],
 // four loads in flight; hit(j) is called, in increasing j, for every j with
 // 0 < |r_ij|^2 < (2h)^2.  In FP64 (lo = hi = (2h)^2) that test is the
@@ -252,16 +277,26 @@ __device__ __forceinline__ void scan_range(const Geo<R> &g, const V4<R> &Pi, con
     const V4<R> q3 = (j + 3 < je) ? P[(size_t)(j + 3) * stride] : q0;
     R d[3];
     unsigned sure = 0, maybe = 0;
-    R rr = pair_vec<R, D, PER>(g, Pi, q0, d);
+    R rra[4];
+    if constexpr (sizeof(R) == 4 && !PER) {
+      rr_pairs_f32x2<D>(Pi, q0, q1, rra[0], rra[1]);
+      rr_pairs_f32x2<D>(Pi, q2, q3, rra[2], rra[3]);
+    } else {
+      rra[0] = pair_vec<R, D, PER>(g, Pi, q0, d);
+      rra[1] = pair_vec<R, D, PER>(g, Pi, q1, d);
+      rra[2] = pair_vec<R, D, PER>(g, Pi, q2, d);
+      rra[3] = pair_vec<R, D, PER>(g, Pi, q3, d);
+    }
+    R rr = rra[0];
     sure |= (rr > (R)0 && rr < lo) ? 1u : 0u;
     if (sizeof(R) == 4) maybe |= (rr < hi) ? 1u : 0u;
-    rr = pair_vec<R, D, PER>(g, Pi, q1, d);
+    rr = rra[1];
     sure |= (j + 1 < je && rr > (R)0 && rr < lo) ? 2u : 0u;
     if (sizeof(R) == 4) maybe |= (j + 1 < je && rr < hi) ? 2u : 0u;
-    rr = pair_vec<R, D, PER>(g, Pi, q2, d);
+    rr = rra[2];
     sure |= (j + 2 < je && rr > (R)0 && rr < lo) ? 4u : 0u;
     if (sizeof(R) == 4) maybe |= (j + 2 < je && rr < hi) ? 4u : 0u;
-    rr = pair_vec<R, D, PER>(g, Pi, q3, d);
+    rr = rra[3];
     sure |= (j + 3 < je && rr > (R)0 && rr < lo) ? 8u : 0u;
     if (sizeof(R) == 4) maybe |= (j + 3 < je && rr < hi) ? 8u : 0u;
     if (sizeof(R) == 4) {
