@@ -457,6 +457,8 @@ def main():
     ap.add_argument("--adjoint-dp", type=float, default=0.002)
     ap.add_argument("--adjoint-only", action="store_true",
                     help="time only the differentiated window and print its record (for profiling)")
+    ap.add_argument("--probe-steps", type=int, default=5000,
+                    help="steps of the FP32-against-FP64 probe-grid comparison in the line (0: skip)")
     ap.add_argument("--probe-error", type=int, default=0, metavar="STEPS",
                     help="only compare the FP32 and FP64 forms of the 2D channel after STEPS steps on a probe grid")
     args = ap.parse_args()
@@ -666,6 +668,13 @@ def main():
         sim64.close()
 
     log("fp64 done")
+    # the FP32 form against the FP64 form over the scope table's long run of
+    # the channel (fields on a fixed probe grid: the particle sets part ways)
+    probe = None
+    if (args.probe_steps > 0 and args.precision == "fp32" and rank == 0 and not args.no_fp64
+            and args.workload == "turbulent_channel"):
+        probe = probe_error(args.probe_steps)
+        log("probe error done")
     adj = None
     if rank == 0 and not args.no_adjoint:
         adj = adjoint_bench(steps=args.adjoint_steps, every=max(1, args.adjoint_steps // 10), dp=args.adjoint_dp)
@@ -701,6 +710,7 @@ def main():
                             "kernel by kernel (value comes from graph replay)",
             "fp64_value": fp64, "fp64_timing": "graph replay of the same K steps, median of repeats",
             "fp32_over_fp64": (value / fp64) if fp64 else None, "fp32_error": fp32_err,
+            "fp32_probe_error": probe,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "eager": eager, "autotune": tuned, "adjoint": adj,
             "clocks": clk.summary(),
         }
