@@ -422,6 +422,22 @@ static int build_inst(const sph_config &c, InstDev &I, std::string &why) {
   fill_sweep_const(I, I.kd);
   for (int a = 0; a < 3; ++a) I.lo_f[a] = (float)I.lo[a];
   I.inv_cs_f = (float)I.inv_cs;
+  {
+    // fixed point of the FP32 form: q = dp 2^-s with 2^s as fine as keeps a
+    // listed pair's coordinate difference (below the cut-off 2h, with 50 %
+    // to spare) under 2^22 units and the domain, with a quarter of its
+    // extent again on either side, inside int32 (coordinates beyond
+    // saturate): s = 20 up to a domain of about 1360 dp
+    double ext = 1.0;
+    for (int a = 0; a < c.dim; ++a) ext = std::max(ext, I.L[a] / c.dp);
+    int sh = 20;
+    while (sh > 0 && (3.0 * c.h / c.dp * std::ldexp(1.0, sh) >= 4194304.0 || 1.5 * ext * std::ldexp(1.0, sh) >= 2147483648.0))
+      --sh;
+    const double q = std::ldexp(c.dp, -sh);
+    I.fx_inv_q = 1.0 / q;
+    I.fx_q = (float)q;
+    for (int a = 0; a < 3; ++a) I.fx_Lu[a] = (a < c.dim && I.periodic[a]) ? (int32_t)std::nearbyint(I.L[a] / q) : 0;
+  }
   I.n_ac = 1;
   return 0;
 }
@@ -479,22 +495,46 @@ static int alloc_packs(sph_ctx *c, Packs<R> &pk, int64_t cap, int64_t nw) {
   pk.Ap = alloc_arr<V4<R>>(c, cap);
   pk.WP = alloc_arr<V4<R>>(c, nw);
   pk.WV = alloc_arr<V4<R>>(c, nw);
-  if (!pk.adv || !pk.adv_b || !pk.mom || !pk.mom_b || !pk.cont || !pk.Ap || !pk.WP || !pk.WV) return -1;
+  // the FP32 form's absolute FP32 positions for the list builder
+  pk.lpos = alloc_arr<V4<R>>(c, sizeof(R) == 4 ? cap : 1);
+  pk.WPf = alloc_arr<V4<R>>(c, sizeof(R) == 4 ? nw : 1);
+  if (!pk.adv || !pk.adv_b || !pk.mom || !pk.mom_b || !pk.cont || !pk.Ap || !pk.WP || !pk.WV || !pk.lpos || !pk.WPf)
+    return -1;
   return 0;
+}
+
+// the fixed-point coordinate of the FP32 form (as fx_encode on the device:
+// the nearest integer to (x - lo) / q, saturating)
+static float host_fx_encode(const InstDev &I, double x, int a) {
+  double u = std::nearbyint((x - I.lo[a]) * I.fx_inv_q);
+  u = std::min(std::max(u, -2147483648.0), 2147483647.0);
+  const int32_t v = (int32_t)u;
+  float f;
+  std::memcpy(&f, &v, sizeof(f));
+  return f;
 }
 
 template <typename R>
 static int upload_walls(sph_ctx *c, Packs<R> &pk, const std::vector<double> &wpos, const std::vector<double> &wvel,
-                        const std::vector<double> &wV) {
+                        const std::vector<double> &wV, const std::vector<int32_t> &winst) {
   int64_t nw = (int64_t)wV.size();
   std::vector<V4<R>> P((size_t)std::max<int64_t>(nw, 1)), V((size_t)std::max<int64_t>(nw, 1));
+  std::vector<V4<R>> Pf((size_t)std::max<int64_t>(nw, 1));
   for (int64_t w = 0; w < nw; ++w) {
     P[w] = V4<R>{(R)wpos[3 * w], (R)wpos[3 * w + 1], (R)wpos[3 * w + 2], (R)wV[w]};
     V[w] = V4<R>{(R)wvel[3 * w], (R)wvel[3 * w + 1], (R)wvel[3 * w + 2], (R)0};
+    if constexpr (sizeof(R) == 4) {
+      // FP32 form: the sweeps' records in fixed point, the list builder's in FP32
+      const InstDev &I = c->inst[winst[w]];
+      Pf[w] = V4<R>{(R)wpos[3 * w], (R)wpos[3 * w + 1], (R)wpos[3 * w + 2], (R)0};
+      P[w] = V4<R>{host_fx_encode(I, wpos[3 * w], 0), host_fx_encode(I, wpos[3 * w + 1], 1),
+                   I.dim == 3 ? host_fx_encode(I, wpos[3 * w + 2], 2) : (R)0, (R)wV[w]};
+    }
   }
   if (nw) {
     CUDA_TRY(cudaMemcpy(pk.WP, P.data(), sizeof(V4<R>) * nw, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(pk.WV, V.data(), sizeof(V4<R>) * nw, cudaMemcpyHostToDevice));
+    if (sizeof(R) == 4) CUDA_TRY(cudaMemcpy(pk.WPf, Pf.data(), sizeof(V4<R>) * nw, cudaMemcpyHostToDevice));
   }
   return 0;
 }
@@ -584,6 +624,7 @@ int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *
   std::vector<uint32_t> next_uid(n_instances, 0);
   std::vector<double> wpos, wvel, wV;
   std::vector<uint32_t> wkey, windex;
+  std::vector<int32_t> winst;
   for (int a = 0; a < 3; ++a) {
     X[a].reserve(n_total);
     Vv[a].reserve(n_total);
@@ -637,6 +678,7 @@ int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *
         wvel.push_back(wv.empty() || a >= I.dim ? 0.0 : wv[3 * w + a]);
       }
       wV.push_back(I.Vw);
+      winst.push_back(i);
       wkey.push_back(host_cell_key(I, x));
       windex.push_back((uint32_t)w);
     }
@@ -647,6 +689,7 @@ int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *
   std::stable_sort(word.begin(), word.end(), [&](int64_t a, int64_t b) { return wkey[a] < wkey[b]; });
   std::vector<double> swpos(3 * nw_total), swvel(3 * nw_total), swV(nw_total);
   std::vector<uint32_t> swkey(nw_total), swindex(nw_total);
+  std::vector<int32_t> swinst(nw_total);
   for (int64_t t = 0; t < nw_total; ++t) {
     int64_t s = word[t];
     for (int a = 0; a < 3; ++a) {
@@ -654,6 +697,7 @@ int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *
       swvel[3 * t + a] = wvel[3 * s + a];
     }
     swV[t] = wV[s];
+    swinst[t] = winst[s];
     swkey[t] = wkey[s];
     swindex[t] = windex[s];
   }
@@ -801,8 +845,8 @@ int sph_create(const sph_config *cfg, int32_t n_instances, const sph_particles *
   rc |= up(c->woff, hwoff.data(), sizeof(uint32_t) * (c->ncell + 1));
   rc |= up(c->wall_index, swindex.data(), sizeof(uint32_t) * nw_total);
   rc |= up(c->next_uid, next_uid.data(), sizeof(uint32_t) * n_instances);
-  rc |= (c->prec == SPH_PREC_FP32) ? upload_walls(c, c->pkf, swpos, swvel, swV)
-                                   : upload_walls(c, c->pkd, swpos, swvel, swV);
+  rc |= (c->prec == SPH_PREC_FP32) ? upload_walls(c, c->pkf, swpos, swvel, swV, swinst)
+                                   : upload_walls(c, c->pkd, swpos, swvel, swV, swinst);
   Counters h{};
   h.m_pending = (int32_t)n_total;
   rc |= up(c->cnt, &h, sizeof(h));

@@ -72,6 +72,12 @@ struct InstDev {
   SweepConst<float> kf;
   SweepConst<double> kd;
   float lo_f[3], inv_cs_f;  // FP32 copies for the cell-index prefilter
+  // FP32 form: record positions in fixed point, X = rint((x - lo) / q) with
+  // q = dp 2^-s (int32 bit patterns in the records), so that the difference
+  // of two positions is exact and a pair vector carries one FP32 rounding
+  float fx_q;
+  int32_t fx_Lu[3];   // periodic lengths in units of q
+  double fx_inv_q;    // 1 / q
   // written every advection step by the time-step kernel
   double dt_ad, dt_ac, dt, t;
   int32_t n_ac;
@@ -143,6 +149,8 @@ struct alignas(4 * sizeof(R)) V4 {
 template <typename R>
 struct Packs {
   V4<R> *adv, *mom, *cont;  // records, RV 4-vectors per particle
+  V4<R> *lpos;              // FP32 form: (x y z 0) in FP32 for the list builder
+  V4<R> *WPf;               // FP32 form: walls (x y z 0) in FP32 for the list builder
   V4<R> *mom_b;             // 3D: the momentum record's B tail (Bzz Bxy Bxz Byz)
   V4<R> *adv_b;             // 3D: the advection record's k-epsilon tail (eps nut - -)
   V4<R> *Ap;                // a_nu + g of the advection step
@@ -223,6 +231,12 @@ __device__ __forceinline__ double f32_to_f64(float x) {
     return (double)x;
   }
   return __hiloint2double((int)((u & 0x80000000u) | ((mag >> 3) + (896u << 20))), (int)(u << 29));
+}
+
+// fixed-point record coordinate of x along axis a (FP32 form): the int32
+// nearest to (x - lo) / q, saturating, as a float bit pattern
+__device__ __forceinline__ float fx_encode(const InstDev &I, double x, int a) {
+  return __int_as_float(__double2int_rn(dmul(dsub(x, I.lo[a]), I.fx_inv_q)));
 }
 
 // conversions into and out of the sweep precision R

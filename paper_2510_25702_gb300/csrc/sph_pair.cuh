@@ -49,12 +49,19 @@ struct Ex<float> {
   static __device__ __forceinline__ float inv_len(float rr, float r) { return rsqrtf(rr); }
 };
 
+template <typename R>
+struct Geo;
+template <typename R, int D, bool PER>
+__device__ __forceinline__ R pair_vec_abs(const Geo<R> &g, const V4<R> &pi, const V4<R> &pj, R d[3]);
+
 // per-thread copy of the instance geometry in sweep precision
 template <typename R>
 struct Geo {
   R L[3];
   int per[3];
   R cut2, inv_h, c5, reg;
+  R q;        // FP32 form: the fixed-point unit of the record positions
+  int Lu[3];  // FP32 form: periodic lengths in units
 };
 
 template <typename R, int D>
@@ -64,20 +71,66 @@ __device__ __forceinline__ Geo<R> make_geo(const InstDev &I) {
   for (int a = 0; a < 3; ++a) {
     g.L[a] = k.L[a];
     g.per[a] = (a < D) ? I.periodic[a] : 0;
+    g.Lu[a] = I.fx_Lu[a];
   }
   g.cut2 = k.cut2;
   g.inv_h = k.inv_h;
   g.c5 = k.c5;
   g.reg = k.reg;
+  g.q = (R)I.fx_q;
   return g;
 }
 
 // r_ij = x_i - x_j (minimum image when PER) from the leading 4-vectors of two
-// records, whose first D components are the position; returns |r_ij|^2
-// summed left to right without contraction (the cut-off test decides
-// membership)
+// records, whose first D components are the position; returns |r_ij|^2.
+// FP64 form: FP64 positions, the plain left-to-right sum without
+// contraction.  FP32 form: fixed-point positions; the difference of the two
+// integers is exact (wrapped by the periodic length in units), and for a
+// listed pair (|r| < 2h, at most 2^22 units) it converts to FP32 exactly by
+// the 2^23 + 2^22 offset; one multiplication by q then rounds it, and the
+// sum of squares is contracted.
 template <typename R, int D, bool PER>
 __device__ __forceinline__ R pair_vec(const Geo<R> &g, const V4<R> &pi, const V4<R> &pj, R d[3]) {
+  if constexpr (sizeof(R) == 4) {
+    const float xi[3] = {pi.x, pi.y, pi.z}, xj[3] = {pj.x, pj.y, pj.z};
+    float rr = 0.0f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      int di = __float_as_int(xi[a]) - __float_as_int(xj[a]);
+      if (PER && g.per[a]) {
+        const int hu = g.Lu[a] >> 1;
+        if (di > hu)
+          di -= g.Lu[a];
+        else if (di < -hu)
+          di += g.Lu[a];
+      }
+      const float t = __int_as_float(0x4B400000 + di) - 12582912.0f;
+      const float v = t * (float)g.q;
+      d[a] = (R)v;
+      rr = (a == 0) ? v * v : fmaf(v, v, rr);
+    }
+    if (D == 2) d[2] = (R)0;
+    return (R)rr;
+  } else {
+    return pair_vec_abs<R, D, PER>(g, pi, pj, d);
+  }
+}
+
+// the absolute coordinate of axis a of a record position (the FP32 form
+// decodes its fixed point; the FP64 form stores it)
+template <typename R>
+__device__ __forceinline__ R rec_abs(const InstDev &I, R x, int a) {
+  if constexpr (sizeof(R) == 4)
+    return I.lo_f[a] + (float)__float_as_int(x) * I.fx_q;
+  else
+    return x;
+}
+
+// r_ij = x_i - x_j (minimum image when PER) from absolute positions in R,
+// |r_ij|^2 summed left to right (FP32: contracted); the list builder's
+// candidate test in both forms and the FP64 form's pair vector
+template <typename R, int D, bool PER>
+__device__ __forceinline__ R pair_vec_abs(const Geo<R> &g, const V4<R> &pi, const V4<R> &pj, R d[3]) {
   R xi[3] = {pi.x, pi.y, pi.z}, xj[3] = {pj.x, pj.y, pj.z};
   R rr = (R)0;
 #pragma unroll
@@ -282,10 +335,10 @@ __device__ __forceinline__ void scan_range(const Geo<R> &g, const V4<R> &Pi, con
       rr_pairs_f32x2<D>(Pi, q0, q1, rra[0], rra[1]);
       rr_pairs_f32x2<D>(Pi, q2, q3, rra[2], rra[3]);
     } else {
-      rra[0] = pair_vec<R, D, PER>(g, Pi, q0, d);
-      rra[1] = pair_vec<R, D, PER>(g, Pi, q1, d);
-      rra[2] = pair_vec<R, D, PER>(g, Pi, q2, d);
-      rra[3] = pair_vec<R, D, PER>(g, Pi, q3, d);
+      rra[0] = pair_vec_abs<R, D, PER>(g, Pi, q0, d);
+      rra[1] = pair_vec_abs<R, D, PER>(g, Pi, q1, d);
+      rra[2] = pair_vec_abs<R, D, PER>(g, Pi, q2, d);
+      rra[3] = pair_vec_abs<R, D, PER>(g, Pi, q3, d);
     }
     R rr = rra[0];
     sure |= (rr > (R)0 && rr < lo) ? 1u : 0u;

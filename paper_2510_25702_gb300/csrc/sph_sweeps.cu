@@ -50,7 +50,10 @@ __device__ __forceinline__ int list_one(const SweepArgs &a, const Packs<R> &pk, 
   const Geo<R> g = make_geo<R, D>(I);
   int cx, cy, cz;
   decode_cell(I, a.keys[i], cx, cy, cz);
-  const V4<R> Pi = pk.adv[RA * (size_t)i];
+  // candidate positions: the FP32 form tests absolute FP32 coordinates (its
+  // records hold fixed point), the FP64 form its records' FP64 ones
+  const bool f32 = sizeof(R) == 4;
+  const V4<R> Pi = f32 ? pk.lpos[i] : pk.adv[RA * (size_t)i];
   uint32_t *__restrict__ out = list_of(a.nl, i);
   const int K = a.nl.kmax;
   int nr = 0, nw = 0;
@@ -82,8 +85,8 @@ __device__ __forceinline__ int list_one(const SweepArgs &a, const Packs<R> &pk, 
   // real neighbours, then wall dummies; 0 < |r|^2 < (2h)^2 excludes i itself
   for (int set = 0; set < 2; ++set) {
     const uint32_t *offs = set == 0 ? a.off : a.woff;
-    const V4<R> *recs = set == 0 ? pk.adv : pk.WP;
-    const int stride = set == 0 ? RA : 1;
+    const V4<R> *recs = set == 0 ? (f32 ? pk.lpos : pk.adv) : (f32 ? pk.WPf : pk.WP);
+    const int stride = (set == 0 && !f32) ? RA : 1;
     // the definition in FP64 on the masters (rare: candidates in the band)
     auto exact = [&](uint32_t j) -> bool {
       if (set == 0 && j == (uint32_t)i) return false;
@@ -263,7 +266,8 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
       Ex<R>::len(rr, r);
       const R F = kernel_F(g, r);  // dW/dr / r
       const R V = vol<R, D>(B0);
-      if (!mirror || !(local0<R, D>(mo, mn, B0.x, B0.y, B0.z) < (R)0)) sym_add_outer<R, D>(A, d, -F * V);
+      if (!mirror || !(local0<R, D>(mo, mn, rec_abs<R>(I, B0.x, 0), rec_abs<R>(I, B0.y, 1), rec_abs<R>(I, B0.z, 2)) < (R)0))
+        sym_add_outer<R, D>(A, d, -F * V);
       if (tvf) {
         const R FV = F * V;
 #pragma unroll
@@ -306,7 +310,8 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
     Ex<R>::len(rr, r);
     const R F = kernel_F(g, r);
     const R V = Wp.w;
-    if (!mirror || !(local0<R, D>(mo, mn, Wp.x, Wp.y, Wp.z) < (R)0)) sym_add_outer<R, D>(A, d, -F * V);
+    if (!mirror || !(local0<R, D>(mo, mn, rec_abs<R>(I, Wp.x, 0), rec_abs<R>(I, Wp.y, 1), rec_abs<R>(I, Wp.z, 2)) < (R)0))
+      sym_add_outer<R, D>(A, d, -F * V);
     if (tvf) {
       const R FV = F * V;
 #pragma unroll
@@ -336,16 +341,19 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   if (mirror) {
     // images m_j = x_j - 2 x'_0(x_j) n_b of every particle on the fluid side
     // of the open face, searched around the image of x_i (two-cell margin)
-    const R si = local0<R, D>(mo, mn, A0.x, A0.y, A0.z);
-    const double q0 = (double)A0.x - 2.0 * (double)si * mb->frame[0];
-    const double q1 = (double)A0.y - 2.0 * (double)si * mb->frame[1];
-    const double q2 = D == 3 ? (double)A0.z - 2.0 * (double)si * mb->frame[2] : 0.0;
+    // absolute positions (the FP32 form decodes its fixed-point records)
+    const R ax = rec_abs<R>(I, A0.x, 0), ay = rec_abs<R>(I, A0.y, 1), az = D == 3 ? rec_abs<R>(I, A0.z, 2) : (R)0;
+    const R si = local0<R, D>(mo, mn, ax, ay, az);
+    const double q0 = (double)ax - 2.0 * (double)si * mb->frame[0];
+    const double q1 = (double)ay - 2.0 * (double)si * mb->frame[1];
+    const double q2 = D == 3 ? (double)az - 2.0 * (double)si * mb->frame[2] : 0.0;
     const int qx = cell_coord(I, q0, 0), qy = cell_coord(I, q1, 1), qz = D == 3 ? cell_coord(I, q2, 2) : 0;
     auto mirror_one = [&](const V4<R> &Pj, R Vj) {
-      const R sj = local0<R, D>(mo, mn, Pj.x, Pj.y, Pj.z);
+      const R jx = rec_abs<R>(I, Pj.x, 0), jy = rec_abs<R>(I, Pj.y, 1), jz = D == 3 ? rec_abs<R>(I, Pj.z, 2) : (R)0;
+      const R sj = local0<R, D>(mo, mn, jx, jy, jz);
       if (sj < (R)0) return;
       const R two_s = Ex<R>::mul((R)2, sj);
-      R xj[3] = {Pj.x, Pj.y, Pj.z}, xi[3] = {A0.x, A0.y, A0.z};
+      R xj[3] = {jx, jy, jz}, xi[3] = {ax, ay, az};
       R d[3] = {0, 0, 0};
       R dd = 0;
 #pragma unroll

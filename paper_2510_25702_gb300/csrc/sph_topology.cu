@@ -64,11 +64,20 @@ __device__ __forceinline__ int permute_one(const TopoArgs &a, const Packs<R> &pk
   // advection-sweep record of this particle
   const R V = to_R<R>(mass) / to_R<R>(rho);
   const R vxr = to_R<R>(vx), vyr = to_R<R>(vy);
+  // positions: FP64 as they are; FP32 in the fixed point of the instance,
+  // with the absolute FP32 coordinates for the list builder beside them
+  R px = to_R<R>(x), py = to_R<R>(y), pz = to_R<R>(z);
+  if constexpr (sizeof(R) == 4) {
+    pk.lpos[t] = V4<R>{px, py, pz, (R)0};
+    px = fx_encode(I, x, 0);
+    py = fx_encode(I, y, 1);
+    pz = d3 ? fx_encode(I, z, 2) : (R)0;
+  }
   if (!d3) {
-    pk.adv[2 * (size_t)t] = V4<R>{to_R<R>(x), to_R<R>(y), V, vxr};
+    pk.adv[2 * (size_t)t] = V4<R>{px, py, V, vxr};
     pk.adv[2 * (size_t)t + 1] = V4<R>{vyr, to_R<R>(k), to_R<R>(eps), to_R<R>(nut)};
   } else {
-    pk.adv[2 * (size_t)t] = V4<R>{to_R<R>(x), to_R<R>(y), to_R<R>(z), V};
+    pk.adv[2 * (size_t)t] = V4<R>{px, py, pz, V};
     pk.adv[2 * (size_t)t + 1] = V4<R>{vxr, vyr, to_R<R>(vz), to_R<R>(k)};
     if (I.rans) pk.adv_b[t] = V4<R>{to_R<R>(eps), to_R<R>(nut), (R)0, (R)0};
   }

@@ -65,11 +65,12 @@ def test_channel_480k_bench_configuration(sph, channel_oracle, tmp_path):
     g = sim.read(["uid", "label", "pos", "vel", "rho", "k", "eps", "B"])
     assert np.array_equal(g["uid"], f["uid"]) and np.array_equal(g["label"], f["label"])
     errs = {k: rel_l2(g[k], f[k]) for k in ("pos", "vel", "rho", "k", "eps", "B")}
-    # FP32 records hold absolute coordinates: at x ~ 6 their spacing (4.8e-7)
-    # is 1e-4 of dp, so pair vectors, kernel gradients and the k-eps sources
-    # built from them carry ~1e-4 relative error; the FP64 state increments
-    # (positions, velocities, densities) stay far below that
-    bounds = {"pos": 1e-8, "vel": 1e-5, "rho": 1e-7, "k": 2e-4, "eps": 2e-4, "B": 2e-4}
+    print("channel 480k fp32", {k: f"{v:.2e}" for k, v in errs.items()})
+    # FP32 records hold fixed-point positions (units dp 2^-20): pair vectors
+    # carry ~1e-6 relative error wherever the particles lie (absolute FP32
+    # coordinates at x ~ 6 would be good to 1e-4 of dp only), and so do B and
+    # the k-eps sources; the FP64 state increments stay far below that
+    bounds = {"pos": 1e-10, "vel": 1e-7, "rho": 1e-9, "k": 1e-5, "eps": 1e-5, "B": 1e-5}
     assert all(errs[k] < bounds[k] for k in bounds), errs
 
 
