@@ -496,8 +496,8 @@ static int alloc_packs(sph_ctx *c, Packs<R> &pk, int64_t cap, int64_t nw) {
   pk.WP = alloc_arr<V4<R>>(c, nw);
   pk.WV = alloc_arr<V4<R>>(c, nw);
   // the FP32 form's absolute FP32 positions for the list builder
-  pk.lpos = alloc_arr<V4<R>>(c, sizeof(R) == 4 ? cap : 1);
-  pk.WPf = alloc_arr<V4<R>>(c, sizeof(R) == 4 ? nw : 1);
+  pk.lpos = alloc_arr<V4<R>>(c, sizeof(R) == 4 ? cap + 4 : 1);
+  pk.WPf = alloc_arr<V4<R>>(c, sizeof(R) == 4 ? nw + 4 : 1);
   if (!pk.adv || !pk.adv_b || !pk.mom || !pk.mom_b || !pk.cont || !pk.Ap || !pk.WP || !pk.WV || !pk.lpos || !pk.WPf)
     return -1;
   return 0;

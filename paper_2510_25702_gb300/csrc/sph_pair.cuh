@@ -324,6 +324,34 @@ __device__ __forceinline__ void scan_range(const Geo<R> &g, const V4<R> &Pi, con
                                            int stride, uint32_t jb, uint32_t je, R lo, R hi, H &&hit,
                                            X &&exact) {
   for (uint32_t j = jb; j < je; j += 4) {
+    if constexpr (sizeof(R) == 4 && !PER) {
+      // FP32 candidate arrays are padded by four entries: the loads need no
+      // bounds, one mask drops the entries past the range
+      const V4<R> q0 = P[j], q1 = P[j + 1], q2 = P[j + 2], q3 = P[j + 3];
+      const unsigned tail = (je - j >= 4u) ? 0xFu : ((1u << (je - j)) - 1u);
+      R r0, r1, r2, r3;
+      rr_pairs_f32x2<D>(Pi, q0, q1, r0, r1);
+      rr_pairs_f32x2<D>(Pi, q2, q3, r2, r3);
+      unsigned sure = ((r0 > (R)0 && r0 < lo) ? 1u : 0u) | ((r1 > (R)0 && r1 < lo) ? 2u : 0u) |
+                      ((r2 > (R)0 && r2 < lo) ? 4u : 0u) | ((r3 > (R)0 && r3 < lo) ? 8u : 0u);
+      const unsigned maybe = ((r0 < hi) ? 1u : 0u) | ((r1 < hi) ? 2u : 0u) | ((r2 < hi) ? 4u : 0u) |
+                             ((r3 < hi) ? 8u : 0u);
+      sure &= tail;
+      unsigned amb = maybe & tail & ~sure;
+      if (__builtin_expect(amb != 0u, 0)) {
+        while (amb) {
+          const int k = __ffs(amb) - 1;
+          amb &= amb - 1;
+          if (exact(j + (uint32_t)k)) sure |= 1u << k;
+        }
+      }
+      while (sure) {
+        const int k = __ffs(sure) - 1;
+        sure &= sure - 1;
+        hit(j + (uint32_t)k);
+      }
+      continue;
+    }
     const V4<R> q0 = P[(size_t)j * stride];
     const V4<R> q1 = (j + 1 < je) ? P[(size_t)(j + 1) * stride] : q0;
     const V4<R> q2 = (j + 2 < je) ? P[(size_t)(j + 2) * stride] : q0;
