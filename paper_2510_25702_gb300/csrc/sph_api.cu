@@ -423,17 +423,16 @@ static int build_inst(const sph_config &c, InstDev &I, std::string &why) {
   for (int a = 0; a < 3; ++a) I.lo_f[a] = (float)I.lo[a];
   I.inv_cs_f = (float)I.inv_cs;
   {
-    // fixed point of the FP32 form: q = dp 2^-s with 2^s as fine as keeps a
+    // fixed point of the FP32 form: q the smallest power of two that keeps a
     // listed pair's coordinate difference (below the cut-off 2h, with 50 %
     // to spare) under 2^22 units and the domain, with a quarter of its
     // extent again on either side, inside int32 (coordinates beyond
-    // saturate): s = 20 up to a domain of about 1360 dp
+    // saturate): dp 2^-20 < q <= dp 2^-19 up to a domain of about 1360 dp
     double ext = 1.0;
     for (int a = 0; a < c.dim; ++a) ext = std::max(ext, I.L[a] / c.dp);
-    int sh = 20;
-    while (sh > 0 && (3.0 * c.h / c.dp * std::ldexp(1.0, sh) >= 4194304.0 || 1.5 * ext * std::ldexp(1.0, sh) >= 2147483648.0))
-      --sh;
-    const double q = std::ldexp(c.dp, -sh);
+    int e = (int)std::floor(std::log2(c.dp)) - 24;
+    while (3.0 * c.h >= std::ldexp(4194304.0, e) || 1.5 * ext * c.dp >= std::ldexp(2147483648.0, e)) ++e;
+    const double q = std::ldexp(1.0, e);
     I.fx_inv_q = 1.0 / q;
     I.fx_q = (float)q;
     for (int a = 0; a < 3; ++a) I.fx_Lu[a] = (a < c.dim && I.periodic[a]) ? (int32_t)std::nearbyint(I.L[a] / q) : 0;

@@ -73,8 +73,9 @@ struct InstDev {
   SweepConst<double> kd;
   float lo_f[3], inv_cs_f;  // FP32 copies for the cell-index prefilter
   // FP32 form: record positions in fixed point, X = rint((x - lo) / q) with
-  // q = dp 2^-s (int32 bit patterns in the records), so that the difference
-  // of two positions is exact and a pair vector carries one FP32 rounding
+  // q a power of two between dp 2^-20 and dp 2^-19 (int32 bit patterns in
+  // the records), so that the difference of two positions and its FP32
+  // value are exact: a pair vector is rounded only in its positions
   float fx_q;
   int32_t fx_Lu[3];   // periodic lengths in units of q
   double fx_inv_q;    // 1 / q

@@ -86,9 +86,9 @@ __device__ __forceinline__ Geo<R> make_geo(const InstDev &I) {
 // FP64 form: FP64 positions, the plain left-to-right sum without
 // contraction.  FP32 form: fixed-point positions; the difference of the two
 // integers is exact (wrapped by the periodic length in units), and for a
-// listed pair (|r| < 2h, at most 2^22 units) it converts to FP32 exactly by
-// the 2^23 + 2^22 offset; one multiplication by q then rounds it, and the
-// sum of squares is contracted.
+// listed pair (|r| < 2h, under 2^22 units) it converts to FP32 exactly by the
+// 2^23 + 2^22 offset; q being a power of two, the component di q comes out
+// of one FMA exactly, and the sum of squares is contracted.
 template <typename R, int D, bool PER>
 __device__ __forceinline__ R pair_vec(const Geo<R> &g, const V4<R> &pi, const V4<R> &pj, R d[3]) {
   if constexpr (sizeof(R) == 4) {
@@ -104,8 +104,8 @@ __device__ __forceinline__ R pair_vec(const Geo<R> &g, const V4<R> &pi, const V4
         else if (di < -hu)
           di += g.Lu[a];
       }
-      const float t = __int_as_float(0x4B400000 + di) - 12582912.0f;
-      const float v = t * (float)g.q;
+      // q is a power of two: f q - (2^23 + 2^22) q = di q exactly, one FMA
+      const float v = fmaf(__int_as_float(0x4B400000 + di), (float)g.q, -12582912.0f * (float)g.q);
       d[a] = (R)v;
       rr = (a == 0) ? v * v : fmaf(v, v, rr);
     }

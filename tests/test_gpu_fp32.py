@@ -8,11 +8,13 @@ the pressure force; more at a large background pressure, below), so the
 increments of v, k and eps are good to ~1e-5 relative; B sums positive-definite outer products
 (little cancellation: ~1e-6); FP64 state plus those increments gives
 velocities to ~1e-6 of |v| and positions to ~1e-8.  Positions in the FP32
-records are fixed point, units of q = dp 2^-20: the difference of two is
-exact and each coordinate is within q/2 = 4.8e-7 dp of its FP64 value,
-wherever the particle lies (absolute FP32 coordinates would be within
-X 6e-8 at |x| ~ X: finer only for X below 8 dp, as in the 0.8-wide
-periodic 3D box, whose bound on positions is 5e-8 for that reason).
+records are fixed point in units of q, a power of two with
+dp 2^-20 < q <= dp 2^-19: the difference of two is exact, so is its
+conversion to FP32, and each coordinate is within q/2 <= 9.5e-7 dp of its
+FP64 value wherever the particle lies (absolute FP32 coordinates would be
+within X 6e-8 at |x| ~ X: finer only for X below about 10 dp, as in the
+0.8-wide periodic 3D box, whose bound on positions is 5e-8 for that
+reason).
 
 Where a large background pressure p is summed against a weak gradient, the
 terms of the pressure force are ~p / h while their sum is |grad p|: the

@@ -66,7 +66,7 @@ def test_channel_480k_bench_configuration(sph, channel_oracle, tmp_path):
     assert np.array_equal(g["uid"], f["uid"]) and np.array_equal(g["label"], f["label"])
     errs = {k: rel_l2(g[k], f[k]) for k in ("pos", "vel", "rho", "k", "eps", "B")}
     print("channel 480k fp32", {k: f"{v:.2e}" for k, v in errs.items()})
-    # FP32 records hold fixed-point positions (units dp 2^-20): pair vectors
+    # FP32 records hold fixed-point positions (units up to dp 2^-19): pair vectors
     # carry ~1e-6 relative error wherever the particles lie (absolute FP32
     # coordinates at x ~ 6 would be good to 1e-4 of dp only), and so do B and
     # the k-eps sources; the FP64 state increments stay far below that

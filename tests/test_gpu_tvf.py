@@ -132,6 +132,9 @@ def test_one_step_fp32_with_tvf_and_density_sum(sph, orc, name):
     # rounding of sum_j V_j grad W (a cancelling sum, terms ~1/h) times
     # 2 alpha h^2, i.e. ~1e-7 h per step in the positions; the reinitialised
     # density the rounding of sum_j W (up to ~80 terms in 3D: ~5e-7), which
-    # the stiff EOS passes to the pressure and so to the velocity increments
-    bounds = {"pos": 1e-7, "vel": 3e-5, "rho": 5e-7}
+    # the stiff EOS passes to the pressure and so to the velocity increments;
+    # the pair vectors of the records carry the position rounding q/2 of the
+    # fixed point (q up to dp 2^-19, in the periodic 3D box 9e-7 h), which
+    # the shift passes on to the positions as well (measured up to 1.04e-7)
+    bounds = {"pos": 2e-7, "vel": 3e-5, "rho": 5e-7}
     assert all(errs[k] < bounds[k] for k in bounds), errs
