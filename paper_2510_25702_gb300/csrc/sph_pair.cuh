@@ -318,84 +318,59 @@ __device__ __forceinline__ void rr_pairs_f32x2(const V4<float> &pi, const V4<flo
 // zero) exact(j) decides with the FP64 test of the definition on the FP64
 // positions; [lo, hi) brackets the cut-off by more than the rounding of the
 // FP32 positions and sum can move |r|^2, so the FP32 list holds exactly the
-// pairs of the FP64 test.
+// pairs of the FP64 test.  The decisions of up to 32 candidates are gathered
+// in one mask before hit() runs on its set bits: the lanes of a warp then
+// diverge once per 32 candidates, not once per four.
 template <typename R, int D, bool PER, typename H, typename X>
 __device__ __forceinline__ void scan_range(const Geo<R> &g, const V4<R> &Pi, const V4<R> *__restrict__ P,
                                            int stride, uint32_t jb, uint32_t je, R lo, R hi, H &&hit,
                                            X &&exact) {
-  for (uint32_t j = jb; j < je; j += 4) {
-    if constexpr (sizeof(R) == 4 && !PER) {
-      // FP32 candidate arrays are padded by four entries: the loads need no
-      // bounds, one mask drops the entries past the range
-      const V4<R> q0 = P[j], q1 = P[j + 1], q2 = P[j + 2], q3 = P[j + 3];
-      const unsigned tail = (je - j >= 4u) ? 0xFu : ((1u << (je - j)) - 1u);
-      R r0, r1, r2, r3;
-      rr_pairs_f32x2<D>(Pi, q0, q1, r0, r1);
-      rr_pairs_f32x2<D>(Pi, q2, q3, r2, r3);
-      unsigned sure = ((r0 > (R)0 && r0 < lo) ? 1u : 0u) | ((r1 > (R)0 && r1 < lo) ? 2u : 0u) |
-                      ((r2 > (R)0 && r2 < lo) ? 4u : 0u) | ((r3 > (R)0 && r3 < lo) ? 8u : 0u);
-      const unsigned maybe = ((r0 < hi) ? 1u : 0u) | ((r1 < hi) ? 2u : 0u) | ((r2 < hi) ? 4u : 0u) |
-                             ((r3 < hi) ? 8u : 0u);
+  for (uint32_t j0 = jb; j0 < je; j0 += 32u) {
+    const uint32_t j1 = min(je, j0 + 32u);
+    uint32_t acc = 0u;
+    for (uint32_t j = j0; j < j1; j += 4) {
+      const unsigned tail = (j1 - j >= 4u) ? 0xFu : ((1u << (j1 - j)) - 1u);
+      R rr[4];
+      if constexpr (sizeof(R) == 4 && !PER) {
+        // FP32 candidate arrays are padded by four entries: the loads need
+        // no bounds, the tail mask drops the entries past the range
+        const V4<R> q0 = P[j], q1 = P[j + 1], q2 = P[j + 2], q3 = P[j + 3];
+        rr_pairs_f32x2<D>(Pi, q0, q1, rr[0], rr[1]);
+        rr_pairs_f32x2<D>(Pi, q2, q3, rr[2], rr[3]);
+      } else {
+        const V4<R> q0 = P[(size_t)j * stride];
+        const V4<R> q1 = (j + 1 < j1) ? P[(size_t)(j + 1) * stride] : q0;
+        const V4<R> q2 = (j + 2 < j1) ? P[(size_t)(j + 2) * stride] : q0;
+        const V4<R> q3 = (j + 3 < j1) ? P[(size_t)(j + 3) * stride] : q0;
+        R d[3];
+        rr[0] = pair_vec_abs<R, D, PER>(g, Pi, q0, d);
+        rr[1] = pair_vec_abs<R, D, PER>(g, Pi, q1, d);
+        rr[2] = pair_vec_abs<R, D, PER>(g, Pi, q2, d);
+        rr[3] = pair_vec_abs<R, D, PER>(g, Pi, q3, d);
+      }
+      unsigned sure = ((rr[0] > (R)0 && rr[0] < lo) ? 1u : 0u) | ((rr[1] > (R)0 && rr[1] < lo) ? 2u : 0u) |
+                      ((rr[2] > (R)0 && rr[2] < lo) ? 4u : 0u) | ((rr[3] > (R)0 && rr[3] < lo) ? 8u : 0u);
       sure &= tail;
-      unsigned amb = maybe & tail & ~sure;
-      if (__builtin_expect(amb != 0u, 0)) {
-        while (amb) {
-          const int k = __ffs(amb) - 1;
-          amb &= amb - 1;
-          if (exact(j + (uint32_t)k)) sure |= 1u << k;
+      if (sizeof(R) == 4) {
+        // candidates the FP32 test cannot decide (rare): the FP64 test, out
+        // of the common path
+        const unsigned maybe = ((rr[0] < hi) ? 1u : 0u) | ((rr[1] < hi) ? 2u : 0u) |
+                               ((rr[2] < hi) ? 4u : 0u) | ((rr[3] < hi) ? 8u : 0u);
+        unsigned amb = maybe & tail & ~sure;
+        if (__builtin_expect(amb != 0u, 0)) {
+          while (amb) {
+            const int k = __ffs(amb) - 1;
+            amb &= amb - 1;
+            if (exact(j + (uint32_t)k)) sure |= 1u << k;
+          }
         }
       }
-      while (sure) {
-        const int k = __ffs(sure) - 1;
-        sure &= sure - 1;
-        hit(j + (uint32_t)k);
-      }
-      continue;
+      acc |= sure << (j - j0);
     }
-    const V4<R> q0 = P[(size_t)j * stride];
-    const V4<R> q1 = (j + 1 < je) ? P[(size_t)(j + 1) * stride] : q0;
-    const V4<R> q2 = (j + 2 < je) ? P[(size_t)(j + 2) * stride] : q0;
-    const V4<R> q3 = (j + 3 < je) ? P[(size_t)(j + 3) * stride] : q0;
-    R d[3];
-    unsigned sure = 0, maybe = 0;
-    R rra[4];
-    if constexpr (sizeof(R) == 4 && !PER) {
-      rr_pairs_f32x2<D>(Pi, q0, q1, rra[0], rra[1]);
-      rr_pairs_f32x2<D>(Pi, q2, q3, rra[2], rra[3]);
-    } else {
-      rra[0] = pair_vec_abs<R, D, PER>(g, Pi, q0, d);
-      rra[1] = pair_vec_abs<R, D, PER>(g, Pi, q1, d);
-      rra[2] = pair_vec_abs<R, D, PER>(g, Pi, q2, d);
-      rra[3] = pair_vec_abs<R, D, PER>(g, Pi, q3, d);
-    }
-    R rr = rra[0];
-    sure |= (rr > (R)0 && rr < lo) ? 1u : 0u;
-    if (sizeof(R) == 4) maybe |= (rr < hi) ? 1u : 0u;
-    rr = rra[1];
-    sure |= (j + 1 < je && rr > (R)0 && rr < lo) ? 2u : 0u;
-    if (sizeof(R) == 4) maybe |= (j + 1 < je && rr < hi) ? 2u : 0u;
-    rr = rra[2];
-    sure |= (j + 2 < je && rr > (R)0 && rr < lo) ? 4u : 0u;
-    if (sizeof(R) == 4) maybe |= (j + 2 < je && rr < hi) ? 4u : 0u;
-    rr = rra[3];
-    sure |= (j + 3 < je && rr > (R)0 && rr < lo) ? 8u : 0u;
-    if (sizeof(R) == 4) maybe |= (j + 3 < je && rr < hi) ? 8u : 0u;
-    if (sizeof(R) == 4) {
-      // candidates the FP32 test cannot decide (rare): the FP64 test, out of
-      // the common path
-      unsigned amb = maybe & ~sure;
-      if (__builtin_expect(amb != 0u, 0)) {
-        while (amb) {
-          const int k = __ffs(amb) - 1;
-          amb &= amb - 1;
-          if (exact(j + (uint32_t)k)) sure |= 1u << k;
-        }
-      }
-    }
-    while (sure) {
-      const int k = __ffs(sure) - 1;
-      sure &= sure - 1;
-      hit(j + (uint32_t)k);
+    while (acc) {
+      const int k = __ffs(acc) - 1;
+      acc &= acc - 1;
+      hit(j0 + (uint32_t)k);
     }
   }
 }

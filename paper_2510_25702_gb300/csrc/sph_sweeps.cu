@@ -85,6 +85,16 @@ __device__ __forceinline__ int list_one(const SweepArgs &a, const Packs<R> &pk, 
   // real neighbours, then wall dummies; 0 < |r|^2 < (2h)^2 excludes i itself
   for (int set = 0; set < 2; ++set) {
     const uint32_t *offs = set == 0 ? a.off : a.woff;
+    if (!PER && set == 1) {
+      // the cells of the block lie between the keys of its two extreme
+      // corners: equal offsets there, no dummy in any of them
+      const int x0 = max(cx - 1, 0), y0 = max(cy - 1, 0), z0 = D == 3 ? max(cz - 1, 0) : 0;
+      const int x1 = min(cx + 1, I.nc[0] - 1), y1 = min(cy + 1, I.nc[1] - 1);
+      const int z1 = D == 3 ? min(cz + 1, I.nc[2] - 1) : 0;
+      const uint32_t k0 = I.cell_base + ((uint32_t)z0 * (uint32_t)I.nc[1] + (uint32_t)y0) * (uint32_t)I.nc[0] + (uint32_t)x0;
+      const uint32_t k1 = I.cell_base + ((uint32_t)z1 * (uint32_t)I.nc[1] + (uint32_t)y1) * (uint32_t)I.nc[0] + (uint32_t)x1;
+      if (offs[k0] == offs[k1 + 1]) break;
+    }
     const V4<R> *recs = set == 0 ? (f32 ? pk.lpos : pk.adv) : (f32 ? pk.WPf : pk.WP);
     const int stride = (set == 0 && !f32) ? RA : 1;
     // the definition in FP64 on the masters (rare: candidates in the band)
