@@ -426,8 +426,8 @@ static int build_inst(const sph_config &c, InstDev &I, std::string &why) {
     // fixed point of the FP32 form: q the smallest power of two that keeps a
     // listed pair's coordinate difference (below the cut-off 2h, with 50 %
     // to spare) under 2^22 units and the domain, with a quarter of its
-    // extent again on either side, inside int32 (coordinates beyond
-    // saturate): dp 2^-20 < q <= dp 2^-19 up to a domain of about 1360 dp
+    // extent again on either side, inside int32 (coordinates beyond wrap
+    // modulo 2^32): dp 2^-20 < q <= dp 2^-19 up to a domain of about 1360 dp
     double ext = 1.0;
     for (int a = 0; a < c.dim; ++a) ext = std::max(ext, I.L[a] / c.dp);
     int e = (int)std::floor(std::log2(c.dp)) - 24;
@@ -435,6 +435,10 @@ static int build_inst(const sph_config &c, InstDev &I, std::string &why) {
     const double q = std::ldexp(1.0, e);
     I.fx_inv_q = 1.0 / q;
     I.fx_q = (float)q;
+    for (int a = 0; a < 3; ++a) {
+      I.fx_c[a] = 6755399441055744.0 - I.lo[a] * I.fx_inv_q;  // 1.5 2^52 - lo / q, rounded
+      I.fx_o[a] = (float)((6755399441055744.0 - I.fx_c[a]) * q);
+    }
     for (int a = 0; a < 3; ++a) I.fx_Lu[a] = (a < c.dim && I.periodic[a]) ? (int32_t)std::nearbyint(I.L[a] / q) : 0;
   }
   I.n_ac = 1;
@@ -502,12 +506,13 @@ static int alloc_packs(sph_ctx *c, Packs<R> &pk, int64_t cap, int64_t nw) {
   return 0;
 }
 
-// the fixed-point coordinate of the FP32 form (as fx_encode on the device:
-// the nearest integer to (x - lo) / q, saturating)
+// the fixed-point coordinate of the FP32 form, as fx_encode on the device:
+// the low word of fma(x, 1 / q, 1.5 2^52 - lo / q)
 static float host_fx_encode(const InstDev &I, double x, int a) {
-  double u = std::nearbyint((x - I.lo[a]) * I.fx_inv_q);
-  u = std::min(std::max(u, -2147483648.0), 2147483647.0);
-  const int32_t v = (int32_t)u;
+  const double u = std::fma(x, I.fx_inv_q, I.fx_c[a]);
+  uint64_t b;
+  std::memcpy(&b, &u, sizeof(b));
+  const uint32_t v = (uint32_t)b;
   float f;
   std::memcpy(&f, &v, sizeof(f));
   return f;

@@ -79,6 +79,10 @@ struct InstDev {
   float fx_q;
   int32_t fx_Lu[3];   // periodic lengths in units of q
   double fx_inv_q;    // 1 / q
+  // 1.5 2^52 - lo / q rounded to an integer (the encoding origin o = lo to
+  // within q / 2): fma(x, 1 / q, fx_c) is 1.5 2^52 + X, X = round((x - o) / q)
+  double fx_c[3];
+  float fx_o[3];      // the origin o in FP32, for decoding
   // written every advection step by the time-step kernel
   double dt_ad, dt_ac, dt, t;
   int32_t n_ac;
@@ -234,10 +238,14 @@ __device__ __forceinline__ double f32_to_f64(float x) {
   return __hiloint2double((int)((u & 0x80000000u) | ((mag >> 3) + (896u << 20))), (int)(u << 29));
 }
 
-// fixed-point record coordinate of x along axis a (FP32 form): the int32
-// nearest to (x - lo) / q, saturating, as a float bit pattern
+// fixed-point record coordinate of x along axis a (FP32 form): the integer
+// X nearest to (x - o) / q, modulo 2^32 (a difference of two coordinates is
+// exact modulo 2^32 all the same), as a float bit pattern.  One FMA: q being
+// a power of two, x / q is exact and the sum with fx_c is rounded once, to
+// an integer (its magnitude lies in [2^52, 2^53)), whose bit pattern is that
+// of 1.5 2^52 (low word 0) plus X while |X| < 2^51
 __device__ __forceinline__ float fx_encode(const InstDev &I, double x, int a) {
-  return __int_as_float(__double2int_rn(dmul(dsub(x, I.lo[a]), I.fx_inv_q)));
+  return __int_as_float(__double2loint(__fma_rn(x, I.fx_inv_q, I.fx_c[a])));
 }
 
 // conversions into and out of the sweep precision R

@@ -121,7 +121,7 @@ __device__ __forceinline__ R pair_vec(const Geo<R> &g, const V4<R> &pi, const V4
 template <typename R>
 __device__ __forceinline__ R rec_abs(const InstDev &I, R x, int a) {
   if constexpr (sizeof(R) == 4)
-    return I.lo_f[a] + (float)__float_as_int(x) * I.fx_q;
+    return I.fx_o[a] + (float)__float_as_int(x) * I.fx_q;
   else
     return x;
 }
