@@ -499,11 +499,9 @@ def main():
     case = workload(args.workload, seed=2 + rank)
     if args.workload == "batched_channels" and world > 1:
         # instances of one batch partitioned across ranks by particle count
-        from paper_2510_25702_gb300.shard import partition_instances
+        from paper_2510_25702_gb300.shard import shard_cases
 
-        full = workload(args.workload)
-        mine = partition_instances([c.n for c in full], world)[rank]
-        case = [full[q] for q in mine]
+        case = shard_cases(workload(args.workload), world, rank)
     sim = sph.Simulation(case, precision=args.precision)
     stream = torch.cuda.current_stream()
 

@@ -28,6 +28,13 @@ def partition_instances(counts: Sequence[int], world: int) -> List[List[int]]:
     return [sorted(p) for p in parts]
 
 
+def shard_cases(cases: Sequence, world: int, rank: int) -> list:
+    """This rank's instances of a batch (partition_instances by particle
+    count), in their batch order."""
+    mine = partition_instances([int(c.n) for c in cases], world)[rank]
+    return [cases[q] for q in mine]
+
+
 def combine_timing(ms: float, particle_steps: float, dist=None) -> Tuple[float, float]:
     """Whole-job timing: the slowest rank's time and the particle-steps of
     all ranks (torch.distributed when dist is given, else this rank's)."""
