@@ -1096,10 +1096,9 @@ int sph_set_profile(sph_ctx *c, int32_t instance, int32_t buffer_id, const doubl
       CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     stage->n_theta = n_theta;
     for (int q = 0; q < n_theta; ++q) stage->theta[q] = theta[q];
-    CUDA_TRY(cudaMemcpyAsync(&c->d_buf[g].n_theta, &stage->n_theta, sizeof(int32_t), cudaMemcpyHostToDevice,
-                             c->stream));
-    CUDA_TRY(cudaMemcpyAsync(c->d_buf[g].theta, stage->theta, sizeof(double) * n_theta, cudaMemcpyHostToDevice,
-                             c->stream));
+    static_assert(offsetof(BufDev, theta) == offsetof(BufDev, n_theta) + 8, "n_theta directly before theta");
+    CUDA_TRY(cudaMemcpyAsync(&c->d_buf[g].n_theta, &stage->n_theta, 8 + sizeof(double) * n_theta,
+                             cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaEventRecord(ev, c->stream));
   }
   return SPH_OK;
@@ -2221,8 +2220,17 @@ extern "C" int sph_debug_convert(const double *in64, float *out32, const float *
 // FP64 mass and momentum of every instance (deterministic order)
 // ------------------------------------------------------------------------
 namespace {
-constexpr int kRedSlices = 128;  // blocks per instance
+constexpr int kRedMaxSlices = 1024;  // blocks per instance, at most
 constexpr int kRedThreads = 256;
+
+// blocks per instance: 1024 for one instance, halved per doubling of the
+// instance count down to 128 (about 1000 blocks or more in all); a power of
+// two, fixed per context, so the summation tree is fixed too
+static int red_slices(int ninst) {
+  int s = kRedMaxSlices;
+  while (s > 128 && (int64_t)s * ninst > kRedMaxSlices) s >>= 1;
+  return s;
+}
 
 // first index in [lo, hi) whose instance is >= q (instances non-decreasing
 // there), found by the 32 lanes of a warp together: each round probes 32
@@ -2252,8 +2260,9 @@ __device__ int inst_lower_bound_warp(const uint16_t *inst, int lo, int hi, int q
 // sentinel key.  Each thread sums a fixed strided subset, the block sums
 // the threads in a fixed tree: the result does not depend on timing.
 __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(Masters m, const uint32_t *keys, uint32_t sentinel,
-                                                                 const Counters *cnt, int dim, double *partial) {
-  const int q = blockIdx.x / kRedSlices, sl = blockIdx.x % kRedSlices;
+                                                                 const Counters *cnt, int dim, int slices,
+                                                                 double *partial) {
+  const int q = blockIdx.x / slices, sl = blockIdx.x % slices;
   const int n1 = cnt->n_live, n2 = cnt->m_pending;
   __shared__ int s_r[4];
   // the four run bounds, one warp each
@@ -2265,7 +2274,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(Masters m, const
   }
   __syncthreads();
   const int a0 = s_r[0], la = s_r[1] - s_r[0], b0 = s_r[2], L = la + (s_r[3] - s_r[2]);
-  const int64_t k0 = (int64_t)L * sl / kRedSlices, k1 = (int64_t)L * (sl + 1) / kRedSlices;
+  const int64_t k0 = (int64_t)L * sl / slices, k1 = (int64_t)L * (sl + 1) / slices;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t k = k0 + threadIdx.x; k < k1; k += kRedThreads) {
     const int i = k < la ? a0 + (int)k : b0 + (int)(k - la);
@@ -2287,12 +2296,13 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(Masters m, const
 }
 
 // one block per instance: the slices' partial sums in a fixed tree
-__global__ void __launch_bounds__(kRedSlices) k_reduce_final(const double *partial, int ninst, double *out) {
+__global__ void __launch_bounds__(kRedMaxSlices) k_reduce_final(const double *partial, int ninst, double *out) {
+  const int slices = blockDim.x;
   const int q = blockIdx.x;
-  __shared__ double red[4][kRedSlices];
-  for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = partial[((size_t)q * kRedSlices + threadIdx.x) * 4 + c];
+  __shared__ double red[4][kRedMaxSlices];
+  for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = partial[((size_t)q * slices + threadIdx.x) * 4 + c];
   __syncthreads();
-  for (int w = kRedSlices / 2; w > 0; w >>= 1) {
+  for (int w = slices / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w)
       for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = sphk::dadd(red[c][threadIdx.x], red[c][threadIdx.x + w]);
     __syncthreads();
@@ -2301,19 +2311,39 @@ __global__ void __launch_bounds__(kRedSlices) k_reduce_final(const double *parti
 }
 }  // namespace
 
-extern "C" int sph_reduce_mass_momentum(sph_ctx *c, double *mass, double *momentum) {
-  if (!c || (!mass && !momentum)) return fail(SPH_ERR_ARG, "NULL argument");
+// the two reduction launches on the context's stream; *res receives the
+// device address of the results [ninst][4] (mass, momentum x y z)
+static int enqueue_mass_momentum(sph_ctx *c, double **res) {
   if (!c->red) {
     // partial sums [ninst * slices][4] and results [ninst][4], owned by the
     // context from the first call on
-    c->red = (double *)c->dalloc(sizeof(double) * 4 * ((size_t)c->ninst * kRedSlices + c->ninst));
+    c->red = (double *)c->dalloc(sizeof(double) * 4 * ((size_t)c->ninst * red_slices(c->ninst) + c->ninst));
     if (!c->red) return fail(SPH_ERR_ALLOC, "reduction buffers");
   }
-  double *partial = c->red, *res = c->red + 4 * (size_t)c->ninst * kRedSlices;
-  k_reduce_partial<<<c->ninst * kRedSlices, kRedThreads, 0, c->stream>>>(c->M[c->cur], c->K[0], c->ncell, c->cnt,
-                                                                         c->dim, partial);
-  k_reduce_final<<<c->ninst, kRedSlices, 0, c->stream>>>(partial, c->ninst, res);
+  const int slices = red_slices(c->ninst);
+  double *partial = c->red;
+  *res = c->red + 4 * (size_t)c->ninst * slices;
+  k_reduce_partial<<<c->ninst * slices, kRedThreads, 0, c->stream>>>(c->M[c->cur], c->K[0], c->ncell, c->cnt,
+                                                                     c->dim, slices, partial);
+  k_reduce_final<<<c->ninst, slices, 0, c->stream>>>(partial, c->ninst, *res);
   CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+extern "C" int sph_reduce_mass_momentum_async(sph_ctx *c, double *out) {
+  if (!c || !out) return fail(SPH_ERR_ARG, "NULL argument");
+  double *res = nullptr;
+  const int rc = enqueue_mass_momentum(c, &res);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(out, res, sizeof(double) * 4 * (size_t)c->ninst, cudaMemcpyDeviceToHost, c->stream));
+  return SPH_OK;
+}
+
+extern "C" int sph_reduce_mass_momentum(sph_ctx *c, double *mass, double *momentum) {
+  if (!c || (!mass && !momentum)) return fail(SPH_ERR_ARG, "NULL argument");
+  double *res = nullptr;
+  const int rc = enqueue_mass_momentum(c, &res);
+  if (rc) return rc;
   std::vector<double> h(4 * (size_t)c->ninst);
   CUDA_TRY(cudaMemcpyAsync(h.data(), res, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));

@@ -101,8 +101,7 @@ __host__ __device__ __forceinline__ const SweepConst<double> &sweep_const<double
 }
 
 struct BufDev {
-  int32_t type, turb, n_theta, inst;
-  int32_t local_id, pad0;
+  int32_t type, turb, inst, local_id;
   double origin[3];
   double frame[9];
   double length, half[2];
@@ -111,6 +110,9 @@ struct BufDev {
   // FP32 bounding sphere of the box, widened for FP32 rounding (a point
   // outside it is outside the box; inside it the exact test decides)
   float cen[3], rad2;
+  // the inlet profile, n_theta directly before theta so that one copy
+  // moves both
+  int32_t n_theta, pad0;
   double theta[SPH_MAX_THETA];
 };
 

@@ -108,7 +108,8 @@ EXPORTS = ("sph_create", "sph_add_buffer", "sph_set_profile", "sph_step", "sph_r
            "sph_cell_sort_noalloc", "sph_set_graph", "sph_set_launch", "sph_get_launch", "sph_autotune",
            "sph_save_state", "sph_restore_state", "sph_drop_state", "sph_adjoint_forward",
            "sph_adjoint_backward", "sph_adjoint_release", "sph_debug_convert", "sph_step_async",
-           "sph_reduce_mass_momentum", "sph_measure_fma_peak", "sph_debug_barrier_timeout")
+           "sph_reduce_mass_momentum", "sph_reduce_mass_momentum_async", "sph_measure_fma_peak",
+           "sph_debug_barrier_timeout")
 NOALLOC_MAX_POINTS = 1 << 19
 N_STAGES = 10
 
@@ -133,6 +134,7 @@ def lib():
         L.sph_step.argtypes = [vp, C.c_int32, C.POINTER(C.c_double)]
         L.sph_step_async.argtypes = [vp, C.c_int32]
         L.sph_reduce_mass_momentum.argtypes = [vp, vp, vp]
+        L.sph_reduce_mass_momentum_async.argtypes = [vp, vp]
         L.sph_read_fields.argtypes = [vp, C.c_uint32, C.POINTER(vp), C.c_int32, C.POINTER(C.c_int64)]
         L.sph_write_fields.argtypes = [vp, C.c_uint32, C.POINTER(vp), C.c_int32, C.c_int64]
         L.sph_get_stats.argtypes = [vp, C.POINTER(Stats)]
@@ -327,6 +329,15 @@ class Simulation:
         p = np.zeros((len(self.cases), 3), np.float64)
         _check(lib().sph_reduce_mass_momentum(self.ctx, m.ctypes.data, p.ctypes.data), "sph_reduce_mass_momentum")
         return m, p
+
+    def mass_momentum_async(self, out):
+        """Enqueue the FP64 totals into out (a page-locked float64 torch
+        tensor of 4 * n_instances elements: mass, momentum x y z per
+        instance) on the context's stream, without waiting; read out after
+        the stream has passed this point (an event recorded after it)."""
+        if out.dtype.itemsize != 8 or out.numel() < 4 * len(self.cases) or out.is_cuda:
+            raise ValueError("out must be a host float64 tensor of 4 * n_instances elements")
+        _check(lib().sph_reduce_mass_momentum_async(self.ctx, out.data_ptr()), "sph_reduce_mass_momentum_async")
 
     def step_rc(self, nsteps: int = 1) -> int:
         """sph_step's return code (no exception)."""

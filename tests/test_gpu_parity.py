@@ -279,6 +279,28 @@ def test_fp64_mass_momentum_reduction(sph, orc):
     assert m2[0] == pytest.approx(sim.count() * mp, rel=1e-13)
 
 
+def test_mass_momentum_async_equals_the_waiting_call(sph):
+    """sph_reduce_mass_momentum_async into page-locked memory: after the
+    stream has passed it, the same bits as sph_reduce_mass_momentum, for
+    every instance of a batch; enqueued behind steps without a wait."""
+    import torch
+
+    batch = cases.batched_channels(n_instances=3, dps=(0.05,), seed=7)
+    sim = sph.Simulation(batch, precision="fp32")
+    sim.step(2)
+    out = torch.full((4 * len(batch),), float("nan"), dtype=torch.float64, pin_memory=True)
+    sim.step_async(2)
+    sim.mass_momentum_async(out)
+    ev = torch.cuda.Event()
+    ev.record(torch.cuda.current_stream())
+    ev.synchronize()
+    m, p = sim.mass_momentum()
+    tot = out.numpy().reshape(len(batch), 4)
+    assert np.array_equal(tot[:, 0], m) and np.array_equal(tot[:, 1:], p)
+    with pytest.raises(ValueError):
+        sim.mass_momentum_async(torch.empty(3, dtype=torch.float64))
+
+
 def test_async_stepping_matches_and_reports_status(sph):
     """sph_step_async + sph_get_stats (one wait per step, profiles staged
     in pinned memory) give the same state as sph_step, bit for bit, and the
