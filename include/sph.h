@@ -426,14 +426,16 @@ int sph_debug_list(sph_ctx *ctx, int64_t *out, int64_t max, int64_t *count);
    SPH_ERR_CUDA. */
 int sph_reduce_mass_momentum(sph_ctx *ctx, double *mass, double *momentum);
 
-/* The same FP64 totals without waiting: the reduction and a copy of its
-   results into out[4 * n_instances] (per instance: mass, then momentum x,
-   y, z) are enqueued on the context's stream.  out is host memory the
-   caller keeps, and leaves unread, until the stream has passed this point
-   (an event recorded on the stream after the call, or sph_get_stats);
-   page-locked memory lets the copy run asynchronously (pageable memory
-   makes the call wait for the copy).  The first call allocates the
-   reduction buffers.  Errors: SPH_ERR_ARG, SPH_ERR_ALLOC, SPH_ERR_CUDA. */
+/* The same FP64 totals without waiting: the reduction is enqueued on the
+   context's stream and its results land in out[4 * n_instances] (per
+   instance: mass, then momentum x, y, z).  out is host memory the caller
+   keeps, and leaves unread, until the stream has passed this point (an
+   event recorded on the stream after the call, or sph_get_stats).
+   Page-locked memory that the device can address is written by the
+   reduction itself; other host memory gets a copy enqueued after it
+   (pageable memory makes the call wait for that copy).  The first call
+   allocates the reduction buffers.  Errors: SPH_ERR_ARG, SPH_ERR_ALLOC,
+   SPH_ERR_CUDA. */
 int sph_reduce_mass_momentum_async(sph_ctx *ctx, double *out);
 
 /* Test aid (no counterpart in the paper): the binary64 -> binary32 and

@@ -2258,13 +2258,17 @@ __device__ int inst_lower_bound_warp(const uint16_t *inst, int lo, int hi, int q
 // [0, n_live) (the sorted particles) and one in [n_live, m_pending) (the
 // copies appended by the last buffer update); deleted rows carry the
 // sentinel key.  Each thread sums a fixed strided subset, the block sums
-// the threads in a fixed tree: the result does not depend on timing.
-__global__ void __launch_bounds__(kRedThreads) k_reduce_partial(Masters m, const uint32_t *keys, uint32_t sentinel,
-                                                                 const Counters *cnt, int dim, int slices,
-                                                                 double *partial) {
+// the threads in a fixed tree.  The last block to finish then sums each
+// instance's slices in a fixed order (thread t takes slices t, t + 256, ...
+// in turn, then a tree over the threads) into out[ninst][4], which may be
+// page-locked host memory: the result does not depend on timing.
+__global__ void __launch_bounds__(kRedThreads) k_reduce(Masters m, const uint32_t *keys, uint32_t sentinel,
+                                                        const Counters *cnt, int dim, int slices, int ninst,
+                                                        double *partial, uint32_t *done, double *out) {
   const int q = blockIdx.x / slices, sl = blockIdx.x % slices;
   const int n1 = cnt->n_live, n2 = cnt->m_pending;
   __shared__ int s_r[4];
+  __shared__ bool s_last;
   // the four run bounds, one warp each
   const int wq = threadIdx.x >> 5;
   if (wq < 4) {
@@ -2284,65 +2288,80 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_partial(Masters m, const
     for (int d = 0; d < dim; ++d) acc[1 + d] = sphk::dadd(acc[1 + d], sphk::dmul(mi, m.v[d][i]));
   }
   __shared__ double red[4][kRedThreads];
-  for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = acc[c];
-  __syncthreads();
-  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-      for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = sphk::dadd(red[c][threadIdx.x], red[c][threadIdx.x + w]);
+  auto tree = [&]() {
+    for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = acc[c];
     __syncthreads();
-  }
-  if (threadIdx.x == 0)
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w)
+        for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = sphk::dadd(red[c][threadIdx.x], red[c][threadIdx.x + w]);
+      __syncthreads();
+    }
+  };
+  tree();
+  if (threadIdx.x == 0) {
     for (int c = 0; c < 4; ++c) partial[(size_t)blockIdx.x * 4 + c] = red[c][0];
-}
-
-// one block per instance: the slices' partial sums in a fixed tree
-__global__ void __launch_bounds__(kRedMaxSlices) k_reduce_final(const double *partial, int ninst, double *out) {
-  const int slices = blockDim.x;
-  const int q = blockIdx.x;
-  __shared__ double red[4][kRedMaxSlices];
-  for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = partial[((size_t)q * slices + threadIdx.x) * 4 + c];
+    __threadfence();
+    s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+  }
   __syncthreads();
-  for (int w = slices / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-      for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = sphk::dadd(red[c][threadIdx.x], red[c][threadIdx.x + w]);
+  if (!s_last) return;
+  __threadfence();
+  for (int qq = 0; qq < ninst; ++qq) {
+    for (int c = 0; c < 4; ++c) acc[c] = 0.0;
+    for (int t = threadIdx.x; t < slices; t += kRedThreads)
+      for (int c = 0; c < 4; ++c) acc[c] = sphk::dadd(acc[c], __ldcg(&partial[((size_t)qq * slices + t) * 4 + c]));
+    tree();
+    if (threadIdx.x < 4) out[(size_t)qq * 4 + threadIdx.x] = red[threadIdx.x][0];
     __syncthreads();
   }
-  if (threadIdx.x < 4) out[(size_t)q * 4 + threadIdx.x] = red[threadIdx.x][0];
+  if (threadIdx.x == 0) *done = 0u;
 }
 }  // namespace
 
-// the two reduction launches on the context's stream; *res receives the
-// device address of the results [ninst][4] (mass, momentum x y z)
-static int enqueue_mass_momentum(sph_ctx *c, double **res) {
-  if (!c->red) {
-    // partial sums [ninst * slices][4] and results [ninst][4], owned by the
-    // context from the first call on
-    c->red = (double *)c->dalloc(sizeof(double) * 4 * ((size_t)c->ninst * red_slices(c->ninst) + c->ninst));
-    if (!c->red) return fail(SPH_ERR_ALLOC, "reduction buffers");
-  }
+// the reduction launch on the context's stream, results [ninst][4] (mass,
+// momentum x y z) into out (device memory or page-locked host memory the
+// device can address); NULL: the context's device result buffer, whose
+// address *res receives
+static int enqueue_mass_momentum(sph_ctx *c, double *out, double **res) {
   const int slices = red_slices(c->ninst);
+  if (!c->red) {
+    // partial sums [ninst * slices][4], results [ninst][4] and the blocks'
+    // completion counter, owned by the context from the first call on
+    c->red = (double *)c->dalloc(sizeof(double) * (4 * ((size_t)c->ninst * slices + c->ninst) + 1));
+    if (!c->red) return fail(SPH_ERR_ALLOC, "reduction buffers");
+    CUDA_TRY(cudaMemsetAsync(c->red, 0, sizeof(double) * (4 * ((size_t)c->ninst * slices + c->ninst) + 1),
+                             c->stream));
+  }
   double *partial = c->red;
-  *res = c->red + 4 * (size_t)c->ninst * slices;
-  k_reduce_partial<<<c->ninst * slices, kRedThreads, 0, c->stream>>>(c->M[c->cur], c->K[0], c->ncell, c->cnt,
-                                                                     c->dim, slices, partial);
-  k_reduce_final<<<c->ninst, slices, 0, c->stream>>>(partial, c->ninst, *res);
+  double *dres = c->red + 4 * (size_t)c->ninst * slices;
+  uint32_t *done = reinterpret_cast<uint32_t *>(dres + 4 * (size_t)c->ninst);
+  if (res) *res = dres;
+  k_reduce<<<c->ninst * slices, kRedThreads, 0, c->stream>>>(c->M[c->cur], c->K[0], c->ncell, c->cnt, c->dim, slices,
+                                                              c->ninst, partial, done, out ? out : dres);
   CUDA_TRY(cudaGetLastError());
   return 0;
 }
 
 extern "C" int sph_reduce_mass_momentum_async(sph_ctx *c, double *out) {
   if (!c || !out) return fail(SPH_ERR_ARG, "NULL argument");
+  // page-locked host memory the device can write: the reduction's last
+  // block writes the totals there; other memory takes a copy
+  cudaPointerAttributes pa{};
+  void *dev = nullptr;
+  if (cudaPointerGetAttributes(&pa, out) == cudaSuccess && pa.type == cudaMemoryTypeHost) dev = pa.devicePointer;
+  cudaGetLastError();
   double *res = nullptr;
-  const int rc = enqueue_mass_momentum(c, &res);
+  const int rc = enqueue_mass_momentum(c, (double *)dev, &res);
   if (rc) return rc;
-  CUDA_TRY(cudaMemcpyAsync(out, res, sizeof(double) * 4 * (size_t)c->ninst, cudaMemcpyDeviceToHost, c->stream));
+  if (!dev)
+    CUDA_TRY(cudaMemcpyAsync(out, res, sizeof(double) * 4 * (size_t)c->ninst, cudaMemcpyDeviceToHost, c->stream));
   return SPH_OK;
 }
 
 extern "C" int sph_reduce_mass_momentum(sph_ctx *c, double *mass, double *momentum) {
   if (!c || (!mass && !momentum)) return fail(SPH_ERR_ARG, "NULL argument");
   double *res = nullptr;
-  const int rc = enqueue_mass_momentum(c, &res);
+  const int rc = enqueue_mass_momentum(c, nullptr, &res);
   if (rc) return rc;
   std::vector<double> h(4 * (size_t)c->ninst);
   CUDA_TRY(cudaMemcpyAsync(h.data(), res, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
