@@ -650,10 +650,11 @@ def main():
         raise RuntimeError(f"device status {st['status']} in the end-to-end loop")
     e2e = {"value": ps / (t1 - t0) * (world if dist is not None else 1), "unit": UNIT,
            "h2d_bytes_per_step": 8 + 8 * theta.size, "d2h_bytes_per_step": 32 * ninst, "steps": e2e_steps,
-           "per_step": "sph_set_profile (one H2D copy of n_theta and theta from pinned staging), sph_step_async, "
-                       "sph_reduce_mass_momentum_async (FP64 totals, D2H into page-locked memory); the host "
-                       "waits for each step's totals after enqueuing the next step and checks them; the "
-                       "status word read once after the loop"}
+           "per_step": "sph_set_profile (n_theta and theta moved from page-locked staging by a one-block "
+                       "kernel), sph_step_async, sph_reduce_mass_momentum_async (FP64 totals written by the "
+                       "reduction into page-locked host memory); the host waits for each step's totals "
+                       "after enqueuing the next step and checks them; the status word read once after "
+                       "the loop"}
 
     log("e2e done")
     fp64 = None

@@ -68,6 +68,7 @@ struct sph_ctx {
     int32_t status;
   };
   Pinned *pin = nullptr;
+  int red_slices = 0;  // reduction blocks per instance, fixed at the first reduction
   char *prof_stage = nullptr;  // ninst x SPH_MAX_BUFFERS slots of kProfSlot bytes
   std::vector<cudaEvent_t> prof_ev;
   int64_t cap = 0, nw = 0;
@@ -1074,6 +1075,11 @@ static int upload_buffers(sph_ctx *c) {
   return 0;
 }
 
+// n 8-byte words from src to dst (one block)
+__global__ void k_copy_words(unsigned long long *__restrict__ dst, const unsigned long long *__restrict__ src, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+}
+
 int sph_set_profile(sph_ctx *c, int32_t instance, int32_t buffer_id, const double *theta, int32_t n_theta) {
   if (!c || !theta) return fail(SPH_ERR_ARG, "NULL argument");
   if (instance < 0 || instance >= c->ninst) return fail(SPH_ERR_ARG, "instance out of range");
@@ -1097,8 +1103,19 @@ int sph_set_profile(sph_ctx *c, int32_t instance, int32_t buffer_id, const doubl
     stage->n_theta = n_theta;
     for (int q = 0; q < n_theta; ++q) stage->theta[q] = theta[q];
     static_assert(offsetof(BufDev, theta) == offsetof(BufDev, n_theta) + 8, "n_theta directly before theta");
-    CUDA_TRY(cudaMemcpyAsync(&c->d_buf[g].n_theta, &stage->n_theta, 8 + sizeof(double) * n_theta,
-                             cudaMemcpyHostToDevice, c->stream));
+    // the slot is page-locked memory the device addresses: a one-block
+    // kernel moves it (no switch to a copy engine between two steps); a
+    // copy where the device cannot address it
+    void *src = nullptr;
+    if (cudaHostGetDevicePointer(&src, &stage->n_theta, 0) == cudaSuccess && src) {
+      k_copy_words<<<1, 64, 0, c->stream>>>(reinterpret_cast<unsigned long long *>(&c->d_buf[g].n_theta),
+                                            static_cast<const unsigned long long *>(src), 1 + n_theta);
+      CUDA_TRY(cudaGetLastError());
+    } else {
+      cudaGetLastError();
+      CUDA_TRY(cudaMemcpyAsync(&c->d_buf[g].n_theta, &stage->n_theta, 8 + sizeof(double) * n_theta,
+                               cudaMemcpyHostToDevice, c->stream));
+    }
     CUDA_TRY(cudaEventRecord(ev, c->stream));
   }
   return SPH_OK;
@@ -2220,16 +2237,20 @@ extern "C" int sph_debug_convert(const double *in64, float *out32, const float *
 // FP64 mass and momentum of every instance (deterministic order)
 // ------------------------------------------------------------------------
 namespace {
-constexpr int kRedMaxSlices = 1024;  // blocks per instance, at most
 constexpr int kRedThreads = 256;
 
-// blocks per instance: 1024 for one instance, halved per doubling of the
-// instance count down to 128 (about 1000 blocks or more in all); a power of
-// two, fixed per context, so the summation tree is fixed too
+// blocks per instance: about two per SM in all.  Every FP64 operation is
+// costly on this GPU (about 1.4 per clock and SM): with more, thinner
+// blocks the shuffle trees that sum the threads outweigh the five
+// operations per particle (1024 blocks: 32 us for 480k particles, FP64
+// pipe 57 % busy).  Fixed per context (the first call), so the summation
+// order is fixed too.
 static int red_slices(int ninst) {
-  int s = kRedMaxSlices;
-  while (s > 128 && (int64_t)s * ninst > kRedMaxSlices) s >>= 1;
-  return s;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+  cudaGetLastError();
+  return std::max(1, (2 * sms + ninst - 1) / ninst);
 }
 
 // first index in [lo, hi) whose instance is >= q (instances non-decreasing
@@ -2258,48 +2279,74 @@ __device__ int inst_lower_bound_warp(const uint16_t *inst, int lo, int hi, int q
 // [0, n_live) (the sorted particles) and one in [n_live, m_pending) (the
 // copies appended by the last buffer update); deleted rows carry the
 // sentinel key.  Each thread sums a fixed strided subset, the block sums
-// the threads in a fixed tree.  The last block to finish then sums each
-// instance's slices in a fixed order (thread t takes slices t, t + 256, ...
-// in turn, then a tree over the threads) into out[ninst][4], which may be
-// page-locked host memory: the result does not depend on timing.
+// its threads in a fixed order (a shuffle tree per warp, then the warps in
+// turn).  The last block to finish then sums each instance's slices in a
+// fixed order (thread t takes slices t, t + 256, ... in turn, then the same
+// block sum) into out[ninst][4], which may be page-locked host memory: the
+// result does not depend on timing.
 __global__ void __launch_bounds__(kRedThreads) k_reduce(Masters m, const uint32_t *keys, uint32_t sentinel,
                                                         const Counters *cnt, int dim, int slices, int ninst,
                                                         double *partial, uint32_t *done, double *out) {
   const int q = blockIdx.x / slices, sl = blockIdx.x % slices;
   const int n1 = cnt->n_live, n2 = cnt->m_pending;
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   __shared__ int s_r[4];
   __shared__ bool s_last;
-  // the four run bounds, one warp each
-  const int wq = threadIdx.x >> 5;
-  if (wq < 4) {
+  __shared__ double s_w[kRedThreads / 32][4];
+  if (ninst == 1) {
+    // one instance: its rows are all of [0, n_live) and [n_live, m_pending)
+    if (threadIdx.x < 4) s_r[threadIdx.x] = threadIdx.x < 2 ? (threadIdx.x == 0 ? 0 : n1) : (threadIdx.x == 2 ? n1 : n2);
+  } else if (wq < 4) {
+    // the four run bounds, one warp each
     const int lo = wq < 2 ? 0 : n1, hi = wq < 2 ? n1 : n2;
     const int r = inst_lower_bound_warp(m.inst, lo, hi, q + (wq & 1));
-    if ((threadIdx.x & 31) == 0) s_r[wq] = r;
+    if (lane == 0) s_r[wq] = r;
   }
   __syncthreads();
   const int a0 = s_r[0], la = s_r[1] - s_r[0], b0 = s_r[2], L = la + (s_r[3] - s_r[2]);
   const int64_t k0 = (int64_t)L * sl / slices, k1 = (int64_t)L * (sl + 1) / slices;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int64_t k = k0 + threadIdx.x; k < k1; k += kRedThreads) {
-    const int i = k < la ? a0 + (int)k : b0 + (int)(k - la);
-    if (keys[i] == sentinel) continue;
-    const double mi = m.mass[i];
-    acc[0] = sphk::dadd(acc[0], mi);
-    for (int d = 0; d < dim; ++d) acc[1 + d] = sphk::dadd(acc[1 + d], sphk::dmul(mi, m.v[d][i]));
+  // four rows per round, their loads issued together; a deleted row adds
+  // nothing (its terms are skipped, not multiplied by zero)
+  constexpr int U = 4;
+  for (int64_t kb = k0 + threadIdx.x; kb < k1; kb += (int64_t)U * kRedThreads) {
+    double mu[U], vu[U][3];
+    bool live[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t k = kb + (int64_t)u * kRedThreads;
+      const int i = k < k1 ? (k < la ? a0 + (int)k : b0 + (int)(k - la)) : 0;
+      live[u] = k < k1 && keys[i] != sentinel;
+      mu[u] = m.mass[i];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) vu[u][d] = d < dim ? m.v[d][i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!live[u]) continue;
+      acc[0] = sphk::dadd(acc[0], mu[u]);
+      for (int d = 0; d < dim; ++d) acc[1 + d] = sphk::dadd(acc[1 + d], sphk::dmul(mu[u], vu[u][d]));
+    }
   }
-  __shared__ double red[4][kRedThreads];
-  auto tree = [&]() {
-    for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = acc[c];
+  // the block's sum in a fixed order: a shuffle tree in each warp, then the
+  // warps' sums in warp order
+  auto block_sum = [&]() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[c] = sphk::dadd(acc[c], __shfl_down_sync(0xffffffffu, acc[c], o));
+    if (lane == 0)
+      for (int c = 0; c < 4; ++c) s_w[wq][c] = acc[c];
     __syncthreads();
-    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
-      if (threadIdx.x < w)
-        for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = sphk::dadd(red[c][threadIdx.x], red[c][threadIdx.x + w]);
-      __syncthreads();
+    if (threadIdx.x < 4) {
+      double t = s_w[0][threadIdx.x];
+      for (int w = 1; w < kRedThreads / 32; ++w) t = sphk::dadd(t, s_w[w][threadIdx.x]);
+      acc[threadIdx.x] = t;
     }
   };
-  tree();
+  block_sum();
+  if (threadIdx.x < 4) partial[(size_t)blockIdx.x * 4 + threadIdx.x] = acc[threadIdx.x];
   if (threadIdx.x == 0) {
-    for (int c = 0; c < 4; ++c) partial[(size_t)blockIdx.x * 4 + c] = red[c][0];
     __threadfence();
     s_last = atomicAdd(done, 1u) == gridDim.x - 1;
   }
@@ -2310,8 +2357,8 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(Masters m, const uint32_
     for (int c = 0; c < 4; ++c) acc[c] = 0.0;
     for (int t = threadIdx.x; t < slices; t += kRedThreads)
       for (int c = 0; c < 4; ++c) acc[c] = sphk::dadd(acc[c], __ldcg(&partial[((size_t)qq * slices + t) * 4 + c]));
-    tree();
-    if (threadIdx.x < 4) out[(size_t)qq * 4 + threadIdx.x] = red[threadIdx.x][0];
+    block_sum();
+    if (threadIdx.x < 4) out[(size_t)qq * 4 + threadIdx.x] = acc[threadIdx.x];
     __syncthreads();
   }
   if (threadIdx.x == 0) *done = 0u;
@@ -2323,7 +2370,8 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(Masters m, const uint32_
 // device can address); NULL: the context's device result buffer, whose
 // address *res receives
 static int enqueue_mass_momentum(sph_ctx *c, double *out, double **res) {
-  const int slices = red_slices(c->ninst);
+  if (!c->red) c->red_slices = red_slices(c->ninst);
+  const int slices = c->red_slices;
   if (!c->red) {
     // partial sums [ninst * slices][4], results [ninst][4] and the blocks'
     // completion counter, owned by the context from the first call on
