@@ -2278,9 +2278,8 @@ __device__ int inst_lower_bound_warp(const uint16_t *inst, int lo, int hi, int q
 // block (q, s): slice s of instance q's rows, which are one run in
 // [0, n_live) (the sorted particles) and one in [n_live, m_pending) (the
 // copies appended by the last buffer update); deleted rows carry the
-// sentinel key.  Each thread sums a fixed strided subset, the block sums
-// its threads in a fixed order (a shuffle tree per warp, then the warps in
-// turn).  The last block to finish then sums each instance's slices in a
+// sentinel key.  Each thread sums a fixed strided subset (momentum by
+// FMA), the block sums its threads in a fixed order (block_sum).  The last block to finish then sums each instance's slices in a
 // fixed order (thread t takes slices t, t + 256, ... in turn, then the same
 // block sum) into out[ninst][4], which may be page-locked host memory: the
 // result does not depend on timing.
@@ -2292,7 +2291,8 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(Masters m, const uint32_
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   __shared__ int s_r[4];
   __shared__ bool s_last;
-  __shared__ double s_w[kRedThreads / 32][4];
+  __shared__ double s_v[4][kRedThreads];
+  __shared__ double s_w[4];
   if (ninst == 1) {
     // one instance: its rows are all of [0, n_live) and [n_live, m_pending)
     if (threadIdx.x < 4) s_r[threadIdx.x] = threadIdx.x < 2 ? (threadIdx.x == 0 ? 0 : n1) : (threadIdx.x == 2 ? n1 : n2);
@@ -2325,24 +2325,25 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(Masters m, const uint32_
     for (int u = 0; u < U; ++u) {
       if (!live[u]) continue;
       acc[0] = sphk::dadd(acc[0], mu[u]);
-      for (int d = 0; d < dim; ++d) acc[1 + d] = sphk::dadd(acc[1 + d], sphk::dmul(mu[u], vu[u][d]));
+      for (int d = 0; d < dim; ++d) acc[1 + d] = __fma_rn(mu[u], vu[u][d], acc[1 + d]);
     }
   }
-  // the block's sum in a fixed order: a shuffle tree in each warp, then the
-  // warps' sums in warp order
+  // the block's sum in a fixed order, one warp per component (every FP64
+  // operation counts here): lane l sums threads l, l + 32, ..., l + 224 in
+  // turn, then a shuffle tree over the lanes
   auto block_sum = [&]() {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[c] = sphk::dadd(acc[c], __shfl_down_sync(0xffffffffu, acc[c], o));
-    if (lane == 0)
-      for (int c = 0; c < 4; ++c) s_w[wq][c] = acc[c];
+    for (int c = 0; c < 4; ++c) s_v[c][threadIdx.x] = acc[c];
     __syncthreads();
-    if (threadIdx.x < 4) {
-      double t = s_w[0][threadIdx.x];
-      for (int w = 1; w < kRedThreads / 32; ++w) t = sphk::dadd(t, s_w[w][threadIdx.x]);
-      acc[threadIdx.x] = t;
+    if (wq < 4) {
+      double x = s_v[wq][lane];
+#pragma unroll
+      for (int k = 1; k < kRedThreads / 32; ++k) x = sphk::dadd(x, s_v[wq][lane + 32 * k]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x = sphk::dadd(x, __shfl_down_sync(0xffffffffu, x, o));
+      if (lane == 0) s_w[wq] = x;
     }
+    __syncthreads();
+    if (threadIdx.x < 4) acc[threadIdx.x] = s_w[threadIdx.x];
   };
   block_sum();
   if (threadIdx.x < 4) partial[(size_t)blockIdx.x * 4 + threadIdx.x] = acc[threadIdx.x];
