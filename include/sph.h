@@ -428,12 +428,12 @@ int sph_reduce_mass_momentum(sph_ctx *ctx, double *mass, double *momentum);
 
 /* The same FP64 totals without waiting: the reduction is enqueued on the
    context's stream and its results land in out[4 * n_instances] (per
-   instance: mass, then momentum x, y, z).  out is host memory the caller
+   instance: mass, then momentum x, y, z).  out is memory the caller
    keeps, and leaves unread, until the stream has passed this point (an
-   event recorded on the stream after the call, or sph_get_stats).
-   Page-locked memory that the device can address is written by the
-   reduction itself; other host memory gets a copy enqueued after it
-   (pageable memory makes the call wait for that copy).  The first call
+   event recorded on the stream after the call, or sph_get_stats).  Device
+   memory and page-locked host memory that the device can address are
+   written by the reduction itself; other host memory gets a copy enqueued
+   after it (pageable memory makes the call wait for that copy).  The first call
    allocates the reduction buffers.  Errors: SPH_ERR_ARG, SPH_ERR_ALLOC,
    SPH_ERR_CUDA. */
 int sph_reduce_mass_momentum_async(sph_ctx *ctx, double *out);

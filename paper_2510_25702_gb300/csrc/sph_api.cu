@@ -2397,7 +2397,9 @@ extern "C" int sph_reduce_mass_momentum_async(sph_ctx *c, double *out) {
   // block writes the totals there; other memory takes a copy
   cudaPointerAttributes pa{};
   void *dev = nullptr;
-  if (cudaPointerGetAttributes(&pa, out) == cudaSuccess && pa.type == cudaMemoryTypeHost) dev = pa.devicePointer;
+  if (cudaPointerGetAttributes(&pa, out) == cudaSuccess &&
+      (pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged))
+    dev = pa.devicePointer;
   cudaGetLastError();
   double *res = nullptr;
   const int rc = enqueue_mass_momentum(c, (double *)dev, &res);

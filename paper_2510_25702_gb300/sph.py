@@ -331,12 +331,15 @@ class Simulation:
         return m, p
 
     def mass_momentum_async(self, out):
-        """Enqueue the FP64 totals into out (a page-locked float64 torch
-        tensor of 4 * n_instances elements: mass, momentum x y z per
-        instance) on the context's stream, without waiting; read out after
+        """Enqueue the FP64 totals into out (a float64 torch tensor of
+        4 * n_instances elements: mass, momentum x y z per instance; on the
+        device or in page-locked host memory the reduction writes it
+        directly) on the context's stream, without waiting; read out after
         the stream has passed this point (an event recorded after it)."""
-        if out.dtype.itemsize != 8 or out.numel() < 4 * len(self.cases) or out.is_cuda:
-            raise ValueError("out must be a host float64 tensor of 4 * n_instances elements")
+        import torch
+
+        if out.dtype != torch.float64 or out.numel() < 4 * len(self.cases) or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float64 tensor of 4 * n_instances elements")
         _check(lib().sph_reduce_mass_momentum_async(self.ctx, out.data_ptr()), "sph_reduce_mass_momentum_async")
 
     def step_rc(self, nsteps: int = 1) -> int:

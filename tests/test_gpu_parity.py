@@ -297,11 +297,14 @@ def test_mass_momentum_async_equals_the_waiting_call(sph):
     m, p = sim.mass_momentum()
     tot = out.numpy().reshape(len(batch), 4)
     assert np.array_equal(tot[:, 0], m) and np.array_equal(tot[:, 1:], p)
-    # pageable memory: the copy path, the same bits
+    # pageable memory: the copy path; device memory: written directly; the same bits
     out2 = torch.full((4 * len(batch),), float("nan"), dtype=torch.float64)
     sim.mass_momentum_async(out2)
+    out3 = torch.full((4 * len(batch),), float("nan"), dtype=torch.float64, device="cuda")
+    sim.mass_momentum_async(out3)
     torch.cuda.synchronize()
     assert np.array_equal(out2.numpy(), out.numpy())
+    assert np.array_equal(out3.cpu().numpy(), out.numpy())
     with pytest.raises(ValueError):
         sim.mass_momentum_async(torch.empty(3, dtype=torch.float64))
 
