@@ -2279,10 +2279,11 @@ __device__ int inst_lower_bound_warp(const uint16_t *inst, int lo, int hi, int q
 // [0, n_live) (the sorted particles) and one in [n_live, m_pending) (the
 // copies appended by the last buffer update); deleted rows carry the
 // sentinel key.  Each thread sums a fixed strided subset (momentum by
-// FMA), the block sums its threads in a fixed order (block_sum).  The last block to finish then sums each instance's slices in a
-// fixed order (thread t takes slices t, t + 256, ... in turn, then the same
-// block sum) into out[ninst][4], which may be page-locked host memory: the
-// result does not depend on timing.
+// FMA), the block sums its threads in a fixed order (block_sum).  The last
+// of an instance's blocks to finish then sums its slices in a fixed order
+// (thread t takes slices t, t + 256, ... in turn, then the same block sum)
+// into out[q][4] (instances in parallel; out may be page-locked host
+// memory): the result does not depend on timing.
 __global__ void __launch_bounds__(kRedThreads) k_reduce(Masters m, const uint32_t *keys, uint32_t sentinel,
                                                         const Counters *cnt, int dim, int slices, int ninst,
                                                         double *partial, uint32_t *done, double *out) {
@@ -2346,23 +2347,21 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(Masters m, const uint32_
     if (threadIdx.x < 4) acc[threadIdx.x] = s_w[threadIdx.x];
   };
   block_sum();
-  if (threadIdx.x < 4) partial[(size_t)blockIdx.x * 4 + threadIdx.x] = acc[threadIdx.x];
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+  if (threadIdx.x < 4) {
+    partial[(size_t)blockIdx.x * 4 + threadIdx.x] = acc[threadIdx.x];
+    __threadfence();  // the partial is visible before the block counts itself done
   }
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&done[q], 1u) == (unsigned)slices - 1u;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  for (int qq = 0; qq < ninst; ++qq) {
-    for (int c = 0; c < 4; ++c) acc[c] = 0.0;
-    for (int t = threadIdx.x; t < slices; t += kRedThreads)
-      for (int c = 0; c < 4; ++c) acc[c] = sphk::dadd(acc[c], __ldcg(&partial[((size_t)qq * slices + t) * 4 + c]));
-    block_sum();
-    if (threadIdx.x < 4) out[(size_t)qq * 4 + threadIdx.x] = acc[threadIdx.x];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *done = 0u;
+  for (int c = 0; c < 4; ++c) acc[c] = 0.0;
+  for (int t = threadIdx.x; t < slices; t += kRedThreads)
+    for (int c = 0; c < 4; ++c) acc[c] = sphk::dadd(acc[c], __ldcg(&partial[((size_t)q * slices + t) * 4 + c]));
+  block_sum();
+  if (threadIdx.x < 4) out[(size_t)q * 4 + threadIdx.x] = acc[threadIdx.x];
+  if (threadIdx.x == 0) done[q] = 0u;
 }
 }  // namespace
 
@@ -2374,12 +2373,13 @@ static int enqueue_mass_momentum(sph_ctx *c, double *out, double **res) {
   if (!c->red) c->red_slices = red_slices(c->ninst);
   const int slices = c->red_slices;
   if (!c->red) {
-    // partial sums [ninst * slices][4], results [ninst][4] and the blocks'
-    // completion counter, owned by the context from the first call on
-    c->red = (double *)c->dalloc(sizeof(double) * (4 * ((size_t)c->ninst * slices + c->ninst) + 1));
+    // partial sums [ninst * slices][4], results [ninst][4] and the
+    // instances' block completion counters, owned by the context from the
+    // first call on
+    const size_t words = 4 * ((size_t)c->ninst * slices + c->ninst) + ((size_t)c->ninst + 1) / 2;
+    c->red = (double *)c->dalloc(sizeof(double) * words);
     if (!c->red) return fail(SPH_ERR_ALLOC, "reduction buffers");
-    CUDA_TRY(cudaMemsetAsync(c->red, 0, sizeof(double) * (4 * ((size_t)c->ninst * slices + c->ninst) + 1),
-                             c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->red, 0, sizeof(double) * words, c->stream));
   }
   double *partial = c->red;
   double *dres = c->red + 4 * (size_t)c->ninst * slices;
