@@ -1075,10 +1075,16 @@ static int upload_buffers(sph_ctx *c) {
   return 0;
 }
 
+}  // extern "C"
+
+namespace {
 // n 8-byte words from src to dst (one block)
 __global__ void k_copy_words(unsigned long long *__restrict__ dst, const unsigned long long *__restrict__ src, int n) {
   for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
 }
+}  // namespace
+
+extern "C" {
 
 int sph_set_profile(sph_ctx *c, int32_t instance, int32_t buffer_id, const double *theta, int32_t n_theta) {
   if (!c || !theta) return fail(SPH_ERR_ARG, "NULL argument");
