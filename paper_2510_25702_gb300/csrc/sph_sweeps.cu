@@ -805,11 +805,12 @@ constexpr int kSubMinBlocks = sizeof(R) == 4 ? (D == 2 ? 5 : 4) : 1;
 // the FP32 list builder at 48 registers as well (few spills)
 template <typename R, int D>
 constexpr int kListMinBlocks = sizeof(R) == 4 ? 5 : 0;
-// the FP32 advection sweep at 85 registers in 3D instead of 97 (5 resident
-// 128-thread blocks instead of 4: 1.79 against 2.27 ms on the 3D mixer) and
-// at 64 in 2D instead of 76 (87.4 against 90.7 us on the 2D channel)
+// the FP32 advection sweep at 64 registers, 8 resident 128-thread blocks:
+// in 2D instead of 76 (87.4 against 90.7 us on the 2D channel), in 3D
+// instead of 80 (1.71 against 1.77 ms on the 3D mixer, some spills
+// included; 97 registers took 2.27 ms)
 template <typename R, int D>
-constexpr int kAdvMinBlocks = sizeof(R) == 4 ? (D == 3 ? 3 : 4) : 0;
+constexpr int kAdvMinBlocks = sizeof(R) == 4 ? 4 : 0;
 
 template <typename R, int D, bool PER>
 __global__ void __launch_bounds__(kMaxBlock, kListMinBlocks<R, D>) k_list(SweepArgs a, Packs<R> pk) {
@@ -857,7 +858,7 @@ __global__ void __launch_bounds__(kMaxBlock, kMomMinBlocks<R, D>) k_mom(SweepArg
 }
 
 template <typename R, int D, bool PER>
-__global__ void __launch_bounds__(kMaxBlock, kContMinBlocks<R, D>) k_cont(SweepArgs a, Packs<R> pk) {
+__device__ __forceinline__ void cont_sweep(const SweepArgs &a, const Packs<R> &pk) {
   if (a.sub >= a.cnt->n_ac_all || a.cnt->status) return;
   const int n = a.cnt->n_live;
   const int step = gridDim.x * blockDim.x;
@@ -866,6 +867,19 @@ __global__ void __launch_bounds__(kMaxBlock, kContMinBlocks<R, D>) k_cont(SweepA
     if ((threadIdx.x & 31) == 0 && i + step < n) prefetch_list_tile(a.nl, i + step);
     cont_one<R, D, PER>(a, pk, i);
   }
+}
+
+template <typename R, int D, bool PER>
+__global__ void __launch_bounds__(kMaxBlock, kContMinBlocks<R, D>) k_cont(SweepArgs a, Packs<R> pk) {
+  cont_sweep<R, D, PER>(a, pk);
+}
+
+// the 3D FP32 continuity sweep at 56 registers: no spills (at 48 it spilled)
+// and 9 resident 128-thread blocks; 1.08 -> 0.96 ms per sweep on the 3D
+// mixer, whose five sub-steps take one each
+template <bool PER>
+__global__ void __maxnreg__(56) k_cont3f(SweepArgs a, Packs<float> pk) {
+  cont_sweep<float, 3, PER>(a, pk);
 }
 
 // Sub-steps 1 .. n_ac_all - 1 in one cooperative launch (2D; 3D contexts
@@ -1042,8 +1056,13 @@ static void launch_sweeps_impl(int which, const SweepArgs &a, Packs<R> &pk, int 
     auto k = k_mom<R, D, PER>;
     k<<<resident_grid(k, b, max_n), b, 0, st>>>(a, pk);
   } else {
-    auto k = k_cont<R, D, PER>;
-    k<<<resident_grid(k, b, max_n), b, 0, st>>>(a, pk);
+    if constexpr (sizeof(R) == 4 && D == 3) {
+      auto k = k_cont3f<PER>;
+      k<<<resident_grid(k, b, max_n), b, 0, st>>>(a, pk);
+    } else {
+      auto k = k_cont<R, D, PER>;
+      k<<<resident_grid(k, b, max_n), b, 0, st>>>(a, pk);
+    }
   }
 }
 
