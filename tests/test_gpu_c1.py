@@ -1,0 +1,50 @@
+"""The plain-method channel at the pressures it is stated with: 2.0 x 1.0,
+dp 0.05, pressure buffers at both ends with p_in 0.1 and p_out 0, nu 0.02,
+FP64 (the laminar channel of Sec. 4.1 driven by two pressure buffers).
+
+Over its first 200 steps -- inside the window before the flow near the
+inlet runs away, which it does on the oracle and on the GPU alike between
+steps 250 and 600 -- the GPU follows the oracle particle by particle:
+the same particles (uid), labels and injected / deleted counts, and the
+fields at 1e-9 relative L2.
+"""
+import numpy as np
+import pytest
+
+from paper_2510_25702_gb300 import cases
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    den = np.linalg.norm(b)
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / (den if den > 0 else 1.0))
+
+
+@pytest.fixture(scope="module")
+def sph():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2510_25702_gb300 import build
+    from paper_2510_25702_gb300 import sph as S
+
+    build.build()
+    return S
+
+
+def test_c1_as_stated_200_steps_fp64(sph, orc):
+    case = cases.poiseuille_channel(length=2.0, height=1.0, dp=0.05, p_in=0.1, p_out=0.0, nu=0.02)
+    sim = sph.Simulation(case, precision="fp64")
+    o = orc.OracleSim(case)
+    sim.step(200)
+    o.step(200)
+    g = sim.read(["uid", "label", "pos", "vel", "rho", "p"])
+    f = o.fields()
+    st = sim.stats()
+    assert o.stats["n_spawned"] > 0 and o.stats["n_deleted"] > 0
+    assert st["spawned"] == o.stats["n_spawned"] and st["deleted"] == o.stats["n_deleted"]
+    assert np.array_equal(g["uid"], f["uid"]) and np.array_equal(g["label"], f["label"])
+    errs = {k: rel_l2(g[k], f[k]) for k in ("pos", "vel", "rho", "p")}
+    print("C1 as stated, 200 steps", {k: f"{v:.2e}" for k, v in errs.items()})
+    assert all(e < 1e-9 for e in errs.values()), errs
