@@ -1,4 +1,6 @@
-"""The plain-method channel at the pressures it is stated with: 2.0 x 1.0,
+"""Longer FP64 trajectories against the oracle.
+
+The plain-method channel at the pressures it is stated with: 2.0 x 1.0,
 dp 0.05, pressure buffers at both ends with p_in 0.1 and p_out 0, nu 0.02,
 FP64 (the laminar channel of Sec. 4.1 driven by two pressure buffers).
 
@@ -48,3 +50,27 @@ def test_c1_as_stated_200_steps_fp64(sph, orc):
     errs = {k: rel_l2(g[k], f[k]) for k in ("pos", "vel", "rho", "p")}
     print("C1 as stated, 200 steps", {k: f"{v:.2e}" for k, v in errs.items()})
     assert all(e < 1e-9 for e in errs.values()), errs
+
+
+def test_batch_instances_follow_the_oracle_300_steps_fp64(sph, orc):
+    """Three instances of the batched workload (a straight channel and
+    U-channels, pressure buffers at every end, different viscosities) in
+    one FP64 context replayed as CUDA graphs, 300 steps (injection and
+    deletion at every instance): each instance, with its own time step and
+    sub-step count, equals the oracle run on that instance alone (same
+    particles and labels, fields at 1e-9)."""
+    batch = cases.batched_channels(n_instances=3, dps=(0.05,), seed=11)
+    sim = sph.Simulation(batch, precision="fp64")
+    sim.set_graph(True)
+    sim.step(300)
+    g = sim.read(["inst", "uid", "label", "pos", "vel", "rho"])
+    for q, c in enumerate(batch):
+        o = orc.OracleSim(c)
+        o.step(300)
+        assert o.stats["n_spawned"] > 0 and o.stats["n_deleted"] > 0, q
+        f = o.fields()
+        gq = {k: v[g["inst"] == q] for k, v in g.items()}
+        assert np.array_equal(gq["uid"], f["uid"]) and np.array_equal(gq["label"], f["label"]), q
+        errs = {k: rel_l2(gq[k], f[k]) for k in ("pos", "vel", "rho")}
+        print("instance", q, c.name, {k: f"{v:.2e}" for k, v in errs.items()})
+        assert all(e < 1e-9 for e in errs.values()), (q, errs)
