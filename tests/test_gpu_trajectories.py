@@ -1,4 +1,4 @@
-"""Longer FP64 trajectories against the oracle.
+"""Longer FP64 trajectories against the oracle (C1 as stated, C3 instances, C5).
 
 The plain-method channel at the pressures it is stated with: 2.0 x 1.0,
 dp 0.05, pressure buffers at both ends with p_in 0.1 and p_out 0, nu 0.02,
@@ -74,3 +74,24 @@ def test_batch_instances_follow_the_oracle_300_steps_fp64(sph, orc):
         errs = {k: rel_l2(gq[k], f[k]) for k in ("pos", "vel", "rho")}
         print("instance", q, c.name, {k: f"{v:.2e}" for k, v in errs.items()})
         assert all(e < 1e-9 for e in errs.values()), (q, errs)
+
+
+def test_mixer_3d_50_steps_fp64(sph, orc):
+    """The 3D mixer (rotating wall, two velocity inlets, a pressure outlet;
+    dp 0.05, 27k particles) in FP64 over 50 steps, with about 250 copies
+    injected and 100 particles deleted: the same particles and labels as
+    the oracle, fields at 1e-9."""
+    case = cases.mixer_3d(dp=0.05)
+    sim = sph.Simulation(case, precision="fp64")
+    o = orc.OracleSim(case)
+    sim.step(50)
+    o.step(50)
+    g = sim.read(["uid", "label", "pos", "vel", "rho"])
+    f = o.fields()
+    st = sim.stats()
+    assert o.stats["n_spawned"] > 100 and o.stats["n_deleted"] > 50
+    assert st["spawned"] == o.stats["n_spawned"] and st["deleted"] == o.stats["n_deleted"]
+    assert np.array_equal(g["uid"], f["uid"]) and np.array_equal(g["label"], f["label"])
+    errs = {k: rel_l2(g[k], f[k]) for k in ("pos", "vel", "rho")}
+    print("mixer 3D, 50 steps", {k: f"{v:.2e}" for k, v in errs.items()})
+    assert all(e < 1e-9 for e in errs.values()), errs
