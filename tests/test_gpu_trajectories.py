@@ -1,4 +1,5 @@
-"""Longer FP64 trajectories against the oracle (C1 as stated, C3 instances, C5).
+"""Longer FP64 trajectories against the oracle (C1 as stated, C3 instances, a
+section of C2, C5).
 
 The plain-method channel at the pressures it is stated with: 2.0 x 1.0,
 dp 0.05, pressure buffers at both ends with p_in 0.1 and p_out 0, nu 0.02,
@@ -95,3 +96,24 @@ def test_mixer_3d_50_steps_fp64(sph, orc):
     errs = {k: rel_l2(g[k], f[k]) for k in ("pos", "vel", "rho")}
     print("mixer 3D, 50 steps", {k: f"{v:.2e}" for k, v in errs.items()})
     assert all(e < 1e-9 for e in errs.values()), errs
+
+
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-9)])
+def test_turbulent_channel_100_steps(sph, orc, precision, bound):
+    """A section of the turbulent channel (0.3 x 0.1, dp 0.005, k-epsilon,
+    velocity inlet with its seeded fluctuation, pressure outlet) over 100
+    steps with about 350 particles injected and as many deleted: the same
+    particles and labels as the oracle; positions, velocities, density and
+    k, epsilon, nu_t at 1e-9."""
+    case = cases.turbulent_channel(length=0.3, height=0.1, dp=0.005, jitter_frac=0.05)
+    sim = sph.Simulation(case, precision=precision)
+    o = orc.OracleSim(case)
+    sim.step(100)
+    o.step(100)
+    g = sim.read(["uid", "label", "pos", "vel", "rho", "k", "eps", "nut"])
+    f = o.fields()
+    assert o.stats["n_spawned"] > 200 and o.stats["n_deleted"] > 200
+    assert np.array_equal(g["uid"], f["uid"]) and np.array_equal(g["label"], f["label"])
+    errs = {k: rel_l2(g[k], f[k]) for k in ("pos", "vel", "rho", "k", "eps", "nut")}
+    print("turbulent channel, 100 steps", precision, {k: f"{v:.2e}" for k, v in errs.items()})
+    assert all(e < bound for e in errs.values()), errs
