@@ -85,6 +85,7 @@ NCU_TRAFFIC = {
     ("advection_sweep", "turbulent_channel", "d7457316e402e35f"): 117.5e6,
     ("advection_sweep", "turbulent_channel", "a395c5c7af995f9d"): 117.3e6,
     ("advection_sweep", "turbulent_channel", "ad3089c508c5cf82"): 117.1e6,
+    ("advection_sweep", "turbulent_channel", "664e195af6d3036d"): 117.2e6,
 }
 
 

@@ -791,13 +791,12 @@ __device__ __forceinline__ void cont_one(const SweepArgs &a, const Packs<R> &pk,
 // ------------------------------------------------------------------------
 // kernels: grid-stride over the live particles
 // ------------------------------------------------------------------------
-// resident 256-thread blocks per SM asked of the FP32 sweeps (registers =
-// 65536 / (256 x blocks)): more warps for their latency-bound gathers where
-// that costs few spills (measured): momentum 2D and continuity at 48, the
-// fused later sub-steps of 2D at 48 (3D takes them as separate launches);
-// the FP64 forms and the 3D momentum sweep keep the compiler's count
-template <typename R, int D>
-constexpr int kMomMinBlocks = (sizeof(R) == 4 && D == 2) ? 5 : 1;
+// resident 256-thread blocks per SM asked of the sweeps (registers =
+// 65536 / (256 x blocks)) where that buys warps for their latency-bound
+// gathers at few spills (measured): the fused later sub-steps of 2D at 48
+// (3D takes them as separate launches).  The FP32 momentum and continuity
+// sweeps take register counts of their own (__maxnreg__, below); the FP64
+// forms keep the compiler's count.
 template <typename R, int D>
 constexpr int kContMinBlocks = sizeof(R) == 4 ? 5 : 1;
 template <typename R, int D>
@@ -846,7 +845,9 @@ __global__ void __launch_bounds__(kMaxBlock, kAdvMinBlocks<R, D>) k_adv(SweepArg
 }
 
 template <typename R, int D, bool PER>
-__global__ void __launch_bounds__(kMaxBlock, kMomMinBlocks<R, D>) k_mom(SweepArgs a, Packs<R> pk) {
+// (the 2D FP32 momentum sweep at 56 registers: 48.7 -> 47.1 us on the 2D
+// channel against 48; the other forms keep the compiler's count)
+__global__ void __maxnreg__((sizeof(R) == 4 && D == 2) ? 56 : 255) k_mom(SweepArgs a, Packs<R> pk) {
   if (a.sub >= a.cnt->n_ac_all || a.cnt->status) return;  // no instance takes this sub-step
   const int n = a.cnt->n_live;
   const int step = gridDim.x * blockDim.x;
@@ -880,6 +881,12 @@ __global__ void __launch_bounds__(kMaxBlock, kContMinBlocks<R, D>) k_cont(SweepA
 template <bool PER>
 __global__ void __maxnreg__(56) k_cont3f(SweepArgs a, Packs<float> pk) {
   cont_sweep<float, 3, PER>(a, pk);
+}
+// and the 2D FP32 continuity sweep likewise (no spills; 38.9 -> 37.7 us on
+// the 2D channel against 48 registers)
+template <bool PER>
+__global__ void __maxnreg__(56) k_cont2f(SweepArgs a, Packs<float> pk) {
+  cont_sweep<float, 2, PER>(a, pk);
 }
 
 // Sub-steps 1 .. n_ac_all - 1 in one cooperative launch (2D; 3D contexts
@@ -1056,7 +1063,10 @@ static void launch_sweeps_impl(int which, const SweepArgs &a, Packs<R> &pk, int 
     auto k = k_mom<R, D, PER>;
     k<<<resident_grid(k, b, max_n), b, 0, st>>>(a, pk);
   } else {
-    if constexpr (sizeof(R) == 4 && D == 3) {
+    if constexpr (sizeof(R) == 4 && D == 2) {
+      auto k = k_cont2f<PER>;
+      k<<<resident_grid(k, b, max_n), b, 0, st>>>(a, pk);
+    } else if constexpr (sizeof(R) == 4 && D == 3) {
       auto k = k_cont3f<PER>;
       k<<<resident_grid(k, b, max_n), b, 0, st>>>(a, pk);
     } else {
