@@ -635,7 +635,7 @@ def main():
             raise RuntimeError("non-finite totals in the end-to-end loop")
         return float((tot[:, 0] / m_part).sum())
 
-    torch.cuda.synchronize()
+    barrier()
     t0 = time.perf_counter()
     ps = 0.0
     for s in range(e2e_steps):
@@ -652,7 +652,9 @@ def main():
     st = sim.stats()
     if st["status"] != 0:
         raise RuntimeError(f"device status {st['status']} in the end-to-end loop")
-    e2e = {"value": ps / (t1 - t0) * (world if dist is not None else 1), "unit": UNIT,
+    # whole job: the slowest rank's wall time, the particle-steps of all ranks
+    e2e_ms, ps = combine_timing(1e3 * (t1 - t0), ps, dist)
+    e2e = {"value": ps / (e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": 8 + 8 * theta.size, "d2h_bytes_per_step": 32 * ninst, "steps": e2e_steps,
            "per_step": "sph_set_profile (n_theta and theta moved from page-locked staging by a one-block "
                        "kernel), sph_step_async, sph_reduce_mass_momentum_async (FP64 totals written by the "
