@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define SPH_ABI_VERSION 2
+#define SPH_ABI_VERSION 3
 
 /* return codes */
 #define SPH_OK 0
@@ -102,18 +102,26 @@ typedef struct sph_config {
   double tvf_alpha;   /* transport-velocity correction (below); 0 = off */
   int32_t wall_function; /* 1: step-wise wall function at the walls (RANS
                             instances; below) */
-  int32_t reserved;
+  int32_t tvf_pbuf;   /* 1: the transport-velocity correction also moves the
+                         particles of pressure buffers, across the buffer
+                         axis only (below); 0 = fluid particles only */
 } sph_config;
 
 /* The two stages of the advection step that Sec. 2.3 names through the
    schemes it cites (without formulas), both switched per instance and both
    taken over the frozen configuration of the step, for fluid particles
-   (label 0) only, after the correction matrix, viscous and k-epsilon terms
+   (label 0; the first with tvf_pbuf also for pressure-buffer particles),
+   after the correction matrix, viscous and k-epsilon terms
    (which use the volumes m / rho from before them):
    - transport-velocity correction: x_i += -2 tvf_alpha h^2 sum_j V_j grad_i W_ij
      over real and wall neighbours (the background-pressure term of the
      transport-velocity formulation, with the background pressure tied to
-     the step so that the shift is a fixed fraction of h^2);
+     the step so that the shift is a fixed fraction of h^2); with tvf_pbuf
+     also for particles labelled in a pressure buffer, whose motion no
+     boundary value prescribes, minus its component along the buffer axis
+     n_b (their support is cut at the open face, so the sum points into the
+     fluid): the shift then only spreads them across the buffer, and the
+     flux through the face stays the momentum equation's;
    - density reinitialisation: rho_i = rho0 sigma_i / sigma_0 with
      sigma_i = W(0) + sum_j W_ij over real and wall neighbours and sigma_0
      the same sum on the perfect lattice of spacing dp.
@@ -501,6 +509,8 @@ void sph_destroy(sph_ctx *ctx);
 const char *sph_error_string(int code);
 /* Message of the last SPH_ERR_ARG / SPH_ERR_CUDA on this thread. */
 const char *sph_last_error(void);
+/* SPH_ABI_VERSION (3: sph_config carries tvf_pbuf in the slot that was
+   reserved, so a zeroed version-2 config keeps its meaning). */
 int sph_abi_version(void);
 
 #ifdef __cplusplus

@@ -51,7 +51,7 @@ class OrcConfig(C.Structure):
         ("gen_offset", C.c_double), ("id_check", C.c_int), ("contain_check", C.c_int),
         ("mirror_B", C.c_int), ("compensation", C.c_int), ("neighbor_mode", C.c_int),
         ("rkgc", C.c_int), ("freeze_turb", C.c_int), ("comp_B", C.c_int), ("bhat_buffer", C.c_int),
-        ("density_sum", C.c_int), ("wall_fn", C.c_int), ("pad_wf", C.c_int), ("tvf_alpha", C.c_double),
+        ("density_sum", C.c_int), ("wall_fn", C.c_int), ("tvf_pbuf", C.c_int), ("tvf_alpha", C.c_double),
     ]
 
 
@@ -206,6 +206,7 @@ class OracleSim:
         c.freeze_turb = freeze_turb
         c.comp_B, c.bhat_buffer = comp_B, bhat_buffer
         c.tvf_alpha = float(getattr(case, "tvf", 0.0))
+        c.tvf_pbuf = int(bool(getattr(case, "tvf_pbuf", False)))
         c.density_sum = int(bool(getattr(case, "density_sum", False)))
         c.wall_fn = int(bool(getattr(case, "wall_function", False)))
         # the open-boundary treatment of the case (Table of Sec. 4.1) sets

@@ -955,11 +955,18 @@ int orc_viscous(const orc_config *c, orc_state *s) {
 /*   dr_i = -2 alpha h^2 sum_j V_j grad_i W_ij                          */
 /* over all real and wall neighbours of the frozen configuration, taken  */
 /* once per advection step (before the sub-steps), for fluid particles   */
-/* (label 0) only: buffer particles keep the motion their boundary       */
-/* condition gives them.  grad_i W points from i towards j, so a         */
-/* particle is moved away from where its neighbours crowd.  The pair     */
-/* geometry of the step stays that of the frozen configuration; the      */
-/* shift takes effect at the next rebuild and in the buffer update.      */
+/* (label 0), and with tvf_pbuf for particles labelled in a pressure     */
+/* buffer too.  A pressure buffer fixes the pressure, not the motion:    */
+/* its particles move under the momentum equation like fluid particles   */
+/* and can crowd like them, but their support is cut at the open face,   */
+/* so the sum points into the fluid; only its part across the buffer     */
+/* axis n_b is taken (dr - (dr . n_b) n_b), which leaves the flux        */
+/* through the face to the momentum equation.  Velocity-buffer particles */
+/* keep the motion their prescribed velocity gives them.  grad_i W       */
+/* points from i towards j, so a particle is moved away from where its   */
+/* neighbours crowd.  The pair geometry of the step stays that of the    */
+/* frozen configuration; the shift takes effect at the next rebuild and  */
+/* in the buffer update.                                                 */
 /* ------------------------------------------------------------------ */
 static int orc_transport_impl(const orc_config *c, orc_state *s, const nblist *Lp) {
   const nblist L = *Lp;
@@ -968,7 +975,8 @@ static int orc_transport_impl(const orc_config *c, orc_state *s, const nblist *L
   double f = -2.0 * c->tvf_alpha * c->h * c->h;
   #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < s->n; ++i) {
-    if (s->dead[i] || s->label[i] != 0) continue;
+    int pb = c->tvf_pbuf && is_pressure_buffer(s, s->label[i]);
+    if (s->dead[i] || (s->label[i] != 0 && !pb)) continue;
     double S[3] = {0, 0, 0};
     for (int64_t t = L.start[i]; t < L.start[i + 1]; ++t) {
       int64_t j = L.nb[t].j;
@@ -977,6 +985,11 @@ static int orc_transport_impl(const orc_config *c, orc_state *s, const nblist *L
       pair_geom(c, &s->pos0[3 * i], xj_of(s, j, wall), &G);
       double V = wall ? Vw : vol_of(s, j);
       for (int a = 0; a < 3; ++a) S[a] += V * G.gw[a];
+    }
+    if (pb) {
+      const double *nb = s->buf[s->label[i] - 1].frame;
+      double sn = dotd(c->dim, S, nb);
+      for (int a = 0; a < c->dim; ++a) S[a] -= sn * nb[a];
     }
     for (int a = 0; a < c->dim; ++a) s->pos[3 * i + a] += f * S[a];
   }

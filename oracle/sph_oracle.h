@@ -76,7 +76,8 @@ typedef struct orc_config {
   int density_sum;   /* 1: fluid density reinitialised by kernel summation   */
                      /* once per advection step (dual-criteria scheme, Sec. 2.3) */
   int wall_fn;       /* 1: step-wise wall function at the walls (RANS, Sec. 2.3) */
-  int pad_wf;
+  int tvf_pbuf;      /* 1: the transport-velocity shift also moves pressure-buffer
+                        particles, across the buffer axis only */
   double tvf_alpha;  /* transport-velocity correction (Sec. 2.3): fluid       */
                      /* particles move by -2 alpha h^2 sum_j V_j grad_i W_ij    */
                      /* once per advection step; 0 = off                       */

@@ -83,6 +83,7 @@ class Case:
     # (3), or "minimal_mirror" (case 4 with B_i from the truncated support)
     obc: str = "improved"
     tvf: float = 0.0  # transport-velocity shift coefficient alpha (0 = off)
+    tvf_pbuf: bool = False  # the shift also moves pressure-buffer particles (across the axis)
     density_sum: bool = False  # density reinitialised by summation every advection step
     wall_function: bool = False  # step-wise wall function at the walls (RANS)
 
@@ -174,7 +175,7 @@ def inlet_turbulence(U: float, height: float, intensity: float = 0.05, mix_frac:
 # --------------------------------------------------------------------------
 def poiseuille_channel(length=2.0, height=1.0, dp=0.05, p_in=0.2, p_out=0.1, nu=0.02,
                        rho0=1.0, jitter_frac=0.01, seed=1, buffer_cells=4,
-                       capacity_factor=1.5) -> Case:
+                       capacity_factor=1.5, tvf=0.0, tvf_pbuf=False, density_sum=False) -> Case:
     """Laminar pressure-driven channel (Sec. 4.1 shape): pressure buffers at both
     ends, 4 wall layers top and bottom extending 4 dp beyond both open faces.
 
@@ -183,6 +184,9 @@ def poiseuille_channel(length=2.0, height=1.0, dp=0.05, p_in=0.2, p_out=0.1, nu=
     the pressures of the paper's laminar channel): without the transport-
     velocity correction a zero-pressure outlet is tensile-unstable.  The
     initial state is at rest with the density of the mean pressure.
+    tvf, tvf_pbuf, density_sum: the transport-velocity shift (also of the
+    pressure-buffer particles) and the density reinitialisation of Sec. 2.3,
+    off by default (pressure_driven_channel turns them on).
     """
     nx, ny = int(round(length / dp)), int(round(height / dp))
     pos = jitter(lattice((nx, ny), dp), 2, jitter_frac * dp, seed)
@@ -205,7 +209,22 @@ def poiseuille_channel(length=2.0, height=1.0, dp=0.05, p_in=0.2, p_out=0.1, nu=
                 rans=False, U_ref=umax,
                 lo=np.array([-margin, -margin, 0.0]), hi=np.array([length + margin, height + margin, 0.0]),
                 periodic=(0, 0, 0), wpos=wpos, wvel=np.zeros_like(wpos), buffers=bufs,
-                seed=seed, capacity=int(capacity_factor * pos.shape[0]) + 64, **arr)
+                seed=seed, capacity=int(capacity_factor * pos.shape[0]) + 64, tvf=tvf, tvf_pbuf=tvf_pbuf,
+                density_sum=density_sum, **arr)
+
+
+def pressure_driven_channel(length=2.0, height=1.0, dp=0.05, p_in=0.1, p_out=0.0, nu=0.02, seed=1,
+                            tvf=0.05, **kw) -> Case:
+    """The laminar channel driven by pressure buffers at both ends with a
+    zero-pressure outlet: 2.0 x 1.0, dp 0.05, inlet 0.1, outlet 0, nu 0.02,
+    from rest (c0 = 10 U_max = 3.125).  With two pressure buffers nothing
+    prescribes the motion of the buffer particles, so they crowd like fluid
+    particles: the transport-velocity shift (alpha 0.05) acts on them too,
+    across the buffer axis only, and the density is re-evaluated from the
+    configuration every advection step (Sec. 2.3).  Without these the flow
+    near the inlet runs away within a few hundred steps."""
+    return poiseuille_channel(length=length, height=height, dp=dp, p_in=p_in, p_out=p_out, nu=nu, seed=seed,
+                              tvf=tvf, tvf_pbuf=True, density_sum=True, **kw)
 
 
 def laminar_channel(length=2.0, height=1.0, dp=0.05, U_max=0.3125, nu=0.02, p_out=0.1, rho0=1.0,

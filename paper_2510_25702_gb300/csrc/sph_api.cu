@@ -351,6 +351,7 @@ static int build_inst(const sph_config &c, InstDev &I, std::string &why) {
   if (c.density_sum != 0 && c.density_sum != 1) return why = "density_sum must be 0 or 1", -1;
   if (!(c.tvf_alpha >= 0.0 && c.tvf_alpha < 1.0)) return why = "tvf_alpha must be in [0, 1)", -1;
   if (c.wall_function != 0 && c.wall_function != 1) return why = "wall_function must be 0 or 1", -1;
+  if (c.tvf_pbuf != 0 && c.tvf_pbuf != 1) return why = "tvf_pbuf must be 0 or 1", -1;
   I.dim = c.dim;
   I.rans = c.rans ? 1 : 0;
   I.dt_mode = c.dt_mode;
@@ -360,6 +361,7 @@ static int build_inst(const sph_config &c, InstDev &I, std::string &why) {
   I.density_sum = c.density_sum;
   I.tvf = c.tvf_alpha > 0.0 ? 1 : 0;
   I.tvf_k = -2.0 * c.tvf_alpha * c.h * c.h;
+  I.tvf_pbuf = c.tvf_pbuf;
   I.wall_fn = c.wall_function ? 1 : 0;
   I.wf_cmu34 = std::pow(kCmu, 0.75);
   I.seed = c.seed;

@@ -51,7 +51,7 @@ struct InstDev {
   int32_t density_sum;  // density reinitialised by kernel summation each advection step
   int32_t tvf;          // transport-velocity shift on
   int32_t wall_fn;      // step-wise wall function at the walls (RANS)
-  int32_t pad_wf;
+  int32_t tvf_pbuf;     // the shift also moves pressure-buffer particles (across n_b)
   double wf_cmu34;      // C_mu^(3/4) of the wall value of eps
   double tvf_k;         // -2 alpha h^2: shift = tvf_k sum_j V_j grad_i W_ij
   double dsum_k;        // rho0 alpha_d / sigma_0: rho = dsum_k (1 + sum_j w^4 (5 - 4 w))

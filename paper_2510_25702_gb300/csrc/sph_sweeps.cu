@@ -199,9 +199,12 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   R sv[3] = {0, 0, 0};
   R G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   R dk = 0, de = 0;
-  // transport-velocity shift: sum_j V_j grad_i W_ij; density reinitialisation:
-  // sum_j W_ij / alpha_d = sum_j w^4 (5 - 4 w), w = 1 - q/2 (fluid particles)
-  const bool tvf = X && I.tvf && lab == 0, dsum = X && I.density_sum && lab == 0;
+  // transport-velocity shift: sum_j V_j grad_i W_ij (fluid particles, and
+  // pressure-buffer particles when the instance asks for it); density
+  // reinitialisation: sum_j W_ij / alpha_d = sum_j w^4 (5 - 4 w), w = 1 - q/2
+  // (fluid particles)
+  const bool tvf_b = X && I.tvf && I.tvf_pbuf && pbuf;
+  const bool tvf = (X && I.tvf && lab == 0) || tvf_b, dsum = X && I.density_sum && lab == 0;
   R gsum[3] = {0, 0, 0};
   R sig = 0;
 
@@ -510,10 +513,24 @@ __device__ __forceinline__ void adv_one(const SweepArgs &a, const Packs<R> &pk, 
   const R p = to_R<R>(rho - I.rho0) * sweep_const<R>(I).c0sq;
   m.rho[i] = rho;
   if (I.n_ac == 1) m.p[i] = from_R<R>(p);
+  // a pressure-buffer particle takes the shift across its buffer axis only:
+  // its support is cut at the open face, so the sum points into the fluid
+  double sh[3] = {0.0, 0.0, 0.0};
+  if (tvf) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) sh[c] = from_R<R>(gsum[c]);
+    if (tvf_b) {
+      double sn = 0.0;
+#pragma unroll
+      for (int c = 0; c < D; ++c) sn += sh[c] * mb->frame[c];
+#pragma unroll
+      for (int c = 0; c < D; ++c) sh[c] -= sn * mb->frame[c];
+    }
+  }
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     double xc = m.x[c][i];
-    if (tvf) xc = xc + I.tvf_k * from_R<R>(gsum[c]);
+    if (tvf) xc = xc + I.tvf_k * sh[c];
     m.x[c][i] = xc + hdt * m.v[c][i];
   }
   // momentum record; pressure-buffer particles are marked so that their

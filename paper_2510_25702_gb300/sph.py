@@ -51,7 +51,7 @@ class Config(C.Structure):
         ("c0", C.c_double), ("nu_l", C.c_double), ("eta", C.c_double), ("U_ref", C.c_double),
         ("dt_ad_fixed", C.c_double), ("gravity", C.c_double * 3), ("domain_lo", C.c_double * 3),
         ("domain_hi", C.c_double * 3), ("obc", C.c_int32), ("density_sum", C.c_int32),
-        ("tvf_alpha", C.c_double), ("wall_function", C.c_int32), ("reserved", C.c_int32),
+        ("tvf_alpha", C.c_double), ("wall_function", C.c_int32), ("tvf_pbuf", C.c_int32),
     ]
 
 
@@ -215,6 +215,7 @@ def make_config(case, precision: str = "fp64", kinematic: bool = False) -> Confi
     c.obc = OBC[getattr(case, "obc", "improved")]
     c.density_sum = int(bool(getattr(case, "density_sum", False)))
     c.tvf_alpha = float(getattr(case, "tvf", 0.0))
+    c.tvf_pbuf = int(bool(getattr(case, "tvf_pbuf", False)))
     c.wall_function = int(bool(getattr(case, "wall_function", False)))
     return c
 

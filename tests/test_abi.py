@@ -45,7 +45,7 @@ def test_error_strings_without_gpu(built_lib):
     from paper_2510_25702_gb300 import sph
 
     L = sph.lib()
-    assert L.sph_abi_version() == 2
+    assert L.sph_abi_version() == 3
     for code, name in sph.ERRORS.items():
         assert L.sph_error_string(code)
     assert L.sph_error_string(0) == b"ok"

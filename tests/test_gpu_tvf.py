@@ -56,6 +56,9 @@ CASES = {
                                                            jitter_frac=0.05).replace(wall_function=True),
     "rans_channel_all": lambda: _on(cases.turbulent_channel(length=0.3, height=0.1, dp=0.005,
                                                             jitter_frac=0.05)).replace(wall_function=True),
+    # the shift also on the pressure-buffer particles (across the buffer axis)
+    "pressure_channel": lambda: cases.pressure_driven_channel(length=1.0, height=0.5, jitter_frac=0.2),
+    "lattice3_buf_pbuf": lambda: _on(_lat3_buf()).replace(tvf_pbuf=True),
 }
 FIELDS = ["pos", "vel", "rho", "p", "B", "acc_nu"]
 
@@ -82,6 +85,37 @@ def test_one_step_fp64_with_tvf_and_density_sum(sph, orc, name):
     if np.array_equal(g0["uid"], g["uid"]):
         assert rel_l2(g0["rho"], g["rho"]) > 1e-12 or rel_l2(g0["pos"], g["pos"]) > 1e-12 or \
             (case.rans and rel_l2(off.read(["eps"])["eps"], g["eps"]) > 1e-12)
+
+
+def test_pressure_buffer_shift_fp64(sph, orc):
+    """With tvf_pbuf the pressure-buffer particles take the shift across
+    their buffer axis: one step equals the oracle (1e-10), and against the
+    same step without tvf_pbuf only the buffer particles' positions move
+    (the pair geometry of the step is the frozen configuration's, so every
+    other field and every fluid particle is bit-identical)."""
+    case = CASES["pressure_channel"]()
+    assert case.tvf_pbuf and case.tvf > 0
+    sim = sph.Simulation(case, precision="fp64")
+    sim.step(1)
+    names = ["uid", "label", "pos", "vel", "rho", "p"]
+    g = sim.read(names)
+    o = orc.OracleSim(case)
+    o.step(1)
+    f = o.fields()
+    assert np.array_equal(g["uid"], f["uid"]) and np.array_equal(g["label"], f["label"])
+    errs = {k: rel_l2(g[k], f[k]) for k in ("pos", "vel", "rho", "p")}
+    assert all(e < 1e-10 for e in errs.values()), errs
+    off = sph.Simulation(case.replace(tvf_pbuf=False), precision="fp64")
+    off.step(1)
+    g0 = off.read(names)
+    assert np.array_equal(g0["uid"], g["uid"]) and np.array_equal(g0["label"], g["label"])
+    inb = g["label"] > 0
+    assert inb.sum() > 0
+    assert np.array_equal(g0["pos"][~inb], g["pos"][~inb])
+    for k in ("vel", "rho", "p"):
+        assert np.array_equal(g0[k], g[k]), k
+    moved = np.any(g0["pos"][inb] != g["pos"][inb], axis=1)
+    assert moved.mean() > 0.5
 
 
 def test_laminar_channel_200_steps_fp64(sph, orc):
@@ -116,7 +150,8 @@ def test_rans_channel_wall_function_trajectory_fp64(sph, orc):
     assert all(e < 1e-9 for e in errs.values()), errs
 
 
-@pytest.mark.parametrize("name", ["laminar_channel", "rans_channel", "box3", "mixer3d", "rans_channel_all"])
+@pytest.mark.parametrize("name", ["laminar_channel", "rans_channel", "box3", "mixer3d", "rans_channel_all",
+                                  "pressure_channel"])
 def test_one_step_fp32_with_tvf_and_density_sum(sph, orc, name):
     case = CASES[name]()
     sim = sph.Simulation(case, precision="fp32")

@@ -10,8 +10,10 @@ re-evaluated from the configuration once per advection step:
 * transport-velocity shift dr_i = -2 alpha h^2 sum_j V_j grad_i W_ij: zero
   on a perfect lattice, a displaced particle is moved back towards its
   site, the disorder of a jittered box decreases under repeated shifts, a
-  particle close to a wall is pushed away from it, and buffer particles and
-  velocities are left alone.
+  particle close to a wall is pushed away from it, pressure-buffer particles
+  (when the switch tvf_pbuf asks for it) are shifted only across their
+  buffer's axis, and velocity-buffer particles and all velocities are left
+  alone.
 """
 import numpy as np
 import pytest
@@ -128,10 +130,44 @@ def test_transport_shift_reduces_disorder(orc):
 
 
 def test_transport_shift_pushes_from_walls_and_skips_buffers(orc):
+    """The first row pressed towards the lower wall is pushed off it, in
+    the fluid and, with tvf_pbuf, in the pressure buffers; a pressure-buffer
+    particle takes only the part of the shift across its buffer's axis (its
+    support is cut at the open face), so nothing moves it along the axis.
+    Without tvf_pbuf the buffer particles stay where they are."""
     c = cases.poiseuille_channel(length=1.0, height=0.5, jitter_frac=0.0).replace(tvf=0.2)
     y = c.pos[:, 1]
     low = np.isclose(y, 0.5 * c.dp)
     c.pos[low, 1] = 0.3 * c.dp  # the first row pressed towards the lower wall
+
+    def shift(case):
+        o = orc.OracleSim(case)
+        o.label()
+        o.configure()
+        x0 = o.a["pos"][: o.n].copy()
+        o.transport()
+        return x0, o.a["pos"][: o.n] - x0, o.a["label"][: o.n].copy(), o.n
+
+    _, s_off, lab_off, _ = shift(c)
+    assert lab_off.max() > 0 and np.all(s_off[lab_off > 0] == 0.0)
+    x0, s, lab, n = shift(c.replace(tvf_pbuf=True))
+    pushed = low[:n] & (lab == 0)
+    assert pushed.sum() > 5 and np.all(s[pushed, 1] > 0)
+    assert np.array_equal(s[lab == 0], s_off[lab_off == 0])
+    inb = lab > 0
+    assert inb.sum() > 0
+    assert np.all(s[inb, 0] == 0.0)  # both buffer axes are +-x
+    pushed_b = low[:n] & inb
+    assert pushed_b.sum() >= 4 and np.all(s[pushed_b, 1] > 0)
+    # untouched rows of a buffer: the transverse part vanishes by symmetry
+    mid = inb & (np.abs(x0[:, 1] - 0.5 * c.pos[:, 1].max()) < 0.6 * c.dp)
+    assert mid.sum() > 0 and np.abs(s[mid]).max() < 1e-12 * c.dp
+
+
+def test_transport_shift_leaves_velocity_buffers(orc):
+    """Velocity-buffer particles keep the motion their prescribed velocity
+    gives them: the shift leaves them where they are."""
+    c = cases.laminar_channel(jitter_frac=0.2).replace(tvf=0.2, tvf_pbuf=True)
     o = orc.OracleSim(c)
     o.label()
     o.configure()
@@ -139,6 +175,7 @@ def test_transport_shift_pushes_from_walls_and_skips_buffers(orc):
     o.transport()
     s = o.a["pos"][: o.n] - x0
     lab = o.a["label"][: o.n]
-    assert np.all(s[lab > 0] == 0.0)
-    pushed = low[: o.n] & (lab == 0)
-    assert pushed.sum() > 5 and np.all(s[pushed, 1] > 0)
+    vel_ids = [q + 1 for q, b in enumerate(c.buffers) if b.kind == "velocity"]
+    vb = np.isin(lab, vel_ids)
+    assert vb.sum() > 0 and np.all(s[vb] == 0.0)
+    assert np.abs(s[lab == 0]).max() > 0
