@@ -54,7 +54,9 @@ def workload(name: str, seed: int = 2):
     if name == "plane_jet":
         return cases.plane_jet(dp=0.002, seed=seed + 2)
     if name == "mixer_3d":
-        return cases.mixer_3d(dp=0.01, seed=seed + 4)
+        # the stated 3000-step run holds with the transport-velocity shift and
+        # the density reinitialisation on
+        return cases.mixer_3d_stable(dp=0.01, seed=seed + 4)
     if name == "mixer_3d_small":
         # 951k fluid + 243k wall particles: the 3D sweeps at a size that a
         # profiler captures quickly, inputs still larger than L2
@@ -215,7 +217,7 @@ def sample_case(work: str):
     if work == "plane_jet":
         return cases.plane_jet(dp=0.002, box=0.4)
     if work == "mixer_3d":
-        return cases.mixer_3d(dp=0.02)
+        return cases.mixer_3d_stable(dp=0.02)
     return workload(work)
 
 

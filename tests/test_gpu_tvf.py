@@ -59,6 +59,7 @@ CASES = {
     # the shift also on the pressure-buffer particles (across the buffer axis)
     "pressure_channel": lambda: cases.pressure_driven_channel(length=1.0, height=0.5, jitter_frac=0.2),
     "lattice3_buf_pbuf": lambda: _on(_lat3_buf()).replace(tvf_pbuf=True),
+    "mixer3d_stable": lambda: cases.mixer_3d_stable(dp=0.05),
 }
 FIELDS = ["pos", "vel", "rho", "p", "B", "acc_nu"]
 
@@ -151,7 +152,7 @@ def test_rans_channel_wall_function_trajectory_fp64(sph, orc):
 
 
 @pytest.mark.parametrize("name", ["laminar_channel", "rans_channel", "box3", "mixer3d", "rans_channel_all",
-                                  "pressure_channel"])
+                                  "pressure_channel", "mixer3d_stable"])
 def test_one_step_fp32_with_tvf_and_density_sum(sph, orc, name):
     case = CASES[name]()
     sim = sph.Simulation(case, precision="fp32")
