@@ -17,7 +17,12 @@ u(y) = G y (H - y) / (2 rho0 nu) with G = (p_in - p_out) / L:
 * the particle count stays within 2 % of its start (no accumulation at the
   inlet, no drain at the outlet);
 * without the shift of the buffer particles the same channel runs away
-  (|v| above three times U_max) within the 2000 steps.
+  (|v| above three times U_max) within the 2000 steps;
+* at half the spacing (dp 0.025, the same physical time) both errors fall:
+  the excess of the interior gradient over G about halves (first order in
+  dp: it is a pressure boundary layer about a support wide at each open
+  face, 0.049 -> 0.025 G measured) and the profile error drops below 5 %
+  (5.9 -> 4.0 % measured).
 """
 import numpy as np
 import pytest
@@ -83,3 +88,36 @@ def test_without_the_buffer_shift_the_channel_runs_away(orc):
             ran_away = True
             break
     assert ran_away
+
+
+def _run_to(orc, dp, T=53.0, avg=10.0):
+    """Run to time T, averaging the profile and gradient over the last avg."""
+    c = cases.pressure_driven_channel(dp=dp, seed=1)
+    o = orc.OracleSim(c)
+    while o.stats["t"] < T - avg:
+        o.step(20)
+    bins = np.linspace(0, H, 21)
+    acc, cnt, grad = np.zeros(20), np.zeros(20), []
+    while o.stats["t"] < T:
+        o.step(10)
+        f = o.fields()
+        x, y = f["pos"][:, 0], f["pos"][:, 1]
+        sel = (f["label"] == 0) & (x > 0.5) & (x < 1.5)
+        b = np.clip(np.digitize(y[sel], bins) - 1, 0, 19)
+        np.add.at(acc, b, f["vel"][sel, 0])
+        np.add.at(cnt, b, 1)
+        A = np.stack([x[sel], np.ones(sel.sum())], 1)
+        grad.append(-np.linalg.lstsq(A, f["p"][sel], rcond=None)[0][0])
+    yc = 0.5 * (bins[1:] + bins[:-1])
+    ua = G * yc * (H - yc) / (2 * NU)
+    u = acc / np.maximum(cnt, 1)
+    return np.linalg.norm(u - ua) / np.linalg.norm(ua), np.mean(grad) / G
+
+
+def test_pressure_driven_channel_converges_with_resolution(orc):
+    e1, g1 = _run_to(orc, 0.05)
+    e2, g2 = _run_to(orc, 0.025)
+    print(f"dp 0.05: profile {e1:.4f}, gradient {g1:.4f} G; dp 0.025: profile {e2:.4f}, gradient {g2:.4f} G")
+    assert e2 < e1 and e2 < 0.05
+    assert g1 > 1 and g2 > 1 and (g2 - 1) < 0.7 * (g1 - 1)
+
