@@ -407,7 +407,7 @@ def u_channel(dp=0.05, width=1.0, r_inner=0.5, leg=1.5, nu=0.01, p_in=2.3, p_out
 
 
 def batched_channels(n_instances=64, seed=3, dps=(0.05, 0.025, 0.0125), re_range=(10.0, 200.0),
-                     U=1.0, dt_mode="single") -> List[Case]:
+                     U=1.0, dt_mode="single", stable=False) -> List[Case]:
     """Independent laminar channels for one batched context: half straight
     2 x 1 channels, half U-channels (inner radius 0.5, width 1, legs 1.5),
     dp drawn from `dps` and Re uniform in `re_range`, nu = U W / Re.
@@ -416,6 +416,13 @@ def batched_channels(n_instances=64, seed=3, dps=(0.05, 0.025, 0.0125), re_range
     U over the centre-line length (dp/dx = 12 nu U / W^2); the outlet
     pressure is 0.01 rho0 c0^2 with c0 = 10 U_max = 15 U, the background that
     keeps the open boundaries free of tensile instability.
+
+    stable: the form that holds long runs -- the transport-velocity shift
+    (alpha 0.05, also on the buffer particles, across the buffer axis) and
+    the density reinitialisation of Sec. 2.3 on every instance, with the
+    outlet at zero pressure: the reinitialised density follows the particle
+    spacing, which carries no background pressure, so a background at the
+    buffers alone would start every instance out of balance.
     """
     rng = np.random.default_rng(seed)
     kinds = np.array([0, 1] * (n_instances // 2) + [0] * (n_instances % 2))
@@ -426,7 +433,7 @@ def batched_channels(n_instances=64, seed=3, dps=(0.05, 0.025, 0.0125), re_range
         Re = float(rng.uniform(*re_range))
         nu = U * 1.0 / Re
         c0 = 15.0 * U
-        p_out = 0.01 * c0 * c0
+        p_out = 0.0 if stable else 0.01 * c0 * c0
         if kinds[q] == 0:
             c = poiseuille_channel(length=2.0, height=1.0, dp=dp, p_in=p_out + 12 * nu * U * 2.0, p_out=p_out,
                                    nu=nu, seed=seed * 1000 + q)
@@ -436,6 +443,8 @@ def batched_channels(n_instances=64, seed=3, dps=(0.05, 0.025, 0.0125), re_range
                           seed=seed * 1000 + q)
         c.name = f"batch{q:02d}_{c.name}_Re{Re:.0f}"
         c.dt_mode = dt_mode
+        if stable:
+            c.tvf, c.tvf_pbuf, c.density_sum = 0.05, True, True
         out.append(c)
     return out
 

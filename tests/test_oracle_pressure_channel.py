@@ -121,3 +121,33 @@ def test_pressure_driven_channel_converges_with_resolution(orc):
     assert e2 < e1 and e2 < 0.05
     assert g1 > 1 and g2 > 1 and (g2 - 1) < 0.7 * (g1 - 1)
 
+
+
+def _holds(orc, case, steps, vmax=4.0):
+    o = orc.OracleSim(case)
+    n0 = o.n
+    for s in range(0, steps, 100):
+        try:
+            o.step(100)
+        except orc.OracleError:
+            return False, s
+        v = o.fields()["vel"]
+        if not np.isfinite(v).all() or np.abs(v).max() > vmax or abs(o.n / n0 - 1) > 0.03:
+            return False, s + 100
+    return True, steps
+
+
+def test_stable_batch_instances_hold_1500_steps(orc):
+    """Three instances of the batched channels and U-channels (pressure
+    buffers at both ends of each): in the batch's long-run form (the shift
+    of fluid and buffer particles, the density reinitialisation, outlets at
+    zero pressure) each holds 1500 steps (speeds below 4 U, count within
+    3 %); in the plain form, with its background pressure of 0.01 rho0 c0^2,
+    each runs away before step 1500 (near step 550-800 measured)."""
+    stable = cases.batched_channels(n_instances=3, dps=(0.05,), seed=11, stable=True)
+    plain = cases.batched_channels(n_instances=3, dps=(0.05,), seed=11)
+    for q in range(3):
+        ok, at = _holds(orc, stable[q], 1500)
+        assert ok, (q, stable[q].name, at)
+        ok, at = _holds(orc, plain[q], 1500)
+        assert not ok, (q, plain[q].name)
