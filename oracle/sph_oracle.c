@@ -1089,9 +1089,14 @@ int orc_density_sum(const orc_config *c, orc_state *s) {
 /*   f_ij = dW/(r + 0.01h); D_k = nu_l + nu_t/sigma_k, D_eps likewise.   */
 /* Walls: v_j = 2 v_wall - v_i in grad v (no-slip on the wall surface,  */
 /* as in the viscous term); no diffusion across walls (zero              */
-/* gradient; the paper's wall function is out of scope).                */
-/* Parity partly pinned: homogeneous decay, uniform fields, linear       */
-/* gradient; the wall treatment is a simplification.                    */
+/* gradient); with wall_fn the step-wise wall function (near_wall)       */
+/* replaces the production and eps of the first fluid layer.             */
+/* Pinned: homogeneous decay against its closed form; one step under     */
+/* linear velocity fields (shear, rotation, strain, dilatation) against  */
+/* the textbook production in both equations; diffusion conserves        */
+/* sum m k, dissipates sum m k^2 and damps a sine mode at its rate.      */
+/* Parity unpinned: the zero-gradient wall treatment of k and eps        */
+/* without the wall function (checked by conservation only).             */
 /* ------------------------------------------------------------------ */
 static int orc_rans_impl(const orc_config *c, orc_state *s, double dt, const nblist *Lp) {
   const nblist L = *Lp;
