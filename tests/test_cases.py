@@ -59,3 +59,29 @@ def test_mixer_layout():
 
     d, _ = cKDTree(c.wpos).query(c.pos)
     assert d.min() > 0.4 * c.dp
+
+
+def test_long_run_forms():
+    """The forms that hold their stated lengths: the stated pressures of the
+    pressure-driven channel, the switches of each, and the same geometry as
+    the plain generators."""
+    c1 = cases.pressure_driven_channel()
+    plain = cases.poiseuille_channel(p_in=0.1, p_out=0.0)
+    assert [b.kind for b in c1.buffers] == ["pressure", "pressure"]
+    assert (c1.buffers[0].p_ob, c1.buffers[1].p_ob) == (0.1, 0.0)
+    assert c1.n == 800 and np.isclose(c1.nu_l, 0.02) and np.isclose(c1.c0, 3.125)
+    assert c1.tvf == 0.05 and c1.tvf_pbuf and c1.density_sum
+    assert not plain.tvf and not plain.tvf_pbuf and not plain.density_sum
+    assert np.array_equal(c1.pos, plain.pos) and np.array_equal(c1.wpos, plain.wpos)
+    m = cases.mixer_3d_stable(dp=0.05)
+    m0 = cases.mixer_3d(dp=0.05)
+    assert m.tvf == 0.05 and m.tvf_pbuf and m.density_sum and not m0.tvf_pbuf
+    assert np.array_equal(m.pos, m0.pos)
+    st = cases.batched_channels(stable=True)
+    pl = cases.batched_channels()
+    for a, b in zip(st, pl):
+        assert np.array_equal(a.pos, b.pos) and a.nu_l == b.nu_l
+        assert a.tvf == 0.05 and a.tvf_pbuf and a.density_sum
+        assert a.buffers[1].p_ob == 0.0
+        # the same pressure drop on a zero background
+        assert np.isclose(a.buffers[0].p_ob, b.buffers[0].p_ob - b.buffers[1].p_ob)
