@@ -63,8 +63,10 @@ def test_struct_sizes_match_header(built_lib):
 #include <stddef.h>
 #include "sph.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(sph_config), sizeof(sph_particles), sizeof(sph_buffer_desc),
-         sizeof(sph_alloc), sizeof(sph_stats), offsetof(sph_config, dp), offsetof(sph_buffer_desc, theta));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(sph_config), sizeof(sph_particles),
+         sizeof(sph_buffer_desc), sizeof(sph_alloc), sizeof(sph_stats), offsetof(sph_config, dp),
+         offsetof(sph_buffer_desc, theta), offsetof(sph_config, obc), offsetof(sph_config, density_sum),
+         offsetof(sph_config, tvf_alpha), offsetof(sph_config, wall_function), offsetof(sph_config, tvf_pbuf));
   return 0;
 }
 '''
@@ -76,5 +78,37 @@ int main(void) {
         out = [int(x) for x in subprocess.check_output([exe]).split()]
     expect = [ctypes.sizeof(sph.Config), ctypes.sizeof(sph.Particles), ctypes.sizeof(sph.BufferDesc),
               ctypes.sizeof(sph.Alloc), ctypes.sizeof(sph.Stats), sph.Config.dp.offset,
-              sph.BufferDesc.theta.offset]
+              sph.BufferDesc.theta.offset, sph.Config.obc.offset, sph.Config.density_sum.offset,
+              sph.Config.tvf_alpha.offset, sph.Config.wall_function.offset, sph.Config.tvf_pbuf.offset]
+    assert out == expect
+
+
+def test_oracle_struct_layout_matches_its_header():
+    """The oracle's ctypes mirrors have its C layout (the switches at the
+    end of orc_config included)."""
+    import subprocess
+    import tempfile
+
+    import oracle
+
+    probe = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "sph_oracle.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(orc_config), sizeof(orc_buffer), sizeof(orc_state),
+         offsetof(orc_config, density_sum), offsetof(orc_config, wall_fn), offsetof(orc_config, tvf_pbuf),
+         offsetof(orc_config, tvf_alpha));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "p.c")
+        open(c, "w").write(probe)
+        exe = os.path.join(d, "p")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "oracle"), c, "-o", exe])
+        out = [int(x) for x in subprocess.check_output([exe]).split()]
+    C = oracle.OrcConfig
+    expect = [ctypes.sizeof(C), ctypes.sizeof(oracle.OrcBuffer), ctypes.sizeof(oracle.OrcState),
+              C.density_sum.offset, C.wall_fn.offset, C.tvf_pbuf.offset, C.tvf_alpha.offset]
     assert out == expect
