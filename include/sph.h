@@ -124,7 +124,10 @@ typedef struct sph_config {
      flux through the face stays the momentum equation's;
    - density reinitialisation: rho_i = rho0 sigma_i / sigma_0 with
      sigma_i = W(0) + sum_j W_ij over real and wall neighbours and sigma_0
-     the same sum on the perfect lattice of spacing dp.
+     the same sum on the perfect lattice of spacing dp.  The summed
+     density follows the particle spacing, so a lattice at dp carries zero
+     pressure: buffers that impose a background pressure on such an
+     instance start it out of balance (give its outlet zero pressure).
    The acoustic sub-steps start from the reinitialised density.
    Step-wise wall function (Sec. 2.3 uses the one of its reference at
    turbulent walls; the standard two-layer wall law): a fluid particle of a
